@@ -1,0 +1,404 @@
+"""Pins that tie the FP64 oracle to the paper and to mathematics (CPU only).
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, a swapped index or axis, a wrong offset or torus size) fails at
+least one of them.  Grids are deliberately rectangular and anisotropic
+(nx != ny, hx != hy) so that a transposition cannot cancel out.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import special
+
+import synth
+from oracle import cs, grad, kriging, matern, philox, rapid
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Matern ----
+
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+def test_matern_closed_forms_equal_bessel_definition(nu):
+    # Eq. (Matern1): half-integer K_nu reduce to elementary functions; the
+    # library Bessel K_nu gives an independent evaluation of the definition.
+    d = np.concatenate([np.geomspace(1e-4, 1.0, 50), np.linspace(1.0, 30.0, 60)])
+    ref = d ** nu * special.kv(nu, d) / (2 ** (nu - 1) * special.gamma(nu))
+    np.testing.assert_allclose(matern.phi(d, nu), ref, rtol=1e-11, atol=1e-300)
+
+
+def test_matern_nu_half_is_exponential():
+    d = np.linspace(0, 10, 101)
+    np.testing.assert_allclose(matern.phi(d, 0.5), np.exp(-d), rtol=1e-15)
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.0, 1.5, 2.5, 0.8])
+def test_matern_at_zero_is_one_and_continuous(nu):
+    assert matern.phi(np.array([0.0]), nu)[0] == 1.0
+    assert abs(matern.phi(np.array([1e-7]), nu)[0] - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.0, 1.5, 2.5, 0.8])
+def test_matern_log_range_derivative(nu):
+    # d/d log rho of phi(d / rho) equals -t phi'(t); check it against a central
+    # difference of phi itself and (for half-integers) against the Bessel identity
+    # d/dt [t^nu K_nu(t)] = -t^nu K_(nu-1)(t).
+    t = np.linspace(0.05, 8.0, 40)
+    h = 1e-6
+    # t phi'(t) is the derivative of phi along log t; -t phi'(t) is its negative
+    fd = -(matern.phi(t * np.exp(h), nu) - matern.phi(t * np.exp(-h), nu)) / (2 * h)
+    np.testing.assert_allclose(matern.neg_t_dphi(t, nu), fd, rtol=2e-6, atol=1e-10)
+    np.testing.assert_allclose(matern.neg_t_dphi(t, nu), matern.neg_t_dphi_bessel(t, nu),
+                               rtol=1e-10)
+
+
+# ---------------------------------------------------------- exact Kriging ----
+
+def _sites(n, seed, extent=(0.0, 1.0, 0.0, 1.0)):
+    return synth.sites_uniform(n, extent, seed)
+
+
+def test_exact_kriging_interpolates_at_zero_nugget():
+    # Section 3.2: with tau = 0 Kriging is the interpolant through the data.
+    xy = _sites(25, 1)
+    z = synth.normals(25, 2)
+    c = kriging.coef(xy, z, 1.5, 0.3, 1.0, 0.0)
+    np.testing.assert_allclose(kriging.predict(xy, c, xy, 1.5, 0.3, 1.0), z, atol=1e-9)
+
+
+def test_exact_kriging_nugget_identity():
+    # M c = z  =>  K_xx c = z - tau^2 c, i.e. g_hat(s_i) = z_i - tau^2 c_i.
+    xy = _sites(40, 3)
+    z = synth.normals(40, 4)
+    tau2 = 0.05
+    c = kriging.coef(xy, z, 0.5, 0.2, 1.3, tau2)
+    np.testing.assert_allclose(kriging.predict(xy, c, xy, 0.5, 0.2, 1.3), z - tau2 * c,
+                               rtol=1e-11, atol=1e-11)
+
+
+def _exact_rational_solve(M, z):
+    """Gauss-Jordan elimination in exact rational arithmetic on the FP64 entries."""
+    n = len(z)
+    A = [[Fraction(float(M[i, j])) for j in range(n)] + [Fraction(float(z[i]))]
+         for i in range(n)]
+    for col in range(n):
+        piv = max(range(col, n), key=lambda r: abs(A[r][col]))
+        A[col], A[piv] = A[piv], A[col]
+        p = A[col][col]
+        A[col] = [x / p for x in A[col]]
+        for r in range(n):
+            if r != col and A[r][col] != 0:
+                f = A[r][col]
+                A[r] = [a - f * b for a, b in zip(A[r], A[col])]
+    return np.array([float(A[i][n]) for i in range(n)])
+
+
+def test_exact_kriging_coef_matches_rational_brute_force():
+    xy = _sites(10, 5)
+    z = synth.normals(10, 6)
+    M = kriging.cov_obs(xy, 1.5, 0.2, 1.0, 0.1)
+    np.testing.assert_allclose(kriging.coef(xy, z, 1.5, 0.2, 1.0, 0.1),
+                               _exact_rational_solve(M, z), rtol=1e-11, atol=1e-12)
+
+
+def test_gls_recovers_exact_trend_and_matches_definition():
+    # Eq. (2): with z = X beta exactly, GLS returns beta and c = 0.
+    xy = _sites(30, 7)
+    X = np.stack([np.ones(30), xy[:, 0], xy[:, 1], xy[:, 0] * xy[:, 1]], axis=1)
+    beta = np.array([1.0, -2.0, 0.5, 3.0])
+    b, c = kriging.gls(xy, X @ beta, X, 1.5, 0.2, 1.0, 0.01)
+    np.testing.assert_allclose(b, beta, rtol=1e-9)
+    assert np.abs(c).max() < 1e-8
+
+
+def test_kriging_variance_vanishes_at_sites_without_nugget():
+    xy = _sites(20, 8)
+    v = kriging.variance(xy, xy, 1.5, 0.3, 1.0, 0.0)
+    assert np.abs(v).max() < 1e-8
+    far = np.array([[50.0, 50.0]])
+    assert abs(kriging.variance(xy, far, 1.5, 0.3, 1.0, 0.0)[0] - 1.0) < 1e-12
+
+
+# --------------------------------------------------------------- weights ----
+
+GRID = dict(nx=23, ny=17, extent=(0.0, 1.3, -0.2, 0.7))
+
+
+def test_box_assignment_and_local_coordinates():
+    g = rapid.Grid(L=2, **GRID)
+    xy = np.array([[0.0, -0.2], [1.3, 0.7], [g.hx * 3, -0.2 + g.hy * 5.5],
+                   [g.hx * 7.25, -0.2 + g.hy * 0.0]])
+    ix, iy, u, v = rapid.box_assign(xy, g)
+    assert list(ix) == [0, g.nx - 2, 3, 7]
+    assert list(iy) == [0, g.ny - 2, 5, 0]
+    np.testing.assert_allclose(u, [0, 1, 0, 0.25], atol=1e-12)
+    np.testing.assert_allclose(v, [0, 1, 0.5, 0], atol=1e-12)
+    with pytest.raises(ValueError):
+        rapid.box_assign(np.array([[1.31, 0.0]]), g)
+    with pytest.raises(ValueError):
+        rapid.box_assign(np.array([[np.nan, 0.0]]), g)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_site_cov_matches_absolute_coordinates(L):
+    # k_i of step 3 from local (u, v) must equal k(s_i, s_q) computed from the
+    # absolute coordinates of the padded nodes it names.
+    g = rapid.Grid(L=L, **GRID)
+    xy = synth.sites_uniform(30, GRID["extent"], 11)
+    ix, iy, u, v = rapid.box_assign(xy, g)
+    k = rapid.site_cov(u, v, g, 1.5, 0.25, 1.7)
+    pn = g.padded_nodes()
+    a, b = rapid.local_offsets(L)
+    for i in range(len(xy)):
+        idx = (iy[i] + b) * g.p1x + ix[i] + a
+        ref = matern.cross_cov(xy[i:i + 1], pn[idx], 1.5, 0.25, 1.7)[0]
+        np.testing.assert_allclose(k[i], ref, rtol=1e-12)
+
+
+def test_neighbour_cov_matches_absolute_coordinates():
+    g = rapid.Grid(L=2, **GRID)
+    a, b = rapid.local_offsets(2)
+    pn = g.padded_nodes()
+    idx = (4 + b) * g.p1x + 6 + a
+    np.testing.assert_allclose(rapid.neighbour_cov(g, 2.5, 0.3, 1.1),
+                               matern.cross_cov(pn[idx], pn[idx], 2.5, 0.3, 1.1), rtol=1e-13)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_weights_one_hot_on_nodes(L):
+    # Eq. (weights): a site on a grid node is reproduced by that node alone.
+    g = rapid.Grid(L=L, **GRID)
+    xy = synth.sites_on_nodes(40, g.nx, g.ny, GRID["extent"], 12)
+    ix, iy, W = rapid.weights(xy, g, 1.5, 0.2, 1.0)
+    for i in range(len(xy)):
+        j = np.argmax(np.abs(W[i]))
+        assert abs(W[i, j] - 1.0) < 1e-9
+        assert np.abs(np.delete(W[i], j)).max() < 1e-9
+
+
+def test_weights_residual_sigma2_and_shift_invariance():
+    g = rapid.Grid(L=3, **GRID)
+    xy = synth.sites_uniform(50, GRID["extent"], 13)
+    ix, iy, u, v = rapid.box_assign(xy, g)
+    _, _, W = rapid.weights(xy, g, 1.5, 0.2, 1.0)
+    KN = rapid.neighbour_cov(g, 1.5, 0.2, 1.0)
+    k = rapid.site_cov(u, v, g, 1.5, 0.2, 1.0)
+    assert np.abs(W @ KN - k).max() < 1e-10 * np.abs(k).max()
+    _, _, W3 = rapid.weights(xy, g, 1.5, 0.2, 3.0)
+    np.testing.assert_allclose(W3, W, rtol=1e-9, atol=1e-11)
+    # the same (u, v) in another box gives the same weights
+    xy2 = xy.copy()
+    xy2[:, 0] = np.where(ix < g.nx - 3, xy[:, 0] + g.hx, xy[:, 0] - g.hx)
+    _, _, W2 = rapid.weights(xy2, g, 1.5, 0.2, 1.0)
+    np.testing.assert_allclose(W2, W, rtol=1e-7, atol=1e-9)
+
+
+# --------------------------------------------------------- approximation ----
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_approximation_is_exact_for_sites_on_distinct_nodes(L):
+    # If every site is a grid node, k_approx = k, so Eq. (9) equals Eq. (4).
+    g = rapid.Grid(L=L, **GRID)
+    xy = synth.sites_on_nodes(60, g.nx, g.ny, GRID["extent"], 14)
+    z = synth.normals(60, 15)
+    c = kriging.coef(xy, z, 1.5, 0.2, 1.0, 1e-3)
+    approx = rapid.predict(xy, c, g, 1.5, 0.2, 1.0, method="bttb")[0]
+    exact = kriging.predict(xy, c, g.nodes(), 1.5, 0.2, 1.0).reshape(g.ny, g.nx)
+    assert np.abs(approx - exact).max() <= 1e-10 * np.abs(exact).max()
+
+
+def test_direct_sum_matches_double_sum_eq8():
+    g = rapid.Grid(L=2, **GRID)
+    xy = synth.sites_uniform(35, GRID["extent"], 16)
+    c = synth.normals((2, 35), 17)
+    a = rapid.predict(xy, c, g, 0.5, 0.15, 1.0, method="bttb")
+    b = rapid.double_sum_predict(xy, c, g, 0.5, 0.15, 1.0)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_fft_steps_match_direct_sum_and_torus_invariance(L):
+    g = rapid.Grid(L=L, **GRID)
+    xy = synth.sites_uniform(50, GRID["extent"], 18)
+    c = synth.normals(50, 19)
+    ix, iy, W = rapid.weights(xy, g, 2.5, 0.2, 1.0)
+    cs_ = rapid.scatter(ix, iy, W, c, g)
+    ref = rapid.bttb_predict(cs_, g, 2.5, 0.2, 1.0)
+    px, py = rapid.torus_size(g.nx, L), rapid.torus_size(g.ny, L)
+    for (qx, qy) in [(px, py), (px + 5, py + 7), (2 * (g.nx + L - 2), 2 * (g.ny + L - 2))]:
+        out = rapid.fft_predict(cs_, g, 2.5, 0.2, 1.0, Px=qx, Py=qy)
+        assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
+    # one node short of the minimal torus aliases and must be caught
+    bad = rapid.fft_predict(cs_, g, 2.5, 0.2, 1.0, Px=2 * (g.nx + L - 2) - 1,
+                            Py=2 * (g.ny + L - 2) - 1)
+    assert np.abs(bad - ref).max() > 1e-9 * np.abs(ref).max()
+
+
+def test_torus_sizes():
+    assert rapid.smooth23(2050) == 2187
+    assert rapid.smooth23(2048) == 2048
+    assert rapid.smooth23(1026) == 1152
+    assert rapid.torus_size(1024, 2) == 2048
+    assert rapid.torus_size(1024, 3) == 2187
+    assert rapid.torus_size(350, 3) == 729
+    assert rapid.torus_size(64, 2) == 128
+
+
+def test_linearity_in_data():
+    g = rapid.Grid(L=2, **GRID)
+    xy = synth.sites_uniform(30, GRID["extent"], 20)
+    z1, z2 = synth.normals(30, 21), synth.normals(30, 22)
+    f = lambda z: rapid.predict(xy, kriging.coef(xy, z, 1.5, 0.2, 1.0, 1e-3), g, 1.5, 0.2, 1.0)
+    np.testing.assert_allclose(f(2.0 * z1 - 3.0 * z2), 2.0 * f(z1) - 3.0 * f(z2),
+                               rtol=1e-9, atol=1e-10)
+
+
+def _approx_error(nu, L, m, reps=4, seed=23):
+    # Section 3.1: data drawn from the GP model, range set by a correlation of
+    # 0.7 at distance 0.2; mean absolute error over several location sets.
+    ext = (0.0, 1.0, 0.0, 1.0)
+    rho = matern.range_for_correlation(nu, 0.2, 0.7)
+    g = rapid.Grid(m, m, ext, L)
+    err = []
+    for r in range(reps):
+        xy = synth.sites_uniform(150, ext, seed + 2 * r)
+        z = kriging.gp_draw(xy, synth.normals(150, seed + 2 * r + 1), nu, rho, 1.0, 1e-2)
+        c = kriging.coef(xy, z, nu, rho, 1.0, 1e-2)
+        approx = rapid.predict(xy, c, g, nu, rho, 1.0, method="fft")[0]
+        exact = kriging.predict(xy, c, g.nodes(), nu, rho, 1.0).reshape(m, m)
+        err.append(np.mean(np.abs(approx - exact)))
+    return float(np.mean(err))
+
+
+def test_error_decreases_with_smoothness_order_and_resolution():
+    # Section 3.1 / Table A2: error falls with nu, with L and with grid size.
+    e_nu = [_approx_error(nu, 2, 48) for nu in (0.5, 1.5, 2.5)]
+    assert e_nu[0] > e_nu[1] > e_nu[2]
+    e_L = [_approx_error(1.5, L, 48) for L in (1, 2, 3)]
+    assert e_L[0] > e_L[1] > e_L[2]
+    e_m = [_approx_error(1.5, 2, m) for m in (24, 48, 96)]
+    assert e_m[0] > e_m[1] > e_m[2]
+
+
+def test_convergence_orders_match_table2():
+    gold = json.load(open(os.path.join(GOLDEN, "table2_slopes.json")))
+    ms = np.array([20, 40, 60, 80, 100, 140, 200])
+    for nu_s, kappa in gold["empirical_kappa"].items():
+        e = [rapid.kernel_error_sup(float(nu_s), gold["range"], m, gold["L"]) for m in ms]
+        slope = -np.polyfit(np.log10(ms), np.log10(e), 1)[0]
+        assert abs(slope - kappa) < 0.15, (nu_s, slope, kappa)
+    mc = ms[ms <= 140]
+    e = [rapid.kernel_error_sup(2.5, gold["range"], m, gold["L"]) for m in mc]
+    slope = -np.polyfit(np.log10(mc), np.log10(e), 1)[0]
+    assert abs(slope - gold["empirical_kappa_nu2.5_coarse"]) < 0.4
+
+
+# ---------------------------------------------------------------- Philox ----
+
+def test_philox_matches_library_implementation():
+    # numpy's Philox bit generator is Philox4x64-10; it pre-increments its
+    # counter, so counter c there yields our block for c + 1.
+    for ctr, key in [((0, 0, 0, 0), (0, 0)), ((5, 7, 9, 11), (123, 456)),
+                     ((2 ** 64 - 2, 1, 2, 3), (2 ** 63 + 5, 77))]:
+        bg = np.random.Philox(counter=np.array(ctr, dtype=np.uint64),
+                              key=np.array(key, dtype=np.uint64))
+        ref = bg.random_raw(4)
+        c0 = (ctr[0] + 1) % 2 ** 64
+        got = philox.philox4x64(c0, ctr[1], ctr[2], ctr[3], key[0], key[1])
+        assert [int(x) for x in got] == [int(x) for x in ref]
+
+
+def test_uniform_and_normals():
+    w = np.array([0, 2 ** 64 - 1], dtype=np.uint64)
+    u = philox.uniform(w)
+    assert u[0] == 0.5 * 2.0 ** -53 and u[1] == 1.0 - 0.5 * 2.0 ** -53
+    xi, eta = philox.normal_pairs(np.arange(200000, dtype=np.uint64), 3, 1, 99)
+    for s in (xi, eta):
+        assert abs(s.mean()) < 0.01 and abs(s.var() - 1) < 0.015
+    assert abs(np.mean(xi * eta)) < 0.01
+
+
+# ---------------------------------------------------- conditional simulation ----
+
+def test_circulant_embedding_reproduces_lags():
+    g = rapid.Grid(14, 11, (0.0, 1.0, 0.0, 0.8), 2)
+    qx, qy, sl = cs.ce_spectrum(g, 1.5, 0.15, 1.0)
+    assert qx >= 2 * (g.p1x - 1) and qy >= 2 * (g.p1y - 1)
+    # the covariance implied by the embedding, restricted to padded-grid lags,
+    # equals the Matern covariance at those lags
+    back = np.fft.ifft2(sl ** 2 * qx * qy).real
+    kx, ky = np.arange(g.p1x), np.arange(g.p1y)
+    ref = matern.cov(np.sqrt((kx[None, :] * g.hx) ** 2 + (ky[:, None] * g.hy) ** 2), 1.5, 0.15, 1.0)
+    np.testing.assert_allclose(back[:g.p1y, :g.p1x], ref, atol=1e-12)
+
+
+def test_unconditional_draw_covariance():
+    g = rapid.Grid(10, 9, (0.0, 1.0, 0.0, 1.0), 1)
+    R = 3000
+    f = cs.unconditional(g, 0.5, 0.3, 1.0, list(range(R)), seed=7)
+    x = f.reshape(R, -1)
+    emp = x.T @ x / R
+    pn = g.padded_nodes()
+    ref = matern.cross_cov(pn, pn, 0.5, 0.3, 1.0)
+    # standard error of a covariance estimate is about sqrt(2 / R)
+    assert np.abs(emp - ref).max() < 6 * np.sqrt(2.0 / R)
+    assert abs(np.mean(np.diag(emp)) - 1.0) < 0.03
+
+
+def test_conditional_simulation_matches_kriging_moments_on_nodes():
+    # With sites on grid nodes the local step is exact and rapid prediction is
+    # exact, so the ensemble must have the Kriging mean and variance (Sec. 5.2).
+    ext = (0.0, 1.0, 0.0, 1.0)
+    g = rapid.Grid(12, 12, ext, 2)
+    xy = synth.sites_on_nodes(15, 12, 12, ext, 24)
+    z = synth.normals(15, 25)
+    th = (1.5, 0.25, 1.0)
+    R = 800
+    sims = cs.simulate(xy, z, g, *th, 0.01, R, seed=5)[0]
+    c = kriging.coef(xy, z, *th, 0.01)
+    mean = kriging.predict(xy, c, g.nodes(), *th).reshape(12, 12)
+    var = kriging.variance(xy, g.nodes(), *th, 0.01).reshape(12, 12)
+    assert np.abs(sims.mean(0) - mean).max() < 5 * np.sqrt(var.max() / R)
+    ratio = sims.var(0).sum() / var.sum()
+    assert abs(ratio - 1.0) < 0.08
+
+
+# ------------------------------------------------------------- gradients ----
+
+def test_adjoint_matches_finite_differences():
+    g = rapid.Grid(13, 11, (0.0, 1.0, 0.0, 0.9), 2)
+    xy = synth.sites_uniform(25, (0.0, 1.0, 0.0, 0.9), 26)
+    z = synth.normals((2, 25), 27)
+    gbar = synth.normals((2, 11, 13), 28)
+    th = (1.5, 0.2, 1.3, 1e-2)
+    zbar, g_rho, g_s2 = grad.adjoint(xy, z, gbar, g, *th)
+    d_rho, d_s2 = grad.finite_difference(xy, z, gbar, g, *th, step=1e-5)
+    np.testing.assert_allclose(g_rho, d_rho, rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(g_s2, d_s2, rtol=1e-6, atol=1e-8)
+    # gradient in z by finite differences of a few coordinates
+    base = grad.loss_linear(xy, z, gbar, g, *th)
+    for i in (0, 7, 19):
+        zp = z.copy()
+        zp[:, i] += 1e-6
+        dz = (grad.loss_linear(xy, zp, gbar, g, *th) - base) / 1e-6
+        np.testing.assert_allclose(zbar[:, i], dz, rtol=1e-4, atol=1e-6)
+
+
+def test_adjoint_close_to_exact_kriging_gradient():
+    # The rapid gradient approaches the exact-Kriging gradient as the grid is
+    # refined, at the level of the approximation error itself.
+    ext = (0.0, 1.0, 0.0, 1.0)
+    xy = synth.sites_uniform(40, ext, 29)
+    z = synth.normals(40, 30)
+    th = (2.5, 0.2, 1.0, 1e-2)
+    errs = []
+    for m in (40, 80):
+        g = rapid.Grid(m, m, ext, 3)
+        gbar = synth.normals((1, m, m), 31)
+        a = grad.adjoint(xy, z, gbar, g, *th)
+        e = grad.exact_adjoint(xy, z, gbar, g, *th)
+        errs.append(max(np.abs(x - y).max() / np.abs(y).max() for x, y in zip(a, e)))
+    assert errs[1] < 2e-4 and errs[1] < 0.2 * errs[0]
