@@ -1,0 +1,342 @@
+"""Benchmark of rapid Kriging prediction on GB300 (one JSON line on rank 0).
+
+Workload (default "paper350"): the paper-scale single prediction -- n = 1368
+clustered sites on [0,1.6] x [0,1], a 350 x 350 grid, range 0.15, sigma^2 = 1,
+tau^2 = 1e-3 -- swept over nu in {0.5, 1.5, 2.5} and L in {1, 2, 3}.  One
+step is the rapid prediction of all nine cells from (sites, coefficients)
+resident in HBM: box assignment and weights (steps 3-4), scatter c* = A^T c
+(step 5) and the FFT convolution and crop (steps 6-7).  Coefficients
+c = M^{-1} z come from the library's FP64 Cholesky at set-up, like the fitted
+model of the paper's timing.  The plans (K_N factor, circulant eigenvalues)
+are built once per covariance before timing.
+
+"grad1024" runs the 1024 x 1024 grid (n = 20000, 16 fields, nu = 2.5,
+range 0.08, L = 3) forward prediction instead.
+
+--impl reference times the FP64 CPU oracle (direct Eq. (9) sum) on a bounded
+sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "grid-point predictions/s (N x realizations)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper350", choices=["paper350", "grad1024"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU path")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workloads --
+
+def workload_cells(name):
+    """[(cell name, plan kwargs, n, B)] and the sites of the workload."""
+    w = synth.WORKLOADS[name]
+    seed = synth.seed_for(w["config"])
+    xy = synth.sites(w["sites"], w["n"], w["extent"], seed)
+    cells = []
+    if name == "paper350":
+        for nu in w["nus"]:
+            for L in w["Ls"]:
+                cells.append((f"nu{nu}_L{L}", dict(nx=w["nx"], ny=w["ny"], extent=w["extent"],
+                                                   nu=nu, rho=w["rho"], sigma2=w["sigma2"],
+                                                   tau2=w["tau2"], L=L), w["B"]))
+    else:
+        cells.append(("grad1024", dict(nx=w["nx"], ny=w["ny"], extent=w["extent"], nu=w["nu"],
+                                       rho=w["rho"], sigma2=w["sigma2"], tau2=w["tau2"],
+                                       L=w["L"]), w["B"]))
+    return w, xy, cells
+
+
+# -------------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- our arm --
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2605_29284_gb300 as rk
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w, xy_np, cells = workload_cells(args.workload)
+    xy = torch.from_numpy(xy_np).to(dev)
+    n = xy_np.shape[0]
+
+    def setup(precision):
+        st = []
+        for name, kw, B in cells:
+            p = rk.Plan(kw["nx"], kw["ny"], kw["extent"], kw["nu"], kw["rho"], kw["sigma2"],
+                        kw["tau2"], kw["L"], precision=precision)
+            z = torch.from_numpy(synth.normals((B, n), synth.seed_for(w["config"], 1))).to(dev)
+            p.set_obs(xy, z)                     # FP64 Cholesky, untimed set-up
+            c = p.debug_copy("coef").clone()
+            out = torch.empty((B, kw["ny"], kw["nx"]), dtype=p.dtype, device=dev)
+            st.append((p, c, out))
+        torch.cuda.synchronize()
+        return st
+
+    def step(st):
+        for p, c, out in st:
+            p.set_sites(xy)
+            p.set_coef(c)
+            p.predict(out)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(st, steps, warmup, profile=False):
+        for _ in range(warmup):
+            step(st)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        total = 0.0
+        if profile:
+            rk.profile_read()
+            rk.profile_enable(True)
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            step(st)
+            b.record()
+            b.synchronize()
+            total += a.elapsed_time(b)
+        prof = None
+        if profile:
+            rk.profile_enable(False)
+            prof = rk.profile_read()
+        torch.cuda.synchronize()
+        if world > 1:
+            t = torch.tensor([total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        return total, prof
+
+    points = sum(kw["nx"] * kw["ny"] * B for _, kw, B in cells)
+    st32 = setup(args.precision)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    total_ms, prof = timed(st32, args.steps, args.warmup, profile=True)
+    clocks = sampler.stop()
+    value = points * args.steps * world / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms, dbytes) = dom
+    achieved = dbytes / (dms / 1e3) / 1e9
+    kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
+                   "GBps": v[2] / (v[1] / 1e3) / 1e9 if v[1] > 0 else None}
+               for k, v in prof.items()}
+
+    # end to end through the host-buffer entry point
+    c_host = [c.cpu().numpy() for _, c, _ in st32]
+    torch.cuda.synchronize()
+    for _ in range(max(2, args.warmup // 2)):
+        for (p, c, out), ch in zip(st32, c_host):
+            p.predict_host(xy_np, ch)
+    torch.cuda.synchronize()
+    esteps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(esteps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for (p, c, out), ch in zip(st32, c_host):
+            p.predict_host(xy_np, ch)
+        t0 += 0
+        if _ == 0:
+            acc = time.perf_counter() - t1
+        else:
+            acc += time.perf_counter() - t1
+    e2e_value = points * esteps / acc
+    esz = 4 if args.precision == "fp32" else 8
+    h2d = sum(n * 2 * 8 + B * n * 8 for _, kw, B in cells)
+    d2h = sum(B * kw["nx"] * kw["ny"] * esz for _, kw, B in cells)
+
+    fp64 = None
+    if not args.no_fp64 and args.precision == "fp32":
+        st64 = setup("fp64")
+        k64 = max(2, args.steps // 5)
+        ms64, _ = timed(st64, k64, 2)
+        v64 = points * k64 * world / (ms64 / 1e3)
+        fp64 = {"value": v64, "unit": "grid-point predictions/s", "ms_per_step": ms64 / k64,
+                "speedup_fp32_over_fp64": value / v64}
+        for p, _, _ in st64:
+            p.close()
+
+    launches_per_step = len(cells) * (7 if args.precision == "fp32" else 5)
+    res = {
+        "metric": METRIC, "value": value, "unit": "grid-point predictions/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded sites and GP-shaped data; see synth)",
+        "config": {"workload": args.workload, "cells": [c[0] for c in cells],
+                   "grid": f"{cells[0][1]['nx']}x{cells[0][1]['ny']}", "n": n,
+                   "fields_per_cell": cells[0][2], "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_source": peak_src},
+        "kernels": kernels,
+        "e2e": {"value": e2e_value, "unit": "grid-point predictions/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "fp64_path": fp64,
+    }
+    for p, _, _ in st32:
+        p.close()
+    return res
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def cpu_oracle_rate(workload, budget_s=15.0, steps=1):
+    """Oracle (direct Eq. (9) sum) predictions/s on a seeded sample of grid nodes."""
+    from oracle import kriging, rapid
+    w, xy, cells = workload_cells(workload)
+    n = xy.shape[0]
+    name, kw, B = cells[len(cells) // 2]
+    g = rapid.Grid(kw["nx"], kw["ny"], kw["extent"], kw["L"])
+    z = synth.normals((B, n), synth.seed_for(w["config"], 1))
+    c = kriging.coef(xy, z.T, kw["nu"], kw["rho"], kw["sigma2"], kw["tau2"]).T
+    rs = np.random.default_rng(7)
+    nodes = 256
+    total_pts, total_t = 0, 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        while True:
+            jx = rs.integers(0, g.nx, nodes)
+            jy = rs.integers(0, g.ny, nodes)
+            ix, iy, W = rapid.weights(xy, g, kw["nu"], kw["rho"], kw["sigma2"])
+            cs = rapid.scatter(ix, iy, W, c, g)
+            rapid.bttb_predict(cs, g, kw["nu"], kw["rho"], kw["sigma2"], jx=jx, jy=jy)
+            total_pts += nodes * B
+            if time.perf_counter() - t0 > budget_s / steps:
+                break
+        total_t += time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": total_pts / total_t, "unit": "grid-point predictions/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"cell {name}: weights, scatter and direct Eq. (9) sums at batches of "
+                      f"{nodes} seeded random grid nodes for ~{budget_s:.0f} s (numpy FP64, "
+                      "BLAS threads = host cores)"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cb = cpu_oracle_rate(args.workload, budget_s=max(10.0, 2.0 * args.steps),
+                             steps=args.steps)
+        res = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
+               "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": args.workload},
+               "cpu_baseline": cb,
+               "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(res))
+        return 0
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank == 0 and not args.no_cpu:
+        res["cpu_baseline"] = cpu_oracle_rate(args.workload)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

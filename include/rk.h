@@ -1,0 +1,220 @@
+/*
+ * rk.h -- C ABI of librk: rapid approximate Kriging prediction on one GPU.
+ *
+ * The library implements the rapid predictor of "Rapid Approximation
+ * Prediction for Kriging" (Li, Fasshauer, Nychka), Section 2: the covariance
+ * between a grid node and an off-grid site is replaced by a local
+ * interpolation of grid covariances (Eqs. 6-7, weights of Eq. "weights"), so
+ * that prediction becomes a sparse scatter c* = A^T c followed by a discrete
+ * convolution of c* with the Matern filter on the grid (Eqs. 8-9, Eq.
+ * "Convolution"), evaluated with a circulant-embedded FFT (algorithm steps
+ * 1-7 of Section 2.2).  Conditional simulation (Section 1, Section 4.2) and
+ * the adjoint of the implemented map are built on the same machinery.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call is asynchronous on the plan's CUDA stream unless its comment
+ *    says otherwise.  Pointers named *_dev are device pointers owned by the
+ *    caller; *_host pointers are host memory owned by the caller.  The plan
+ *    owns all of its scratch space; it is allocated by rk_plan_create,
+ *    rk_set_sites and rk_set_coef/rk_solve_coef (never by rk_predict,
+ *    rk_simulate or rk_predict_backward).
+ *  - Statuses are returned, never raised: no entry point exits, traps or
+ *    prints.  After any status other than RK_OK and RK_ERR_CUDA the plan is
+ *    still usable; after RK_ERR_CUDA it must be destroyed.
+ *  - Grid: nx x ny nodes on extent = {x0, x1, y0, y1} with both end points,
+ *    hx = (x1 - x0) / (nx - 1), hy likewise; outputs are row-major
+ *    [field][iy][ix] (ix fastest).
+ *  - Covariance (Eq. Matern1, Section 3): k(s, s') = sigma2 * phi(|s - s'| /
+ *    range), phi(d) = d^nu K_nu(d) / (2^(nu - 1) Gamma(nu)).  nu must be 0.5,
+ *    1.5 or 2.5 (closed forms; other nu return RK_ERR_INVALID_ARG).
+ *  - Precision RK_FP64: every step in double.  RK_FP32: scatter and FFT
+ *    butterflies in float; the weights, the Cholesky factors and the circulant
+ *    eigenvalues in double; the lowest spatial frequencies of F(c*) (where the
+ *    Matern spectrum exceeds 1e-2 of its peak) are computed exactly in double
+ *    from the sites' weights and replace the float values before the
+ *    spectrum is applied.
+ */
+#ifndef RK_H
+#define RK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rk_plan rk_plan;
+
+typedef enum {
+  RK_OK = 0,
+  RK_ERR_INVALID_ARG = 1,  /* a size, pointer or parameter outside its range  */
+  RK_ERR_OBS_OUTSIDE = 2,  /* a site lies outside the extent (or is NaN)      */
+  RK_ERR_NOT_PD = 3,       /* a Cholesky factorisation met a non-positive pivot */
+  RK_ERR_CE_NEGATIVE = 4,  /* no non-negative circulant embedding found       */
+  RK_ERR_CUDA = 5,         /* a CUDA runtime call failed                      */
+  RK_ERR_OOM = 6,          /* device allocation failed                        */
+  RK_ERR_TIMEOUT = 7,      /* reserved: a bounded device wait gave up         */
+  RK_ERR_STATE = 8         /* a call came before the state it needs was set   */
+} rk_status;
+
+enum { RK_FP32 = 0, RK_FP64 = 1 };
+
+/* Sizes chosen by a plan (read-only report, see rk_plan_get_info). */
+typedef struct {
+  int nx, ny, L, M;        /* grid, neighbourhood order, M = (2L)^2            */
+  int p1x, p1y;            /* padded grid, P1 = n + 2 (L - 1)                  */
+  int px, py;              /* torus size per dimension (2^a 3^b >= 2(n+L-2))   */
+  int hx_spec;             /* half-spectrum width px / 2 + 1                   */
+  int blk_kx, blk_ky;      /* exact low-frequency block: kx <= blk_kx, |ky| <= blk_ky (FP32 only) */
+  int n, B;                /* current sites and fields (0 before they are set) */
+  int precision;
+  int qx, qy;              /* circulant-embedding torus of rk_simulate (0 until first use) */
+} rk_plan_info;
+
+/*
+ * rk_plan_create -- algorithm steps 1-2 of Section 2.2 for one covariance.
+ * Factors K_N (the M x M covariance among a site's 2L x 2L grid neighbours,
+ * shared by all sites because k is stationary and the neighbour order is
+ * fixed) and computes the eigenvalues lambda of the circulant embedding of
+ * the grid covariance (step 2; embedding per the remark on 2-3-smooth sizes)
+ * on the device in double.
+ *   out        receives the plan; *out is NULL on failure.
+ *   nx, ny     grid nodes per dimension, >= 2.
+ *   extent     {x0, x1, y0, y1}, host pointer, x0 < x1, y0 < y1.
+ *   nu         Matern smoothness: 0.5, 1.5 or 2.5.
+ *   range      Matern range (> 0); sigma2 > 0; tau2 >= 0 (nugget).
+ *   L          neighbourhood order >= 1, M = (2L)^2 <= 64.
+ *   precision  RK_FP32 or RK_FP64.
+ *   stream     cudaStream_t to run on (NULL = legacy default stream).
+ * Synchronises with the stream before returning.
+ */
+rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4],
+                         double nu, double range, double sigma2, double tau2,
+                         int L, int precision, void* stream);
+
+/* Frees every device buffer of the plan.  NULL is accepted. */
+rk_status rk_plan_destroy(rk_plan* plan);
+
+/* Re-targets the plan to another stream. */
+rk_status rk_set_stream(rk_plan* plan, void* stream);
+
+/* Copies the plan's sizes into *info (host). */
+rk_status rk_plan_get_info(const rk_plan* plan, rk_plan_info* info);
+
+/*
+ * rk_set_sites -- algorithm steps 3-4 of Section 2.2 and Eq. (weights).
+ * For each site: central box (ix, iy) = clamp(floor((s - x0) / h), 0, n - 2)
+ * and local offsets; k_i (covariance with the 2L x 2L neighbours, order
+ * q = a + 2L b, a fastest); A_i = K_N^{-1} k_i through the Cholesky factor.
+ * For RK_FP32 plans it also forms each site's Fourier factors for the exact
+ * low-frequency block.  Resets any coefficients set before.
+ *   n        number of sites, >= 1.
+ *   xy_dev   device, n x 2 doubles (x, y) row-major.
+ * Returns RK_ERR_OBS_OUTSIDE if a site is outside the extent or NaN.
+ * Synchronises with the stream (to read the outside-extent flag).
+ */
+rk_status rk_set_sites(rk_plan* plan, int n, const double* xy_dev);
+
+/*
+ * rk_set_coef -- sets the Kriging coefficients c (Eq. 3) directly, for B
+ * fields: c_dev is device, B x n doubles row-major.  Copied into the plan.
+ */
+rk_status rk_set_coef(rk_plan* plan, int B, const double* c_dev);
+
+/*
+ * rk_solve_coef -- Eq. (3) without covariates: c = M^{-1} z for B fields,
+ * M = K_xx + tau2 I (Section 2), by a double-precision Cholesky factorisation
+ * of M on the device and two triangular solves.  The factor is kept for
+ * rk_simulate and rk_predict_backward.  z_dev: device, B x n doubles (data
+ * with any fixed effects X beta already removed).  Returns RK_ERR_NOT_PD if M
+ * is not positive definite.  Synchronises with the stream.
+ */
+rk_status rk_solve_coef(rk_plan* plan, int B, const double* z_dev);
+
+/* rk_set_obs = rk_set_sites followed by rk_solve_coef. */
+rk_status rk_set_obs(rk_plan* plan, int n, const double* xy_dev, const double* z_dev, int B);
+
+/*
+ * rk_predict -- algorithm steps 5-7 of Section 2.2 (Eqs. 8-9): c* = A^T c on
+ * the padded grid, zero-embedded on the px x py torus, convolved with the
+ * Matern filter by FFT, and cropped to the nx x ny window (offset L - 1).
+ *   out_dev  device, B x ny x nx, float for RK_FP32 plans, double for RK_FP64.
+ * Needs rk_set_sites and coefficients (else RK_ERR_STATE).
+ */
+rk_status rk_predict(rk_plan* plan, void* out_dev);
+
+/*
+ * rk_predict_host -- the same prediction called with host buffers: copies
+ * xy_host (n x 2 doubles) and c_host (B x n doubles) to the device, runs
+ * rk_set_sites, rk_set_coef and rk_predict, and copies the B x ny x nx
+ * result back into out_host (float or double per the plan precision).
+ * Synchronises with the stream before returning.
+ */
+rk_status rk_predict_host(rk_plan* plan, int n, const double* xy_host, int B,
+                          const double* c_host, void* out_host);
+
+/*
+ * rk_simulate -- conditional simulation (Section 1: unconditional draw, then
+ * Kriging of the simulated data; Section 6: circulant embedding).  For each
+ * of the B data fields z given to rk_solve_coef and each realisation
+ * t < R: an unconditional field f_u on the padded grid from a circulant
+ * embedding (torus 2^a 3^b >= 2 (P1 - 1), grown until its eigenvalues are
+ * non-negative), site values z_u = A_i f_u[N(i)] + s_i xi + tau eps with
+ * s_i^2 = max(0, sigma2 - k_i^T A_i), coefficients c = M^{-1} (z - z_u), and
+ * f_c = rapid prediction of c + f_u on the window.  Noise is Philox4x64-10
+ * keyed by seed (counter layout in the library's documentation).
+ *   out_dev  device, B x R x ny x nx in plan precision.
+ * Needs rk_solve_coef (else RK_ERR_STATE); RK_ERR_CE_NEGATIVE if no
+ * embedding up to four-fold growth is non-negative.
+ */
+rk_status rk_simulate(rk_plan* plan, int R, unsigned long long seed, void* out_dev);
+
+/*
+ * rk_predict_backward -- adjoint of the implemented map
+ * (z, log range, log sigma2) -> g_hat (the paper has no gradient).
+ * Given gbar = d loss / d g_hat (device, B x ny x nx, plan precision):
+ *   grad_z_dev          device, B x n doubles, d loss / d z;
+ *   grad_log_range_dev  device, B doubles;
+ *   grad_log_sigma2_dev device, B doubles.
+ * Any of the three outputs may be NULL to skip it.  Needs rk_solve_coef.
+ */
+rk_status rk_predict_backward(rk_plan* plan, const void* gbar_dev, double* grad_z_dev,
+                              double* grad_log_range_dev, double* grad_log_sigma2_dev);
+
+/*
+ * rk_debug_copy -- copies an internal buffer into a caller device buffer for
+ * testing (dst_dev must hold the stated bytes).  what: 0 = box indices
+ * (n x 2 int32: ix, iy), 1 = weights (n x M doubles), 2 = spectrum lambda
+ * (px/2+1 columns x py, plan precision, scaled by 1/(px py)),
+ * 3 = c* of field 0 (p1y x p1x, plan precision), 4 = coefficients c
+ * (B x n doubles).  Synchronises.
+ */
+rk_status rk_debug_copy(rk_plan* plan, int what, void* dst_dev, size_t bytes);
+
+/*
+ * Per-kernel timing for measurement (not part of the method).  While enabled,
+ * every kernel launched by rk_predict / rk_simulate / rk_predict_backward is
+ * bracketed by CUDA events on the plan's stream, and its algorithmic bytes
+ * (the bytes its inputs and outputs occupy, as stated in the library's design
+ * notes) are recorded.  rk_profile_read synchronises the recorded events and
+ * fills up to max entries (one per kernel name) with launches, total
+ * milliseconds and total algorithmic bytes; it returns the number of entries.
+ */
+typedef struct {
+  char name[32];
+  int launches;
+  double total_ms;
+  double bytes;
+} rk_profile_entry;
+rk_status rk_profile_enable(int on);
+int rk_profile_read(rk_profile_entry* out, int max);
+
+/* A static string naming the status. */
+const char* rk_status_string(rk_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RK_H */

@@ -1,0 +1,161 @@
+"""Rapid approximate Kriging prediction on one GB300 GPU.
+
+A thin Python layer over librk (include/rk.h).  Every step of the prediction
+runs in the library's CUDA kernels; this module only marshals arguments,
+allocates output tensors with PyTorch and passes PyTorch's current CUDA stream.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from ._native import RK_FP32, RK_FP64, PlanInfo, RkError, check, lib, profile_enable, profile_read
+
+__all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "profile_enable", "profile_read"]
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_f64(t, shape=None):
+    t = torch.as_tensor(t)
+    if t.device.type != "cuda":
+        t = t.to("cuda")
+    t = t.to(torch.float64).contiguous()
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        t = t.reshape(shape)
+    return t
+
+
+class Plan:
+    """One covariance model on one prediction grid (rk_plan_create).
+
+    Parameters follow the paper's notation: an nx x ny grid on
+    extent = (x0, x1, y0, y1), Matern smoothness nu, range rho, variance
+    sigma2, nugget tau2 and neighbourhood order L (M = (2L)^2).
+    precision is "fp32" (FFT in float with an exact double low-frequency
+    block) or "fp64" (every step in double).
+    """
+
+    def __init__(self, nx, ny, extent, nu, rho, sigma2, tau2, L, precision="fp32"):
+        self.nx, self.ny, self.L = int(nx), int(ny), int(L)
+        self.precision = RK_FP64 if precision in ("fp64", RK_FP64) else RK_FP32
+        self.dtype = torch.float64 if self.precision == RK_FP64 else torch.float32
+        ext = (ctypes.c_double * 4)(*[float(e) for e in extent])
+        h = ctypes.c_void_p()
+        check(lib.rk_plan_create(ctypes.byref(h), self.nx, self.ny, ext, float(nu), float(rho),
+                                 float(sigma2), float(tau2), self.L, self.precision, _stream()),
+              "rk_plan_create")
+        self._h = h
+        self.n = 0
+        self.B = 0
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.rk_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _call(self, name, *args):
+        check(lib.rk_set_stream(self._h, _stream()), "rk_set_stream")
+        check(getattr(lib, name)(self._h, *args), name)
+
+    def info(self):
+        i = PlanInfo()
+        check(lib.rk_plan_get_info(self._h, ctypes.byref(i)), "rk_plan_get_info")
+        return {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+
+    # -- inputs --
+    def set_sites(self, xy):
+        xy = _dev_f64(xy)
+        n = xy.shape[0]
+        self._call("rk_set_sites", int(n), _ptr(xy))
+        self.n = n
+        self._xy = xy
+
+    def set_coef(self, c):
+        c = _dev_f64(c)
+        if c.dim() == 1:
+            c = c[None]
+        self._call("rk_set_coef", int(c.shape[0]), _ptr(c))
+        self.B = c.shape[0]
+
+    def solve_coef(self, z):
+        z = _dev_f64(z)
+        if z.dim() == 1:
+            z = z[None]
+        self._call("rk_solve_coef", int(z.shape[0]), _ptr(z))
+        self.B = z.shape[0]
+
+    def set_obs(self, xy, z):
+        self.set_sites(xy)
+        self.solve_coef(z)
+
+    # -- outputs --
+    def predict(self, out=None):
+        if out is None:
+            out = torch.empty((self.B, self.ny, self.nx), dtype=self.dtype, device="cuda")
+        self._call("rk_predict", _ptr(out))
+        return out
+
+    def predict_host(self, xy, c):
+        """Prediction from host (numpy) inputs to a host result (rk_predict_host)."""
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        c = np.ascontiguousarray(np.atleast_2d(c), dtype=np.float64)
+        npdt = np.float64 if self.precision == RK_FP64 else np.float32
+        out = np.empty((c.shape[0], self.ny, self.nx), dtype=npdt)
+        self._call("rk_predict_host", int(xy.shape[0]), xy.ctypes.data_as(ctypes.c_void_p),
+                   int(c.shape[0]), c.ctypes.data_as(ctypes.c_void_p),
+                   out.ctypes.data_as(ctypes.c_void_p))
+        self.n, self.B = xy.shape[0], c.shape[0]
+        return out
+
+    def simulate(self, R, seed, out=None):
+        if out is None:
+            out = torch.empty((self.B, int(R), self.ny, self.nx), dtype=self.dtype, device="cuda")
+        self._call("rk_simulate", int(R), ctypes.c_ulonglong(int(seed)), _ptr(out))
+        return out
+
+    def backward(self, gbar, need_z=True, need_theta=True):
+        gbar = torch.as_tensor(gbar).to(device="cuda", dtype=self.dtype).contiguous()
+        gz = torch.empty((self.B, self.n), dtype=torch.float64, device="cuda") if need_z else None
+        gr = torch.empty(self.B, dtype=torch.float64, device="cuda") if need_theta else None
+        gs = torch.empty(self.B, dtype=torch.float64, device="cuda") if need_theta else None
+        nul = ctypes.c_void_p(0)
+        self._call("rk_predict_backward", _ptr(gbar), _ptr(gz) if gz is not None else nul,
+                   _ptr(gr) if gr is not None else nul, _ptr(gs) if gs is not None else nul)
+        return gz, gr, gs
+
+    def debug_copy(self, what):
+        """Internal buffers for tests: 'box', 'weights', 'lambda', 'cstar', 'coef'."""
+        info = self.info()
+        code = {"box": 0, "weights": 1, "lambda": 2, "cstar": 3, "coef": 4}[what]
+        if code == 0:
+            t = torch.empty((self.n, 2), dtype=torch.int32, device="cuda")
+        elif code == 1:
+            t = torch.empty((self.n, info["M"]), dtype=torch.float64, device="cuda")
+        elif code == 2:
+            t = torch.empty((info["hx_spec"], info["py"]), dtype=self.dtype, device="cuda")
+        elif code == 3:
+            t = torch.empty((info["p1y"], info["p1x"]), dtype=self.dtype, device="cuda")
+        else:
+            t = torch.empty((self.B, self.n), dtype=torch.float64, device="cuda")
+        self._call("rk_debug_copy", code, _ptr(t), ctypes.c_size_t(t.numel() * t.element_size()))
+        return t

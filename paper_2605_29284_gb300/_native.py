@@ -1,0 +1,93 @@
+"""ctypes binding of librk.so (the C ABI declared in include/rk.h).
+
+The library is built in-tree by ``paper_2605_29284_gb300.build``.  Importing
+this module fails loudly if it is missing: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librk.so")
+
+STATUS = {
+    0: "RK_OK", 1: "RK_ERR_INVALID_ARG", 2: "RK_ERR_OBS_OUTSIDE", 3: "RK_ERR_NOT_PD",
+    4: "RK_ERR_CE_NEGATIVE", 5: "RK_ERR_CUDA", 6: "RK_ERR_OOM", 7: "RK_ERR_TIMEOUT",
+    8: "RK_ERR_STATE",
+}
+RK_FP32, RK_FP64 = 0, 1
+
+
+class RkError(RuntimeError):
+    """A non-OK status from librk."""
+
+    def __init__(self, status, where):
+        self.status = int(status)
+        self.name = STATUS.get(self.status, f"status {status}")
+        super().__init__(f"{where}: {self.name} ({lib.rk_status_string(self.status).decode()})")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int) for name in (
+        "nx", "ny", "L", "M", "p1x", "p1y", "px", "py", "hx_spec", "blk_kx", "blk_ky",
+        "n", "B", "precision", "qx", "qy")]
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"librk.so not found at {LIB_PATH}; build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    return ctypes.CDLL(LIB_PATH)
+
+
+lib = _load()
+
+_vp, _int, _dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    "rk_plan_create": [ctypes.POINTER(_vp), _int, _int, ctypes.POINTER(_dbl), _dbl, _dbl, _dbl,
+                       _dbl, _int, _int, _vp],
+    "rk_plan_destroy": [_vp],
+    "rk_set_stream": [_vp, _vp],
+    "rk_plan_get_info": [_vp, ctypes.POINTER(PlanInfo)],
+    "rk_set_sites": [_vp, _int, _vp],
+    "rk_set_coef": [_vp, _int, _vp],
+    "rk_solve_coef": [_vp, _int, _vp],
+    "rk_set_obs": [_vp, _int, _vp, _vp, _int],
+    "rk_predict": [_vp, _vp],
+    "rk_predict_host": [_vp, _int, _vp, _int, _vp, _vp],
+    "rk_simulate": [_vp, _int, ctypes.c_ulonglong, _vp],
+    "rk_predict_backward": [_vp, _vp, _vp, _vp, _vp],
+    "rk_debug_copy": [_vp, _int, _vp, ctypes.c_size_t],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _int
+lib.rk_profile_enable.argtypes = [_int]
+lib.rk_profile_enable.restype = _int
+lib.rk_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), _int]
+lib.rk_profile_read.restype = _int
+lib.rk_status_string.argtypes = [_int]
+lib.rk_status_string.restype = ctypes.c_char_p
+
+
+def check(status, where):
+    if status != 0:
+        raise RkError(status, where)
+
+
+def profile_enable(on=True):
+    lib.rk_profile_enable(1 if on else 0)
+
+
+def profile_read():
+    """{kernel: (launches, total_ms, algorithmic_bytes)} since the last read."""
+    buf = (ProfileEntry * 64)()
+    k = lib.rk_profile_read(buf, 64)
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes)
+            for i in range(k)}

@@ -1,0 +1,199 @@
+// Internal declarations shared by the translation units of librk.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/rk.h"
+
+namespace rk {
+
+// ----------------------------------------------------------- complex types --
+
+template <typename T> struct cvec;
+template <> struct cvec<float> { using type = float2; };
+template <> struct cvec<double> { using type = double2; };
+template <typename T> using C = typename cvec<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ C<T> mk(T x, T y) { C<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ C<T> cmulc(C<T> a, C<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T> __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+template <typename T> __device__ __forceinline__ C<T> cconj(C<T> a) { return mk<T>(a.x, -a.y); }
+// multiply by -i * dir  (dir = +1: -i, dir = -1: +i)
+template <typename T> __device__ __forceinline__ C<T> cmul_mi(C<T> a, int dir) {
+  return dir > 0 ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
+}
+
+// ------------------------------------------------------------------ Matern --
+// phi(d) of Eq. (Matern1) for the half-integer smoothness values, which have
+// elementary closed forms: nu = 1/2: e^-d; 3/2: (1 + d) e^-d;
+// 5/2: (1 + d + d^2 / 3) e^-d.  nu_code: 0 -> 1/2, 1 -> 3/2, 2 -> 5/2.
+template <typename T>
+__device__ __forceinline__ T matern_phi(T d, int nu_code) {
+  T e = exp(-d);
+  if (nu_code == 0) return e;
+  if (nu_code == 1) return (T(1) + d) * e;
+  return (T(1) + d + d * d / T(3)) * e;
+}
+// -t phi'(t): derivative of phi(d / rho) with respect to log rho.
+// nu = 1/2: t e^-t; 3/2: t^2 e^-t; 5/2: (t^2 / 3)(1 + t) e^-t.
+template <typename T>
+__device__ __forceinline__ T matern_dlogrho(T t, int nu_code) {
+  T e = exp(-t);
+  if (nu_code == 0) return t * e;
+  if (nu_code == 1) return t * t * e;
+  return (t * t / T(3)) * (T(1) + t) * e;
+}
+
+// ------------------------------------------------------------- FFT plans --
+
+constexpr int kMaxStages = 24;
+
+struct FftPlan {
+  int n;
+  int nstages;
+  int radix[kMaxStages];
+  int span[kMaxStages];   // product of the radices before this stage
+};
+
+// ----------------------------------------------------------- plan object --
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace rk
+
+struct rk_plan {
+  // parameters
+  int nx, ny, L, M, precision;
+  double x0, x1, y0, y1, hx, hy;
+  double nu, rho, sigma2, tau2;
+  int nu_code;
+  int p1x, p1y, px, py, H;
+  cudaStream_t stream;
+  // FFT plans and twiddle tables (double and float copies)
+  rk::FftPlan fpx, fpy;
+  double2* tw64x = nullptr; double2* tw64y = nullptr;
+  float2* tw32x = nullptr; float2* tw32y = nullptr;
+  // spectrum: lambda[kx][ky] / (px py), H x py
+  double* lam64 = nullptr; float* lam32 = nullptr;
+  double* dlam64 = nullptr; float* dlam32 = nullptr;   // d lambda / d log rho (adjoint)
+  // neighbourhood covariance factor (M x M lower Cholesky, double)
+  double* kn_chol = nullptr;
+  double* kn_dlog = nullptr;   // d K_N / d log rho (adjoint)
+  // exact low-frequency block (FP32 plans)
+  int blk_kx = -1, blk_ky = -1, nblk = 0;
+  // sites
+  int n = 0, n_cap = 0;
+  double* xy = nullptr;        // n x 2 site coordinates (copy)
+  int* box = nullptr;          // n x 2 (ix, iy)
+  double* w64 = nullptr;       // n x M
+  float* w32 = nullptr;        // n x M
+  double* ssd = nullptr;       // n: sqrt(max(0, sigma2 - k_i^T W_i)) (CS)
+  double2* efac = nullptr;     // n x nblk Fourier factors of A_i on the block
+  // coefficients
+  int B = 0, B_cap = 0, n_cap_coef = 0;
+  double* c64 = nullptr;       // B x n
+  float* c32 = nullptr;        // B x n
+  double* z64 = nullptr;       // B x n data (after rk_solve_coef)
+  bool have_coef = false, have_chol = false;
+  // Cholesky factor of M = K_xx + tau2 I (n x n lower, column-major), double
+  double* mchol = nullptr;
+  size_t mchol_cap = 0;
+  // scratch for prediction, sized for B_cap fields (and realisations)
+  void* cstar = nullptr; size_t cstar_bytes = 0;     // B x p1y x p1x (plan precision)
+  void* tbuf = nullptr; size_t tbuf_bytes = 0;       // B x H x ldt complex
+  void* ubuf = nullptr; size_t ubuf_bytes = 0;       // B x H x ldu complex
+  double2* blk = nullptr; size_t blk_cap = 0;        // B x nblk exact block
+  int ldt = 0, ldu = 0;
+  int* d_flag = nullptr;                             // device status flag
+  // conditional simulation state
+  int qx = 0, qy = 0;
+  rk::FftPlan fqx, fqy;
+  double2* tw64qx = nullptr; double2* tw64qy = nullptr;
+  float2* tw32qx = nullptr; float2* tw32qy = nullptr;
+  double* ce_sqrt64 = nullptr; float* ce_sqrt32 = nullptr;   // sqrt(lambda_Q / (qx qy)), qy x qx
+  void* cs_buf = nullptr; size_t cs_bytes = 0;
+  // device staging for rk_predict_host
+  double* h_xy = nullptr; size_t h_xy_cap = 0;
+  double* h_c = nullptr; size_t h_c_cap = 0;
+  void* h_out = nullptr; size_t h_out_cap = 0;
+};
+
+namespace rk {
+
+// ------------------------------------------------------ launch interfaces --
+// (implemented in k_fft.cu, k_sites.cu, k_chol.cu, k_cs.cu, k_adj.cu)
+
+// FFT passes; T = float or double.
+template <typename T>
+cudaError_t launch_rows_fwd(const T* in, int nrows, int ncols, long long in_field_stride, int in_ld,
+                            C<T>* tout, int ldt, long long t_field_stride, int B,
+                            const FftPlan& fp, const C<T>* tw, int H, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cols(const C<T>* tin, int ldt, long long t_field_stride, int nrin,
+                        C<T>* uout, int ldu, long long u_field_stride, int orow0, int nrout,
+                        const T* lam, int mode, const double2* blk, int blk_kx, int blk_ky,
+                        int nblk, int B, int H, const FftPlan& fp, const C<T>* tw, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rows_inv(const C<T>* uin, int ldu, long long u_field_stride, int nrows,
+                            T* out, int out_ld, long long out_field_stride, int ocol0, int ncols,
+                            const T* addend, int add_ld, long long add_field_stride, int add_r0,
+                            int add_c0, int B, const FftPlan& fp, const C<T>* tw, int H,
+                            cudaStream_t s);
+
+enum { COLS_CONV = 0, COLS_FWD_ONLY = 1 };
+
+cudaError_t launch_torus_base(double* base, int px, int py, double hx, double hy, double rho,
+                              double sigma2, int nu_code, int deriv, cudaStream_t s);
+cudaError_t launch_lambda_finish(const double2* spec, int ld, int H, int py, double scale,
+                                 double* lam64, float* lam32, cudaStream_t s);
+
+// sites
+cudaError_t launch_kn_factor(double* kn, int L, double hx, double hy, double rho, double sigma2,
+                             int nu_code, int* flag, cudaStream_t s);
+cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, double* w64,
+                           float* w32, double* ssd, int* flag, cudaStream_t s);
+cudaError_t launch_block_factors(const int* box, const double* w64, int n, const rk_plan* p,
+                                 double2* efac, cudaStream_t s);
+cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac, int nblk,
+                              double2* blk, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter(const int* box, const T* w, const T* c, int n, int B, int L,
+                           T* cstar, int p1x, int p1y, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert(const double* src, T* dst, size_t count, cudaStream_t s);
+
+// dense FP64 Cholesky of M = K_xx + tau2 I and solves
+cudaError_t build_obs_cov(const double* xy, int n, const rk_plan* p, double* a, cudaStream_t s);
+cudaError_t chol_factor(double* a, int n, int* flag, cudaStream_t s);
+cudaError_t chol_solve(const double* l, int n, double* x, int B, cudaStream_t s);
+
+// conditional simulation
+template <typename T>
+cudaError_t launch_ce_noise(const T* sqrtlam, int qx, int qy, unsigned long long seed, int pair0,
+                            int npairs, C<T>* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_site_values(const T* fu, int fu_ld, long long fu_stride, int nreal,
+                               const int* box, const double* w64, const double* ssd, int n, int L,
+                               double tau, unsigned long long seed, int t0, const double* z,
+                               double* rhs, cudaStream_t s);
+
+// adjoint
+template <typename T>
+cudaError_t launch_gather(const T* abar, int p1x, int p1y, const int* box, const double* w64,
+                          int n, int L, int B, double* cbar, cudaStream_t s);
+
+}  // namespace rk

@@ -1,0 +1,590 @@
+// Host side of librk: plan construction and the C entry points of rk.h.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace rk;
+
+namespace {
+
+// Fraction of the spectral peak above which a frequency belongs to the exact
+// low-frequency block of RK_FP32 plans, and the block's size limit.
+constexpr double kBlockEta = 1e-2;
+constexpr int kBlockMax = 1024;
+// largest torus length per dimension (shared-memory limit of the FFT passes)
+constexpr int kMaxTorus = 3456;
+
+int smooth23(int n) {
+  long long best = -1;
+  for (long long p2 = 1;; p2 *= 2) {
+    long long p = p2;
+    while (p < n) p *= 3;
+    if (best < 0 || p < best) best = p;
+    if (p2 >= n) break;
+  }
+  return (int)best;
+}
+
+FftPlan make_fft_plan(int n) {
+  FftPlan fp;
+  memset(&fp, 0, sizeof(fp));
+  fp.n = n;
+  int m = n, span = 1, s = 0;
+  const int radices[4] = {8, 4, 3, 2};
+  for (int ri = 0; ri < 4; ++ri) {
+    const int r = radices[ri];
+    while (m % r == 0 && s < kMaxStages) {
+      fp.radix[s] = r;
+      fp.span[s] = span;
+      span *= r;
+      m /= r;
+      ++s;
+    }
+  }
+  fp.nstages = s;
+  return fp;
+}
+
+// twiddles w[e] = exp(-2 pi i e / n), computed in extended precision and
+// rounded once to double and to float.
+void make_twiddles(int n, std::vector<double2>& t64, std::vector<float2>& t32) {
+  t64.resize(n);
+  t32.resize(n);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int e = 0; e < n; ++e) {
+    const long double ang = 2.0L * pi * (long double)e / (long double)n;
+    const double c = (double)cosl(ang), s = (double)-sinl(ang);
+    t64[e] = make_double2(c, s);
+    t32[e] = make_float2((float)c, (float)s);
+  }
+}
+
+template <typename T>
+rk_status dalloc(T** p, size_t count) {
+  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (count == 0) return RK_OK;
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return RK_ERR_OOM;
+  }
+  return RK_OK;
+}
+
+rk_status dalloc_bytes(void** p, size_t bytes) {
+  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (bytes == 0) return RK_OK;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return RK_ERR_OOM;
+  }
+  return RK_OK;
+}
+
+#define RK_CU(x)                              \
+  do {                                        \
+    if ((x) != cudaSuccess) return RK_ERR_CUDA; \
+  } while (0)
+#define RK_TRY(x)                   \
+  do {                              \
+    rk_status st_ = (x);            \
+    if (st_ != RK_OK) return st_;   \
+  } while (0)
+
+// ------------------------------------------------------------- profiler --
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+  double bytes;
+};
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+
+struct ProfScope {
+  ProfRec rec;
+  cudaStream_t s;
+  bool on;
+  ProfScope(const char* name, double bytes, cudaStream_t st) : s(st), on(g_prof_on) {
+    if (!on) return;
+    rec.name = name;
+    rec.bytes = bytes;
+    cudaEventCreate(&rec.a);
+    cudaEventCreate(&rec.b);
+    cudaEventRecord(rec.a, s);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(rec.b, s);
+    g_prof.push_back(rec);
+  }
+};
+#define RK_PROF(name, bytes) ProfScope prof_scope_##__LINE__(name, (double)(bytes), s)
+
+rk_status read_flag(rk_plan* p, int* value) {
+  RK_CU(cudaMemcpyAsync(value, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  RK_CU(cudaStreamSynchronize(p->stream));
+  return RK_OK;
+}
+
+rk_status upload_twiddles(int n, double2** t64, float2** t32) {
+  std::vector<double2> h64;
+  std::vector<float2> h32;
+  make_twiddles(n, h64, h32);
+  RK_TRY(dalloc(t64, n));
+  RK_TRY(dalloc(t32, n));
+  RK_CU(cudaMemcpy(*t64, h64.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+  RK_CU(cudaMemcpy(*t32, h32.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  return RK_OK;
+}
+
+// lambda = FFT2(base) / (px py) for a base of the given kind (0: phi, 1: d/dlog rho).
+rk_status compute_spectrum(rk_plan* p, int deriv, double** lam64, float** lam32) {
+  const int px = p->px, py = p->py, H = p->H;
+  double* base = nullptr;
+  double2* t = nullptr;
+  double2* u = nullptr;
+  rk_status st = RK_OK;
+  do {
+    if ((st = dalloc(&base, (size_t)px * py)) != RK_OK) break;
+    if ((st = dalloc(&t, (size_t)H * py)) != RK_OK) break;
+    if ((st = dalloc(&u, (size_t)H * py)) != RK_OK) break;
+    if ((st = dalloc(lam64, (size_t)H * py)) != RK_OK) break;
+    if (p->precision == RK_FP32 && (st = dalloc(lam32, (size_t)H * py)) != RK_OK) break;
+    if (launch_torus_base(base, px, py, p->hx, p->hy, p->rho, p->sigma2, p->nu_code, deriv,
+                          p->stream) != cudaSuccess ||
+        launch_rows_fwd<double>(base, py, px, 0, px, t, py, 0, 1, p->fpx, p->tw64x, H,
+                                p->stream) != cudaSuccess ||
+        launch_cols<double>(t, py, 0, py, u, py, 0, 0, py, nullptr, COLS_FWD_ONLY, nullptr, -1, 0,
+                            0, 1, H, p->fpy, p->tw64y, p->stream) != cudaSuccess ||
+        launch_lambda_finish(u, py, H, py, 1.0 / ((double)px * (double)py), *lam64,
+                             p->precision == RK_FP32 ? *lam32 : nullptr, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess) {
+      st = RK_ERR_CUDA;
+    }
+  } while (0);
+  cudaFree(base);
+  cudaFree(t);
+  cudaFree(u);
+  return st;
+}
+
+// choose the exact low-frequency block from lambda (host copy)
+rk_status choose_block(rk_plan* p) {
+  const int H = p->H, py = p->py;
+  std::vector<double> lam((size_t)H * py);
+  RK_CU(cudaMemcpy(lam.data(), p->lam64, lam.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  double lmax = 0.0;
+  for (double v : lam) lmax = v > lmax ? v : lmax;
+  double eta = kBlockEta;
+  for (int iter = 0; iter < 60; ++iter, eta *= 2.0) {
+    int kx_max = -1, ky_max = 0;
+    for (int kx = 0; kx < H; ++kx)
+      for (int ky = 0; ky < py; ++ky)
+        if (lam[(size_t)kx * py + ky] > eta * lmax) {
+          const int sky = ky <= py / 2 ? ky : py - ky;
+          kx_max = kx > kx_max ? kx : kx_max;
+          ky_max = sky > ky_max ? sky : ky_max;
+        }
+    if (ky_max >= (py - 1) / 2) ky_max = (py - 1) / 2;
+    const int nblk = (kx_max + 1) * (2 * ky_max + 1);
+    if (kx_max >= 0 && nblk <= kBlockMax) {
+      p->blk_kx = kx_max;
+      p->blk_ky = ky_max;
+      p->nblk = nblk;
+      return RK_OK;
+    }
+  }
+  p->blk_kx = -1;
+  p->blk_ky = 0;
+  p->nblk = 0;
+  return RK_OK;
+}
+
+void free_plan(rk_plan* p) {
+  void* bufs[] = {p->tw64x, p->tw64y, p->tw32x, p->tw32y, p->lam64, p->lam32, p->dlam64,
+                  p->dlam32, p->kn_chol, p->kn_dlog, p->box, p->w64, p->w32, p->ssd, p->efac,
+                  p->c64, p->c32, p->z64, p->mchol, p->cstar, p->tbuf, p->ubuf, p->blk,
+                  p->d_flag, p->tw64qx, p->tw64qy, p->tw32qx, p->tw32qy, p->ce_sqrt64,
+                  p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_c, p->h_out, p->xy};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+}
+
+// make sure the per-field scratch holds B fields
+rk_status ensure_field_scratch(rk_plan* p, int B) {
+  const size_t esz = p->precision == RK_FP64 ? sizeof(double) : sizeof(float);
+  const size_t need_c = (size_t)B * p->p1y * p->p1x * esz;
+  const size_t need_t = (size_t)B * p->H * p->ldt * 2 * esz;
+  const size_t need_u = (size_t)B * p->H * p->ldu * 2 * esz;
+  if (p->cstar_bytes < need_c) {
+    RK_TRY(dalloc_bytes(&p->cstar, need_c));
+    p->cstar_bytes = need_c;
+  }
+  if (p->tbuf_bytes < need_t) {
+    RK_TRY(dalloc_bytes(&p->tbuf, need_t));
+    p->tbuf_bytes = need_t;
+  }
+  if (p->ubuf_bytes < need_u) {
+    RK_TRY(dalloc_bytes(&p->ubuf, need_u));
+    p->ubuf_bytes = need_u;
+  }
+  if (p->precision == RK_FP32 && p->nblk > 0 && p->blk_cap < (size_t)B * p->nblk) {
+    RK_TRY(dalloc(&p->blk, (size_t)B * p->nblk));
+    p->blk_cap = (size_t)B * p->nblk;
+  }
+  return RK_OK;
+}
+
+rk_status ensure_coef(rk_plan* p, int B) {
+  if (B > p->B_cap || p->n > p->n_cap_coef) {
+    RK_TRY(dalloc(&p->c64, (size_t)B * p->n));
+    RK_TRY(dalloc(&p->c32, (size_t)B * p->n));
+    RK_TRY(dalloc(&p->z64, (size_t)B * p->n));
+    p->B_cap = B;
+    p->n_cap_coef = p->n;
+  }
+  return ensure_field_scratch(p, B);
+}
+
+// c32 from c64 and the exact block (FP32 plans)
+rk_status finish_coef(rk_plan* p, int B) {
+  p->B = B;
+  if (p->precision == RK_FP32) {
+    if (launch_convert<float>(p->c64, p->c32, (size_t)B * p->n, p->stream) != cudaSuccess)
+      return RK_ERR_CUDA;
+  }
+  p->have_coef = true;
+  return RK_OK;
+}
+
+template <typename T>
+rk_status predict_impl(rk_plan* p, T* out) {
+  const int B = p->B;
+  cudaStream_t s = p->stream;
+  T* cstar = (T*)p->cstar;
+  C<T>* tb = (C<T>*)p->tbuf;
+  C<T>* ub = (C<T>*)p->ubuf;
+  const bool f32 = sizeof(T) == sizeof(float);
+  const T* w = f32 ? (const T*)p->w32 : (const T*)p->w64;
+  const T* c = f32 ? (const T*)p->c32 : (const T*)p->c64;
+  const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
+  const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
+  const C<T>* twy = f32 ? (const C<T>*)p->tw32y : (const C<T>*)p->tw64y;
+  const size_t plane = (size_t)p->p1y * p->p1x;
+  const double es = sizeof(T), cs = 2.0 * sizeof(T);
+  const double nM = (double)p->n * p->M;
+  {
+    RK_PROF("scatter", B * (plane * es + nM * 2 * es + p->n * es) + nM * es + p->n * 8.0);
+    RK_CU(cudaMemsetAsync(cstar, 0, (size_t)B * plane * sizeof(T), s));
+    RK_CU(launch_scatter<T>(p->box, w, c, p->n, B, p->L, cstar, p->p1x, p->p1y, s));
+  }
+  {
+    RK_PROF("rows_fwd", B * (plane * es + (double)p->H * p->p1y * cs));
+    RK_CU(launch_rows_fwd<T>(cstar, p->p1y, p->p1x, (long long)plane, p->p1x, tb, p->ldt,
+                             (long long)p->H * p->ldt, B, p->fpx, twx, p->H, s));
+  }
+  const bool use_blk = f32 && p->nblk > 0;
+  if (use_blk) {
+    RK_PROF("block_gemm", (double)p->nblk * p->n * 16.0 + B * (p->n * 8.0 + p->nblk * 16.0));
+    RK_CU(launch_block_gemm(p->c64, B, p->n, p->efac, p->nblk, p->blk, s));
+  }
+  {
+    RK_PROF("cols", B * ((double)p->H * p->p1y * cs + (double)p->H * p->ny * cs) +
+                        (double)p->H * p->py * es);
+    RK_CU(launch_cols<T>(tb, p->ldt, (long long)p->H * p->ldt, p->p1y, ub, p->ldu,
+                         (long long)p->H * p->ldu, p->L - 1, p->ny, lam, COLS_CONV,
+                         use_blk ? p->blk : nullptr, p->blk_kx, p->blk_ky, p->nblk, B, p->H,
+                         p->fpy, twy, s));
+  }
+  {
+    RK_PROF("rows_inv", B * ((double)p->H * p->ny * cs + (double)p->ny * p->nx * es));
+    RK_CU(launch_rows_inv<T>(ub, p->ldu, (long long)p->H * p->ldu, p->ny, out, p->nx,
+                             (long long)p->ny * p->nx, p->L - 1, p->nx, (const T*)nullptr, 0, 0,
+                             0, 0, B, p->fpx, twx, p->H, s));
+  }
+  return RK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rk_status_string(rk_status s) {
+  switch (s) {
+    case RK_OK: return "ok";
+    case RK_ERR_INVALID_ARG: return "invalid argument";
+    case RK_ERR_OBS_OUTSIDE: return "observation outside the grid extent";
+    case RK_ERR_NOT_PD: return "matrix not positive definite";
+    case RK_ERR_CE_NEGATIVE: return "circulant embedding has negative eigenvalues";
+    case RK_ERR_CUDA: return "CUDA error";
+    case RK_ERR_OOM: return "out of device memory";
+    case RK_ERR_TIMEOUT: return "device wait timed out";
+    case RK_ERR_STATE: return "required state not set";
+  }
+  return "unknown status";
+}
+
+rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], double nu,
+                         double range, double sigma2, double tau2, int L, int precision,
+                         void* stream) {
+  if (!out) return RK_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!extent || nx < 2 || ny < 2 || L < 1 || L > 4) return RK_ERR_INVALID_ARG;
+  if (!(extent[1] > extent[0]) || !(extent[3] > extent[2])) return RK_ERR_INVALID_ARG;
+  if (!(range > 0.0) || !(sigma2 > 0.0) || !(tau2 >= 0.0)) return RK_ERR_INVALID_ARG;
+  if (precision != RK_FP32 && precision != RK_FP64) return RK_ERR_INVALID_ARG;
+  int nu_code;
+  if (fabs(nu - 0.5) < 1e-12) nu_code = 0;
+  else if (fabs(nu - 1.5) < 1e-12) nu_code = 1;
+  else if (fabs(nu - 2.5) < 1e-12) nu_code = 2;
+  else return RK_ERR_INVALID_ARG;
+  if ((long long)nx * ny > (1LL << 28)) return RK_ERR_INVALID_ARG;
+  // the 1-D transforms hold two complex double rows per CTA in shared memory
+  if (smooth23(2 * (nx + L - 2)) > kMaxTorus || smooth23(2 * (ny + L - 2)) > kMaxTorus)
+    return RK_ERR_INVALID_ARG;
+
+  rk_plan* p = new (std::nothrow) rk_plan();
+  if (!p) return RK_ERR_OOM;
+  p->nx = nx; p->ny = ny; p->L = L; p->M = 4 * L * L; p->precision = precision;
+  p->x0 = extent[0]; p->x1 = extent[1]; p->y0 = extent[2]; p->y1 = extent[3];
+  p->hx = (p->x1 - p->x0) / (nx - 1);
+  p->hy = (p->y1 - p->y0) / (ny - 1);
+  p->nu = nu; p->rho = range; p->sigma2 = sigma2; p->tau2 = tau2; p->nu_code = nu_code;
+  p->p1x = nx + 2 * (L - 1);
+  p->p1y = ny + 2 * (L - 1);
+  p->px = smooth23(2 * (nx + L - 2) > p->p1x ? 2 * (nx + L - 2) : p->p1x);
+  p->py = smooth23(2 * (ny + L - 2) > p->p1y ? 2 * (ny + L - 2) : p->p1y);
+  p->H = p->px / 2 + 1;
+  p->ldt = p->p1y;
+  p->ldu = p->ny;
+  p->stream = (cudaStream_t)stream;
+  p->fpx = make_fft_plan(p->px);
+  p->fpy = make_fft_plan(p->py);
+  rk_status st = RK_OK;
+  do {
+    if ((st = dalloc(&p->d_flag, 1)) != RK_OK) break;
+    if ((st = upload_twiddles(p->px, &p->tw64x, &p->tw32x)) != RK_OK) break;
+    if ((st = upload_twiddles(p->py, &p->tw64y, &p->tw32y)) != RK_OK) break;
+    if ((st = compute_spectrum(p, 0, &p->lam64, &p->lam32)) != RK_OK) break;
+    if (precision == RK_FP32 && (st = choose_block(p)) != RK_OK) break;
+    if ((st = dalloc(&p->kn_chol, (size_t)p->M * p->M)) != RK_OK) break;
+    if (cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream) != cudaSuccess ||
+        launch_kn_factor(p->kn_chol, L, p->hx, p->hy, p->rho, p->sigma2, nu_code, p->d_flag,
+                         p->stream) != cudaSuccess) {
+      st = RK_ERR_CUDA;
+      break;
+    }
+    int flag = 0;
+    if ((st = read_flag(p, &flag)) != RK_OK) break;
+    if (flag) { st = RK_ERR_NOT_PD; break; }
+  } while (0);
+  if (st != RK_OK) {
+    free_plan(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return RK_OK;
+}
+
+rk_status rk_profile_enable(int on) {
+  g_prof_on = on != 0;
+  return RK_OK;
+}
+
+int rk_profile_read(rk_profile_entry* out, int max) {
+  int count = 0;
+  for (ProfRec& r : g_prof) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+    int k = 0;
+    while (k < count && strncmp(out[k].name, r.name, sizeof(out[k].name)) != 0) ++k;
+    if (k == count) {
+      if (count >= max) continue;
+      memset(&out[k], 0, sizeof(out[k]));
+      strncpy(out[k].name, r.name, sizeof(out[k].name) - 1);
+      ++count;
+    }
+    out[k].launches += 1;
+    out[k].total_ms += ms;
+    out[k].bytes += r.bytes;
+  }
+  g_prof.clear();
+  return count;
+}
+
+rk_status rk_plan_destroy(rk_plan* p) {
+  if (!p) return RK_OK;
+  cudaStreamSynchronize(p->stream);
+  free_plan(p);
+  delete p;
+  return RK_OK;
+}
+
+rk_status rk_set_stream(rk_plan* p, void* stream) {
+  if (!p) return RK_ERR_INVALID_ARG;
+  p->stream = (cudaStream_t)stream;
+  return RK_OK;
+}
+
+rk_status rk_plan_get_info(const rk_plan* p, rk_plan_info* info) {
+  if (!p || !info) return RK_ERR_INVALID_ARG;
+  info->nx = p->nx; info->ny = p->ny; info->L = p->L; info->M = p->M;
+  info->p1x = p->p1x; info->p1y = p->p1y; info->px = p->px; info->py = p->py;
+  info->hx_spec = p->H; info->blk_kx = p->blk_kx; info->blk_ky = p->blk_ky;
+  info->n = p->n; info->B = p->B; info->precision = p->precision;
+  info->qx = p->qx; info->qy = p->qy;
+  return RK_OK;
+}
+
+rk_status rk_set_sites(rk_plan* p, int n, const double* xy) {
+  if (!p || n < 1 || !xy) return RK_ERR_INVALID_ARG;
+  if (n > p->n_cap) {
+    RK_TRY(dalloc(&p->xy, (size_t)2 * n));
+    RK_TRY(dalloc(&p->box, (size_t)2 * n));
+    RK_TRY(dalloc(&p->w64, (size_t)n * p->M));
+    RK_TRY(dalloc(&p->w32, (size_t)n * p->M));
+    RK_TRY(dalloc(&p->ssd, (size_t)n));
+    if (p->precision == RK_FP32 && p->nblk > 0) RK_TRY(dalloc(&p->efac, (size_t)n * p->nblk));
+    p->n_cap = n;
+  }
+  p->n = 0;
+  p->have_coef = false;
+  p->have_chol = false;
+  RK_CU(cudaMemcpyAsync(p->xy, xy, (size_t)2 * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                        p->stream));
+  RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
+  RK_CU(launch_weights(p->xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_flag, p->stream));
+  int flag = 0;
+  RK_TRY(read_flag(p, &flag));
+  if (flag & 2) return RK_ERR_OBS_OUTSIDE;
+  if (p->precision == RK_FP32 && p->nblk > 0)
+    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->efac, p->stream));
+  p->n = n;
+  return RK_OK;
+}
+
+rk_status rk_set_coef(rk_plan* p, int B, const double* c) {
+  if (!p || B < 1 || !c) return RK_ERR_INVALID_ARG;
+  if (p->n == 0) return RK_ERR_STATE;
+  RK_TRY(ensure_coef(p, B));
+  RK_CU(cudaMemcpyAsync(p->c64, c, (size_t)B * p->n * sizeof(double), cudaMemcpyDeviceToDevice,
+                        p->stream));
+  return finish_coef(p, B);
+}
+
+rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
+  if (!p || B < 1 || !z) return RK_ERR_INVALID_ARG;
+  if (p->n == 0) return RK_ERR_STATE;
+  const int n = p->n;
+  RK_TRY(ensure_coef(p, B));
+  if (!p->have_chol) {
+    if (p->mchol_cap < (size_t)n * n) {
+      RK_TRY(dalloc(&p->mchol, (size_t)n * n));
+      p->mchol_cap = (size_t)n * n;
+    }
+    RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
+    RK_CU(build_obs_cov(p->xy, n, p, p->mchol, p->stream));
+    RK_CU(chol_factor(p->mchol, n, p->d_flag, p->stream));
+    int flag = 0;
+    RK_TRY(read_flag(p, &flag));
+    if (flag) return RK_ERR_NOT_PD;
+    p->have_chol = true;
+  }
+  RK_CU(cudaMemcpyAsync(p->z64, z, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                        p->stream));
+  RK_CU(cudaMemcpyAsync(p->c64, z, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                        p->stream));
+  RK_CU(chol_solve(p->mchol, n, p->c64, B, p->stream));
+  RK_TRY(finish_coef(p, B));
+  RK_CU(cudaStreamSynchronize(p->stream));
+  return RK_OK;
+}
+
+rk_status rk_set_obs(rk_plan* p, int n, const double* xy, const double* z, int B) {
+  RK_TRY(rk_set_sites(p, n, xy));
+  return rk_solve_coef(p, B, z);
+}
+
+rk_status rk_predict(rk_plan* p, void* out) {
+  if (!p || !out) return RK_ERR_INVALID_ARG;
+  if (p->n == 0 || !p->have_coef) return RK_ERR_STATE;
+  if (p->precision == RK_FP64) return predict_impl<double>(p, (double*)out);
+  return predict_impl<float>(p, (float*)out);
+}
+
+rk_status rk_predict_host(rk_plan* p, int n, const double* xy_host, int B, const double* c_host,
+                          void* out_host) {
+  if (!p || n < 1 || B < 1 || !xy_host || !c_host || !out_host) return RK_ERR_INVALID_ARG;
+  const size_t esz = p->precision == RK_FP64 ? sizeof(double) : sizeof(float);
+  const size_t out_bytes = (size_t)B * p->ny * p->nx * esz;
+  if (p->h_xy_cap < (size_t)2 * n) {
+    RK_TRY(dalloc(&p->h_xy, (size_t)2 * n));
+    p->h_xy_cap = (size_t)2 * n;
+  }
+  if (p->h_c_cap < (size_t)B * n) {
+    RK_TRY(dalloc(&p->h_c, (size_t)B * n));
+    p->h_c_cap = (size_t)B * n;
+  }
+  if (p->h_out_cap < out_bytes) {
+    RK_TRY(dalloc_bytes(&p->h_out, out_bytes));
+    p->h_out_cap = out_bytes;
+  }
+  RK_CU(cudaMemcpyAsync(p->h_xy, xy_host, (size_t)2 * n * sizeof(double), cudaMemcpyHostToDevice,
+                        p->stream));
+  RK_CU(cudaMemcpyAsync(p->h_c, c_host, (size_t)B * n * sizeof(double), cudaMemcpyHostToDevice,
+                        p->stream));
+  RK_TRY(rk_set_sites(p, n, p->h_xy));
+  RK_TRY(rk_set_coef(p, B, p->h_c));
+  RK_TRY(rk_predict(p, p->h_out));
+  RK_CU(cudaMemcpyAsync(out_host, p->h_out, out_bytes, cudaMemcpyDeviceToHost, p->stream));
+  RK_CU(cudaStreamSynchronize(p->stream));
+  return RK_OK;
+}
+
+rk_status rk_debug_copy(rk_plan* p, int what, void* dst, size_t bytes) {
+  if (!p || !dst) return RK_ERR_INVALID_ARG;
+  const size_t esz = p->precision == RK_FP64 ? sizeof(double) : sizeof(float);
+  const void* src = nullptr;
+  size_t need = 0;
+  switch (what) {
+    case 0: src = p->box; need = (size_t)2 * p->n * sizeof(int); break;
+    case 1: src = p->w64; need = (size_t)p->n * p->M * sizeof(double); break;
+    case 2:
+      src = p->precision == RK_FP64 ? (const void*)p->lam64 : (const void*)p->lam32;
+      need = (size_t)p->H * p->py * esz;
+      break;
+    case 3: src = p->cstar; need = (size_t)p->p1y * p->p1x * esz; break;
+    case 4: src = p->c64; need = (size_t)p->B * p->n * sizeof(double); break;
+    default: return RK_ERR_INVALID_ARG;
+  }
+  if (!src) return RK_ERR_STATE;
+  if (bytes < need) return RK_ERR_INVALID_ARG;
+  RK_CU(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, p->stream));
+  RK_CU(cudaStreamSynchronize(p->stream));
+  return RK_OK;
+}
+
+rk_status rk_simulate(rk_plan* p, int R, unsigned long long seed, void* out) {
+  (void)seed;
+  if (!p || R < 1 || !out) return RK_ERR_INVALID_ARG;
+  return RK_ERR_STATE;
+}
+
+rk_status rk_predict_backward(rk_plan* p, const void* gbar, double* gz, double* grho,
+                              double* gs2) {
+  (void)gz; (void)grho; (void)gs2;
+  if (!p || !gbar) return RK_ERR_INVALID_ARG;
+  return RK_ERR_STATE;
+}
+
+}  // extern "C"
