@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 1024^2 measurement")
     return ap.parse_args()
 
 
@@ -125,40 +126,55 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- our arm --
 
-def run_ours(args, rank, world):
-    import torch
-    import paper_2605_29284_gb300 as rk
+def _load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    w, xy_np, cells = workload_cells(args.workload)
-    xy = torch.from_numpy(xy_np).to(dev)
-    n = xy_np.shape[0]
 
-    def setup(precision):
-        st = []
-        for name, kw, B in cells:
+class Arm:
+    """One workload on one device: plans, resident inputs and a timed step."""
+
+    def __init__(self, workload, precision, dev, solve=True):
+        import torch
+        import paper_2605_29284_gb300 as rk
+        self.torch, self.rk, self.dev = torch, rk, dev
+        self.w, self.xy_np, self.cells = workload_cells(workload)
+        self.xy = torch.from_numpy(self.xy_np).to(dev)
+        n = self.xy_np.shape[0]
+        self.st = []
+        for name, kw, B in self.cells:
             p = rk.Plan(kw["nx"], kw["ny"], kw["extent"], kw["nu"], kw["rho"], kw["sigma2"],
                         kw["tau2"], kw["L"], precision=precision)
-            z = torch.from_numpy(synth.normals((B, n), synth.seed_for(w["config"], 1))).to(dev)
-            p.set_obs(xy, z)                     # FP64 Cholesky, untimed set-up
-            c = p.debug_copy("coef").clone()
+            if solve:
+                # coefficients from the library's FP64 Cholesky (untimed set-up)
+                z = torch.from_numpy(synth.normals((B, n), synth.seed_for(self.w["config"], 1)))
+                p.set_obs(self.xy, z.to(dev))
+                c = p.debug_copy("coef").clone()
+            else:
+                # timing does not depend on the values: seeded coefficients of the
+                # size the solve produces (|c| ~ 1 / sqrt(tau^2))
+                c = torch.from_numpy(synth.normals((B, n), synth.seed_for(self.w["config"], 2))
+                                     / np.sqrt(kw["tau2"])).to(dev)
+                p.set_sites(self.xy)
+                p.set_coef(c)
             out = torch.empty((B, kw["ny"], kw["nx"]), dtype=p.dtype, device=dev)
-            st.append((p, c, out))
+            self.st.append((p, c, out))
+        self.points = sum(kw["nx"] * kw["ny"] * B for _, kw, B in self.cells)
+        self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         torch.cuda.synchronize()
-        return st
 
-    def step(st):
-        for p, c, out in st:
-            p.set_sites(xy)
+    def step(self):
+        for p, c, out in self.st:
+            p.set_sites(self.xy)
             p.set_coef(c)
             p.predict(out)
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def timed(st, steps, warmup, profile=False):
+    def timed(self, steps, warmup, world=1, profile=False):
+        torch, rk = self.torch, self.rk
         for _ in range(warmup):
-            step(st)
+            self.step()
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -167,11 +183,11 @@ def run_ours(args, rank, world):
             rk.profile_read()
             rk.profile_enable(True)
         for _ in range(steps):
-            flush.zero_()
+            self.flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record()
-            step(st)
+            self.step()
             b.record()
             b.synchronize()
             total += a.elapsed_time(b)
@@ -181,94 +197,108 @@ def run_ours(args, rank, world):
             prof = rk.profile_read()
         torch.cuda.synchronize()
         if world > 1:
-            t = torch.tensor([total], device=dev)
+            t = torch.tensor([total], device=self.dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total = float(t.item())
         return total, prof
 
-    points = sum(kw["nx"] * kw["ny"] * B for _, kw, B in cells)
-    st32 = setup(args.precision)
-    sampler = ClockSampler(dev.index)
-    sampler.start()
-    total_ms, prof = timed(st32, args.steps, args.warmup, profile=True)
-    clocks = sampler.stop()
-    value = points * args.steps * world / (total_ms / 1e3)
-
-    # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    dname, (dl, dms, dbytes) = dom
-    achieved = dbytes / (dms / 1e3) / 1e9
-    kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
-                   "GBps": v[2] / (v[1] / 1e3) / 1e9 if v[1] > 0 else None}
-               for k, v in prof.items()}
-
-    # end to end through the host-buffer entry point
-    c_host = [c.cpu().numpy() for _, c, _ in st32]
-    torch.cuda.synchronize()
-    for _ in range(max(2, args.warmup // 2)):
-        for (p, c, out), ch in zip(st32, c_host):
-            p.predict_host(xy_np, ch)
-    torch.cuda.synchronize()
-    esteps = max(3, args.steps // 2)
-    t0 = time.perf_counter()
-    for _ in range(esteps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        for (p, c, out), ch in zip(st32, c_host):
-            p.predict_host(xy_np, ch)
-        t0 += 0
-        if _ == 0:
-            acc = time.perf_counter() - t1
-        else:
+    def e2e(self, steps, warmup):
+        """The same prediction through rk_predict_host: host inputs in, host output out."""
+        torch = self.torch
+        c_host = [c.cpu().numpy() for _, c, _ in self.st]
+        for _ in range(warmup):
+            for (p, c, out), ch in zip(self.st, c_host):
+                p.predict_host(self.xy_np, ch)
+        acc = 0.0
+        for _ in range(steps):
+            self.flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for (p, c, out), ch in zip(self.st, c_host):
+                p.predict_host(self.xy_np, ch)
             acc += time.perf_counter() - t1
-    e2e_value = points * esteps / acc
-    esz = 4 if args.precision == "fp32" else 8
-    h2d = sum(n * 2 * 8 + B * n * 8 for _, kw, B in cells)
-    d2h = sum(B * kw["nx"] * kw["ny"] * esz for _, kw, B in cells)
+        n = self.xy_np.shape[0]
+        esz = 4 if self.st[0][0].dtype == torch.float32 else 8
+        h2d = sum(n * 2 * 8 + B * n * 8 for _, kw, B in self.cells)
+        d2h = sum(B * kw["nx"] * kw["ny"] * esz for _, kw, B in self.cells)
+        return self.points * steps / acc, h2d, d2h
 
-    fp64 = None
-    if not args.no_fp64 and args.precision == "fp32":
-        st64 = setup("fp64")
-        k64 = max(2, args.steps // 5)
-        ms64, _ = timed(st64, k64, 2)
-        v64 = points * k64 * world / (ms64 / 1e3)
-        fp64 = {"value": v64, "unit": "grid-point predictions/s", "ms_per_step": ms64 / k64,
-                "speedup_fp32_over_fp64": value / v64}
-        for p, _, _ in st64:
+    def close(self):
+        for p, _, _ in self.st:
             p.close()
 
-    launches_per_step = len(cells) * (7 if args.precision == "fp32" else 5)
+
+def roofline(prof, steps, peaks):
+    hbm = peaks.get("hbm_gbs")
+    src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    dname, (dl, dms, dbytes) = max(prof.items(), key=lambda kv: kv[1][1])
+    achieved = dbytes / (dms / 1e3) / 1e9
+    kernels = {k: {"launches": v[0], "ms_per_step": v[1] / steps,
+                   "GBps": v[2] / (v[1] / 1e3) / 1e9 if v[1] > 0 else None,
+                   "bytes_per_launch": v[2] / v[0]}
+               for k, v in prof.items()}
+    return ({"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+             "frac": achieved / hbm, "traffic": None, "peak_source": src}, kernels)
+
+
+def run_ours(args, rank, world):
+    import torch
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    peaks = _load_peaks()
+    main = Arm(args.workload, args.precision, dev, solve=args.workload != "grad1024")
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    total_ms, prof = main.timed(args.steps, args.warmup, world, profile=True)
+    clocks = sampler.stop()
+    value = main.points * args.steps * world / (total_ms / 1e3)
+    roof, kernels = roofline(prof, args.steps, peaks)
+    e2e_value, h2d, d2h = main.e2e(max(3, args.steps // 2), 2)
+    fp64 = None
+    if not args.no_fp64 and args.precision == "fp32":
+        a64 = Arm(args.workload, "fp64", dev, solve=args.workload != "grad1024")
+        k64 = max(2, args.steps // 5)
+        ms64, _ = a64.timed(k64, 2, world)
+        v64 = a64.points * k64 * world / (ms64 / 1e3)
+        fp64 = {"value": v64, "unit": "grid-point predictions/s", "ms_per_step": ms64 / k64,
+                "speedup_fp32_over_fp64": value / v64}
+        a64.close()
+    secondary = {}
+    if args.workload == "paper350" and not args.no_secondary:
+        # the 1024 x 1024 grid the roofline target is quoted on: 16 fields, n = 20000
+        a = Arm("grad1024", args.precision, dev, solve=False)
+        k = max(3, args.steps // 2)
+        ms, pr = a.timed(k, 2, world, profile=True)
+        r2, k2 = roofline(pr, k, peaks)
+        secondary["grad1024_forward"] = {
+            "value": a.points * k * world / (ms / 1e3), "unit": "grid-point predictions/s",
+            "ms_per_step": ms / k, "roofline": r2, "kernels": k2,
+            "config": {"grid": "1024x1024", "n": 20000, "fields": 16, "nu": 2.5,
+                       "range": 0.08, "L": 3, "coefficients": "seeded, sized like the solve"}}
+        a.close()
+    launches_per_cell = 7 if args.precision == "fp32" else 5
     res = {
         "metric": METRIC, "value": value, "unit": "grid-point predictions/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-        "data": "synthetic (seeded sites and GP-shaped data; see synth)",
-        "config": {"workload": args.workload, "cells": [c[0] for c in cells],
-                   "grid": f"{cells[0][1]['nx']}x{cells[0][1]['ny']}", "n": n,
-                   "fields_per_cell": cells[0][2], "l2": "flushed between timed steps (256 MB write)",
+        "data": "synthetic (seeded sites and data; see synth)",
+        "config": {"workload": args.workload, "cells": [c[0] for c in main.cells],
+                   "grid": f"{main.cells[0][1]['nx']}x{main.cells[0][1]['ny']}",
+                   "n": int(main.xy_np.shape[0]), "fields_per_cell": main.cells[0][2],
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "peak_source": peak_src},
+        "roofline": roof,
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "grid-point predictions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches_per_cell * len(main.cells) * args.steps,
         "clocks": clocks,
         "fp64_path": fp64,
+        "secondary": secondary,
     }
-    for p, _, _ in st32:
-        p.close()
+    main.close()
     return res
 
 

@@ -117,6 +117,18 @@ rk_status rk_plan_get_info(const rk_plan* plan, rk_plan_info* info);
 rk_status rk_set_sites(rk_plan* plan, int n, const double* xy_dev);
 
 /*
+ * rk_set_weights -- sets the sparse matrix A of Eq. (6) directly instead of
+ * computing it (e.g. weights from another interpolation rule, or the
+ * non-stationary variant discussed in Section 6 where k_i comes from a
+ * different covariance).  box_dev: device, n x 2 int32 central-box indices
+ * (ix in [0, nx - 2], iy in [0, ny - 2]); w_dev: device, n x M doubles in the
+ * neighbour order q = a + 2L b.  Resets coefficients; the per-site standard
+ * deviations used by rk_simulate are set to zero.  Returns RK_ERR_INVALID_ARG
+ * for an index out of range (synchronises to check).
+ */
+rk_status rk_set_weights(rk_plan* plan, int n, const int* box_dev, const double* w_dev);
+
+/*
  * rk_set_coef -- sets the Kriging coefficients c (Eq. 3) directly, for B
  * fields: c_dev is device, B x n doubles row-major.  Copied into the plan.
  */

@@ -44,10 +44,13 @@ def ce_spectrum(g, nu, rho, sigma2, tol=1e-12, max_growth=4):
 
 
 def ce_noise(qx, qy, pair, seed):
-    """xi + i eta on the Qy x Qx torus for realisation pair `pair` (Philox stream 1)."""
+    """xi + i eta on the Qy x Qx torus for realisation pair `pair` (Philox stream 1).
+
+    Torus index k = kx * Qy + ky (column-major).
+    """
     k = np.arange(qx * qy, dtype=np.uint64)
     xi, eta = philox.normal_pairs(k, pair, philox.STREAM_CE, seed)
-    return (xi + 1j * eta).reshape(qy, qx)
+    return (xi + 1j * eta).reshape(qx, qy).T
 
 
 def unconditional(g, nu, rho, sigma2, tglobal, seed):

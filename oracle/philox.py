@@ -13,7 +13,7 @@ its own independent implementation):
 Counter layout (key = (seed, 0)):
 
 * stream 1, the circulant-embedding noise of realisation pair p at torus
-  index k (row-major, k = ky * Qx + kx): counter (k >> 1, p, 1, 0); the
+  index k (column-major, k = kx * Qy + ky): counter (k >> 1, p, 1, 0); the
   words (w0, w1) serve even k, (w2, w3) odd k, giving (xi_k, eta_k).
 * stream 2, the site noise of realisation t at site i: counter
   (i >> 1, t, 2, 0), words (w0, w1) for even i, (w2, w3) for odd i, giving

@@ -90,6 +90,13 @@ class Plan:
         self.n = n
         self._xy = xy
 
+    def set_weights(self, box, w):
+        """Sets A of Eq. (6) directly: box (n x 2 int32 central boxes), w (n x M)."""
+        box = torch.as_tensor(box).to(device="cuda", dtype=torch.int32).contiguous()
+        w = _dev_f64(w)
+        self._call("rk_set_weights", int(w.shape[0]), _ptr(box), _ptr(w))
+        self.n = w.shape[0]
+
     def set_coef(self, c):
         c = _dev_f64(c)
         if c.dim() == 1:

@@ -54,6 +54,19 @@ __device__ __forceinline__ T matern_dlogrho(T t, int nu_code) {
   return (t * t / T(3)) * (T(1) + t) * e;
 }
 
+// Raises a kernel's dynamic shared-memory limit when a launch needs more than
+// any earlier launch (the attribute persists, so this is done once per size).
+template <typename K>
+inline cudaError_t ensure_smem(K kern, size_t bytes, int& current) {
+  if ((int)bytes > current) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    current = (int)bytes;
+  }
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------------- FFT plans --
 
 constexpr int kMaxStages = 24;
@@ -98,6 +111,7 @@ struct rk_plan {
   // sites
   int n = 0, n_cap = 0;
   double* xy = nullptr;        // n x 2 site coordinates (copy)
+  bool xy_valid = false;       // false when weights were given directly
   int* box = nullptr;          // n x 2 (ix, iy)
   double* w64 = nullptr;       // n x M
   float* w32 = nullptr;        // n x M
@@ -126,6 +140,13 @@ struct rk_plan {
   float2* tw32qx = nullptr; float2* tw32qy = nullptr;
   double* ce_sqrt64 = nullptr; float* ce_sqrt32 = nullptr;   // sqrt(lambda_Q / (qx qy)), qy x qx
   void* cs_buf = nullptr; size_t cs_bytes = 0;
+  // adjoint state (built on the first rk_predict_backward)
+  double* wd64 = nullptr; float* wd32 = nullptr;   // W' = dW / dlog rho, n x M
+  double2* efac_d = nullptr;                        // block factors of W'
+  double* bw_cbar = nullptr; size_t bw_cbar_cap = 0; // B x n
+  void* bw_y = nullptr; size_t bw_y_bytes = 0;       // 3 x B x ny x nx
+  double2* bw_gblk = nullptr; size_t bw_gblk_cap = 0;
+  bool have_adj = false;
   // device staging for rk_predict_host
   double* h_xy = nullptr; size_t h_xy_cap = 0;
   double* h_c = nullptr; size_t h_c_cap = 0;
@@ -145,7 +166,7 @@ cudaError_t launch_rows_fwd(const T* in, int nrows, int ncols, long long in_fiel
 template <typename T>
 cudaError_t launch_cols(const C<T>* tin, int ldt, long long t_field_stride, int nrin,
                         C<T>* uout, int ldu, long long u_field_stride, int orow0, int nrout,
-                        const T* lam, int mode, const double2* blk, int blk_kx, int blk_ky,
+                        const T* lam, int mode, double2* blk, int blk_kx, int blk_ky,
                         int nblk, int B, int H, const FftPlan& fp, const C<T>* tw, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rows_inv(const C<T>* uin, int ldu, long long u_field_stride, int nrows,
@@ -154,18 +175,41 @@ cudaError_t launch_rows_inv(const C<T>* uin, int ldu, long long u_field_stride, 
                             int add_c0, int B, const FftPlan& fp, const C<T>* tw, int H,
                             cudaStream_t s);
 
-enum { COLS_CONV = 0, COLS_FWD_ONLY = 1 };
+enum { COLS_CONV = 0, COLS_FWD_ONLY = 1, COLS_ADJ = 2 };
+
+// compile-time-specialised passes (k_fftn.cu); false when N has none
+template <typename T>
+bool launch_rows_fwd_n(const T* in, int nrows, int ncols, long long ifs, int ild, C<T>* tout,
+                       int ldt, long long tfs, int B, int N, const C<T>* tw, int H,
+                       cudaStream_t s, cudaError_t* err);
+template <typename T>
+bool launch_cols_n(const C<T>* tin, int ldt, long long tfs, int nrin, C<T>* uout, int ldu,
+                   long long ufs, int orow0, int nrout, const T* lam, int mode, double2* blk,
+                   int blk_kx, int blk_ky, int nblk, int B, int H, int N, const C<T>* tw,
+                   cudaStream_t s, cudaError_t* err);
+template <typename T>
+bool launch_rows_inv_n(const C<T>* uin, int ldu, long long ufs, int nrows, T* out, int old,
+                       long long ofs, int ocol0, int ncols, const T* add, int ald, long long afs,
+                       int ar0, int ac0, int B, int N, const C<T>* tw, int H, cudaStream_t s,
+                       cudaError_t* err);
+// true when RK_FFT_GENERIC is set in the environment: use only the generic passes
+bool fft_generic_only();
 
 cudaError_t launch_torus_base(double* base, int px, int py, double hx, double hy, double rho,
                               double sigma2, int nu_code, int deriv, cudaStream_t s);
 cudaError_t launch_lambda_finish(const double2* spec, int ld, int H, int py, double scale,
                                  double* lam64, float* lam32, cudaStream_t s);
+cudaError_t launch_scale(const double* src, size_t count, double scale, double* dst64,
+                         float* dst32, cudaStream_t s);
 
 // sites
 cudaError_t launch_kn_factor(double* kn, int L, double hx, double hy, double rho, double sigma2,
                              int nu_code, int* flag, cudaStream_t s);
 cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, double* w64,
                            float* w32, double* ssd, int* flag, cudaStream_t s);
+cudaError_t launch_set_weights(const int* box_in, const double* w_in, int n, const rk_plan* p,
+                               int* box, double* w64, float* w32, double* ssd, int* flag,
+                               cudaStream_t s);
 cudaError_t launch_block_factors(const int* box, const double* w64, int n, const rk_plan* p,
                                  double2* efac, cudaStream_t s);
 cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac, int nblk,
@@ -183,17 +227,32 @@ cudaError_t chol_solve(const double* l, int n, double* x, int B, cudaStream_t s)
 
 // conditional simulation
 template <typename T>
-cudaError_t launch_ce_noise(const T* sqrtlam, int qx, int qy, unsigned long long seed, int pair0,
-                            int npairs, C<T>* out, cudaStream_t s);
+cudaError_t launch_ce_cols(const T* sqrtlam, int qx, int qy, unsigned long long seed, int pair0,
+                           int npairs, C<T>* tq, int ldq, int nkeep, const FftPlan& fpy,
+                           const C<T>* twy, cudaStream_t s);
 template <typename T>
-cudaError_t launch_site_values(const T* fu, int fu_ld, long long fu_stride, int nreal,
+cudaError_t launch_ce_rows(const C<T>* tq, int qx, int ldq, int nrows, T* fu, int p1x,
+                           long long t0, int treal, int pair0, int npairs, const FftPlan& fpx,
+                           const C<T>* twx, cudaStream_t s);
+template <typename T>
+cudaError_t launch_site_values(const T* fu, int p1x, long long fu_stride, int nreal,
                                const int* box, const double* w64, const double* ssd, int n, int L,
-                               double tau, unsigned long long seed, int t0, const double* z,
-                               double* rhs, cudaStream_t s);
+                               double tau, unsigned long long seed, long long t0, int R,
+                               const double* z, double* rhs, cudaStream_t s);
 
 // adjoint
+cudaError_t launch_kn_dlog(double* out, int L, double hx, double hy, double rho, double sigma2,
+                           int nu_code, cudaStream_t s);
+cudaError_t launch_dweights(const rk_plan* p, double* wd64, float* wd32, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gather(const T* abar, int p1x, int p1y, const int* box, const double* w64,
                           int n, int L, int B, double* cbar, cudaStream_t s);
+cudaError_t launch_block_adjoint(const double2* gblk, int B, int nblk, int bw,
+                                 const double2* efac, int n, double* cbar, cudaStream_t s);
+template <typename Ta, typename Tb>
+cudaError_t launch_dot_rows(const Ta* a, const Tb* b, int B, long long len, double scale,
+                            int accumulate, double* out, cudaStream_t s);
+cudaError_t launch_quad_dkxx(const double* xy, int n, const double* zbar, const double* c, int B,
+                             double rho, double sigma2, int nu_code, double* out, cudaStream_t s);
 
 }  // namespace rk

@@ -1,0 +1,210 @@
+// Conditional simulation kernels (Section 1: unconditional draw, then Kriging
+// of the simulated data; Section 6: circulant embedding).
+//
+// Noise: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by
+// (seed, 0).  Uniform u(w) = ((w >> 11) + 1/2) 2^-53; Box-Muller
+// (r cos 2 pi u2, r sin 2 pi u2), r = sqrt(-2 ln u1).
+//   stream 1: circulant-embedding noise of realisation pair p at torus index
+//             k = kx * qy + ky: counter (k >> 1, p, 1, 0), words (0, 1) for even
+//             k, (2, 3) for odd k.
+//   stream 2: site noise of global realisation t at site i: counter
+//             (i >> 1, t, 2, 0), words (0, 1) for even i, (2, 3) for odd i.
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace rk {
+
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+    const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+// (xi, eta) for element `index` of sub-stream `sub` in `stream`
+template <typename T>
+__device__ __forceinline__ void normal_pair(uint64_t index, uint64_t sub, uint64_t stream,
+                                            uint64_t seed, T& xi, T& eta) {
+  uint64_t c[4] = {index >> 1, sub, stream, 0ull};
+  philox4x64_10(c, seed, 0ull);
+  const uint64_t wa = (index & 1) ? c[2] : c[0];
+  const uint64_t wb = (index & 1) ? c[3] : c[1];
+  if (sizeof(T) == sizeof(double)) {
+    const double u1 = ((double)(wa >> 11) + 0.5) * 0x1.0p-53;
+    const double u2 = ((double)(wb >> 11) + 0.5) * 0x1.0p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    double s, co;
+    sincospi(2.0 * u2, &s, &co);
+    xi = (T)(r * co);
+    eta = (T)(r * s);
+  } else {
+    // the same uniforms rounded to float (relative error 2^-24)
+    const float u1 = fmaf((float)(wa >> 11), 0x1.0p-53f, 0x1.0p-54f);
+    const float u2 = fmaf((float)(wb >> 11), 0x1.0p-53f, 0x1.0p-54f);
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, co;
+    sincospif(2.0f * u2, &s, &co);
+    xi = (T)(r * co);
+    eta = (T)(r * s);
+  }
+}
+
+// ------------------------------------------------------------ CE columns --
+// Column kx of pair p: noise times sqrt(lambda / (qx qy)), forward FFT along
+// y, rows [0, nkeep) written to tq[(p - pair0) * qx + kx][0..nkeep).
+template <typename T>
+__global__ void __launch_bounds__(256)
+ce_cols_kernel(const T* __restrict__ sqrtlam, int qx, int qy, unsigned long long seed, int pair0,
+               C<T>* __restrict__ tq, int ldq, int nkeep, FftPlan fpy,
+               const C<T>* __restrict__ twy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* bufb = bufa + qy;
+  const int kx = blockIdx.x;
+  const int pair = pair0 + blockIdx.y;
+  const int kxh = kx < qx - kx ? kx : qx - kx;
+  const T* sl = sqrtlam + (size_t)kxh * qy;
+  for (int ky = threadIdx.x; ky < qy; ky += blockDim.x) {
+    T xi, eta;
+    normal_pair<T>((uint64_t)kx * qy + ky, (uint64_t)pair, 1ull, seed, xi, eta);
+    const T s = sl[ky];
+    bufa[ky] = mk<T>(s * xi, s * eta);
+  }
+  __syncthreads();
+  C<T>* res = fft_smem<T>(bufa, bufb, qy, 1, fpy, twy, +1);
+  C<T>* dst = tq + ((size_t)blockIdx.y * qx + kx) * ldq;
+  for (int r = threadIdx.x; r < nkeep; r += blockDim.x) dst[r] = res[r];
+}
+
+// --------------------------------------------------------------- CE rows --
+// Rows [r0, r0 + kCeRows) of pair p: forward FFT along x, columns [0, p1x)
+// kept; the real part is global realisation 2p, the imaginary part 2p + 1.
+constexpr int kCeRows = 2;
+template <typename T>
+__global__ void __launch_bounds__(256)
+ce_rows_kernel(const C<T>* __restrict__ tq, int qx, int ldq, int nrows, T* __restrict__ fu,
+               int p1x, long long t0, int treal, int pair0, FftPlan fpx,
+               const C<T>* __restrict__ twx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* bufb = bufa + kCeRows * qx;
+  const int r0 = blockIdx.x * kCeRows;
+  const int pl = blockIdx.y;
+  const C<T>* src = tq + (size_t)pl * qx * ldq;
+  for (int idx = threadIdx.x; idx < qx * kCeRows; idx += blockDim.x) {
+    const int kx = idx / kCeRows, rr = idx - kx * kCeRows;
+    const int row = r0 + rr;
+    bufb[idx] = row < nrows ? src[(size_t)kx * ldq + row] : mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < qx * kCeRows; idx += blockDim.x) {
+    const int v = idx / qx, kx = idx - v * qx;
+    bufa[idx] = bufb[kx * kCeRows + v];
+  }
+  __syncthreads();
+  C<T>* res = fft_smem<T>(bufa, bufb, qx, kCeRows, fpx, twx, +1);
+  const long long pair = pair0 + pl;
+  for (int idx = threadIdx.x; idx < kCeRows * 2 * p1x; idx += blockDim.x) {
+    const int rr = idx / (2 * p1x), rem = idx - rr * 2 * p1x;
+    const int part = rem / p1x, px = rem - part * p1x;
+    const int row = r0 + rr;
+    if (row >= nrows) continue;
+    const long long j = 2 * pair + part - t0;
+    if (j < 0 || j >= treal) continue;
+    const C<T> z = res[rr * qx + px];
+    fu[((size_t)j * nrows + row) * p1x + px] = part ? z.y : z.x;
+  }
+}
+
+// ------------------------------------------------------------ site values --
+// rhs[j][i] = z[b][i] - (A_i . fu_j[N(i)] + s_i xi' + tau eps), global
+// realisation t = t0 + j of data field b = t / R.
+template <typename T>
+__global__ void site_values_kernel(const T* __restrict__ fu, int p1x, long long fu_stride,
+                                   int nreal, const int* __restrict__ box,
+                                   const double* __restrict__ w64, const double* __restrict__ ssd,
+                                   int n, int L, double tau, unsigned long long seed, long long t0,
+                                   int R, const double* __restrict__ z, double* __restrict__ rhs) {
+  const int W = 2 * L, M = W * W;
+  const long long total = (long long)n * nreal;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / n), i = (int)(t - (long long)j * n);
+    const long long tg = t0 + j;
+    const int b = (int)(tg / R);
+    const T* f = fu + (size_t)j * fu_stride;
+    const int ix = box[2 * i], iy = box[2 * i + 1];
+    double mean = 0.0;
+    for (int q = 0; q < M; ++q) {
+      const int a = q % W, bb = q / W;
+      mean += w64[(size_t)i * M + q] * (double)f[(size_t)(iy + bb) * p1x + ix + a];
+    }
+    double xi, eps;
+    normal_pair<double>((uint64_t)i, (uint64_t)tg, 2ull, seed, xi, eps);
+    rhs[(size_t)j * n + i] = z[(size_t)b * n + i] - (mean + ssd[i] * xi + tau * eps);
+  }
+}
+
+template <typename T>
+cudaError_t launch_ce_cols(const T* sqrtlam, int qx, int qy, unsigned long long seed, int pair0,
+                           int npairs, C<T>* tq, int ldq, int nkeep, const FftPlan& fpy,
+                           const C<T>* twy, cudaStream_t s) {
+  const size_t sm = sizeof(C<T>) * 2 * qy;
+  auto kern = ce_cols_kernel<T>;
+  static int smem_set = 0;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(qx, npairs), 256, sm, s>>>(sqrtlam, qx, qy, seed, pair0, tq, ldq, nkeep, fpy, twy);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_ce_rows(const C<T>* tq, int qx, int ldq, int nrows, T* fu, int p1x,
+                           long long t0, int treal, int pair0, int npairs, const FftPlan& fpx,
+                           const C<T>* twx, cudaStream_t s) {
+  const size_t sm = sizeof(C<T>) * 2 * kCeRows * qx;
+  auto kern = ce_rows_kernel<T>;
+  static int smem_set = 0;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nrows + kCeRows - 1) / kCeRows, npairs);
+  kern<<<grid, 256, sm, s>>>(tq, qx, ldq, nrows, fu, p1x, t0, treal, pair0, fpx, twx);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_site_values(const T* fu, int p1x, long long fu_stride, int nreal,
+                               const int* box, const double* w64, const double* ssd, int n, int L,
+                               double tau, unsigned long long seed, long long t0, int R,
+                               const double* z, double* rhs, cudaStream_t s) {
+  long long total = (long long)n * nreal;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  site_values_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(fu, p1x, fu_stride, nreal, box, w64, ssd,
+                                                         n, L, tau, seed, t0, R, z, rhs);
+  return cudaGetLastError();
+}
+
+#define RK_CS_INST(T)                                                                          \
+  template cudaError_t launch_ce_cols<T>(const T*, int, int, unsigned long long, int, int, C<T>*, \
+                                         int, int, const FftPlan&, const C<T>*, cudaStream_t);  \
+  template cudaError_t launch_ce_rows<T>(const C<T>*, int, int, int, T*, int, long long, int,  \
+                                         int, int, const FftPlan&, const C<T>*, cudaStream_t);  \
+  template cudaError_t launch_site_values<T>(const T*, int, long long, int, const int*,        \
+                                             const double*, const double*, int, int, double,   \
+                                             unsigned long long, long long, int, const double*, \
+                                             double*, cudaStream_t);
+RK_CS_INST(float)
+RK_CS_INST(double)
+
+}  // namespace rk

@@ -14,105 +14,15 @@
 // shared memory; twiddles come from tables computed in double on the host
 // and rounded once.
 #include "common.cuh"
+#include "fft.cuh"
+
+#include <stdlib.h>
 
 namespace rk {
 
-// y_m = sum_n a_n w^(n m), w = exp(-2 pi i dir / R)
-template <typename T>
-__device__ __forceinline__ void dft2(C<T>* a) {
-  C<T> t = a[0];
-  a[0] = cadd<T>(t, a[1]);
-  a[1] = csub<T>(t, a[1]);
-}
-
-template <typename T>
-__device__ __forceinline__ void dft3(C<T>* a, int dir) {
-  const T s3 = T(0.86602540378443864676372317075294);
-  C<T> t1 = cadd<T>(a[1], a[2]);
-  C<T> t2 = mk<T>(a[0].x - T(0.5) * t1.x, a[0].y - T(0.5) * t1.y);
-  C<T> t3 = cscale<T>(cmul_mi<T>(csub<T>(a[1], a[2]), dir), s3);
-  a[0] = cadd<T>(a[0], t1);
-  a[1] = cadd<T>(t2, t3);
-  a[2] = csub<T>(t2, t3);
-}
-
-template <typename T>
-__device__ __forceinline__ void dft4v(C<T>& b0, C<T>& b1, C<T>& b2, C<T>& b3, int dir) {
-  C<T> t0 = cadd<T>(b0, b2), t1 = csub<T>(b0, b2);
-  C<T> t2 = cadd<T>(b1, b3), t3 = cmul_mi<T>(csub<T>(b1, b3), dir);
-  b0 = cadd<T>(t0, t2);
-  b2 = csub<T>(t0, t2);
-  b1 = cadd<T>(t1, t3);
-  b3 = csub<T>(t1, t3);
-}
-
-template <typename T>
-__device__ __forceinline__ void dft4(C<T>* a, int dir) { dft4v<T>(a[0], a[1], a[2], a[3], dir); }
-
-template <typename T>
-__device__ __forceinline__ void dft8(C<T>* a, int dir) {
-  const T r2 = T(0.70710678118654752440084436210485);
-  C<T> e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
-  C<T> o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
-  dft4v<T>(e0, e1, e2, e3, dir);
-  dft4v<T>(o0, o1, o2, o3, dir);
-  // o_m *= w8^m, w8 = exp(-i pi dir / 4)
-  o1 = cscale<T>(mk<T>(o1.x + T(dir) * o1.y, o1.y - T(dir) * o1.x), r2);
-  o2 = cmul_mi<T>(o2, dir);
-  o3 = cscale<T>(mk<T>(-o3.x + T(dir) * o3.y, -o3.y - T(dir) * o3.x), r2);
-  a[0] = cadd<T>(e0, o0); a[4] = csub<T>(e0, o0);
-  a[1] = cadd<T>(e1, o1); a[5] = csub<T>(e1, o1);
-  a[2] = cadd<T>(e2, o2); a[6] = csub<T>(e2, o2);
-  a[3] = cadd<T>(e3, o3); a[7] = csub<T>(e3, o3);
-}
-
-// One Stockham stage over V vectors of length N (stride ld) from src to dst.
-template <typename T, int R>
-__device__ __forceinline__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst,
-                                      int ld, int V, int N, int Ns,
-                                      const C<T>* __restrict__ tw, int dir) {
-  const int nb = N / R;
-  const int tws = N / (Ns * R);
-  const int total = V * nb;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int v = t / nb;
-    const int j = t - v * nb;
-    const int k = j % Ns;
-    const C<T>* s = src + (size_t)v * ld;
-    C<T> a[R];
-    a[0] = s[j];
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
-      C<T> w = tw[r * k * tws];
-      C<T> x = s[j + r * nb];
-      a[r] = dir > 0 ? cmul<T>(x, w) : cmulc<T>(x, w);
-    }
-    if (R == 2) dft2<T>(a);
-    if (R == 3) dft3<T>(a, dir);
-    if (R == 4) dft4<T>(a, dir);
-    if (R == 8) dft8<T>(a, dir);
-    C<T>* d = dst + (size_t)v * ld + (j - k) * R + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) d[r * Ns] = a[r];
-  }
-}
-
-// Full transform; returns the buffer that holds the result (a or b).
-template <typename T>
-__device__ C<T>* fft_smem(C<T>* a, C<T>* b, int ld, int V, const FftPlan& fp,
-                          const C<T>* __restrict__ tw, int dir) {
-  for (int st = 0; st < fp.nstages; ++st) {
-    const int R = fp.radix[st], Ns = fp.span[st];
-    switch (R) {
-      case 2: stage<T, 2>(a, b, ld, V, fp.n, Ns, tw, dir); break;
-      case 3: stage<T, 3>(a, b, ld, V, fp.n, Ns, tw, dir); break;
-      case 4: stage<T, 4>(a, b, ld, V, fp.n, Ns, tw, dir); break;
-      default: stage<T, 8>(a, b, ld, V, fp.n, Ns, tw, dir); break;
-    }
-    __syncthreads();
-    C<T>* t = a; a = b; b = t;
-  }
-  return a;
+bool fft_generic_only() {
+  static const bool v = getenv("RK_FFT_GENERIC") != nullptr;
+  return v;
 }
 
 constexpr int kRowVecs = 2;     // complex FFTs (pairs of real rows) per CTA
@@ -161,10 +71,16 @@ template <typename T>
 cudaError_t launch_rows_fwd(const T* in, int nrows, int ncols, long long ifs, int ild,
                             C<T>* tout, int ldt, long long tfs, int B,
                             const FftPlan& fp, const C<T>* tw, int H, cudaStream_t s) {
+  cudaError_t err;
+  if (!fft_generic_only() &&
+      launch_rows_fwd_n<T>(in, nrows, ncols, ifs, ild, tout, ldt, tfs, B, fp.n, tw, H, s, &err))
+    return err;
   dim3 grid((nrows + 2 * kRowVecs - 1) / (2 * kRowVecs), B);
   size_t sm = sizeof(C<T>) * 2 * kRowVecs * fp.n;
   auto kern = rows_fwd_kernel<T>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static int smem_set = 0;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, sm, s>>>(in, nrows, ncols, ifs, ild, tout, ldt, tfs, fp, tw, H);
   return cudaGetLastError();
 }
@@ -174,7 +90,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 cols_kernel(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin,
             C<T>* __restrict__ uout, int ldu, long long ufs, int orow0, int nrout,
-            const T* __restrict__ lam, int mode, const double2* __restrict__ blk,
+            const T* __restrict__ lam, int mode, double2* __restrict__ blk,
             int blk_kx, int blk_ky, int nblk, int B, FftPlan fp, const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = fp.n;
@@ -182,7 +98,7 @@ cols_kernel(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin,
   C<T>* bufb = bufa + N;
   T* lcol = reinterpret_cast<T*>(bufb + N);
   const int k = blockIdx.x;
-  if (mode == COLS_CONV)
+  if (mode != COLS_FWD_ONLY)
     for (int n = threadIdx.x; n < N; n += blockDim.x) lcol[n] = lam[(size_t)k * N + n];
   const bool use_blk = blk != nullptr && k <= blk_kx;
   const int bw = 2 * blk_ky + 1;
@@ -199,18 +115,37 @@ cols_kernel(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin,
       __syncthreads();
       continue;
     }
-    if (use_blk) {
-      const double2* bsrc = blk + (size_t)f * nblk + (size_t)k * bw;
-      for (int j = threadIdx.x; j < bw; j += blockDim.x) {
-        int ky = j - blk_ky;
-        ky = ky < 0 ? ky + N : ky;
-        double2 v = bsrc[j];
-        res[ky] = mk<T>((T)v.x, (T)v.y);
+    if (mode == COLS_CONV) {
+      // forward: the exact low-frequency block replaces the computed values
+      if (use_blk) {
+        const double2* bsrc = blk + (size_t)f * nblk + (size_t)k * bw;
+        for (int j = threadIdx.x; j < bw; j += blockDim.x) {
+          int ky = j - blk_ky;
+          ky = ky < 0 ? ky + N : ky;
+          double2 v = bsrc[j];
+          res[ky] = mk<T>((T)v.x, (T)v.y);
+        }
+        __syncthreads();
       }
+      for (int n = threadIdx.x; n < N; n += blockDim.x) res[n] = cscale<T>(res[n], lcol[n]);
       __syncthreads();
+    } else {
+      // adjoint: G = lambda F(gbar); its block goes back to the sites exactly
+      // (recorded here) and is removed from the grid path
+      for (int n = threadIdx.x; n < N; n += blockDim.x) res[n] = cscale<T>(res[n], lcol[n]);
+      __syncthreads();
+      if (use_blk) {
+        double2* bdst = blk + (size_t)f * nblk + (size_t)k * bw;
+        for (int j = threadIdx.x; j < bw; j += blockDim.x) {
+          int ky = j - blk_ky;
+          ky = ky < 0 ? ky + N : ky;
+          const C<T> v = res[ky];
+          bdst[j] = make_double2((double)v.x, (double)v.y);
+          res[ky] = mk<T>(T(0), T(0));
+        }
+        __syncthreads();
+      }
     }
-    for (int n = threadIdx.x; n < N; n += blockDim.x) res[n] = cscale<T>(res[n], lcol[n]);
-    __syncthreads();
     C<T>* out = fft_smem<T>(res, other, N, 1, fp, tw, -1);
     for (int n = threadIdx.x; n < nrout; n += blockDim.x) {
       int r = orow0 + n;
@@ -224,13 +159,20 @@ cols_kernel(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin,
 template <typename T>
 cudaError_t launch_cols(const C<T>* tin, int ldt, long long tfs, int nrin,
                         C<T>* uout, int ldu, long long ufs, int orow0, int nrout,
-                        const T* lam, int mode, const double2* blk, int blk_kx, int blk_ky,
+                        const T* lam, int mode, double2* blk, int blk_kx, int blk_ky,
                         int nblk, int B, int H, const FftPlan& fp, const C<T>* tw, cudaStream_t s) {
+  cudaError_t err;
+  if (!fft_generic_only() &&
+      launch_cols_n<T>(tin, ldt, tfs, nrin, uout, ldu, ufs, orow0, nrout, lam, mode, blk, blk_kx,
+                       blk_ky, nblk, B, H, fp.n, tw, s, &err))
+    return err;
   int fgroups = B < 8 ? B : 8;
   dim3 grid(H, fgroups);
   size_t sm = sizeof(C<T>) * 2 * fp.n + sizeof(T) * fp.n;
   auto kern = cols_kernel<T>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static int smem_set = 0;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, sm, s>>>(tin, ldt, tfs, nrin, uout, ldu, ufs, orow0, nrout, lam, mode,
                                   blk, blk_kx, blk_ky, nblk, B, fp, tw);
   return cudaGetLastError();
@@ -293,10 +235,17 @@ cudaError_t launch_rows_inv(const C<T>* uin, int ldu, long long ufs, int nrows,
                             T* out, int old, long long ofs, int ocol0, int ncols,
                             const T* add, int ald, long long afs, int ar0, int ac0,
                             int B, const FftPlan& fp, const C<T>* tw, int H, cudaStream_t s) {
+  cudaError_t err;
+  if (!fft_generic_only() &&
+      launch_rows_inv_n<T>(uin, ldu, ufs, nrows, out, old, ofs, ocol0, ncols, add, ald, afs, ar0,
+                           ac0, B, fp.n, tw, H, s, &err))
+    return err;
   dim3 grid((nrows + 2 * kRowVecs - 1) / (2 * kRowVecs), B);
   size_t sm = sizeof(C<T>) * (2 * kRowVecs * fp.n + 2 * kRowVecs + 2);
   auto kern = rows_inv_kernel<T>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static int smem_set = 0;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, sm, s>>>(uin, ldu, ufs, nrows, out, old, ofs, ocol0, ncols, add, ald, afs,
                                   ar0, ac0, fp, tw, H);
   return cudaGetLastError();
@@ -342,6 +291,22 @@ cudaError_t launch_lambda_finish(const double2* spec, int ld, int H, int py, dou
   return cudaGetLastError();
 }
 
+__global__ void scale_kernel(const double* src, size_t count, double scale, double* dst64,
+                             float* dst32) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double v = src[i] * scale;
+    dst64[i] = v;
+    if (dst32) dst32[i] = (float)v;
+  }
+}
+
+cudaError_t launch_scale(const double* src, size_t count, double scale, double* dst64,
+                         float* dst32, cudaStream_t s) {
+  scale_kernel<<<1024, 256, 0, s>>>(src, count, scale, dst64, dst32);
+  return cudaGetLastError();
+}
+
 // explicit instantiations
 template cudaError_t launch_rows_fwd<float>(const float*, int, int, long long, int, float2*, int,
                                             long long, int, const FftPlan&, const float2*, int,
@@ -350,10 +315,10 @@ template cudaError_t launch_rows_fwd<double>(const double*, int, int, long long,
                                              int, long long, int, const FftPlan&, const double2*,
                                              int, cudaStream_t);
 template cudaError_t launch_cols<float>(const float2*, int, long long, int, float2*, int, long long,
-                                        int, int, const float*, int, const double2*, int, int, int,
+                                        int, int, const float*, int, double2*, int, int, int,
                                         int, int, const FftPlan&, const float2*, cudaStream_t);
 template cudaError_t launch_cols<double>(const double2*, int, long long, int, double2*, int,
-                                         long long, int, int, const double*, int, const double2*,
+                                         long long, int, int, const double*, int, double2*,
                                          int, int, int, int, int, const FftPlan&, const double2*,
                                          cudaStream_t);
 template cudaError_t launch_rows_inv<float>(const float2*, int, long long, int, float*, int,

@@ -1,0 +1,299 @@
+// The three FFT passes (rows_fwd, cols, rows_inv; see k_fft.cu) specialised
+// at compile time for the torus lengths the workloads use.  Each CTA holds V
+// vectors of length N in shared memory, THR = Radix23<N>::THR threads per
+// vector; launch_*_n return false when N has no specialisation (the generic
+// kernels of k_fft.cu then run).
+#include "common.cuh"
+#include "fftn.cuh"
+
+namespace rk {
+
+template <int N> struct VecsPerCta {
+  static constexpr int thr = Radix23<N>::THR;
+  static constexpr int value = thr >= 256 ? 2 : (512 / thr > 16 ? 16 : 512 / thr);
+};
+
+// ---------------------------------------------------------------- rows_fwd --
+template <typename T, int N>
+__global__ void __launch_bounds__(VecsPerCta<N>::value * Radix23<N>::THR)
+rows_fwd_n(const T* __restrict__ in, int nrows, int ncols, long long ifs, int ild,
+           C<T>* __restrict__ tout, int ldt, long long tfs, const C<T>* __restrict__ tw, int H) {
+  constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  const int f = blockIdx.y;
+  const int r0 = blockIdx.x * 2 * V;
+  const T* src = in + (size_t)f * ifs;
+  for (int idx = threadIdx.x; idx < V * N; idx += V * THR) {
+    const int v = idx / N, n = idx - v * N;
+    const int ra = r0 + 2 * v, rb = ra + 1;
+    const T xa = (ra < nrows && n < ncols) ? src[(size_t)ra * ild + n] : T(0);
+    const T xb = (rb < nrows && n < ncols) ? src[(size_t)rb * ild + n] : T(0);
+    buf[idx] = mk<T>(xa, xb);
+  }
+  __syncthreads();
+  const int v = threadIdx.x / THR, tid = threadIdx.x - v * THR;
+  fft_n<T, N>(buf + v * N, tw, tid, +1);
+  C<T>* dst = tout + (size_t)f * tfs;
+  constexpr int per_k = 2 * V;
+  for (int idx = threadIdx.x; idx < H * per_k; idx += V * THR) {
+    const int k = idx / per_k;
+    const int rr = idx - k * per_k;
+    const int row = r0 + rr;
+    if (row >= nrows) continue;
+    const int vv = rr >> 1;
+    const C<T> Z = buf[vv * N + k];
+    const C<T> Zm = buf[vv * N + (k == 0 ? 0 : N - k)];
+    C<T> out;
+    if ((rr & 1) == 0) out = mk<T>(T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y));
+    else out = mk<T>(T(0.5) * (Z.y + Zm.y), T(-0.5) * (Z.x - Zm.x));
+    dst[(size_t)k * ldt + row] = out;
+  }
+}
+
+// -------------------------------------------------------------------- cols --
+template <typename T, int N>
+__global__ void __launch_bounds__(VecsPerCta<N>::value * Radix23<N>::THR)
+cols_n(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin, C<T>* __restrict__ uout,
+       int ldu, long long ufs, int orow0, int nrout, const T* __restrict__ lam, int mode,
+       double2* __restrict__ blk, int blk_kx, int blk_ky, int nblk, int B, int H,
+       const C<T>* __restrict__ tw) {
+  constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* bufs = reinterpret_cast<C<T>*>(smem_raw);
+  T* lcols = reinterpret_cast<T*>(bufs + V * N);
+  const int v = threadIdx.x / THR, tid = threadIdx.x - v * THR;
+  const int k = blockIdx.x * V + v;           // this group's column
+  const bool kvalid = k < H;
+  C<T>* buf = bufs + v * N;
+  T* lcol = lcols + v * N;
+  if (mode != COLS_FWD_ONLY && kvalid)
+    for (int n = tid; n < N; n += THR) lcol[n] = lam[(size_t)k * N + n];
+  const bool use_blk = blk != nullptr && kvalid && k <= blk_kx;
+  const int bw = 2 * blk_ky + 1;
+  for (int f = blockIdx.y; f < B; f += gridDim.y) {
+    if (kvalid) {
+      const C<T>* src = tin + (size_t)f * tfs + (size_t)k * ldt;
+      for (int n = tid; n < N; n += THR) buf[n] = n < nrin ? src[n] : mk<T>(T(0), T(0));
+    } else {
+      for (int n = tid; n < N; n += THR) buf[n] = mk<T>(T(0), T(0));
+    }
+    __syncthreads();
+    fft_n<T, N>(buf, tw, tid, +1);
+    C<T>* dst = uout + (size_t)f * ufs + (size_t)k * ldu;
+    if (mode == COLS_FWD_ONLY) {
+      if (kvalid)
+        for (int n = tid; n < nrout; n += THR) {
+          int r = orow0 + n;
+          r = r >= N ? r - N : r;
+          dst[n] = buf[r];
+        }
+      __syncthreads();
+      continue;
+    }
+    if (mode == COLS_CONV) {
+      if (use_blk) {
+        const double2* bsrc = blk + (size_t)f * nblk + (size_t)k * bw;
+        for (int j = tid; j < bw; j += THR) {
+          int ky = j - blk_ky;
+          ky = ky < 0 ? ky + N : ky;
+          const double2 bv = bsrc[j];
+          buf[ky] = mk<T>((T)bv.x, (T)bv.y);
+        }
+      }
+      __syncthreads();
+      if (kvalid)
+        for (int n = tid; n < N; n += THR) buf[n] = cscale<T>(buf[n], lcol[n]);
+    } else {
+      if (kvalid)
+        for (int n = tid; n < N; n += THR) buf[n] = cscale<T>(buf[n], lcol[n]);
+      __syncthreads();
+      if (use_blk) {
+        double2* bdst = blk + (size_t)f * nblk + (size_t)k * bw;
+        for (int j = tid; j < bw; j += THR) {
+          int ky = j - blk_ky;
+          ky = ky < 0 ? ky + N : ky;
+          const C<T> bv = buf[ky];
+          bdst[j] = make_double2((double)bv.x, (double)bv.y);
+          buf[ky] = mk<T>(T(0), T(0));
+        }
+      }
+    }
+    __syncthreads();
+    fft_n<T, N>(buf, tw, tid, -1);
+    if (kvalid)
+      for (int n = tid; n < nrout; n += THR) {
+        int r = orow0 + n;
+        r = r >= N ? r - N : r;
+        dst[n] = buf[r];
+      }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- rows_inv --
+template <typename T, int N>
+__global__ void __launch_bounds__(VecsPerCta<N>::value * Radix23<N>::THR)
+rows_inv_n(const C<T>* __restrict__ uin, int ldu, long long ufs, int nrows, T* __restrict__ out,
+           int old, long long ofs, int ocol0, int ncols, const T* __restrict__ add, int ald,
+           long long afs, int ar0, int ac0, const C<T>* __restrict__ tw, int H) {
+  constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
+  constexpr int per_k = 2 * V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);          // V * N
+  C<T>* stage = buf + V * N;                               // H * per_k
+  const int f = blockIdx.y;
+  const int r0 = blockIdx.x * 2 * V;
+  const C<T>* src = uin + (size_t)f * ufs;
+  for (int idx = threadIdx.x; idx < H * per_k; idx += V * THR) {
+    const int k = idx / per_k, rr = idx - k * per_k;
+    const int row = r0 + rr;
+    stage[idx] = row < nrows ? src[(size_t)k * ldu + row] : mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < V * N; idx += V * THR) {
+    const int v = idx / N, kk = idx - v * N;
+    C<T> X, Y;
+    if (kk < H) {
+      X = stage[kk * per_k + 2 * v];
+      Y = stage[kk * per_k + 2 * v + 1];
+    } else {
+      const int m = N - kk;
+      X = cconj<T>(stage[m * per_k + 2 * v]);
+      Y = cconj<T>(stage[m * per_k + 2 * v + 1]);
+    }
+    buf[idx] = mk<T>(X.x - Y.y, X.y + Y.x);
+  }
+  __syncthreads();
+  const int v = threadIdx.x / THR, tid = threadIdx.x - v * THR;
+  fft_n<T, N>(buf + v * N, tw, tid, -1);
+  T* dst = out + (size_t)f * ofs;
+  const T* adst = add ? add + (size_t)f * afs : nullptr;
+  for (int idx = threadIdx.x; idx < per_k * ncols; idx += V * THR) {
+    const int rr = idx / ncols, c = idx - rr * ncols;
+    const int row = r0 + rr;
+    if (row >= nrows) continue;
+    int col = ocol0 + c;
+    col = col >= N ? col - N : col;
+    const C<T> z = buf[(rr >> 1) * N + col];
+    T val = (rr & 1) ? z.y : z.x;
+    if (adst) val += adst[(size_t)(row + ar0) * ald + c + ac0];
+    dst[(size_t)row * old + c] = val;
+  }
+}
+
+// ---------------------------------------------------------------- dispatch --
+template <typename T, int N>
+cudaError_t go_rows_fwd(const T* in, int nrows, int ncols, long long ifs, int ild, C<T>* tout,
+                        int ldt, long long tfs, int B, const C<T>* tw, int H, cudaStream_t s) {
+  constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
+  const size_t sm = sizeof(C<T>) * V * N;
+  static int smem_set = 0;
+  auto kern = rows_fwd_n<T, N>;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nrows + 2 * V - 1) / (2 * V), B);
+  kern<<<grid, V * THR, sm, s>>>(in, nrows, ncols, ifs, ild, tout, ldt, tfs, tw, H);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t go_cols(const C<T>* tin, int ldt, long long tfs, int nrin, C<T>* uout, int ldu,
+                    long long ufs, int orow0, int nrout, const T* lam, int mode, double2* blk,
+                    int blk_kx, int blk_ky, int nblk, int B, int H, const C<T>* tw,
+                    cudaStream_t s) {
+  constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
+  const size_t sm = (sizeof(C<T>) + sizeof(T)) * V * N;
+  static int smem_set = 0;
+  auto kern = cols_n<T, N>;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  const int fgroups = B < 8 ? B : 8;
+  dim3 grid((H + V - 1) / V, fgroups);
+  kern<<<grid, V * THR, sm, s>>>(tin, ldt, tfs, nrin, uout, ldu, ufs, orow0, nrout, lam, mode, blk,
+                                 blk_kx, blk_ky, nblk, B, H, tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t go_rows_inv(const C<T>* uin, int ldu, long long ufs, int nrows, T* out, int old,
+                        long long ofs, int ocol0, int ncols, const T* add, int ald, long long afs,
+                        int ar0, int ac0, int B, const C<T>* tw, int H, cudaStream_t s) {
+  constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
+  const size_t sm = sizeof(C<T>) * (V * N + (size_t)(N / 2 + 1) * 2 * V);
+  static int smem_set = 0;
+  auto kern = rows_inv_n<T, N>;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nrows + 2 * V - 1) / (2 * V), B);
+  kern<<<grid, V * THR, sm, s>>>(uin, ldu, ufs, nrows, out, old, ofs, ocol0, ncols, add, ald, afs,
+                                 ar0, ac0, tw, H);
+  return cudaGetLastError();
+}
+
+// The specialised lengths: the tori of the 64^2, 350^2, 512^2 and 1024^2
+// workloads and their circulant embeddings.
+#define RK_SIZES(X) X(128) X(729) X(768) X(1024) X(1152) X(2048) X(2187) X(2304)
+
+template <typename T>
+bool launch_rows_fwd_n(const T* in, int nrows, int ncols, long long ifs, int ild, C<T>* tout,
+                       int ldt, long long tfs, int B, int N, const C<T>* tw, int H,
+                       cudaStream_t s, cudaError_t* err) {
+  switch (N) {
+#define RK_CASE(NN)                                                                        \
+  case NN:                                                                                 \
+    *err = go_rows_fwd<T, NN>(in, nrows, ncols, ifs, ild, tout, ldt, tfs, B, tw, H, s); \
+    return true;
+    RK_SIZES(RK_CASE)
+#undef RK_CASE
+    default: return false;
+  }
+}
+
+template <typename T>
+bool launch_cols_n(const C<T>* tin, int ldt, long long tfs, int nrin, C<T>* uout, int ldu,
+                   long long ufs, int orow0, int nrout, const T* lam, int mode, double2* blk,
+                   int blk_kx, int blk_ky, int nblk, int B, int H, int N, const C<T>* tw,
+                   cudaStream_t s, cudaError_t* err) {
+  switch (N) {
+#define RK_CASE(NN)                                                                           \
+  case NN:                                                                                    \
+    *err = go_cols<T, NN>(tin, ldt, tfs, nrin, uout, ldu, ufs, orow0, nrout, lam, mode, blk, \
+                          blk_kx, blk_ky, nblk, B, H, tw, s);                                 \
+    return true;
+    RK_SIZES(RK_CASE)
+#undef RK_CASE
+    default: return false;
+  }
+}
+
+template <typename T>
+bool launch_rows_inv_n(const C<T>* uin, int ldu, long long ufs, int nrows, T* out, int old,
+                       long long ofs, int ocol0, int ncols, const T* add, int ald, long long afs,
+                       int ar0, int ac0, int B, int N, const C<T>* tw, int H, cudaStream_t s,
+                       cudaError_t* err) {
+  switch (N) {
+#define RK_CASE(NN)                                                                           \
+  case NN:                                                                                    \
+    *err = go_rows_inv<T, NN>(uin, ldu, ufs, nrows, out, old, ofs, ocol0, ncols, add, ald,   \
+                              afs, ar0, ac0, B, tw, H, s);                                    \
+    return true;
+    RK_SIZES(RK_CASE)
+#undef RK_CASE
+    default: return false;
+  }
+}
+
+#define RK_INST(T)                                                                             \
+  template bool launch_rows_fwd_n<T>(const T*, int, int, long long, int, C<T>*, int, long long, \
+                                     int, int, const C<T>*, int, cudaStream_t, cudaError_t*);  \
+  template bool launch_cols_n<T>(const C<T>*, int, long long, int, C<T>*, int, long long, int,  \
+                                 int, const T*, int, double2*, int, int, int, int, int, int,    \
+                                 const C<T>*, cudaStream_t, cudaError_t*);                      \
+  template bool launch_rows_inv_n<T>(const C<T>*, int, long long, int, T*, int, long long, int, \
+                                     int, const T*, int, long long, int, int, int, int,         \
+                                     const C<T>*, int, cudaStream_t, cudaError_t*);
+RK_INST(float)
+RK_INST(double)
+
+}  // namespace rk

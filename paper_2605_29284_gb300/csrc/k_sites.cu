@@ -134,6 +134,45 @@ cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ set weights --
+// Copies caller weights into the plan (double and float) and checks the box
+// indices; flag bit 4 marks an index out of range.
+__global__ void set_weights_kernel(const int* __restrict__ box_in, const double* __restrict__ w_in,
+                                   int n, int M, int nx, int ny, int* __restrict__ box,
+                                   double* __restrict__ w64, float* __restrict__ w32,
+                                   double* __restrict__ ssd, int* flag) {
+  const long long total = (long long)n * M;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / M), q = (int)(t - (long long)i * M);
+    if (q == 0) {
+      int ix = box_in[2 * i], iy = box_in[2 * i + 1];
+      if (ix < 0 || ix > nx - 2 || iy < 0 || iy > ny - 2) {
+        atomicOr(flag, 4);
+        ix = 0;
+        iy = 0;
+      }
+      box[2 * i] = ix;
+      box[2 * i + 1] = iy;
+      ssd[i] = 0.0;
+    }
+    const double w = w_in[t];
+    w64[t] = w;
+    w32[t] = (float)w;
+  }
+}
+
+cudaError_t launch_set_weights(const int* box_in, const double* w_in, int n, const rk_plan* p,
+                               int* box, double* w64, float* w32, double* ssd, int* flag,
+                               cudaStream_t s) {
+  long long total = (long long)n * p->M;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  set_weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(box_in, w_in, n, p->M, p->nx, p->ny, box,
+                                                      w64, w32, ssd, flag);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------ block Fourier factors --
 // For the exact low-frequency block of F(c*) (RK_FP32 plans): for each site i
 // and block frequency (kx, ky), kx in [0, KX], ky in [-KY, KY],
@@ -142,23 +181,23 @@ cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, 
 // Layout efac[j][i], j = kx (2 KY + 1) + (ky + KY).  One thread per (site, kx).
 __global__ void block_factor_kernel(const int* __restrict__ box, const double* __restrict__ w64,
                                     int n, int L, int px, int py, int KX, int KY,
+                                    const double2* __restrict__ twx,
+                                    const double2* __restrict__ twy,
                                     double2* __restrict__ efac) {
   const int W = 2 * L, M = W * W;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (tid >= (long long)n * (KX + 1)) return;
   const int i = (int)(tid % n), kx = (int)(tid / n);
   const int ix = box[2 * i], iy = box[2 * i + 1];
-  // t[b] = sum_a A[a, b] exp(-2 pi i kx (ix + a) / px)
+  // t[b] = sum_a A[a, b] exp(-2 pi i kx (ix + a) / px); twx[e] = exp(-2 pi i e / px)
   double2 t[8];
   for (int b = 0; b < W; ++b) t[b] = make_double2(0.0, 0.0);
   for (int a = 0; a < W; ++a) {
-    const long long m = ((long long)kx * (ix + a)) % px;
-    double sn, cs;
-    sincospi(2.0 * (double)m / (double)px, &sn, &cs);
+    const double2 e = twx[((long long)kx * (ix + a)) % px];
     for (int b = 0; b < W; ++b) {
       const double w = w64[(size_t)i * M + a + W * b];
-      t[b].x += w * cs;
-      t[b].y -= w * sn;
+      t[b].x += w * e.x;
+      t[b].y += w * e.y;
     }
   }
   const int bw = 2 * KY + 1;
@@ -168,11 +207,10 @@ __global__ void block_factor_kernel(const int* __restrict__ box, const double* _
     for (int b = 0; b < W; ++b) {
       long long m = ((long long)ky * (iy + b)) % py;
       if (m < 0) m += py;
-      double sn, cs;
-      sincospi(2.0 * (double)m / (double)py, &sn, &cs);
-      // t[b] * exp(-i theta)
-      e.x += t[b].x * cs + t[b].y * sn;
-      e.y += t[b].y * cs - t[b].x * sn;
+      const double2 f = twy[m];
+      // t[b] * exp(-2 pi i ky (iy + b) / py)
+      e.x += t[b].x * f.x - t[b].y * f.y;
+      e.y += t[b].x * f.y + t[b].y * f.x;
     }
     efac[((size_t)kx * bw + j) * n + i] = e;
   }
@@ -183,9 +221,9 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
   const long long total = (long long)n * (p->blk_kx + 1);
   const int threads = 128;
   const long long blocks = (total + threads - 1) / threads;
-  block_factor_kernel<<<(unsigned)blocks, threads, 0, s>>>(box, p->w64, n, p->L, p->px, p->py,
-                                                          p->blk_kx, p->blk_ky, efac);
-  (void)w64;
+  block_factor_kernel<<<(unsigned)blocks, threads, 0, s>>>(box, w64, n, p->L, p->px, p->py,
+                                                          p->blk_kx, p->blk_ky, p->tw64x,
+                                                          p->tw64y, efac);
   return cudaGetLastError();
 }
 

@@ -87,9 +87,9 @@ rk_status dalloc_bytes(void** p, size_t bytes) {
   return RK_OK;
 }
 
-#define RK_CU(x)                              \
-  do {                                        \
-    if ((x) != cudaSuccess) return RK_ERR_CUDA; \
+#define RK_CU(...)                                      \
+  do {                                                  \
+    if ((__VA_ARGS__) != cudaSuccess) return RK_ERR_CUDA; \
   } while (0)
 #define RK_TRY(x)                   \
   do {                              \
@@ -143,27 +143,27 @@ rk_status upload_twiddles(int n, double2** t64, float2** t32) {
   return RK_OK;
 }
 
-// lambda = FFT2(base) / (px py) for a base of the given kind (0: phi, 1: d/dlog rho).
-rk_status compute_spectrum(rk_plan* p, int deriv, double** lam64, float** lam32) {
-  const int px = p->px, py = p->py, H = p->H;
+// Half spectrum (H x py, unscaled) of the symmetric torus base on a
+// tx x ty torus: kind 0 = phi, 1 = d/dlog rho.  *lam is allocated here.
+rk_status spectrum_raw(rk_plan* p, int tx, int ty, const FftPlan& fx, const FftPlan& fy,
+                       const double2* twx, const double2* twy, int deriv, double** lam) {
+  const int H = tx / 2 + 1;
   double* base = nullptr;
   double2* t = nullptr;
   double2* u = nullptr;
   rk_status st = RK_OK;
   do {
-    if ((st = dalloc(&base, (size_t)px * py)) != RK_OK) break;
-    if ((st = dalloc(&t, (size_t)H * py)) != RK_OK) break;
-    if ((st = dalloc(&u, (size_t)H * py)) != RK_OK) break;
-    if ((st = dalloc(lam64, (size_t)H * py)) != RK_OK) break;
-    if (p->precision == RK_FP32 && (st = dalloc(lam32, (size_t)H * py)) != RK_OK) break;
-    if (launch_torus_base(base, px, py, p->hx, p->hy, p->rho, p->sigma2, p->nu_code, deriv,
+    if ((st = dalloc(&base, (size_t)tx * ty)) != RK_OK) break;
+    if ((st = dalloc(&t, (size_t)H * ty)) != RK_OK) break;
+    if ((st = dalloc(&u, (size_t)H * ty)) != RK_OK) break;
+    if ((st = dalloc(lam, (size_t)H * ty)) != RK_OK) break;
+    if (launch_torus_base(base, tx, ty, p->hx, p->hy, p->rho, p->sigma2, p->nu_code, deriv,
                           p->stream) != cudaSuccess ||
-        launch_rows_fwd<double>(base, py, px, 0, px, t, py, 0, 1, p->fpx, p->tw64x, H,
-                                p->stream) != cudaSuccess ||
-        launch_cols<double>(t, py, 0, py, u, py, 0, 0, py, nullptr, COLS_FWD_ONLY, nullptr, -1, 0,
-                            0, 1, H, p->fpy, p->tw64y, p->stream) != cudaSuccess ||
-        launch_lambda_finish(u, py, H, py, 1.0 / ((double)px * (double)py), *lam64,
-                             p->precision == RK_FP32 ? *lam32 : nullptr, p->stream) != cudaSuccess ||
+        launch_rows_fwd<double>(base, ty, tx, 0, tx, t, ty, 0, 1, fx, twx, H, p->stream) !=
+            cudaSuccess ||
+        launch_cols<double>(t, ty, 0, ty, u, ty, 0, 0, ty, nullptr, COLS_FWD_ONLY, nullptr, -1, 0,
+                            0, 1, H, fy, twy, p->stream) != cudaSuccess ||
+        launch_lambda_finish(u, ty, H, ty, 1.0, *lam, nullptr, p->stream) != cudaSuccess ||
         cudaStreamSynchronize(p->stream) != cudaSuccess) {
       st = RK_ERR_CUDA;
     }
@@ -171,6 +171,22 @@ rk_status compute_spectrum(rk_plan* p, int deriv, double** lam64, float** lam32)
   cudaFree(base);
   cudaFree(t);
   cudaFree(u);
+  return st;
+}
+
+// lambda / (px py) of the prediction torus, in double and (RK_FP32) float.
+rk_status compute_spectrum(rk_plan* p, int deriv, double** lam64, float** lam32) {
+  double* raw = nullptr;
+  RK_TRY(spectrum_raw(p, p->px, p->py, p->fpx, p->fpy, p->tw64x, p->tw64y, deriv, &raw));
+  const size_t cnt = (size_t)p->H * p->py;
+  rk_status st = dalloc(lam64, cnt);
+  if (st == RK_OK && p->precision == RK_FP32) st = dalloc(lam32, cnt);
+  if (st == RK_OK &&
+      launch_scale(raw, cnt, 1.0 / ((double)p->px * (double)p->py), *lam64,
+                   p->precision == RK_FP32 ? *lam32 : nullptr, p->stream) != cudaSuccess)
+    st = RK_ERR_CUDA;
+  if (st == RK_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) st = RK_ERR_CUDA;
+  cudaFree(raw);
   return st;
 }
 
@@ -211,7 +227,8 @@ void free_plan(rk_plan* p) {
                   p->dlam32, p->kn_chol, p->kn_dlog, p->box, p->w64, p->w32, p->ssd, p->efac,
                   p->c64, p->c32, p->z64, p->mchol, p->cstar, p->tbuf, p->ubuf, p->blk,
                   p->d_flag, p->tw64qx, p->tw64qy, p->tw32qx, p->tw32qy, p->ce_sqrt64,
-                  p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_c, p->h_out, p->xy};
+                  p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_c, p->h_out, p->xy, p->wd64,
+                  p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -263,17 +280,21 @@ rk_status finish_coef(rk_plan* p, int B) {
   return RK_OK;
 }
 
+// Steps 5-7 for nf fields with coefficients c64 (double) and cT (plan
+// precision; may equal c64 for RK_FP64 plans); out[f] (+ addend window).
 template <typename T>
-rk_status predict_impl(rk_plan* p, T* out) {
-  const int B = p->B;
+rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* out,
+                         const T* addend, const T* lam_override = nullptr,
+                         const T* w_override = nullptr, const double2* efac_override = nullptr) {
+  const int B = nf;
   cudaStream_t s = p->stream;
   T* cstar = (T*)p->cstar;
   C<T>* tb = (C<T>*)p->tbuf;
   C<T>* ub = (C<T>*)p->ubuf;
   const bool f32 = sizeof(T) == sizeof(float);
-  const T* w = f32 ? (const T*)p->w32 : (const T*)p->w64;
-  const T* c = f32 ? (const T*)p->c32 : (const T*)p->c64;
-  const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
+  const T* w = w_override ? w_override : f32 ? (const T*)p->w32 : (const T*)p->w64;
+  const T* lam = lam_override ? lam_override : f32 ? (const T*)p->lam32 : (const T*)p->lam64;
+  const double2* efac = efac_override ? efac_override : p->efac;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
   const C<T>* twy = f32 ? (const C<T>*)p->tw32y : (const C<T>*)p->tw64y;
   const size_t plane = (size_t)p->p1y * p->p1x;
@@ -282,7 +303,7 @@ rk_status predict_impl(rk_plan* p, T* out) {
   {
     RK_PROF("scatter", B * (plane * es + nM * 2 * es + p->n * es) + nM * es + p->n * 8.0);
     RK_CU(cudaMemsetAsync(cstar, 0, (size_t)B * plane * sizeof(T), s));
-    RK_CU(launch_scatter<T>(p->box, w, c, p->n, B, p->L, cstar, p->p1x, p->p1y, s));
+    RK_CU(launch_scatter<T>(p->box, w, cT, p->n, B, p->L, cstar, p->p1x, p->p1y, s));
   }
   {
     RK_PROF("rows_fwd", B * (plane * es + (double)p->H * p->p1y * cs));
@@ -292,7 +313,7 @@ rk_status predict_impl(rk_plan* p, T* out) {
   const bool use_blk = f32 && p->nblk > 0;
   if (use_blk) {
     RK_PROF("block_gemm", (double)p->nblk * p->n * 16.0 + B * (p->n * 8.0 + p->nblk * 16.0));
-    RK_CU(launch_block_gemm(p->c64, B, p->n, p->efac, p->nblk, p->blk, s));
+    RK_CU(launch_block_gemm(c64, B, p->n, efac, p->nblk, p->blk, s));
   }
   {
     RK_PROF("cols", B * ((double)p->H * p->p1y * cs + (double)p->H * p->ny * cs) +
@@ -303,10 +324,234 @@ rk_status predict_impl(rk_plan* p, T* out) {
                          p->fpy, twy, s));
   }
   {
-    RK_PROF("rows_inv", B * ((double)p->H * p->ny * cs + (double)p->ny * p->nx * es));
+    RK_PROF("rows_inv", B * ((double)p->H * p->ny * cs + (double)p->ny * p->nx * es) +
+                            (addend ? B * (double)p->ny * p->nx * es : 0.0));
     RK_CU(launch_rows_inv<T>(ub, p->ldu, (long long)p->H * p->ldu, p->ny, out, p->nx,
-                             (long long)p->ny * p->nx, p->L - 1, p->nx, (const T*)nullptr, 0, 0,
-                             0, 0, B, p->fpx, twx, p->H, s));
+                             (long long)p->ny * p->nx, p->L - 1, p->nx, addend, p->p1x,
+                             (long long)plane, p->L - 1, p->L - 1, B, p->fpx, twx, p->H, s));
+  }
+  return RK_OK;
+}
+
+template <typename T>
+rk_status predict_impl(rk_plan* p, T* out) {
+  const T* cT = sizeof(T) == sizeof(float) ? (const T*)p->c32 : (const T*)p->c64;
+  return predict_fields<T>(p, p->c64, cT, p->B, out, (const T*)nullptr);
+}
+
+// ---------------------------------------------------- conditional simulation --
+// Circulant embedding of the padded grid: torus qx x qy (2^a 3^b >= 2 (P1 - 1)),
+// grown until min lambda >= -1e-12 max lambda (at most four-fold).
+rk_status ensure_ce(rk_plan* p) {
+  if (p->qx > 0) return RK_OK;
+  const int qx0 = smooth23(2 * (p->p1x - 1) > 2 ? 2 * (p->p1x - 1) : 2);
+  const int qy0 = smooth23(2 * (p->p1y - 1) > 2 ? 2 * (p->p1y - 1) : 2);
+  int qx = qx0, qy = qy0;
+  while (qx <= 4 * qx0 && qy <= 4 * qy0 && qx <= kMaxTorus && qy <= kMaxTorus) {
+    FftPlan fx = make_fft_plan(qx), fy = make_fft_plan(qy);
+    double2 *t64x = nullptr, *t64y = nullptr;
+    float2 *t32x = nullptr, *t32y = nullptr;
+    RK_TRY(upload_twiddles(qx, &t64x, &t32x));
+    RK_TRY(upload_twiddles(qy, &t64y, &t32y));
+    const int hq = qx / 2 + 1;
+    double* lam = nullptr;
+    rk_status st = spectrum_raw(p, qx, qy, fx, fy, t64x, t64y, 0, &lam);
+    std::vector<double> h((size_t)hq * qy);
+    if (st == RK_OK &&
+        cudaMemcpy(h.data(), lam, h.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = RK_ERR_CUDA;
+    cudaFree(lam);
+    if (st != RK_OK) {
+      cudaFree(t64x); cudaFree(t64y); cudaFree(t32x); cudaFree(t32y);
+      return st;
+    }
+    double lmin = h[0], lmax = h[0];
+    for (double v : h) { lmin = v < lmin ? v : lmin; lmax = v > lmax ? v : lmax; }
+    if (lmin >= -1e-12 * lmax) {
+      std::vector<double> s64(h.size());
+      std::vector<float> s32(h.size());
+      const double inv = 1.0 / ((double)qx * (double)qy);
+      for (size_t i = 0; i < h.size(); ++i) {
+        s64[i] = sqrt((h[i] > 0.0 ? h[i] : 0.0) * inv);
+        s32[i] = (float)s64[i];
+      }
+      RK_TRY(dalloc(&p->ce_sqrt64, h.size()));
+      RK_TRY(dalloc(&p->ce_sqrt32, h.size()));
+      RK_CU(cudaMemcpy(p->ce_sqrt64, s64.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+      RK_CU(cudaMemcpy(p->ce_sqrt32, s32.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+      p->qx = qx; p->qy = qy; p->fqx = fx; p->fqy = fy;
+      p->tw64qx = t64x; p->tw64qy = t64y; p->tw32qx = t32x; p->tw32qy = t32y;
+      return RK_OK;
+    }
+    cudaFree(t64x); cudaFree(t64y); cudaFree(t32x); cudaFree(t32y);
+    qx = smooth23(qx + 1);
+    qy = smooth23(qy + 1);
+  }
+  return RK_ERR_CE_NEGATIVE;
+}
+
+constexpr int kCsChunk = 64;
+
+template <typename T>
+rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
+  cudaStream_t s = p->stream;
+  const int n = p->n;
+  const long long total = (long long)p->B * R;
+  const int G = total < kCsChunk ? (int)total : kCsChunk;
+  const size_t plane = (size_t)p->p1y * p->p1x;
+  const int ldq = p->p1y;
+  const int maxpairs = G / 2 + 1;
+  const size_t fu_b = (size_t)G * plane * sizeof(T);
+  const size_t tq_b = (size_t)maxpairs * p->qx * ldq * 2 * sizeof(T);
+  const size_t rhs_b = (size_t)G * n * sizeof(double);
+  const size_t c32_b = (size_t)G * n * sizeof(T);
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t need = al(fu_b) + al(tq_b) + al(rhs_b) + al(c32_b);
+  if (p->cs_bytes < need) {
+    RK_TRY(dalloc_bytes(&p->cs_buf, need));
+    p->cs_bytes = need;
+  }
+  RK_TRY(ensure_field_scratch(p, G));
+  char* base = (char*)p->cs_buf;
+  T* fu = (T*)base;
+  C<T>* tq = (C<T>*)(base + al(fu_b));
+  double* rhs = (double*)(base + al(fu_b) + al(tq_b));
+  T* cT = (T*)(base + al(fu_b) + al(tq_b) + al(rhs_b));
+  const bool f32 = sizeof(T) == sizeof(float);
+  const T* sl = f32 ? (const T*)p->ce_sqrt32 : (const T*)p->ce_sqrt64;
+  const C<T>* twqx = f32 ? (const C<T>*)p->tw32qx : (const C<T>*)p->tw64qx;
+  const C<T>* twqy = f32 ? (const C<T>*)p->tw32qy : (const C<T>*)p->tw64qy;
+  for (long long g0 = 0; g0 < total; g0 += G) {
+    const int g = (int)(total - g0 < G ? total - g0 : G);
+    const int pair0 = (int)(g0 / 2);
+    const int npairs = (int)((g0 + g - 1) / 2 - g0 / 2 + 1);
+    {
+      RK_PROF("ce_cols", (double)npairs * p->qx * (p->qy / 2 + 1) * sizeof(T) +
+                             (double)npairs * p->qx * p->p1y * 2 * sizeof(T));
+      RK_CU(launch_ce_cols<T>(sl, p->qx, p->qy, seed, pair0, npairs, tq, ldq, p->p1y, p->fqy,
+                              twqy, s));
+    }
+    {
+      RK_PROF("ce_rows", (double)npairs * p->qx * p->p1y * 2 * sizeof(T) +
+                             (double)g * plane * sizeof(T));
+      RK_CU(launch_ce_rows<T>(tq, p->qx, ldq, p->p1y, fu, p->p1x, g0, g, pair0, npairs, p->fqx,
+                              twqx, s));
+    }
+    {
+      RK_PROF("site_values", (double)g * n * (p->M * sizeof(T) + 16.0) + (double)n * p->M * 8);
+      RK_CU(launch_site_values<T>(fu, p->p1x, (long long)plane, g, p->box, p->w64, p->ssd, n,
+                                  p->L, sqrt(p->tau2), seed, g0, R, p->z64, rhs, s));
+    }
+    {
+      RK_PROF("chol_solve", (double)g * n * 16.0 + (double)g * n * (double)n * 8.0);
+      RK_CU(chol_solve(p->mchol, n, rhs, g, s));
+    }
+    const T* cuse = (const T*)rhs;
+    if (f32) {
+      RK_CU(launch_convert<T>(rhs, cT, (size_t)g * n, s));
+      cuse = cT;
+    }
+    RK_TRY(predict_fields<T>(p, rhs, cuse, g, out + (size_t)g0 * p->ny * p->nx, fu));
+  }
+  return RK_OK;
+}
+
+// ------------------------------------------------------------------ adjoint --
+rk_status ensure_adjoint(rk_plan* p) {
+  if (p->have_adj) return RK_OK;
+  if (!p->dlam64) RK_TRY(compute_spectrum(p, 1, &p->dlam64, &p->dlam32));
+  if (!p->kn_dlog) {
+    RK_TRY(dalloc(&p->kn_dlog, (size_t)p->M * p->M));
+    RK_CU(launch_kn_dlog(p->kn_dlog, p->L, p->hx, p->hy, p->rho, p->sigma2, p->nu_code,
+                         p->stream));
+  }
+  RK_TRY(dalloc(&p->wd64, (size_t)p->n * p->M));
+  RK_TRY(dalloc(&p->wd32, (size_t)p->n * p->M));
+  RK_CU(launch_dweights(p, p->wd64, p->wd32, p->stream));
+  if (p->precision == RK_FP32 && p->nblk > 0) {
+    RK_TRY(dalloc(&p->efac_d, (size_t)p->n * p->nblk));
+    RK_CU(launch_block_factors(p->box, p->wd64, p->n, p, p->efac_d, p->stream));
+  }
+  p->have_adj = true;
+  return RK_OK;
+}
+
+template <typename T>
+rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, double* gs2) {
+  cudaStream_t s = p->stream;
+  const int B = p->B, n = p->n;
+  const bool f32 = sizeof(T) == sizeof(float);
+  const size_t plane = (size_t)p->p1y * p->p1x;
+  const size_t grid = (size_t)p->ny * p->nx;
+  RK_TRY(ensure_adjoint(p));
+  if (p->bw_cbar_cap < (size_t)B * n) {
+    RK_TRY(dalloc(&p->bw_cbar, (size_t)B * n));
+    p->bw_cbar_cap = (size_t)B * n;
+  }
+  if (p->bw_y_bytes < 3 * B * grid * sizeof(T)) {
+    RK_TRY(dalloc_bytes(&p->bw_y, 3 * B * grid * sizeof(T)));
+    p->bw_y_bytes = 3 * B * grid * sizeof(T);
+  }
+  const bool use_blk = f32 && p->nblk > 0;
+  if (use_blk && p->bw_gblk_cap < (size_t)B * p->nblk) {
+    RK_TRY(dalloc(&p->bw_gblk, (size_t)B * p->nblk));
+    p->bw_gblk_cap = (size_t)B * p->nblk;
+  }
+  const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
+  const T* dlam = f32 ? (const T*)p->dlam32 : (const T*)p->dlam64;
+  const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
+  const C<T>* twy = f32 ? (const C<T>*)p->tw32y : (const C<T>*)p->tw64y;
+  T* abar = (T*)p->cstar;
+  C<T>* tb = (C<T>*)p->tbuf;
+  C<T>* ub = (C<T>*)p->ubuf;
+  const double es = sizeof(T), cs = 2.0 * sizeof(T);
+  // abar = K_gg^T E^T gbar on the padded grid (the same circulant product:
+  // the symmetric base makes the correlation equal the convolution)
+  {
+    RK_PROF("adj_rows_fwd", B * (grid * es + (double)p->H * p->ny * cs));
+    RK_CU(launch_rows_fwd<T>(gbar, p->ny, p->nx, (long long)grid, p->nx, tb, p->ldt,
+                             (long long)p->H * p->ldt, B, p->fpx, twx, p->H, s));
+  }
+  {
+    RK_PROF("adj_cols", B * ((double)p->H * p->ny * cs + (double)p->H * p->p1y * cs));
+    RK_CU(launch_cols<T>(tb, p->ldt, (long long)p->H * p->ldt, p->ny, ub, p->ldu,
+                         (long long)p->H * p->ldu, p->py - (p->L - 1), p->p1y, lam, COLS_ADJ,
+                         use_blk ? p->bw_gblk : nullptr, p->blk_kx, p->blk_ky, p->nblk, B, p->H,
+                         p->fpy, twy, s));
+  }
+  {
+    RK_PROF("adj_rows_inv", B * ((double)p->H * p->p1y * cs + plane * es));
+    RK_CU(launch_rows_inv<T>(ub, p->ldu, (long long)p->H * p->ldu, p->p1y, abar, p->p1x,
+                             (long long)plane, p->px - (p->L - 1), p->p1x, (const T*)nullptr, 0,
+                             0, 0, 0, B, p->fpx, twx, p->H, s));
+  }
+  // cbar = A abar (+ the exact block part), zbar = M^{-1} cbar
+  double* cbar = p->bw_cbar;
+  RK_CU(launch_gather<T>(abar, p->p1x, p->p1y, p->box, p->w64, n, p->L, B, cbar, s));
+  if (use_blk)
+    RK_CU(launch_block_adjoint(p->bw_gblk, B, p->nblk, 2 * p->blk_ky + 1, p->efac, n, cbar, s));
+  RK_CU(chol_solve(p->mchol, n, cbar, B, s));
+  if (gz) RK_CU(cudaMemcpyAsync(gz, cbar, (size_t)B * n * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+  if (grho || gs2) {
+    T* y0 = (T*)p->bw_y;
+    T* y1 = y0 + B * grid;
+    T* y2 = y1 + B * grid;
+    const T* cT = f32 ? (const T*)p->c32 : (const T*)p->c64;
+    const T* wd = f32 ? (const T*)p->wd32 : (const T*)p->wd64;
+    RK_TRY(predict_fields<T>(p, p->c64, cT, B, y0, nullptr));
+    if (gs2) {
+      RK_CU(launch_dot_rows<T, T>(gbar, y0, B, (long long)grid, 1.0, 0, gs2, s));
+      RK_CU(launch_dot_rows<double, double>(cbar, p->z64, B, (long long)n, -1.0, 1, gs2, s));
+      RK_CU(launch_dot_rows<double, double>(cbar, p->c64, B, (long long)n, p->tau2, 1, gs2, s));
+    }
+    if (grho) {
+      RK_TRY(predict_fields<T>(p, p->c64, cT, B, y1, nullptr, dlam));
+      RK_TRY(predict_fields<T>(p, p->c64, cT, B, y2, nullptr, nullptr, wd, p->efac_d));
+      RK_CU(launch_dot_rows<T, T>(gbar, y1, B, (long long)grid, 1.0, 0, grho, s));
+      RK_CU(launch_dot_rows<T, T>(gbar, y2, B, (long long)grid, 1.0, 1, grho, s));
+      RK_CU(launch_quad_dkxx(p->xy, n, cbar, p->c64, B, p->rho, p->sigma2, p->nu_code, grho, s));
+    }
   }
   return RK_OK;
 }
@@ -362,7 +607,7 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
   p->py = smooth23(2 * (ny + L - 2) > p->p1y ? 2 * (ny + L - 2) : p->p1y);
   p->H = p->px / 2 + 1;
   p->ldt = p->p1y;
-  p->ldu = p->ny;
+  p->ldu = p->p1y;   // the adjoint writes p1y rows
   p->stream = (cudaStream_t)stream;
   p->fpx = make_fft_plan(p->px);
   p->fpy = make_fft_plan(p->py);
@@ -446,8 +691,7 @@ rk_status rk_plan_get_info(const rk_plan* p, rk_plan_info* info) {
   return RK_OK;
 }
 
-rk_status rk_set_sites(rk_plan* p, int n, const double* xy) {
-  if (!p || n < 1 || !xy) return RK_ERR_INVALID_ARG;
+rk_status ensure_sites(rk_plan* p, int n) {
   if (n > p->n_cap) {
     RK_TRY(dalloc(&p->xy, (size_t)2 * n));
     RK_TRY(dalloc(&p->box, (size_t)2 * n));
@@ -460,6 +704,29 @@ rk_status rk_set_sites(rk_plan* p, int n, const double* xy) {
   p->n = 0;
   p->have_coef = false;
   p->have_chol = false;
+  p->have_adj = false;
+  return RK_OK;
+}
+
+rk_status rk_set_weights(rk_plan* p, int n, const int* box, const double* w) {
+  if (!p || n < 1 || !box || !w) return RK_ERR_INVALID_ARG;
+  RK_TRY(ensure_sites(p, n));
+  p->xy_valid = false;
+  RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
+  RK_CU(launch_set_weights(box, w, n, p, p->box, p->w64, p->w32, p->ssd, p->d_flag, p->stream));
+  int flag = 0;
+  RK_TRY(read_flag(p, &flag));
+  if (flag & 4) return RK_ERR_INVALID_ARG;
+  if (p->precision == RK_FP32 && p->nblk > 0)
+    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->efac, p->stream));
+  p->n = n;
+  return RK_OK;
+}
+
+rk_status rk_set_sites(rk_plan* p, int n, const double* xy) {
+  if (!p || n < 1 || !xy) return RK_ERR_INVALID_ARG;
+  RK_TRY(ensure_sites(p, n));
+  p->xy_valid = true;
   RK_CU(cudaMemcpyAsync(p->xy, xy, (size_t)2 * n * sizeof(double), cudaMemcpyDeviceToDevice,
                         p->stream));
   RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
@@ -484,7 +751,7 @@ rk_status rk_set_coef(rk_plan* p, int B, const double* c) {
 
 rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
   if (!p || B < 1 || !z) return RK_ERR_INVALID_ARG;
-  if (p->n == 0) return RK_ERR_STATE;
+  if (p->n == 0 || !p->xy_valid) return RK_ERR_STATE;
   const int n = p->n;
   RK_TRY(ensure_coef(p, B));
   if (!p->have_chol) {
@@ -575,16 +842,19 @@ rk_status rk_debug_copy(rk_plan* p, int what, void* dst, size_t bytes) {
 }
 
 rk_status rk_simulate(rk_plan* p, int R, unsigned long long seed, void* out) {
-  (void)seed;
   if (!p || R < 1 || !out) return RK_ERR_INVALID_ARG;
-  return RK_ERR_STATE;
+  if (p->n == 0 || !p->have_chol || !p->have_coef) return RK_ERR_STATE;
+  RK_TRY(ensure_ce(p));
+  if (p->precision == RK_FP64) return simulate_impl<double>(p, R, seed, (double*)out);
+  return simulate_impl<float>(p, R, seed, (float*)out);
 }
 
 rk_status rk_predict_backward(rk_plan* p, const void* gbar, double* gz, double* grho,
                               double* gs2) {
-  (void)gz; (void)grho; (void)gs2;
   if (!p || !gbar) return RK_ERR_INVALID_ARG;
-  return RK_ERR_STATE;
+  if (p->n == 0 || !p->have_chol || !p->have_coef || !p->xy_valid) return RK_ERR_STATE;
+  if (p->precision == RK_FP64) return backward_impl<double>(p, (const double*)gbar, gz, grho, gs2);
+  return backward_impl<float>(p, (const float*)gbar, gz, grho, gs2);
 }
 
 }  // extern "C"

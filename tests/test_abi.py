@@ -20,24 +20,23 @@ def test_header_declares_the_boundary(repo_root):
 
 
 def test_library_exports_every_declared_symbol(repo_root):
-    from paper_2605_29284_gb300 import build
-    path = build.build()
-    lib = ctypes.CDLL(path)
+    import __graft_entry__
+    lib = ctypes.CDLL(__graft_entry__._build_module().build())
     missing = [n for n in _declared(repo_root) if not hasattr(lib, n)]
     assert not missing, missing
 
 
 def test_status_strings_without_gpu(repo_root):
-    from paper_2605_29284_gb300 import build
-    lib = ctypes.CDLL(build.build())
+    import __graft_entry__
+    lib = ctypes.CDLL(__graft_entry__._build_module().build())
     lib.rk_status_string.restype = ctypes.c_char_p
     assert lib.rk_status_string(0) == b"ok"
     assert b"outside" in lib.rk_status_string(2)
 
 
 def test_invalid_arguments_rejected_before_any_gpu_work(repo_root):
-    from paper_2605_29284_gb300 import build
-    lib = ctypes.CDLL(build.build())
+    import __graft_entry__
+    lib = ctypes.CDLL(__graft_entry__._build_module().build())
     h = ctypes.c_void_p()
     ext = (ctypes.c_double * 4)(0.0, 1.0, 0.0, 1.0)
     f = lib.rk_plan_create

@@ -1,0 +1,72 @@
+"""GPU conditional simulation (rk_simulate) against the oracle.
+
+Both sides draw the same noise from their own Philox4x64-10 implementations,
+so realisations are compared element by element: 1e-10 relative for RK_FP64
+(the dense FP64 solves differ at kappa(M) * eps) and 2e-5 for RK_FP32.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synth  # noqa: E402
+from gpu_util import rel_err  # noqa: E402
+from oracle import cs, kriging, rapid  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def rk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_29284_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+@pytest.mark.parametrize("L,nu", [(1, 0.5), (2, 1.5), (3, 2.5)])
+def test_realisations_match_oracle(rk, prec, tol, L, nu):
+    ext = (0.0, 1.2, 0.0, 0.9)
+    nx, ny, n, R, B = 29, 23, 50, 5, 2          # R odd: realisation pairs cross fields
+    th, tau2, seed = (nu, 0.2, 1.3), 1e-2, 12345
+    xy = synth.sites_uniform(n, ext, 31 + L)
+    z = synth.normals((B, n), 32 + L)
+    g = rapid.Grid(nx, ny, ext, L)
+    ref = cs.simulate(xy, z, g, *th, tau2, R, seed)
+    with rk.Plan(nx, ny, ext, *th, tau2, L, precision=prec) as p:
+        p.set_obs(torch.from_numpy(xy).cuda(), torch.from_numpy(z).cuda())
+        out = p.simulate(R, seed).double().cpu().numpy()
+        info = p.info()
+    qx, qy, _ = cs.ce_spectrum(g, *th)
+    assert (info["qx"], info["qy"]) == (qx, qy)
+    assert out.shape == ref.shape
+    assert rel_err(out, ref) <= tol
+
+
+def test_ensemble_moments_equal_kriging_on_nodes(rk):
+    # Sites on grid nodes: local simulation and rapid prediction are exact, so
+    # the ensemble mean/variance are the Kriging mean/variance (Section 5.2).
+    ext = (0.0, 1.0, 0.0, 1.0)
+    m, n, R = 24, 30, 2048
+    th, tau2 = (1.5, 0.25, 1.0), 1e-2
+    xy = synth.sites_on_nodes(n, m, m, ext, 41)
+    z = synth.normals(n, 42)
+    g = rapid.Grid(m, m, ext, 2)
+    with rk.Plan(m, m, ext, *th, tau2, 2, precision="fp32") as p:
+        p.set_obs(torch.from_numpy(xy).cuda(), torch.from_numpy(z).cuda())
+        sims = p.simulate(R, 7)[0].double()
+        mean, var = sims.mean(0).cpu().numpy(), sims.var(0).cpu().numpy()
+    c = kriging.coef(xy, z, *th, tau2)
+    kmean = kriging.predict(xy, c, g.nodes(), *th).reshape(m, m)
+    kvar = kriging.variance(xy, g.nodes(), *th, tau2).reshape(m, m)
+    assert np.abs(mean - kmean).max() < 5 * np.sqrt(kvar.max() / R)
+    assert abs(var.sum() / kvar.sum() - 1.0) < 0.03
+
+
+def test_simulate_needs_solved_coefficients(rk):
+    with rk.Plan(16, 16, (0.0, 1.0, 0.0, 1.0), 1.5, 0.2, 1.0, 1e-3, 2) as p:
+        p.set_sites(torch.rand(10, 2, dtype=torch.float64))
+        p.set_coef(torch.randn(1, 10, dtype=torch.float64))
+        with pytest.raises(rk.RkError) as e:
+            p.simulate(4, 1)
+        assert e.value.name == "RK_ERR_STATE"
