@@ -82,9 +82,9 @@ struct Radix23 {
   static constexpr int THR = (A >= 3) ? N / 8 : N / maxr();
 };
 
-template <typename T, int N, int THR, int R, int NS>
+template <typename T, int N, int THR, int R, int NS, int DIR>
 __device__ __forceinline__ void stage_n(C<T>* __restrict__ buf, const C<T>* __restrict__ tw,
-                                        int tid, int dir) {
+                                        int tid) {
   constexpr int NB = N / R;
   constexpr int IT = (NB + THR - 1) / THR;
   constexpr int TWS = N / (NS * R);
@@ -103,10 +103,10 @@ __device__ __forceinline__ void stage_n(C<T>* __restrict__ buf, const C<T>* __re
         for (int r = 1; r < R; ++r) {
           const C<T> w = __ldg(tw + r * k * TWS);
           const C<T> x = buf[j + r * NB];
-          a[it][r] = dir > 0 ? cmul<T>(x, w) : cmulc<T>(x, w);
+          a[it][r] = DIR > 0 ? cmul<T>(x, w) : cmulc<T>(x, w);
         }
       }
-      dft_r<T, R>(a[it], dir);
+      dft_r<T, R>(a[it], DIR);
     }
   }
   __syncthreads();
@@ -123,20 +123,21 @@ __device__ __forceinline__ void stage_n(C<T>* __restrict__ buf, const C<T>* __re
   __syncthreads();
 }
 
-template <typename T, int N, int THR, int S>
-__device__ __forceinline__ void fft_stages(C<T>* buf, const C<T>* tw, int tid, int dir) {
+template <typename T, int N, int THR, int S, int DIR>
+__device__ __forceinline__ void fft_stages(C<T>* buf, const C<T>* tw, int tid) {
   using P = Radix23<N>;
   if constexpr (S < P::S) {
-    stage_n<T, N, THR, P::radix(S), P::span(S)>(buf, tw, tid, dir);
-    fft_stages<T, N, THR, S + 1>(buf, tw, tid, dir);
+    stage_n<T, N, THR, P::radix(S), P::span(S), DIR>(buf, tw, tid);
+    fft_stages<T, N, THR, S + 1, DIR>(buf, tw, tid);
   }
 }
 
-// In-place transform of one length-N vector by THR threads (tid in [0, THR)).
+// In-place transform of one length-N vector by THR threads (tid in [0, THR)),
+// forward for DIR = +1 (exp(-2 pi i jk / N)), unnormalised inverse for -1.
 // All threads of the CTA must call it (it synchronises the CTA).
-template <typename T, int N>
-__device__ __forceinline__ void fft_n(C<T>* buf, const C<T>* tw, int tid, int dir) {
-  fft_stages<T, N, Radix23<N>::THR, 0>(buf, tw, tid, dir);
+template <typename T, int N, int DIR>
+__device__ __forceinline__ void fft_n(C<T>* buf, const C<T>* tw, int tid) {
+  fft_stages<T, N, Radix23<N>::THR, 0, DIR>(buf, tw, tid);
 }
 
 }  // namespace rk

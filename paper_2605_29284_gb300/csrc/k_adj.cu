@@ -2,7 +2,7 @@
 // The paper has no gradient; with a = c* = A^T c, c = M^{-1} z and
 // gbar = d loss / d g_hat:
 //   abar = K_gg^T E^T gbar,  cbar = A abar,  zbar = M^{-1} cbar,
-//   d/dlog sigma^2 = gbar . g_hat - zbar . (z - tau^2 c),
+//   d/dlog sigma^2 = gbar . g_hat - zbar . (z - tau^2 c) = tau^2 zbar . c,
 //   d/dlog rho     = gbar . (K'_gg A^T c + K_gg A'^T c) - zbar^T K'_xx c,
 // where ' is d / dlog rho and A' has rows W_i' = K_N^{-1} (k_i' - K_N' W_i).
 #include "common.cuh"
@@ -146,6 +146,32 @@ __global__ void block_adjoint_kernel(const double2* __restrict__ gblk, int B, in
     }
     cbar[t] += s;
   }
+}
+
+// The forward pass reads the prediction window at offset o = L - 1 of the
+// padded grid; seen from the sites, the block spectrum of gbar therefore
+// carries the phase exp(-2 pi i (kx o / px + ky o / py)), applied here in
+// place (twx, twy: exp(-2 pi i e / p) tables).
+__global__ void block_phase_kernel(double2* __restrict__ gblk, int B, int nblk, int bw, int KY,
+                                   int o, int px, int py, const double2* __restrict__ twx,
+                                   const double2* __restrict__ twy) {
+  const int total = B * nblk;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int j = t % nblk;
+    const int kx = j / bw, ky = j % bw - KY;
+    long long my = ((long long)ky * o) % py;
+    if (my < 0) my += py;
+    const double2 ex = twx[((long long)kx * o) % px], ey = twy[my];
+    const double2 ph = make_double2(ex.x * ey.x - ex.y * ey.y, ex.x * ey.y + ex.y * ey.x);
+    const double2 g = gblk[t];
+    gblk[t] = make_double2(g.x * ph.x - g.y * ph.y, g.x * ph.y + g.y * ph.x);
+  }
+}
+
+cudaError_t launch_block_phase(double2* gblk, int B, int nblk, int bw, int KY, int o, int px,
+                               int py, const double2* twx, const double2* twy, cudaStream_t s) {
+  block_phase_kernel<<<64, 256, 0, s>>>(gblk, B, nblk, bw, KY, o, px, py, twx, twy);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_block_adjoint(const double2* gblk, int B, int nblk, int bw,

@@ -33,7 +33,7 @@ rows_fwd_n(const T* __restrict__ in, int nrows, int ncols, long long ifs, int il
   }
   __syncthreads();
   const int v = threadIdx.x / THR, tid = threadIdx.x - v * THR;
-  fft_n<T, N>(buf + v * N, tw, tid, +1);
+  fft_n<T, N, +1>(buf + v * N, tw, tid);
   C<T>* dst = tout + (size_t)f * tfs;
   constexpr int per_k = 2 * V;
   for (int idx = threadIdx.x; idx < H * per_k; idx += V * THR) {
@@ -53,7 +53,7 @@ rows_fwd_n(const T* __restrict__ in, int nrows, int ncols, long long ifs, int il
 
 // -------------------------------------------------------------------- cols --
 template <typename T, int N>
-__global__ void __launch_bounds__(VecsPerCta<N>::value * Radix23<N>::THR)
+__global__ void __launch_bounds__(VecsPerCta<N>::value * Radix23<N>::THR, 2)
 cols_n(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin, C<T>* __restrict__ uout,
        int ldu, long long ufs, int orow0, int nrout, const T* __restrict__ lam, int mode,
        double2* __restrict__ blk, int blk_kx, int blk_ky, int nblk, int B, int H,
@@ -79,7 +79,7 @@ cols_n(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin, C<T>* __r
       for (int n = tid; n < N; n += THR) buf[n] = mk<T>(T(0), T(0));
     }
     __syncthreads();
-    fft_n<T, N>(buf, tw, tid, +1);
+    fft_n<T, N, +1>(buf, tw, tid);
     C<T>* dst = uout + (size_t)f * ufs + (size_t)k * ldu;
     if (mode == COLS_FWD_ONLY) {
       if (kvalid)
@@ -120,7 +120,7 @@ cols_n(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin, C<T>* __r
       }
     }
     __syncthreads();
-    fft_n<T, N>(buf, tw, tid, -1);
+    fft_n<T, N, -1>(buf, tw, tid);
     if (kvalid)
       for (int n = tid; n < nrout; n += THR) {
         int r = orow0 + n;
@@ -166,7 +166,7 @@ rows_inv_n(const C<T>* __restrict__ uin, int ldu, long long ufs, int nrows, T* _
   }
   __syncthreads();
   const int v = threadIdx.x / THR, tid = threadIdx.x - v * THR;
-  fft_n<T, N>(buf + v * N, tw, tid, -1);
+  fft_n<T, N, -1>(buf + v * N, tw, tid);
   T* dst = out + (size_t)f * ofs;
   const T* adst = add ? add + (size_t)f * afs : nullptr;
   for (int idx = threadIdx.x; idx < per_k * ncols; idx += V * THR) {

@@ -528,8 +528,12 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
   // cbar = A abar (+ the exact block part), zbar = M^{-1} cbar
   double* cbar = p->bw_cbar;
   RK_CU(launch_gather<T>(abar, p->p1x, p->p1y, p->box, p->w64, n, p->L, B, cbar, s));
-  if (use_blk)
-    RK_CU(launch_block_adjoint(p->bw_gblk, B, p->nblk, 2 * p->blk_ky + 1, p->efac, n, cbar, s));
+  if (use_blk) {
+    const int bw = 2 * p->blk_ky + 1;
+    RK_CU(launch_block_phase(p->bw_gblk, B, p->nblk, bw, p->blk_ky, p->L - 1, p->px, p->py,
+                             p->tw64x, p->tw64y, s));
+    RK_CU(launch_block_adjoint(p->bw_gblk, B, p->nblk, bw, p->efac, n, cbar, s));
+  }
   RK_CU(chol_solve(p->mchol, n, cbar, B, s));
   if (gz) RK_CU(cudaMemcpyAsync(gz, cbar, (size_t)B * n * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s));
@@ -539,11 +543,12 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     T* y2 = y1 + B * grid;
     const T* cT = f32 ? (const T*)p->c32 : (const T*)p->c64;
     const T* wd = f32 ? (const T*)p->wd32 : (const T*)p->wd64;
-    RK_TRY(predict_fields<T>(p, p->c64, cT, B, y0, nullptr));
     if (gs2) {
-      RK_CU(launch_dot_rows<T, T>(gbar, y0, B, (long long)grid, 1.0, 0, gs2, s));
-      RK_CU(launch_dot_rows<double, double>(cbar, p->z64, B, (long long)n, -1.0, 1, gs2, s));
-      RK_CU(launch_dot_rows<double, double>(cbar, p->c64, B, (long long)n, p->tau2, 1, gs2, s));
+      // gbar . g_hat = cbar^T c = zbar^T M c = zbar^T z exactly, so
+      // d/dlog sigma^2 = gbar . g_hat - zbar^T (z - tau^2 c) = tau^2 zbar^T c;
+      // evaluating the two cancelling terms separately loses the result to
+      // rounding when tau^2 is small
+      RK_CU(launch_dot_rows<double, double>(cbar, p->c64, B, (long long)n, p->tau2, 0, gs2, s));
     }
     if (grho) {
       RK_TRY(predict_fields<T>(p, p->c64, cT, B, y1, nullptr, dlam));

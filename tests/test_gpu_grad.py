@@ -43,9 +43,8 @@ def test_adjoint_matches_oracle(rk, prec, tol, nu, L):
         p.set_obs(torch.from_numpy(xy).cuda(), torch.from_numpy(z).cuda())
         gz_, gr_, gs_ = p.backward(torch.from_numpy(gbar).cuda())
         gz_, gr_, gs_ = (t.cpu().numpy() for t in (gz_, gr_, gs_))
-    assert _rel(gz_, zb) <= tol
-    assert _rel(gr_, gr) <= tol, (gr_, gr)
-    assert _rel(gs_, gs) <= tol, (gs_, gs)
+    ez, er, es = _rel(gz_, zb), _rel(gr_, gr), _rel(gs_, gs)
+    assert ez <= tol and er <= tol and es <= tol, (ez, er, es)
 
 
 def test_adjoint_dot_product_identity(rk):
@@ -68,10 +67,14 @@ def test_adjoint_dot_product_identity(rk):
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
 def test_theta_gradients_match_finite_differences(rk, prec, tol):
-    # central differences of the GPU's own forward map in log range / log sigma^2
+    # central differences of the GPU's own FP64 forward map in log range and
+    # log sigma^2, on a well-conditioned neighbourhood (nu = 3/2, L = 2: the
+    # rounding of W stays far below the difference step; for nu = 5/2 with
+    # large L, cond(K_N) ~ 1e10+ makes finite differences of the computed map
+    # meaningless, and the adjoint is checked against the oracle's instead)
     ext = (0.0, 1.0, 0.0, 1.0)
-    nx, ny, n, L = 40, 36, 80, 3
-    nu, rho, s2, tau2 = 2.5, 0.18, 1.2, 1e-3
+    nx, ny, n, L = 40, 36, 80, 2
+    nu, rho, s2, tau2 = 1.5, 0.18, 1.2, 1e-2
     xy = torch.from_numpy(synth.sites_uniform(n, ext, 71)).cuda()
     z = torch.from_numpy(synth.normals((2, n), 72)).cuda()
     gb = torch.from_numpy(synth.normals((2, ny, nx), 73)).cuda()
@@ -89,8 +92,8 @@ def test_theta_gradients_match_finite_differences(rk, prec, tol):
     with rk.Plan(nx, ny, ext, nu, rho, s2, tau2, L, precision=prec) as p:
         p.set_obs(xy, z)
         _, gr, gs = p.backward(gb.to(p.dtype))
-    assert _rel(gr.cpu().numpy(), fd_r) <= tol
-    assert _rel(gs.cpu().numpy(), fd_s) <= tol
+    er, es = _rel(gr.cpu().numpy(), fd_r), _rel(gs.cpu().numpy(), fd_s)
+    assert er <= tol and es <= tol, (er, es)
 
 
 def test_autograd_gradcheck_fp64(rk):
@@ -108,7 +111,31 @@ def test_autograd_gradcheck_fp64(rk):
         return (y * proj).sum()
 
     try:
-        assert torch.autograd.gradcheck(f, (z, lr, ls), eps=1e-6, atol=1e-6, rtol=1e-5,
-                                        fast_mode=True)
+        # the scatter accumulates with float atomics, so repeated backward calls
+        # agree to rounding, not bit for bit
+        # eps = 1e-4: with 1e-6 the rounding of the neighbourhood solve in the
+        # re-created plans (cond K_N ~ 1e6 here) dominates the difference quotient
+        assert torch.autograd.gradcheck(f, (z, lr, ls), eps=1e-4, atol=1e-5, rtol=1e-4,
+                                        fast_mode=True, nondet_tol=1e-10)
     finally:
         clear_cache()
+
+
+def test_grad1024_geometry_fp32_against_fp64(rk):
+    # the differentiation workload's geometry (nu = 5/2, range 0.08, L = 3) on a
+    # smaller grid: the FP32 adjoint against the FP64 adjoint (itself checked
+    # against the oracle above)
+    ext = (0.0, 1.0, 0.0, 1.0)
+    m, n, B = 192, 2000, 4
+    xy = torch.from_numpy(synth.sites_uniform(n, ext, 81)).cuda()
+    z = torch.from_numpy(synth.normals((B, n), 82)).cuda()
+    gb = torch.from_numpy(synth.normals((B, m, m), 83)).cuda()
+    res = {}
+    for prec in ("fp64", "fp32"):
+        with rk.Plan(m, m, ext, 2.5, 0.08, 1.0, 1e-3, 3, precision=prec) as p:
+            p.set_obs(xy, z)
+            res[prec] = [t.cpu().numpy() for t in p.backward(gb.to(p.dtype))]
+    errs = {k: _rel(a, b) for k, a, b in zip(("z", "log_range", "log_sigma2"), res["fp32"],
+                                             res["fp64"])}
+    print("fp32 vs fp64 adjoint:", errs)
+    assert max(errs.values()) <= 1e-4, errs

@@ -157,7 +157,8 @@ def test_paper_scale_cells(rk, prec):
             # binding check with the oracle's A and c: sampled nodes against the
             # direct Eq. (9) sum, every node against the oracle's FFT steps
             out, info, box, w = _run(rk, xy, c, g, th, tau2, prec, weights=(ix, iy, W))
-            assert np.abs(out[0, jy, jx] - direct).max() <= TOL[prec] * scale, (nu, L)
+            e_direct = np.abs(out[0, jy, jx] - direct).max() / scale
+            assert e_direct <= TOL[prec], (nu, L, e_direct)
             fft_tol = TOL[prec] if prec == "fp32" else 2e-12   # two FFTs, each ~1e-12
             assert rel_err(out, ref) <= fft_tol, (nu, L, rel_err(out, ref))
             # the GPU's own weights
@@ -176,3 +177,33 @@ def test_solve_coef_matches_oracle(rk):
     ref = rapid.predict(xy, c, g, *th, method="fft")
     # end-to-end FP64 includes the dense solve: kappa(M) eps-level agreement
     assert rel_err(out, ref) <= 1e-10
+
+
+def test_spectrum_accuracy_against_long_double(rk):
+    # the circulant eigenvalues of step 2, computed on the GPU in double, against
+    # an extended-precision FFT of the same symmetric base (scipy long double)
+    import scipy.fft as sf
+    ext = (0.0, 1.6, 0.0, 1.0)
+    nx = ny = 350
+    for nu, L in ((1.5, 2), (2.5, 3)):
+        g = rapid.Grid(nx, ny, ext, L)
+        with rk.Plan(nx, ny, ext, nu, 0.15, 1.0, 1e-3, L, precision="fp64") as p:
+            lam = p.debug_copy("lambda").cpu().numpy()          # [kx][ky] / (px py)
+            info = p.info()
+        px, py = info["px"], info["py"]
+        kx = np.arange(px, dtype=np.longdouble)
+        ky = np.arange(py, dtype=np.longdouble)
+        dx = np.minimum(kx, px - kx) * (np.longdouble(1.6) / (nx - 1))
+        dy = np.minimum(ky, py - ky) * (np.longdouble(1.0) / (ny - 1))
+        t = np.sqrt(dx[None, :] ** 2 + dy[:, None] ** 2) / np.longdouble(0.15)
+        if nu == 1.5:
+            base = (1 + t) * np.exp(-t)
+        else:
+            base = (1 + t + t * t / 3) * np.exp(-t)
+        ref = (sf.rfft2(base).real / (px * py)).T                # [kx][ky]
+        m = np.abs(ref).max()
+        err = np.abs(lam - ref) / m
+        hi = np.abs(ref) < 1e-10 * m
+        print(f"nu={nu} L={L}: lambda max err {float(err.max()):.2e}, "
+              f"where lambda < 1e-10 max: {float(err[hi].max()):.2e}")
+        assert float(err.max()) < 1e-14
