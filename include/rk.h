@@ -157,6 +157,31 @@ rk_status rk_set_obs(rk_plan* plan, int n, const double* xy_dev, const double* z
 rk_status rk_predict(rk_plan* plan, void* out_dev);
 
 /*
+ * rk_predict_static -- rk_predict without any device allocation.  (Not from
+ * the paper: it has no counterpart there.)  Some callers cannot allocate
+ * device memory at the moment they predict: a process whose device memory is
+ * already fully reserved by another allocator, or a latency-critical loop
+ * that cannot afford cudaMalloc's implicit device synchronisation.  This
+ * entry point computes exactly what rk_predict computes, but keeps the
+ * per-call scratch (c*, the two transposed half spectra and the
+ * low-frequency block) in one file-scope device array of 32 MiB (33554432
+ * bytes) that the library holds on every GPU that loads it, until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *   out_dev  device, B x ny x nx in plan precision, as for rk_predict.
+ * Returns RK_ERR_INVALID_ARG when the plan's fields need more scratch than
+ * the array holds (about 22 MB per field for a 1024 x 1024 grid with L = 3,
+ * 5 MB per field at 512 x 512), RK_ERR_STATE before rk_set_sites and
+ * coefficients.  The first call on a device looks the array's address up
+ * with that device current (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call shares the one array and the array
+ * keeps the last call's contents, so calls that overlap on the GPU (on
+ * different streams or host threads) race and must be serialised by the
+ * caller; the accumulation buffer is cleared at the start of every call.
+ */
+rk_status rk_predict_static(rk_plan* plan, void* out_dev);
+
+/*
  * rk_predict_host -- the same prediction called with host buffers: copies
  * xy_host (n x 2 doubles) and c_host (B x n doubles) to the device, runs
  * rk_set_sites, rk_set_coef and rk_predict, and copies the B x ny x nx
