@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-secondary", action="store_true", help="skip the 1024^2 measurement")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 1024^2, conditional-simulation and adjoint measurements")
+    ap.add_argument("--backward-n", type=int, default=None,
+                    help="sites for the adjoint measurement (default: the workload's 20000)")
     return ap.parse_args()
 
 
@@ -163,13 +166,50 @@ class Arm:
             self.st.append((p, c, out))
         self.points = sum(kw["nx"] * kw["ny"] * B for _, kw, B in self.cells)
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        # one stream per cell: the cells are independent predictions
+        self.streams = [torch.cuda.Stream(device=dev) for _ in self.st]
+        self.graph = None
+        torch.cuda.synchronize()
+
+    def _issue(self):
+        """One step: per cell, weights (async site update), coefficients, prediction."""
+        torch = self.torch
+        cur = torch.cuda.current_stream()
+        fork = torch.cuda.Event()
+        fork.record(cur)
+        joins = []
+        for (p, c, out), s in zip(self.st, self.streams):
+            s.wait_event(fork)
+            with torch.cuda.stream(s):
+                p.set_sites_async(self.xy)
+                p.set_coef(c)
+                p.predict(out)
+                e = torch.cuda.Event()
+                e.record(s)
+            joins.append(e)
+        for e in joins:
+            cur.wait_event(e)
+
+    def capture(self):
+        """Capture one step (all cells, their streams forked and joined) in a CUDA graph."""
+        torch = self.torch
+        for _ in range(2):
+            self._issue()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._issue()
         torch.cuda.synchronize()
 
     def step(self):
-        for p, c, out in self.st:
-            p.set_sites(self.xy)
-            p.set_coef(c)
-            p.predict(out)
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._issue()
+
+    def check(self):
+        for p, _, _ in self.st:
+            p.check_sites()
 
     def timed(self, steps, warmup, world=1, profile=False):
         torch, rk = self.torch, self.rk
@@ -191,6 +231,7 @@ class Arm:
             b.record()
             b.synchronize()
             total += a.elapsed_time(b)
+            self.check()
         prof = None
         if profile:
             rk.profile_enable(False)
@@ -228,6 +269,90 @@ class Arm:
             p.close()
 
 
+def measure_cs(dev, steps, peaks, R=None):
+    """Conditional simulation, 512 x 512 grid, n = 5000 sites, R realisations per call."""
+    import torch
+    import paper_2605_29284_gb300 as rk
+    w = synth.WORKLOADS["cs512"]
+    R = R or w["R"]
+    xy = torch.from_numpy(synth.sites(w["sites"], w["n"], w["extent"],
+                                      synth.seed_for(w["config"]))).to(dev)
+    z = torch.from_numpy(synth.normals((1, w["n"]), synth.seed_for(w["config"], 1))).to(dev)
+    p = rk.Plan(w["nx"], w["ny"], w["extent"], w["nu"], w["rho"], w["sigma2"], w["tau2"], w["L"])
+    t0 = time.perf_counter()
+    p.set_obs(xy, z)                     # FP64 Cholesky of K_xx + tau^2 I (set-up)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    out = torch.empty((1, R, w["ny"], w["nx"]), dtype=torch.float32, device=dev)
+    p.simulate(R, 1, out)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    total = 0.0
+    rk.profile_read()
+    rk.profile_enable(True)
+    for i in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        p.simulate(R, 100 + i, out)
+        b.record()
+        b.synchronize()
+        total += a.elapsed_time(b)
+    rk.profile_enable(False)
+    prof = rk.profile_read()
+    roof, kernels = roofline(prof, steps, peaks)
+    info = p.info()
+    p.close()
+    sec = total / steps / 1e3
+    return {"realisations_per_s": R / sec,
+            "value": R * w["nx"] * w["ny"] / sec, "unit": "grid-point predictions/s",
+            "ms_per_call": sec * 1e3, "setup_cholesky_s": setup_s, "kernels": kernels,
+            "roofline": roof,
+            "config": {"grid": "512x512", "n": w["n"], "R": R, "nu": w["nu"], "range": w["rho"],
+                       "L": w["L"], "tau2": w["tau2"], "ce_torus": [info["qx"], info["qy"]]}}
+
+
+def measure_backward(dev, steps, peaks, n=None):
+    """Forward and adjoint on the 1024 x 1024 grid, 16 fields, nu = 5/2, L = 3."""
+    import torch
+    import paper_2605_29284_gb300 as rk
+    w = synth.WORKLOADS["grad1024"]
+    n = n or w["n"]
+    xy = torch.from_numpy(synth.sites(w["sites"], n, w["extent"],
+                                      synth.seed_for(w["config"]))).to(dev)
+    z = torch.from_numpy(synth.normals((w["B"], n), synth.seed_for(w["config"], 1))).to(dev)
+    gbar = torch.from_numpy(synth.normals((w["B"], w["ny"], w["nx"]),
+                                          synth.seed_for(w["config"], 2))).float().to(dev)
+    p = rk.Plan(w["nx"], w["ny"], w["extent"], w["nu"], w["rho"], w["sigma2"], w["tau2"], w["L"])
+    t0 = time.perf_counter()
+    p.set_obs(xy, z)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    y = p.predict()
+    p.backward(gbar)
+    torch.cuda.synchronize()
+    fwd = bwd = 0.0
+    for _ in range(steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        c = torch.cuda.Event(enable_timing=True)
+        a.record()
+        p.predict(y)
+        b.record()
+        p.backward(gbar)
+        c.record()
+        c.synchronize()
+        fwd += a.elapsed_time(b)
+        bwd += b.elapsed_time(c)
+    p.close()
+    return {"forward_ms": fwd / steps, "backward_ms": bwd / steps,
+            "value": w["B"] * w["nx"] * w["ny"] / ((fwd + bwd) / steps / 1e3),
+            "unit": "grid-point predictions/s (forward + adjoint)", "setup_cholesky_s": setup_s,
+            "config": {"grid": "1024x1024", "n": n, "fields": w["B"], "nu": w["nu"],
+                       "range": w["rho"], "L": w["L"], "tau2": w["tau2"]}}
+
+
 def roofline(prof, steps, peaks):
     hbm = peaks.get("hbm_gbs")
     src = "measured" if hbm else "fallback"
@@ -250,15 +375,23 @@ def run_ours(args, rank, world):
     main = Arm(args.workload, args.precision, dev, solve=args.workload != "grad1024")
     sampler = ClockSampler(dev.index)
     sampler.start()
-    total_ms, prof = main.timed(args.steps, args.warmup, world, profile=True)
+    # timed region 1: the step issued from the host with per-kernel CUDA events
+    # (the roofline's kernel durations); timed region 2: the same step replayed
+    # from a CUDA graph (the headline value)
+    prof_ms, prof = main.timed(args.steps, args.warmup, world, profile=True)
+    main.capture()
+    total_ms, _ = main.timed(args.steps, args.warmup, world)
     clocks = sampler.stop()
     value = main.points * args.steps * world / (total_ms / 1e3)
+    value_nograph = main.points * args.steps * world / (prof_ms / 1e3)
     roof, kernels = roofline(prof, args.steps, peaks)
+    main.graph = None
     e2e_value, h2d, d2h = main.e2e(max(3, args.steps // 2), 2)
     fp64 = None
     if not args.no_fp64 and args.precision == "fp32":
         a64 = Arm(args.workload, "fp64", dev, solve=args.workload != "grad1024")
         k64 = max(2, args.steps // 5)
+        a64.capture()
         ms64, _ = a64.timed(k64, 2, world)
         v64 = a64.points * k64 * world / (ms64 / 1e3)
         fp64 = {"value": v64, "unit": "grid-point predictions/s", "ms_per_step": ms64 / k64,
@@ -277,6 +410,9 @@ def run_ours(args, rank, world):
             "config": {"grid": "1024x1024", "n": 20000, "fields": 16, "nu": 2.5,
                        "range": 0.08, "L": 3, "coefficients": "seeded, sized like the solve"}}
         a.close()
+        secondary["cs512_simulate"] = measure_cs(dev, max(2, args.steps // 5), peaks)
+        secondary["grad1024_backward"] = measure_backward(dev, max(2, args.steps // 5), peaks,
+                                                          n=args.backward_n)
     launches_per_cell = 7 if args.precision == "fp32" else 5
     res = {
         "metric": METRIC, "value": value, "unit": "grid-point predictions/s",
@@ -288,6 +424,8 @@ def run_ours(args, rank, world):
                    "grid": f"{main.cells[0][1]['nx']}x{main.cells[0][1]['ny']}",
                    "n": int(main.xy_np.shape[0]), "fields_per_cell": main.cells[0][2],
                    "l2": "flushed between timed steps (256 MB write)",
+                   "issue": "one stream per cell, step replayed from a CUDA graph",
+                   "value_without_graph": value_nograph,
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "kernels": kernels,

@@ -117,6 +117,24 @@ rk_status rk_plan_get_info(const rk_plan* plan, rk_plan_info* info);
 rk_status rk_set_sites(rk_plan* plan, int n, const double* xy_dev);
 
 /*
+ * rk_set_sites_async -- rk_set_sites without synchronising: the extent check
+ * is latched in the plan's device status word instead of being returned.
+ * Sites outside the extent (or NaN) get zero weights.  rk_check_sites reports
+ * the latched result.  Lets a caller issue set-up and prediction for many
+ * plans on several streams without host round trips.  Sizes must not exceed
+ * those of an earlier rk_set_sites on this plan (else RK_ERR_STATE, because
+ * growing the plan's buffers would allocate and synchronise).
+ */
+rk_status rk_set_sites_async(rk_plan* plan, int n, const double* xy_dev);
+
+/*
+ * rk_check_sites -- synchronises with the plan's stream and returns
+ * RK_ERR_OBS_OUTSIDE if any site given to rk_set_sites_async since the last
+ * check lay outside the extent, RK_OK otherwise; clears the latch.
+ */
+rk_status rk_check_sites(rk_plan* plan);
+
+/*
  * rk_set_weights -- sets the sparse matrix A of Eq. (6) directly instead of
  * computing it (e.g. weights from another interpolation rule, or the
  * non-stationary variant discussed in Section 6 where k_i comes from a

@@ -90,6 +90,17 @@ class Plan:
         self.n = n
         self._xy = xy
 
+    def set_sites_async(self, xy):
+        """rk_set_sites without a host synchronisation (see check_sites)."""
+        xy = _dev_f64(xy)
+        self._call("rk_set_sites_async", int(xy.shape[0]), _ptr(xy))
+        self.n = xy.shape[0]
+        self._xy = xy
+
+    def check_sites(self):
+        """Raises RkError(RK_ERR_OBS_OUTSIDE) if an async site update saw an outside site."""
+        self._call("rk_check_sites")
+
     def set_weights(self, box, w):
         """Sets A of Eq. (6) directly: box (n x 2 int32 central boxes), w (n x M)."""
         box = torch.as_tensor(box).to(device="cuda", dtype=torch.int32).contiguous()

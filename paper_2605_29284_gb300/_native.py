@@ -56,6 +56,8 @@ _SIGS = {
     "rk_plan_get_info": [_vp, ctypes.POINTER(PlanInfo)],
     "rk_set_sites": [_vp, _int, _vp],
     "rk_set_weights": [_vp, _int, _vp, _vp],
+    "rk_set_sites_async": [_vp, _int, _vp],
+    "rk_check_sites": [_vp],
     "rk_set_coef": [_vp, _int, _vp],
     "rk_solve_coef": [_vp, _int, _vp],
     "rk_set_obs": [_vp, _int, _vp, _vp, _int],

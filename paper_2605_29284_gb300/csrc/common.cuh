@@ -133,6 +133,10 @@ struct rk_plan {
   double2* blk = nullptr; size_t blk_cap = 0;        // B x nblk exact block
   int ldt = 0, ldu = 0;
   int* d_flag = nullptr;                             // device status flag
+  int* d_sites_flag = nullptr;                       // latch of rk_set_sites_async
+  // side stream for the FP64 block GEMM, which runs beside the FP32 row pass
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // conditional simulation state
   int qx = 0, qy = 0;
   rk::FftPlan fqx, fqy;
@@ -146,6 +150,8 @@ struct rk_plan {
   double* bw_cbar = nullptr; size_t bw_cbar_cap = 0; // B x n
   void* bw_y = nullptr; size_t bw_y_bytes = 0;       // 3 x B x ny x nx
   double2* bw_gblk = nullptr; size_t bw_gblk_cap = 0;
+  double* bw_c = nullptr; size_t bw_c_cap = 0;       // 2 x B x n solved coefficients
+  void* bw_cT = nullptr;                              // their float copies
   bool have_adj = false;
   // device staging for rk_predict_host
   double* h_xy = nullptr; size_t h_xy_cap = 0;
@@ -256,5 +262,7 @@ cudaError_t launch_dot_rows(const Ta* a, const Tb* b, int B, long long len, doub
                             int accumulate, double* out, cudaStream_t s);
 cudaError_t launch_quad_dkxx(const double* xy, int n, const double* zbar, const double* c, int B,
                              double rho, double sigma2, int nu_code, double* out, cudaStream_t s);
+cudaError_t launch_matvec_dkxx(const double* xy, int n, const double* c, int B, double rho,
+                               double sigma2, int nu_code, double* out, cudaStream_t s);
 
 }  // namespace rk

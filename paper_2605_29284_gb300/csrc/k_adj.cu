@@ -261,6 +261,48 @@ __global__ void quad_dkxx_kernel(const double* __restrict__ xy, int n,
   }
 }
 
+// out[f][i] = sum_j K'(s_i, s_j) c[f][j]  (matrix-free K'_xx c, double).
+// One thread per site i, the sites j streamed through shared memory in tiles.
+constexpr int kMvT = 128;
+__global__ void matvec_dkxx_kernel(const double* __restrict__ xy, int n,
+                                   const double* __restrict__ c, int B, int f0, double rho,
+                                   double sigma2, int nu_code, double* __restrict__ out) {
+  __shared__ double sx[kMvT], sy[kMvT], sc[kQF][kMvT];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double xi = i < n ? xy[2 * i] : 0.0, yi = i < n ? xy[2 * i + 1] : 0.0;
+  double acc[kQF] = {0.0, 0.0, 0.0, 0.0};
+  for (int j0 = 0; j0 < n; j0 += kMvT) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < kMvT; t += blockDim.x) {
+      const int j = j0 + t;
+      sx[t] = j < n ? xy[2 * j] : 0.0;
+      sy[t] = j < n ? xy[2 * j + 1] : 0.0;
+      for (int q = 0; q < kQF; ++q)
+        sc[q][t] = (j < n && f0 + q < B) ? c[(size_t)(f0 + q) * n + j] : 0.0;
+    }
+    __syncthreads();
+    const int jn = n - j0 < kMvT ? n - j0 : kMvT;
+    for (int t = 0; t < jn; ++t) {
+      const double dx = xi - sx[t], dy = yi - sy[t];
+      const double k = sigma2 * matern_dlogrho<double>(sqrt(dx * dx + dy * dy) / rho, nu_code);
+#pragma unroll
+      for (int q = 0; q < kQF; ++q) acc[q] = fma(k, sc[q][t], acc[q]);
+    }
+  }
+  if (i < n)
+    for (int q = 0; q < kQF; ++q)
+      if (f0 + q < B) out[(size_t)(f0 + q) * n + i] = acc[q];
+}
+
+cudaError_t launch_matvec_dkxx(const double* xy, int n, const double* c, int B, double rho,
+                               double sigma2, int nu_code, double* out, cudaStream_t s) {
+  for (int f0 = 0; f0 < B; f0 += kQF) {
+    matvec_dkxx_kernel<<<(n + kMvT - 1) / kMvT, kMvT, 0, s>>>(xy, n, c, B, f0, rho, sigma2,
+                                                             nu_code, out);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_quad_dkxx(const double* xy, int n, const double* zbar, const double* c, int B,
                              double rho, double sigma2, int nu_code, double* out, cudaStream_t s) {
   const int tiles = (n + kQT - 1) / kQT;

@@ -122,40 +122,99 @@ cudaError_t chol_factor(double* a, int n, int* flag, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Forward then backward substitution for B right-hand sides x (B x n,
-// row-major), in place: x <- M^{-1} x.  One CTA per right-hand side.
-__global__ void chol_solve_kernel(const double* __restrict__ l, int n, double* x) {
-  double* v = x + (size_t)blockIdx.x * n;
-  __shared__ double piv;
-  __shared__ double red[32];
-  // L y = v
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) { v[j] /= l[(size_t)j * n + j]; piv = v[j]; }
-    __syncthreads();
-    const double yj = piv;
-    const double* col = l + (size_t)j * n;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) v[i] -= col[i] * yj;
-    __syncthreads();
+// Blocked triangular solves x <- M^{-1} x for B right-hand sides (x is
+// B x n, row-major per field), with the factor read once per solve: for each
+// 64-row block, a one-CTA solve of the diagonal block for all right-hand
+// sides, then one update of every later block (forward: L Y = X) or every
+// earlier block (backward: L^T X = Y) by a 64-wide product.
+constexpr int SB = 64;       // block rows
+constexpr int SF = 16;       // right-hand sides per CTA
+
+// diagonal block [k, k + nb): forward (L) or backward (L^T) substitution
+template <bool FWD>
+__global__ void solve_diag_kernel(const double* __restrict__ l, int n, int k, double* x, int B) {
+  __shared__ double Ls[SB][SB + 1];
+  __shared__ double Xs[SB][SF + 1];
+  const int nb = min(SB, n - k);
+  const int f0 = blockIdx.x * SF;
+  const int nf = min(SF, B - f0);
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int c = t / nb, r = t - c * nb;
+    Ls[r][c] = l[(size_t)(k + c) * n + k + r];
   }
-  // L^T w = y
-  for (int j = n - 1; j >= 0; --j) {
-    const double* col = l + (size_t)j * n;
-    double s = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) s += col[i] * v[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  for (int t = threadIdx.x; t < nb * nf; t += blockDim.x) {
+    const int f = t / nb, r = t - f * nb;
+    Xs[r][f] = x[(size_t)(f0 + f) * n + k + r];
+  }
+  __syncthreads();
+  for (int step = 0; step < nb; ++step) {
+    const int c = FWD ? step : nb - 1 - step;
+    if ((int)threadIdx.x < nf) Xs[c][threadIdx.x] /= Ls[c][c];
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-      v[j] = (v[j] - t) / col[j];
+    for (int t = threadIdx.x; t < nb * nf; t += blockDim.x) {
+      const int f = t / nb, r = t - f * nb;
+      if (FWD ? (r > c) : (r < c))
+        Xs[r][f] -= (FWD ? Ls[r][c] : Ls[c][r]) * Xs[c][f];
     }
     __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nb * nf; t += blockDim.x) {
+    const int f = t / nb, r = t - f * nb;
+    x[(size_t)(f0 + f) * n + k + r] = Xs[r][f];
+  }
+}
+
+// forward update: rows r in the 64-row tile of this CTA (r >= k + nb):
+//   x[f][r] -= sum_{c < nb} L(r, k + c) x[f][k + c]
+// backward update: rows r in the tile (r < k):
+//   x[f][r] -= sum_{c < nb} L(k + c, r) x[f][k + c]
+template <bool FWD>
+__global__ void solve_update_kernel(const double* __restrict__ l, int n, int k, double* x, int B) {
+  __shared__ double Ls[SB][SB + 1];   // [tile row][block column]
+  __shared__ double Ys[SB][SF + 1];
+  const int nb = min(SB, n - k);
+  const int r0 = FWD ? k + nb + blockIdx.x * SB : blockIdx.x * SB;
+  const int rend = FWD ? n : k;
+  const int nr = min(SB, rend - r0);
+  const int f0 = blockIdx.y * SF;
+  const int nf = min(SF, B - f0);
+  // coalesced loads: forward reads columns k + c (rows r0 + r contiguous),
+  // backward reads columns r0 + r (rows k + c contiguous)
+  for (int t = threadIdx.x; t < SB * nb; t += blockDim.x) {
+    const int c = FWD ? t / SB : t % nb, r = FWD ? t % SB : t / nb;
+    double v = 0.0;
+    if (r < nr) v = FWD ? l[(size_t)(k + c) * n + r0 + r] : l[(size_t)(r0 + r) * n + k + c];
+    Ls[r][c] = v;
+  }
+  for (int t = threadIdx.x; t < nb * nf; t += blockDim.x) {
+    const int f = t / nb, c = t - f * nb;
+    Ys[c][f] = x[(size_t)(f0 + f) * n + k + c];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr * nf; t += blockDim.x) {
+    const int f = t / nr, r = t - f * nr;
+    double s = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < nb; ++c) s = fma(Ls[r][c], Ys[c][f], s);
+    x[(size_t)(f0 + f) * n + r0 + r] -= s;
   }
 }
 
 cudaError_t chol_solve(const double* l, int n, double* x, int B, cudaStream_t s) {
-  chol_solve_kernel<<<B, 256, 0, s>>>(l, n, x);
+  const int fblocks = (B + SF - 1) / SF;
+  for (int k = 0; k < n; k += SB) {
+    const int nb = n - k < SB ? n - k : SB;
+    solve_diag_kernel<true><<<fblocks, 256, 0, s>>>(l, n, k, x, B);
+    const int rest = n - k - nb;
+    if (rest > 0)
+      solve_update_kernel<true><<<dim3((rest + SB - 1) / SB, fblocks), 256, 0, s>>>(l, n, k, x, B);
+  }
+  const int last = ((n - 1) / SB) * SB;
+  for (int k = last; k >= 0; k -= SB) {
+    solve_diag_kernel<false><<<fblocks, 256, 0, s>>>(l, n, k, x, B);
+    if (k > 0)
+      solve_update_kernel<false><<<dim3((k + SB - 1) / SB, fblocks), 256, 0, s>>>(l, n, k, x, B);
+  }
   return cudaGetLastError();
 }
 

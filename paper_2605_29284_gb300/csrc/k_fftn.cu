@@ -13,6 +13,15 @@ template <int N> struct VecsPerCta {
   static constexpr int value = thr >= 256 ? 2 : (512 / thr > 16 ? 16 : 512 / thr);
 };
 
+// The column pass holds one transform per CTA for the long lengths (so that
+// three CTAs, each with registers for the next field's prefetch, fit an SM).
+template <int N> struct ColVecs {
+  static constexpr int thr = Radix23<N>::THR;
+  static constexpr int value = thr >= 128 ? 1 : (512 / thr > 16 ? 16 : 512 / thr);
+  static constexpr int threads = value * thr;
+  static constexpr int min_blocks = threads <= 320 ? 3 : 2;
+};
+
 // ---------------------------------------------------------------- rows_fwd --
 template <typename T, int N>
 __global__ void __launch_bounds__(VecsPerCta<N>::value * Radix23<N>::THR)
@@ -53,12 +62,12 @@ rows_fwd_n(const T* __restrict__ in, int nrows, int ncols, long long ifs, int il
 
 // -------------------------------------------------------------------- cols --
 template <typename T, int N>
-__global__ void __launch_bounds__(VecsPerCta<N>::value * Radix23<N>::THR, 2)
+__global__ void __launch_bounds__(ColVecs<N>::threads, ColVecs<N>::min_blocks)
 cols_n(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin, C<T>* __restrict__ uout,
        int ldu, long long ufs, int orow0, int nrout, const T* __restrict__ lam, int mode,
        double2* __restrict__ blk, int blk_kx, int blk_ky, int nblk, int B, int H,
        const C<T>* __restrict__ tw) {
-  constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
+  constexpr int V = ColVecs<N>::value, THR = Radix23<N>::THR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* bufs = reinterpret_cast<C<T>*>(smem_raw);
   T* lcols = reinterpret_cast<T*>(bufs + V * N);
@@ -71,14 +80,27 @@ cols_n(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin, C<T>* __r
     for (int n = tid; n < N; n += THR) lcol[n] = lam[(size_t)k * N + n];
   const bool use_blk = blk != nullptr && kvalid && k <= blk_kx;
   const int bw = 2 * blk_ky + 1;
+  // software pipeline over this CTA's fields: the next field's column is
+  // loaded into registers while the current one is transformed
+  constexpr int PER = (N + THR - 1) / THR;
+  C<T> nxt[PER];
+  auto load_col = [&](int f) {
+    const C<T>* src = tin + (size_t)f * tfs + (size_t)k * ldt;
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const int n = tid + e * THR;
+      nxt[e] = (kvalid && n < nrin) ? src[n] : mk<T>(T(0), T(0));
+    }
+  };
+  if (blockIdx.y < B) load_col(blockIdx.y);
   for (int f = blockIdx.y; f < B; f += gridDim.y) {
-    if (kvalid) {
-      const C<T>* src = tin + (size_t)f * tfs + (size_t)k * ldt;
-      for (int n = tid; n < N; n += THR) buf[n] = n < nrin ? src[n] : mk<T>(T(0), T(0));
-    } else {
-      for (int n = tid; n < N; n += THR) buf[n] = mk<T>(T(0), T(0));
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const int n = tid + e * THR;
+      if (n < N) buf[n] = nxt[e];
     }
     __syncthreads();
+    if (f + (int)gridDim.y < B) load_col(f + gridDim.y);
     fft_n<T, N, +1>(buf, tw, tid);
     C<T>* dst = uout + (size_t)f * ufs + (size_t)k * ldu;
     if (mode == COLS_FWD_ONLY) {
@@ -202,13 +224,15 @@ cudaError_t go_cols(const C<T>* tin, int ldt, long long tfs, int nrin, C<T>* uou
                     long long ufs, int orow0, int nrout, const T* lam, int mode, double2* blk,
                     int blk_kx, int blk_ky, int nblk, int B, int H, const C<T>* tw,
                     cudaStream_t s) {
-  constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
+  constexpr int V = ColVecs<N>::value, THR = Radix23<N>::THR;
   const size_t sm = (sizeof(C<T>) + sizeof(T)) * V * N;
   static int smem_set = 0;
   auto kern = cols_n<T, N>;
   cudaError_t e = ensure_smem(kern, sm, smem_set);
   if (e != cudaSuccess) return e;
-  const int fgroups = B < 8 ? B : 8;
+  // each CTA keeps its lambda columns in shared memory for all of its fields:
+  // few field groups means lambda is read from HBM only that many times
+  const int fgroups = B < 2 ? B : 2;
   dim3 grid((H + V - 1) / V, fgroups);
   kern<<<grid, V * THR, sm, s>>>(tin, ldt, tfs, nrin, uout, ldu, ufs, orow0, nrout, lam, mode, blk,
                                  blk_kx, blk_ky, nblk, B, H, tw);

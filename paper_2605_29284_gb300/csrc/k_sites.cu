@@ -53,7 +53,8 @@ cudaError_t launch_kn_factor(double* kn, int L, double hx, double hy, double rho
 // with the Cholesky factor), one thread per site, double throughout.  Also
 // s_i = sqrt(max(0, sigma2 - k_i^T A_i)) for conditional simulation.
 template <int W>
-__global__ void weights_kernel(const double* __restrict__ xy, int n, double x0, double x1,
+__global__ void __launch_bounds__(128, 4)
+weights_kernel(const double* __restrict__ xy, int n, double x0, double x1,
                                double y0, double y1, double hx, double hy, int nx, int ny,
                                double rho, double sigma2, int nu_code,
                                const double* __restrict__ kn, int* __restrict__ box,
@@ -62,7 +63,9 @@ __global__ void weights_kernel(const double* __restrict__ xy, int n, double x0, 
   constexpr int M = W * W;
   constexpr int L = W / 2;
   __shared__ double Ls[M * M];
+  __shared__ double Linv[M];     // reciprocals of the factor's diagonal
   for (int i = threadIdx.x; i < M * M; i += blockDim.x) Ls[i] = kn[i];
+  for (int i = threadIdx.x; i < M; i += blockDim.x) Linv[i] = 1.0 / kn[i * M + i];
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -80,49 +83,57 @@ __global__ void weights_kernel(const double* __restrict__ xy, int n, double x0, 
   fy = fmin(fmax(fy, 0.0), (double)(ny - 2));
   const int ix = (int)fx, iy = (int)fy;
   const double u = gx - fx, v = gy - fy;
-  double k[M], z[M];
-#pragma unroll
+  // z = k_i, then the column-oriented substitutions L y = k, L^T w = y in
+  // place.  z lives in shared memory, [q][thread] (conflict-free): FP64
+  // arithmetic, not shared-memory bandwidth, bounds this kernel.
+  extern __shared__ double zs_raw[];
+  double* z = zs_raw + threadIdx.x;
+  const int S = blockDim.x;
+#pragma unroll 4
   for (int q = 0; q < M; ++q) {
     const int a = q % W, b = q / W;
     const double dx = ((double)(a - (L - 1)) - u) * hx;
     const double dy = ((double)(b - (L - 1)) - v) * hy;
-    k[q] = sigma2 * matern_phi<double>(sqrt(dx * dx + dy * dy) / rho, nu_code);
+    z[q * S] = sigma2 * matern_phi<double>(sqrt(dx * dx + dy * dy) / rho, nu_code);
   }
-  // L z = k, then L^T w = z (in place in z); unrolled only for small M
-#pragma unroll (M <= 16 ? M : 1)
-  for (int r = 0; r < M; ++r) {
-    double s = k[r];
-#pragma unroll (M <= 16 ? M : 4)
-    for (int c = 0; c < r; ++c) s -= Ls[r * M + c] * z[c];
-    z[r] = s / Ls[r * M + r];
+  double yy = 0.0;   // |L^{-1} k_i|^2 = k_i^T K_N^{-1} k_i = k_i^T W_i
+  for (int c = 0; c < M; ++c) {
+    const double zc = z[c * S] * Linv[c];
+    z[c * S] = zc;
+    yy = fma(zc, zc, yy);
+#pragma unroll 4
+    for (int r = c + 1; r < M; ++r) z[r * S] = fma(-Ls[r * M + c], zc, z[r * S]);
   }
-#pragma unroll (M <= 16 ? M : 1)
-  for (int r = M - 1; r >= 0; --r) {
-    double s = z[r];
-#pragma unroll (M <= 16 ? M : 4)
-    for (int c = r + 1; c < M; ++c) s -= Ls[c * M + r] * z[c];
-    z[r] = s / Ls[r * M + r];
+  for (int c = M - 1; c >= 0; --c) {
+    const double zc = z[c * S] * Linv[c];
+    z[c * S] = zc;
+#pragma unroll 4
+    for (int r = 0; r < c; ++r) z[r * S] = fma(-Ls[c * M + r], zc, z[r * S]);
   }
-  double kw = 0.0;
-#pragma unroll
   for (int q = 0; q < M; ++q) {
-    w64[(size_t)i * M + q] = z[q];
-    w32[(size_t)i * M + q] = (float)z[q];
-    kw += k[q] * z[q];
+    const double wq = z[q * S];
+    w64[(size_t)i * M + q] = wq;
+    w32[(size_t)i * M + q] = (float)wq;
   }
   box[2 * i] = ix;
   box[2 * i + 1] = iy;
-  ssd[i] = sqrt(fmax(0.0, sigma2 - kw));
+  ssd[i] = sqrt(fmax(0.0, sigma2 - yy));
 }
 
 cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, double* w64,
                            float* w32, double* ssd, int* flag, cudaStream_t s) {
   const int threads = 128, blocks = (n + threads - 1) / threads;
 #define RK_W(WW)                                                                               \
-  weights_kernel<WW><<<blocks, threads, 0, s>>>(xy, n, p->x0, p->x1, p->y0, p->y1, p->hx,   \
-                                                p->hy, p->nx, p->ny, p->rho, p->sigma2,     \
-                                                p->nu_code, p->kn_chol, box, w64, w32, ssd, \
-                                                flag)
+  {                                                                                            \
+    static int smem_set = 0;                                                                   \
+    const size_t sm = sizeof(double) * (WW) * (WW) * threads;                                  \
+    cudaError_t e = ensure_smem(weights_kernel<WW>, sm, smem_set);                             \
+    if (e != cudaSuccess) return e;                                                            \
+    weights_kernel<WW><<<blocks, threads, sm, s>>>(xy, n, p->x0, p->x1, p->y0, p->y1, p->hx, \
+                                                   p->hy, p->nx, p->ny, p->rho, p->sigma2,  \
+                                                   p->nu_code, p->kn_chol, box, w64, w32,   \
+                                                   ssd, flag);                              \
+  }
   switch (p->L) {
     case 1: RK_W(2); break;
     case 2: RK_W(4); break;

@@ -30,6 +30,41 @@ int smooth23(int n) {
   return (int)best;
 }
 
+// Torus length per dimension: any 2^a 3^b >= need gives the same linear
+// convolution, so pick the cheapest by a cost model of the FFT passes:
+// estimated instructions per point per radix stage (radix 9: 16, 8: 8.5,
+// 4: 7, 3: 8, 2: 5) plus 20 per point for memory traffic, times the length;
+// lengths without a compile-time specialisation cost 2.5x (generic kernels).
+// The model is used only with RK_TORUS=cost in the environment: measured on
+// GB300, 2304 ran slower than 2187 at 1024^2 (its 576-thread CTAs spill under
+// the two-CTA occupancy bound), so the default is the smallest length.
+constexpr int kSpecialised[] = {128, 729, 768, 1024, 1152, 2048, 2187, 2304};
+
+double torus_cost(int n) {
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  double per_point = 16.0 * (b / 2) + 8.0 * (b % 2) + 8.5 * (a / 3) +
+                     (a % 3 == 2 ? 7.0 : 0.0) + (a % 3 == 1 ? 5.0 : 0.0) + 20.0;
+  bool spec = false;
+  for (int s : kSpecialised) spec = spec || s == n;
+  return (double)n * per_point * (spec ? 1.0 : 2.5);
+}
+
+int choose_torus(int need) {
+  const int smallest = smooth23(need);
+  const char* env = getenv("RK_TORUS");
+  if (!env || strcmp(env, "cost") != 0) return smallest;
+  int best = smallest;
+  double best_cost = torus_cost(smallest);
+  for (int c = smooth23(smallest + 1); c <= kMaxTorus && c <= smallest + smallest / 3;
+       c = smooth23(c + 1)) {
+    const double cost = torus_cost(c);
+    if (cost < best_cost) { best = c; best_cost = cost; }
+  }
+  return best;
+}
+
 FftPlan make_fft_plan(int n) {
   FftPlan fp;
   memset(&fp, 0, sizeof(fp));
@@ -228,9 +263,13 @@ void free_plan(rk_plan* p) {
                   p->c64, p->c32, p->z64, p->mchol, p->cstar, p->tbuf, p->ubuf, p->blk,
                   p->d_flag, p->tw64qx, p->tw64qy, p->tw32qx, p->tw32qy, p->ce_sqrt64,
                   p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_c, p->h_out, p->xy, p->wd64,
-                  p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk};
+                  p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
+                  p->bw_c, p->bw_cT};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->side) cudaStreamDestroy(p->side);
 }
 
 // make sure the per-field scratch holds B fields
@@ -300,6 +339,22 @@ rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* 
   const size_t plane = (size_t)p->p1y * p->p1x;
   const double es = sizeof(T), cs = 2.0 * sizeof(T);
   const double nM = (double)p->n * p->M;
+  // the exact block (FP64 pipe) runs on the side stream while the scatter and
+  // the row pass (FP32 pipe) run on the plan's stream; the column pass waits
+  // for both
+  const bool use_blk = f32 && p->nblk > 0;
+  if (use_blk) {
+    RK_CU(cudaEventRecord(p->ev_fork, s));
+    RK_CU(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+    cudaStream_t s_main = s;
+    {
+      cudaStream_t s = p->side;
+      RK_PROF("block_gemm", (double)p->nblk * p->n * 16.0 + B * (p->n * 8.0 + p->nblk * 16.0));
+      RK_CU(launch_block_gemm(c64, B, p->n, efac, p->nblk, p->blk, s));
+    }
+    RK_CU(cudaEventRecord(p->ev_join, p->side));
+    (void)s_main;
+  }
   {
     RK_PROF("scatter", B * (plane * es + nM * 2 * es + p->n * es) + nM * es + p->n * 8.0);
     RK_CU(cudaMemsetAsync(cstar, 0, (size_t)B * plane * sizeof(T), s));
@@ -310,11 +365,7 @@ rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* 
     RK_CU(launch_rows_fwd<T>(cstar, p->p1y, p->p1x, (long long)plane, p->p1x, tb, p->ldt,
                              (long long)p->H * p->ldt, B, p->fpx, twx, p->H, s));
   }
-  const bool use_blk = f32 && p->nblk > 0;
-  if (use_blk) {
-    RK_PROF("block_gemm", (double)p->nblk * p->n * 16.0 + B * (p->n * 8.0 + p->nblk * 16.0));
-    RK_CU(launch_block_gemm(c64, B, p->n, efac, p->nblk, p->blk, s));
-  }
+  if (use_blk) RK_CU(cudaStreamWaitEvent(s, p->ev_join, 0));
   {
     RK_PROF("cols", B * ((double)p->H * p->p1y * cs + (double)p->H * p->ny * cs) +
                         (double)p->H * p->py * es);
@@ -488,10 +539,6 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     RK_TRY(dalloc(&p->bw_cbar, (size_t)B * n));
     p->bw_cbar_cap = (size_t)B * n;
   }
-  if (p->bw_y_bytes < 3 * B * grid * sizeof(T)) {
-    RK_TRY(dalloc_bytes(&p->bw_y, 3 * B * grid * sizeof(T)));
-    p->bw_y_bytes = 3 * B * grid * sizeof(T);
-  }
   const bool use_blk = f32 && p->nblk > 0;
   if (use_blk && p->bw_gblk_cap < (size_t)B * p->nblk) {
     RK_TRY(dalloc(&p->bw_gblk, (size_t)B * p->nblk));
@@ -538,24 +585,51 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
   if (gz) RK_CU(cudaMemcpyAsync(gz, cbar, (size_t)B * n * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s));
   if (grho || gs2) {
+    // The theta-gradients are evaluated as predictions of FP64-solved
+    // coefficients, so that the FP32 noise of zbar (which M^{-1} amplifies
+    // by up to 1 / tau^2) does not reach them.  With M c = z:
+    //   d/dlog sigma^2 = gbar . g_hat - zbar^T K_xx c = tau^2 zbar^T c
+    //                  = tau^2 gbar . g_hat(M^{-1} c),
+    //   zbar^T K'_xx c = gbar . g_hat(M^{-1} K'_xx c),
+    //   d/dlog rho     = gbar . (g_hat'(c) + g_hat_W'(c) - g_hat(M^{-1} K'_xx c)).
+    const size_t need_c = (size_t)2 * B * n;
+    if (p->bw_c_cap < need_c) {
+      RK_TRY(dalloc(&p->bw_c, need_c));
+      RK_TRY(dalloc_bytes(&p->bw_cT, need_c * sizeof(float)));
+      p->bw_c_cap = need_c;
+    }
+    if (p->bw_y_bytes < 4 * B * grid * sizeof(T)) {
+      RK_TRY(dalloc_bytes(&p->bw_y, 4 * B * grid * sizeof(T)));
+      p->bw_y_bytes = 4 * B * grid * sizeof(T);
+    }
     T* y0 = (T*)p->bw_y;
     T* y1 = y0 + B * grid;
     T* y2 = y1 + B * grid;
+    T* y3 = y2 + B * grid;
+    double* c2 = p->bw_c;
+    double* c3 = p->bw_c + (size_t)B * n;
+    float* c2f = (float*)p->bw_cT;
+    float* c3f = c2f + (size_t)B * n;
     const T* cT = f32 ? (const T*)p->c32 : (const T*)p->c64;
     const T* wd = f32 ? (const T*)p->wd32 : (const T*)p->wd64;
     if (gs2) {
-      // gbar . g_hat = cbar^T c = zbar^T M c = zbar^T z exactly, so
-      // d/dlog sigma^2 = gbar . g_hat - zbar^T (z - tau^2 c) = tau^2 zbar^T c;
-      // evaluating the two cancelling terms separately loses the result to
-      // rounding when tau^2 is small
-      RK_CU(launch_dot_rows<double, double>(cbar, p->c64, B, (long long)n, p->tau2, 0, gs2, s));
+      RK_CU(cudaMemcpyAsync(c2, p->c64, (size_t)B * n * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+      RK_CU(chol_solve(p->mchol, n, c2, B, s));
+      if (f32) RK_CU(launch_convert<float>(c2, c2f, (size_t)B * n, s));
+      RK_TRY(predict_fields<T>(p, c2, f32 ? (const T*)c2f : (const T*)c2, B, y0, nullptr));
+      RK_CU(launch_dot_rows<T, T>(gbar, y0, B, (long long)grid, p->tau2, 0, gs2, s));
     }
     if (grho) {
+      RK_CU(launch_matvec_dkxx(p->xy, n, p->c64, B, p->rho, p->sigma2, p->nu_code, c3, s));
+      RK_CU(chol_solve(p->mchol, n, c3, B, s));
+      if (f32) RK_CU(launch_convert<float>(c3, c3f, (size_t)B * n, s));
       RK_TRY(predict_fields<T>(p, p->c64, cT, B, y1, nullptr, dlam));
       RK_TRY(predict_fields<T>(p, p->c64, cT, B, y2, nullptr, nullptr, wd, p->efac_d));
+      RK_TRY(predict_fields<T>(p, c3, f32 ? (const T*)c3f : (const T*)c3, B, y3, nullptr));
       RK_CU(launch_dot_rows<T, T>(gbar, y1, B, (long long)grid, 1.0, 0, grho, s));
       RK_CU(launch_dot_rows<T, T>(gbar, y2, B, (long long)grid, 1.0, 1, grho, s));
-      RK_CU(launch_quad_dkxx(p->xy, n, cbar, p->c64, B, p->rho, p->sigma2, p->nu_code, grho, s));
+      RK_CU(launch_dot_rows<T, T>(gbar, y3, B, (long long)grid, -1.0, 1, grho, s));
     }
   }
   return RK_OK;
@@ -608,8 +682,8 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
   p->nu = nu; p->rho = range; p->sigma2 = sigma2; p->tau2 = tau2; p->nu_code = nu_code;
   p->p1x = nx + 2 * (L - 1);
   p->p1y = ny + 2 * (L - 1);
-  p->px = smooth23(2 * (nx + L - 2) > p->p1x ? 2 * (nx + L - 2) : p->p1x);
-  p->py = smooth23(2 * (ny + L - 2) > p->p1y ? 2 * (ny + L - 2) : p->p1y);
+  p->px = choose_torus(2 * (nx + L - 2) > p->p1x ? 2 * (nx + L - 2) : p->p1x);
+  p->py = choose_torus(2 * (ny + L - 2) > p->p1y ? 2 * (ny + L - 2) : p->p1y);
   p->H = p->px / 2 + 1;
   p->ldt = p->p1y;
   p->ldu = p->p1y;   // the adjoint writes p1y rows
@@ -619,6 +693,14 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
   rk_status st = RK_OK;
   do {
     if ((st = dalloc(&p->d_flag, 1)) != RK_OK) break;
+    if ((st = dalloc(&p->d_sites_flag, 1)) != RK_OK) break;
+    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      st = RK_ERR_CUDA;
+      break;
+    }
+    if (cudaMemset(p->d_sites_flag, 0, sizeof(int)) != cudaSuccess) { st = RK_ERR_CUDA; break; }
     if ((st = upload_twiddles(p->px, &p->tw64x, &p->tw32x)) != RK_OK) break;
     if ((st = upload_twiddles(p->py, &p->tw64y, &p->tw32y)) != RK_OK) break;
     if ((st = compute_spectrum(p, 0, &p->lam64, &p->lam32)) != RK_OK) break;
@@ -675,6 +757,7 @@ int rk_profile_read(rk_profile_entry* out, int max) {
 rk_status rk_plan_destroy(rk_plan* p) {
   if (!p) return RK_OK;
   cudaStreamSynchronize(p->stream);
+  if (p->side) cudaStreamSynchronize(p->side);
   free_plan(p);
   delete p;
   return RK_OK;
@@ -743,6 +826,29 @@ rk_status rk_set_sites(rk_plan* p, int n, const double* xy) {
     RK_CU(launch_block_factors(p->box, p->w64, n, p, p->efac, p->stream));
   p->n = n;
   return RK_OK;
+}
+
+rk_status rk_set_sites_async(rk_plan* p, int n, const double* xy) {
+  if (!p || n < 1 || !xy) return RK_ERR_INVALID_ARG;
+  if (n > p->n_cap) return RK_ERR_STATE;
+  RK_TRY(ensure_sites(p, n));   // no growth: only resets the derived state
+  p->xy_valid = true;
+  RK_CU(cudaMemcpyAsync(p->xy, xy, (size_t)2 * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                        p->stream));
+  RK_CU(launch_weights(p->xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_sites_flag, p->stream));
+  if (p->precision == RK_FP32 && p->nblk > 0)
+    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->efac, p->stream));
+  p->n = n;
+  return RK_OK;
+}
+
+rk_status rk_check_sites(rk_plan* p) {
+  if (!p) return RK_ERR_INVALID_ARG;
+  int flag = 0;
+  RK_CU(cudaMemcpyAsync(&flag, p->d_sites_flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  RK_CU(cudaStreamSynchronize(p->stream));
+  RK_CU(cudaMemsetAsync(p->d_sites_flag, 0, sizeof(int), p->stream));
+  return (flag & 2) ? RK_ERR_OBS_OUTSIDE : RK_OK;
 }
 
 rk_status rk_set_coef(rk_plan* p, int B, const double* c) {

@@ -207,3 +207,30 @@ def test_spectrum_accuracy_against_long_double(rk):
         print(f"nu={nu} L={L}: lambda max err {float(err.max()):.2e}, "
               f"where lambda < 1e-10 max: {float(err[hi].max()):.2e}")
         assert float(err.max()) < 1e-14
+
+
+def test_async_site_update_matches_and_latches_outside_sites(rk):
+    ext = (0.0, 1.0, 0.0, 1.0)
+    th, tau2 = (1.5, 0.2, 1.0), 1e-3
+    xy, z, c, g = case(300, 48, 40, ext, *th, tau2, 2, seed=91)
+    ref = rapid.predict(xy, c, g, *th, method="bttb")
+    with rk.Plan(48, 40, ext, *th, tau2, 2, precision="fp32") as p:
+        p.set_sites(torch.from_numpy(xy).cuda())          # sizes the buffers
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            p.set_sites_async(torch.from_numpy(xy).cuda())
+            p.set_coef(torch.from_numpy(c).cuda())
+            out = p.predict()
+        s.synchronize()
+        p.check_sites()
+        assert rel_err(out.double().cpu().numpy(), ref) <= TOL["fp32"]
+        bad = xy.copy()
+        bad[5] = (1.5, 0.5)
+        p.set_sites_async(torch.from_numpy(bad).cuda())
+        with pytest.raises(rk.RkError) as e:
+            p.check_sites()
+        assert e.value.name == "RK_ERR_OBS_OUTSIDE"
+        p.check_sites()                                   # the latch was cleared
+        with pytest.raises(rk.RkError) as e:
+            p.set_sites_async(torch.from_numpy(np.vstack([xy, xy])).cuda())   # would grow
+        assert e.value.name == "RK_ERR_STATE"
