@@ -146,11 +146,17 @@ struct rk_plan {
   void* cs_buf = nullptr; size_t cs_bytes = 0;
   // adjoint state (built on the first rk_predict_backward)
   double* wd64 = nullptr; float* wd32 = nullptr;   // W' = dW / dlog rho, n x M
-  double2* efac_d = nullptr;                        // block factors of W'
-  double* bw_cbar = nullptr; size_t bw_cbar_cap = 0; // B x n
+  // the gradient path's exact block (a smaller eta than the forward block:
+  // the theta-gradients contract predictions of rough coefficient vectors)
+  int gblk_kx = -1, gblk_ky = 0, ngblk = 0;
+  double2* efac_g = nullptr;                        // block factors of W, n x ngblk
+  double2* efac_d = nullptr;                        // block factors of W', n x ngblk
+  double2* gblk = nullptr; size_t gblk_cap = 0;     // B x ngblk block GEMM result
+  double* bw_dk = nullptr; size_t bw_dk_cap = 0;     // per-tile partials of K'_xx c
+  double* bw_cbar = nullptr; size_t bw_cbar_cap = 0; // 3 x B x n: zbar, M^-1 c, M^-1 K' c
   void* bw_y = nullptr; size_t bw_y_bytes = 0;       // 3 x B x ny x nx
   double2* bw_gblk = nullptr; size_t bw_gblk_cap = 0;
-  double* bw_c = nullptr; size_t bw_c_cap = 0;       // 2 x B x n solved coefficients
+  size_t bw_c_cap = 0;                               // capacity of bw_cT (values)
   void* bw_cT = nullptr;                              // their float copies
   bool have_adj = false;
   // device staging for rk_predict_host
@@ -217,6 +223,7 @@ cudaError_t launch_set_weights(const int* box_in, const double* w_in, int n, con
                                int* box, double* w64, float* w32, double* ssd, int* flag,
                                cudaStream_t s);
 cudaError_t launch_block_factors(const int* box, const double* w64, int n, const rk_plan* p,
+                                 int kx, int ky,
                                  double2* efac, cudaStream_t s);
 cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac, int nblk,
                               double2* blk, cudaStream_t s);
@@ -229,7 +236,8 @@ cudaError_t launch_convert(const double* src, T* dst, size_t count, cudaStream_t
 // dense FP64 Cholesky of M = K_xx + tau2 I and solves
 cudaError_t build_obs_cov(const double* xy, int n, const rk_plan* p, double* a, cudaStream_t s);
 cudaError_t chol_factor(double* a, int n, int* flag, cudaStream_t s);
-cudaError_t chol_solve(const double* l, int n, double* x, int B, cudaStream_t s);
+cudaError_t chol_mirror(double* a, int n, cudaStream_t s);
+cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s);
 
 // conditional simulation
 template <typename T>
@@ -260,9 +268,9 @@ cudaError_t launch_block_adjoint(const double2* gblk, int B, int nblk, int bw,
 template <typename Ta, typename Tb>
 cudaError_t launch_dot_rows(const Ta* a, const Tb* b, int B, long long len, double scale,
                             int accumulate, double* out, cudaStream_t s);
-cudaError_t launch_quad_dkxx(const double* xy, int n, const double* zbar, const double* c, int B,
-                             double rho, double sigma2, int nu_code, double* out, cudaStream_t s);
+size_t dkxx_scratch_doubles(int n, int B);
 cudaError_t launch_matvec_dkxx(const double* xy, int n, const double* c, int B, double rho,
-                               double sigma2, int nu_code, double* out, cudaStream_t s);
+                               double sigma2, int nu_code, double* part, double* out,
+                               cudaStream_t s);
 
 }  // namespace rk

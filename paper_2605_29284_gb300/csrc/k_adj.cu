@@ -210,104 +210,107 @@ cudaError_t launch_dot_rows(const Ta* a, const Tb* b, int B, long long len, doub
   return cudaGetLastError();
 }
 
-// out[f] -= sum_{i,j} zbar[f][i] K'(s_i, s_j) c[f][j]  (matrix-free, double).
-// Tiles of 64 x 64 site pairs; each CTA adds its partial sums atomically.
-constexpr int kQT = 64;
-constexpr int kQF = 4;
-__global__ void quad_dkxx_kernel(const double* __restrict__ xy, int n,
-                                 const double* __restrict__ zbar, const double* __restrict__ c,
-                                 int B, double rho, double sigma2, int nu_code,
-                                 double* __restrict__ out) {
-  __shared__ double sx[kQT], sy[kQT], sc[kQF][kQT];
-  const int i0 = blockIdx.x * kQT, j0 = blockIdx.y * kQT, f0 = blockIdx.z * kQF;
-  for (int t = threadIdx.x; t < kQT; t += blockDim.x) {
-    const int j = j0 + t;
-    sx[t] = j < n ? xy[2 * j] : 0.0;
-    sy[t] = j < n ? xy[2 * j + 1] : 0.0;
-    for (int q = 0; q < kQF; ++q) sc[q][t] = (j < n && f0 + q < B) ? c[(size_t)(f0 + q) * n + j] : 0.0;
+// out[f] = K'_xx c[f], K'(s_i, s_j) = sigma^2 (-t phi'(t)), t = |s_i - s_j| / rho
+// (the log-range derivative of the observation covariance), matrix-free in
+// double.  K'_xx is symmetric, so each CTA evaluates one 64 x 64 tile (I, J),
+// I <= J, of it once and forms both K'_IJ c_J (for rows I) and K'_IJ^T c_I
+// (for rows J).  The kernel values are the costly part (an FP64 exponential
+// each), so every tile serves all fields of a pass.  The partial vectors go
+// to a per-tile scratch and a second kernel sums them in a fixed order, so
+// the result does not depend on the CTA schedule.
+constexpr int kDT = 64;      // sites per tile
+constexpr int kDF = 8;       // fields per pass over a tile
+__global__ void __launch_bounds__(256) matvec_dkxx_kernel(const double* __restrict__ xy, int n,
+                                                          const double* __restrict__ c, int B,
+                                                          double inv_rho, double sigma2,
+                                                          int nu_code,
+                                                          double* __restrict__ part) {
+  __shared__ double Ks[kDT][kDT + 1];
+  __shared__ double xi[kDT], yi[kDT], xj[kDT], yj[kDT];
+  __shared__ double cI[kDF][kDT], cJ[kDF][kDT];
+  const int tile = blockIdx.x;
+  int J = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);      // tiles (I, J), I <= J
+  while ((J + 1) * (J + 2) / 2 <= tile) ++J;
+  while (J * (J + 1) / 2 > tile) --J;
+  const int I = tile - J * (J + 1) / 2;
+  const int i0 = I * kDT, j0 = J * kDT;
+  if (threadIdx.x < kDT) {
+    const int t = threadIdx.x;
+    xi[t] = i0 + t < n ? xy[2 * (i0 + t)] : 0.0;
+    yi[t] = i0 + t < n ? xy[2 * (i0 + t) + 1] : 0.0;
+    xj[t] = j0 + t < n ? xy[2 * (j0 + t)] : 0.0;
+    yj[t] = j0 + t < n ? xy[2 * (j0 + t) + 1] : 0.0;
   }
   __syncthreads();
-  double acc[kQF] = {0.0, 0.0, 0.0, 0.0};
-  // each thread: one i, a quarter of the j's
-  const int ti = threadIdx.x % kQT, tj = threadIdx.x / kQT;
-  const int nthr_j = blockDim.x / kQT;
-  const int i = i0 + ti;
-  if (i < n) {
-    const double xi = xy[2 * i], yi = xy[2 * i + 1];
-    double part[kQF] = {0.0, 0.0, 0.0, 0.0};
-    for (int t = tj; t < kQT; t += nthr_j) {
-      if (j0 + t >= n) break;
-      const double dx = xi - sx[t], dy = yi - sy[t];
-      const double k = sigma2 * matern_dlogrho<double>(sqrt(dx * dx + dy * dy) / rho, nu_code);
-#pragma unroll
-      for (int q = 0; q < kQF; ++q) part[q] += k * sc[q][t];
-    }
-#pragma unroll
-    for (int q = 0; q < kQF; ++q)
-      if (f0 + q < B) acc[q] = zbar[(size_t)(f0 + q) * n + i] * part[q];
-  }
-  __shared__ double red[kQF][32];
-#pragma unroll
-  for (int q = 0; q < kQF; ++q) {
-    double v = acc[q];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < kQF) {
+  for (int e = threadIdx.x; e < kDT * kDT; e += blockDim.x) {
+    const int a = e / kDT, b = e % kDT;
     double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-    if (f0 + threadIdx.x < B) atomicAdd(out + f0 + threadIdx.x, -v);
+    if (i0 + a < n && j0 + b < n) {
+      const double dx = xi[a] - xj[b], dy = yi[a] - yj[b];
+      v = sigma2 * matern_dlogrho<double>(sqrt(dx * dx + dy * dy) * inv_rho, nu_code);
+    }
+    Ks[a][b] = v;
+  }
+  const bool diag = I == J;
+  for (int f0 = 0; f0 < B; f0 += kDF) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kDF * kDT; e += blockDim.x) {
+      const int f = e / kDT, t = e % kDT;
+      const bool fo = f0 + f < B;
+      cI[f][t] = fo && i0 + t < n ? c[(size_t)(f0 + f) * n + i0 + t] : 0.0;
+      cJ[f][t] = fo && j0 + t < n ? c[(size_t)(f0 + f) * n + j0 + t] : 0.0;
+    }
+    __syncthreads();
+    // rows: (f, a) -> sum_b K[a][b] cJ[f][b]; columns: (f, b) -> sum_a K[a][b] cI[f][a]
+    for (int e = threadIdx.x; e < 2 * kDF * kDT; e += blockDim.x) {
+      const bool rows = e < kDF * kDT;
+      const int ee = rows ? e : e - kDF * kDT;
+      const int f = ee / kDT, t = ee % kDT;
+      if (f0 + f >= B || (!rows && diag)) continue;
+      double acc = 0.0;
+      if (rows) {
+#pragma unroll 8
+        for (int b = 0; b < kDT; ++b) acc = fma(Ks[t][b], cJ[f][b], acc);
+      } else {
+#pragma unroll 8
+        for (int a = 0; a < kDT; ++a) acc = fma(Ks[a][t], cI[f][a], acc);
+      }
+      // part[tile][side][f][t], side 0: rows I, side 1: rows J
+      part[(((size_t)tile * 2 + (rows ? 0 : 1)) * B + f0 + f) * kDT + t] = acc;
+    }
   }
 }
 
-// out[f][i] = sum_j K'(s_i, s_j) c[f][j]  (matrix-free K'_xx c, double).
-// One thread per site i, the sites j streamed through shared memory in tiles.
-constexpr int kMvT = 128;
-__global__ void matvec_dkxx_kernel(const double* __restrict__ xy, int n,
-                                   const double* __restrict__ c, int B, int f0, double rho,
-                                   double sigma2, int nu_code, double* __restrict__ out) {
-  __shared__ double sx[kMvT], sy[kMvT], sc[kQF][kMvT];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const double xi = i < n ? xy[2 * i] : 0.0, yi = i < n ? xy[2 * i + 1] : 0.0;
-  double acc[kQF] = {0.0, 0.0, 0.0, 0.0};
-  for (int j0 = 0; j0 < n; j0 += kMvT) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < kMvT; t += blockDim.x) {
-      const int j = j0 + t;
-      sx[t] = j < n ? xy[2 * j] : 0.0;
-      sy[t] = j < n ? xy[2 * j + 1] : 0.0;
-      for (int q = 0; q < kQF; ++q)
-        sc[q][t] = (j < n && f0 + q < B) ? c[(size_t)(f0 + q) * n + j] : 0.0;
-    }
-    __syncthreads();
-    const int jn = n - j0 < kMvT ? n - j0 : kMvT;
-    for (int t = 0; t < jn; ++t) {
-      const double dx = xi - sx[t], dy = yi - sy[t];
-      const double k = sigma2 * matern_dlogrho<double>(sqrt(dx * dx + dy * dy) / rho, nu_code);
-#pragma unroll
-      for (int q = 0; q < kQF; ++q) acc[q] = fma(k, sc[q][t], acc[q]);
-    }
+// out[f][K * 64 + t] = sum_{J >= K} part(K, J)[0][f][t] + sum_{I < K} part(I, K)[1][f][t]
+__global__ void dkxx_reduce_kernel(const double* __restrict__ part, int n, int B, int T,
+                                   double* __restrict__ out) {
+  const int K = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
+  const int i = K * kDT + t;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int J = K; J < T; ++J) {
+    const size_t tile = (size_t)J * (J + 1) / 2 + K;
+    acc += part[((tile * 2 + 0) * B + f) * kDT + t];
   }
-  if (i < n)
-    for (int q = 0; q < kQF; ++q)
-      if (f0 + q < B) out[(size_t)(f0 + q) * n + i] = acc[q];
+  for (int I = 0; I < K; ++I) {
+    const size_t tile = (size_t)K * (K + 1) / 2 + I;
+    acc += part[((tile * 2 + 1) * B + f) * kDT + t];
+  }
+  out[(size_t)f * n + i] = acc;
+}
+
+size_t dkxx_scratch_doubles(int n, int B) {
+  const size_t T = (size_t)(n + kDT - 1) / kDT;
+  return T * (T + 1) / 2 * 2 * (size_t)B * kDT;
 }
 
 cudaError_t launch_matvec_dkxx(const double* xy, int n, const double* c, int B, double rho,
-                               double sigma2, int nu_code, double* out, cudaStream_t s) {
-  for (int f0 = 0; f0 < B; f0 += kQF) {
-    matvec_dkxx_kernel<<<(n + kMvT - 1) / kMvT, kMvT, 0, s>>>(xy, n, c, B, f0, rho, sigma2,
-                                                             nu_code, out);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_quad_dkxx(const double* xy, int n, const double* zbar, const double* c, int B,
-                             double rho, double sigma2, int nu_code, double* out, cudaStream_t s) {
-  const int tiles = (n + kQT - 1) / kQT;
-  dim3 grid(tiles, tiles, (B + kQF - 1) / kQF);
-  quad_dkxx_kernel<<<grid, 256, 0, s>>>(xy, n, zbar, c, B, rho, sigma2, nu_code, out);
+                               double sigma2, int nu_code, double* part, double* out,
+                               cudaStream_t s) {
+  const int T = (n + kDT - 1) / kDT;
+  matvec_dkxx_kernel<<<(unsigned)((long long)T * (T + 1) / 2), 256, 0, s>>>(
+      xy, n, c, B, 1.0 / rho, sigma2, nu_code, part);
+  dkxx_reduce_kernel<<<dim3(T, B), kDT, 0, s>>>(part, n, B, T, out);
   return cudaGetLastError();
 }
 

@@ -122,98 +122,131 @@ cudaError_t chol_factor(double* a, int n, int* flag, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Blocked triangular solves x <- M^{-1} x for B right-hand sides (x is
-// B x n, row-major per field), with the factor read once per solve: for each
-// 64-row block, a one-CTA solve of the diagonal block for all right-hand
-// sides, then one update of every later block (forward: L Y = X) or every
-// earlier block (backward: L^T X = Y) by a 64-wide product.
-constexpr int SB = 64;       // block rows
-constexpr int SF = 16;       // right-hand sides per CTA
-
-// diagonal block [k, k + nb): forward (L) or backward (L^T) substitution
-template <bool FWD>
-__global__ void solve_diag_kernel(const double* __restrict__ l, int n, int k, double* x, int B) {
-  __shared__ double Ls[SB][SB + 1];
-  __shared__ double Xs[SB][SF + 1];
-  const int nb = min(SB, n - k);
-  const int f0 = blockIdx.x * SF;
-  const int nf = min(SF, B - f0);
-  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-    const int c = t / nb, r = t - c * nb;
-    Ls[r][c] = l[(size_t)(k + c) * n + k + r];
-  }
-  for (int t = threadIdx.x; t < nb * nf; t += blockDim.x) {
-    const int f = t / nb, r = t - f * nb;
-    Xs[r][f] = x[(size_t)(f0 + f) * n + k + r];
+// Copy the lower triangle of the factor into the upper one, a[j n + i] =
+// a[i n + j] for i < j, so that both triangular solves read L column by
+// column: column k + c then holds L(r, k + c) for r > k + c and
+// L(k + c, r) for r < k + c, each contiguous in r.
+constexpr int MT = 32;
+__global__ void chol_mirror_kernel(double* a, int n) {
+  __shared__ double t[MT][MT + 1];
+  const int tile = blockIdx.x;
+  int I = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);      // I >= J
+  while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+  while (I * (I + 1) / 2 > tile) --I;
+  const int J = tile - I * (I + 1) / 2;
+  const int r0 = I * MT, c0 = J * MT;                         // lower block (r0, c0)
+  for (int e = threadIdx.x; e < MT * MT; e += blockDim.x) {
+    const int c = e / MT, r = e % MT;
+    if (r0 + r < n && c0 + c < n) t[r][c] = a[(size_t)(c0 + c) * n + r0 + r];
   }
   __syncthreads();
+  // upper block (c0, r0): element (c0 + c, r0 + r) = L(r0 + r, c0 + c)
+  for (int e = threadIdx.x; e < MT * MT; e += blockDim.x) {
+    const int r = e / MT, c = e % MT;
+    if (r0 + r < n && c0 + c < n && c0 + c < r0 + r) a[(size_t)(r0 + r) * n + c0 + c] = t[r][c];
+  }
+}
+
+cudaError_t chol_mirror(double* a, int n, cudaStream_t s) {
+  const int T = (n + MT - 1) / MT;
+  chol_mirror_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(a, n);
+  return cudaGetLastError();
+}
+
+// Blocked triangular solves x <- M^{-1} x = L^{-T} L^{-1} x for B right-hand
+// sides (x is B x n, one row per field), on a factor mirrored by chol_mirror.
+// Per 64-row block k, in block order (forward) or reverse order (backward):
+//   diagonal: substitution with L_kk (forward) or L_kk^T (backward), one warp
+//     per right-hand side, lane l holding rows l and l + 32 of the block;
+//   update:   every later (forward) or earlier (backward) row r loses
+//     sum_c a[(k + c) n + r] x[k + c], i.e. L(r, k + c) or L(k + c, r),
+//     one thread per row and SF right-hand sides.
+// FP64 throughput bounds both (n^2 B multiply-adds per solve); the split
+// into many CTAs keeps every SM's FP64 pipe fed.
+constexpr int SB = 64;       // block rows
+constexpr int SF = 4;        // right-hand sides per update thread
+constexpr int SU = 128;      // rows per update CTA
+
+template <bool FWD>
+__global__ void solve_diag_kernel(const double* __restrict__ a, int n, int k, double* x, int B) {
+  __shared__ double Ls[SB * SB];            // Ls[c * SB + r] = a[(k + c) n + k + r]
+  __shared__ double rd[SB];                 // 1 / L(k + c, k + c)
+  const int nb = min(SB, n - k);
+#pragma unroll 8
+  for (int t = threadIdx.x; t < nb * SB; t += blockDim.x) {
+    const int c = t / SB, r = t % SB;
+    Ls[t] = r < nb ? a[(size_t)(k + c) * n + k + r] : 0.0;
+  }
+  if (threadIdx.x < nb) rd[threadIdx.x] = 1.0 / a[(size_t)(k + threadIdx.x) * n + k + threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (f >= B) return;
+  double* xf = x + (size_t)f * n + k;
+  double v0 = lane < nb ? xf[lane] : 0.0;
+  double v1 = lane + 32 < nb ? xf[lane + 32] : 0.0;
   for (int step = 0; step < nb; ++step) {
     const int c = FWD ? step : nb - 1 - step;
-    if ((int)threadIdx.x < nf) Xs[c][threadIdx.x] /= Ls[c][c];
-    __syncthreads();
-    for (int t = threadIdx.x; t < nb * nf; t += blockDim.x) {
-      const int f = t / nb, r = t - f * nb;
-      if (FWD ? (r > c) : (r < c))
-        Xs[r][f] -= (FWD ? Ls[r][c] : Ls[c][r]) * Xs[c][f];
+    const double* col = Ls + c * SB;
+    const double l0 = col[lane];
+    const double l1 = col[lane + 32];
+    const double own = __shfl_sync(0xffffffffu, c < 32 ? v0 : v1, c & 31);
+    const double xc = own * rd[c];
+    if (lane == (c & 31)) {
+      if (c < 32) v0 = xc; else v1 = xc;
     }
-    __syncthreads();
+    if (FWD ? (lane > c) : (lane < c)) v0 -= l0 * xc;
+    if (FWD ? (lane + 32 > c) : (lane + 32 < c)) v1 -= l1 * xc;
   }
-  for (int t = threadIdx.x; t < nb * nf; t += blockDim.x) {
-    const int f = t / nb, r = t - f * nb;
-    x[(size_t)(f0 + f) * n + k + r] = Xs[r][f];
-  }
+  if (lane < nb) xf[lane] = v0;
+  if (lane + 32 < nb) xf[lane + 32] = v1;
 }
 
-// forward update: rows r in the 64-row tile of this CTA (r >= k + nb):
-//   x[f][r] -= sum_{c < nb} L(r, k + c) x[f][k + c]
-// backward update: rows r in the tile (r < k):
-//   x[f][r] -= sum_{c < nb} L(k + c, r) x[f][k + c]
 template <bool FWD>
-__global__ void solve_update_kernel(const double* __restrict__ l, int n, int k, double* x, int B) {
-  __shared__ double Ls[SB][SB + 1];   // [tile row][block column]
-  __shared__ double Ys[SB][SF + 1];
+__global__ void __launch_bounds__(SU) solve_update_kernel(const double* __restrict__ a, int n,
+                                                          int k, double* x, int B) {
+  __shared__ double Xs[SB][SF];
   const int nb = min(SB, n - k);
-  const int r0 = FWD ? k + nb + blockIdx.x * SB : blockIdx.x * SB;
-  const int rend = FWD ? n : k;
-  const int nr = min(SB, rend - r0);
   const int f0 = blockIdx.y * SF;
   const int nf = min(SF, B - f0);
-  // coalesced loads: forward reads columns k + c (rows r0 + r contiguous),
-  // backward reads columns r0 + r (rows k + c contiguous)
-  for (int t = threadIdx.x; t < SB * nb; t += blockDim.x) {
-    const int c = FWD ? t / SB : t % nb, r = FWD ? t % SB : t / nb;
-    double v = 0.0;
-    if (r < nr) v = FWD ? l[(size_t)(k + c) * n + r0 + r] : l[(size_t)(r0 + r) * n + k + c];
-    Ls[r][c] = v;
-  }
-  for (int t = threadIdx.x; t < nb * nf; t += blockDim.x) {
-    const int f = t / nb, c = t - f * nb;
-    Ys[c][f] = x[(size_t)(f0 + f) * n + k + c];
+  for (int t = threadIdx.x; t < SB * SF; t += blockDim.x) {
+    const int f = t / SB, c = t % SB;
+    Xs[c][f] = (c < nb && f < nf) ? x[(size_t)(f0 + f) * n + k + c] : 0.0;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nr * nf; t += blockDim.x) {
-    const int f = t / nr, r = t - f * nr;
-    double s = 0.0;
-#pragma unroll 8
-    for (int c = 0; c < nb; ++c) s = fma(Ls[r][c], Ys[c][f], s);
-    x[(size_t)(f0 + f) * n + r0 + r] -= s;
+  const int r = (FWD ? k + nb : 0) + blockIdx.x * SU + threadIdx.x;
+  if (r >= (FWD ? n : k)) return;
+  double acc[SF];
+#pragma unroll
+  for (int f = 0; f < SF; ++f) acc[f] = 0.0;
+  const double* col = a + (size_t)k * n + r;
+#pragma unroll 16
+  for (int c = 0; c < nb; ++c) {
+    const double l = __ldg(col + (size_t)c * n);
+#pragma unroll
+    for (int f = 0; f < SF; ++f) acc[f] = fma(l, Xs[c][f], acc[f]);
   }
+#pragma unroll
+  for (int f = 0; f < SF; ++f)
+    if (f < nf) x[(size_t)(f0 + f) * n + r] -= acc[f];
 }
 
-cudaError_t chol_solve(const double* l, int n, double* x, int B, cudaStream_t s) {
+cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s) {
+  if (n <= 0 || B <= 0) return cudaSuccess;
+  const int dgrid = (B + 3) / 4;              // four warps (right-hand sides) per CTA
   const int fblocks = (B + SF - 1) / SF;
   for (int k = 0; k < n; k += SB) {
     const int nb = n - k < SB ? n - k : SB;
-    solve_diag_kernel<true><<<fblocks, 256, 0, s>>>(l, n, k, x, B);
+    solve_diag_kernel<true><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     const int rest = n - k - nb;
     if (rest > 0)
-      solve_update_kernel<true><<<dim3((rest + SB - 1) / SB, fblocks), 256, 0, s>>>(l, n, k, x, B);
+      solve_update_kernel<true><<<dim3((rest + SU - 1) / SU, fblocks), SU, 0, s>>>(a, n, k, x, B);
   }
   const int last = ((n - 1) / SB) * SB;
   for (int k = last; k >= 0; k -= SB) {
-    solve_diag_kernel<false><<<fblocks, 256, 0, s>>>(l, n, k, x, B);
+    solve_diag_kernel<false><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     if (k > 0)
-      solve_update_kernel<false><<<dim3((k + SB - 1) / SB, fblocks), 256, 0, s>>>(l, n, k, x, B);
+      solve_update_kernel<false><<<dim3((k + SU - 1) / SU, fblocks), SU, 0, s>>>(a, n, k, x, B);
   }
   return cudaGetLastError();
 }

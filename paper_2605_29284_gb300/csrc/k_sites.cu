@@ -228,13 +228,12 @@ __global__ void block_factor_kernel(const int* __restrict__ box, const double* _
 }
 
 cudaError_t launch_block_factors(const int* box, const double* w64, int n, const rk_plan* p,
-                                 double2* efac, cudaStream_t s) {
-  const long long total = (long long)n * (p->blk_kx + 1);
+                                 int kx, int ky, double2* efac, cudaStream_t s) {
+  const long long total = (long long)n * (kx + 1);
   const int threads = 128;
   const long long blocks = (total + threads - 1) / threads;
-  block_factor_kernel<<<(unsigned)blocks, threads, 0, s>>>(box, w64, n, p->L, p->px, p->py,
-                                                          p->blk_kx, p->blk_ky, p->tw64x,
-                                                          p->tw64y, efac);
+  block_factor_kernel<<<(unsigned)blocks, threads, 0, s>>>(box, w64, n, p->L, p->px, p->py, kx,
+                                                          ky, p->tw64x, p->tw64y, efac);
   return cudaGetLastError();
 }
 

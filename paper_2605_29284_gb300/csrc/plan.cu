@@ -15,6 +15,7 @@ namespace {
 // Fraction of the spectral peak above which a frequency belongs to the exact
 // low-frequency block of RK_FP32 plans, and the block's size limit.
 constexpr double kBlockEta = 1e-2;
+constexpr double kBlockEtaGrad = 1e-4;
 constexpr int kBlockMax = 1024;
 // largest torus length per dimension (shared-memory limit of the FFT passes)
 constexpr int kMaxTorus = 3456;
@@ -225,14 +226,14 @@ rk_status compute_spectrum(rk_plan* p, int deriv, double** lam64, float** lam32)
   return st;
 }
 
-// choose the exact low-frequency block from lambda (host copy)
-rk_status choose_block(rk_plan* p) {
-  const int H = p->H, py = p->py;
-  std::vector<double> lam((size_t)H * py);
-  RK_CU(cudaMemcpy(lam.data(), p->lam64, lam.size() * sizeof(double), cudaMemcpyDeviceToHost));
+// The exact low-frequency block: the smallest rectangle kx <= KX, |ky| <= KY
+// holding every lambda > eta max(lambda), eta doubled from eta0 until the
+// rectangle has at most kBlockMax entries (none if that never happens).
+void block_for_eta(const std::vector<double>& lam, int H, int py, double eta0, int* kx_out,
+                   int* ky_out, int* nblk_out) {
   double lmax = 0.0;
   for (double v : lam) lmax = v > lmax ? v : lmax;
-  double eta = kBlockEta;
+  double eta = eta0;
   for (int iter = 0; iter < 60; ++iter, eta *= 2.0) {
     int kx_max = -1, ky_max = 0;
     for (int kx = 0; kx < H; ++kx)
@@ -245,15 +246,27 @@ rk_status choose_block(rk_plan* p) {
     if (ky_max >= (py - 1) / 2) ky_max = (py - 1) / 2;
     const int nblk = (kx_max + 1) * (2 * ky_max + 1);
     if (kx_max >= 0 && nblk <= kBlockMax) {
-      p->blk_kx = kx_max;
-      p->blk_ky = ky_max;
-      p->nblk = nblk;
-      return RK_OK;
+      *kx_out = kx_max;
+      *ky_out = ky_max;
+      *nblk_out = nblk;
+      return;
     }
   }
-  p->blk_kx = -1;
-  p->blk_ky = 0;
-  p->nblk = 0;
+  *kx_out = -1;
+  *ky_out = 0;
+  *nblk_out = 0;
+}
+
+rk_status lambda_host(rk_plan* p, std::vector<double>& lam) {
+  lam.resize((size_t)p->H * p->py);
+  RK_CU(cudaMemcpy(lam.data(), p->lam64, lam.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  return RK_OK;
+}
+
+rk_status choose_block(rk_plan* p) {
+  std::vector<double> lam;
+  RK_TRY(lambda_host(p, lam));
+  block_for_eta(lam, p->H, p->py, kBlockEta, &p->blk_kx, &p->blk_ky, &p->nblk);
   return RK_OK;
 }
 
@@ -264,7 +277,7 @@ void free_plan(rk_plan* p) {
                   p->d_flag, p->tw64qx, p->tw64qy, p->tw32qx, p->tw32qy, p->ce_sqrt64,
                   p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_c, p->h_out, p->xy, p->wd64,
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
-                  p->bw_c, p->bw_cT};
+                  p->bw_cT, p->efac_g, p->gblk, p->bw_dk};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
@@ -319,12 +332,21 @@ rk_status finish_coef(rk_plan* p, int B) {
   return RK_OK;
 }
 
+// An exact low-frequency block: its extent, the per-site factors E_i(k) of
+// the weights in use, and the B x nblk buffer for sum_i c_i E_i(k).
+struct BlockUse {
+  int kx, ky, nblk;
+  const double2* efac;
+  double2* blk;
+};
+
 // Steps 5-7 for nf fields with coefficients c64 (double) and cT (plan
 // precision; may equal c64 for RK_FP64 plans); out[f] (+ addend window).
+// FP32 plans use the forward block unless bu names another one.
 template <typename T>
 rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* out,
                          const T* addend, const T* lam_override = nullptr,
-                         const T* w_override = nullptr, const double2* efac_override = nullptr) {
+                         const T* w_override = nullptr, const BlockUse* bu = nullptr) {
   const int B = nf;
   cudaStream_t s = p->stream;
   T* cstar = (T*)p->cstar;
@@ -333,7 +355,8 @@ rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* 
   const bool f32 = sizeof(T) == sizeof(float);
   const T* w = w_override ? w_override : f32 ? (const T*)p->w32 : (const T*)p->w64;
   const T* lam = lam_override ? lam_override : f32 ? (const T*)p->lam32 : (const T*)p->lam64;
-  const double2* efac = efac_override ? efac_override : p->efac;
+  const BlockUse fwd = {p->blk_kx, p->blk_ky, p->nblk, p->efac, p->blk};
+  const BlockUse& bk = bu ? *bu : fwd;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
   const C<T>* twy = f32 ? (const C<T>*)p->tw32y : (const C<T>*)p->tw64y;
   const size_t plane = (size_t)p->p1y * p->p1x;
@@ -342,15 +365,15 @@ rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* 
   // the exact block (FP64 pipe) runs on the side stream while the scatter and
   // the row pass (FP32 pipe) run on the plan's stream; the column pass waits
   // for both
-  const bool use_blk = f32 && p->nblk > 0;
+  const bool use_blk = f32 && bk.nblk > 0;
   if (use_blk) {
     RK_CU(cudaEventRecord(p->ev_fork, s));
     RK_CU(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
     cudaStream_t s_main = s;
     {
       cudaStream_t s = p->side;
-      RK_PROF("block_gemm", (double)p->nblk * p->n * 16.0 + B * (p->n * 8.0 + p->nblk * 16.0));
-      RK_CU(launch_block_gemm(c64, B, p->n, efac, p->nblk, p->blk, s));
+      RK_PROF("block_gemm", (double)bk.nblk * p->n * 16.0 + B * (p->n * 8.0 + bk.nblk * 16.0));
+      RK_CU(launch_block_gemm(c64, B, p->n, bk.efac, bk.nblk, bk.blk, s));
     }
     RK_CU(cudaEventRecord(p->ev_join, p->side));
     (void)s_main;
@@ -371,8 +394,8 @@ rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* 
                         (double)p->H * p->py * es);
     RK_CU(launch_cols<T>(tb, p->ldt, (long long)p->H * p->ldt, p->p1y, ub, p->ldu,
                          (long long)p->H * p->ldu, p->L - 1, p->ny, lam, COLS_CONV,
-                         use_blk ? p->blk : nullptr, p->blk_kx, p->blk_ky, p->nblk, B, p->H,
-                         p->fpy, twy, s));
+                         use_blk ? bk.blk : nullptr, bk.kx, bk.ky, bk.nblk, B, p->H, p->fpy,
+                         twy, s));
   }
   {
     RK_PROF("rows_inv", B * ((double)p->H * p->ny * cs + (double)p->ny * p->nx * es) +
@@ -441,20 +464,28 @@ rk_status ensure_ce(rk_plan* p) {
   return RK_ERR_CE_NEGATIVE;
 }
 
-constexpr int kCsChunk = 64;
+constexpr int kCsChunk = 64;     // fields per CE / prediction pass
+constexpr int kCsSolve = 512;    // right-hand sides per FP64 solve
 
+// Conditional simulation (Section 2, the linearity form): for each group of
+// up to kCsSolve realisations, (1) unconditional fields on the padded grid
+// and their values at the sites, kCsChunk at a time, (2) one FP64 solve of
+// M c_r = z - z_u,r for the whole group (the solve is FP64-throughput bound,
+// and more right-hand sides per pass keep more SMs busy), (3) the rapid
+// prediction of every c_r with f_u,r added in the last pass.
 template <typename T>
 rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
   cudaStream_t s = p->stream;
   const int n = p->n;
   const long long total = (long long)p->B * R;
   const int G = total < kCsChunk ? (int)total : kCsChunk;
+  const int S = total < kCsSolve ? (int)total : kCsSolve;
   const size_t plane = (size_t)p->p1y * p->p1x;
   const int ldq = p->p1y;
   const int maxpairs = G / 2 + 1;
-  const size_t fu_b = (size_t)G * plane * sizeof(T);
+  const size_t fu_b = (size_t)S * plane * sizeof(T);
   const size_t tq_b = (size_t)maxpairs * p->qx * ldq * 2 * sizeof(T);
-  const size_t rhs_b = (size_t)G * n * sizeof(double);
+  const size_t rhs_b = (size_t)S * n * sizeof(double);
   const size_t c32_b = (size_t)G * n * sizeof(T);
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t need = al(fu_b) + al(tq_b) + al(rhs_b) + al(c32_b);
@@ -472,37 +503,47 @@ rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
   const T* sl = f32 ? (const T*)p->ce_sqrt32 : (const T*)p->ce_sqrt64;
   const C<T>* twqx = f32 ? (const C<T>*)p->tw32qx : (const C<T>*)p->tw64qx;
   const C<T>* twqy = f32 ? (const C<T>*)p->tw32qy : (const C<T>*)p->tw64qy;
-  for (long long g0 = 0; g0 < total; g0 += G) {
-    const int g = (int)(total - g0 < G ? total - g0 : G);
-    const int pair0 = (int)(g0 / 2);
-    const int npairs = (int)((g0 + g - 1) / 2 - g0 / 2 + 1);
-    {
-      RK_PROF("ce_cols", (double)npairs * p->qx * (p->qy / 2 + 1) * sizeof(T) +
-                             (double)npairs * p->qx * p->p1y * 2 * sizeof(T));
-      RK_CU(launch_ce_cols<T>(sl, p->qx, p->qy, seed, pair0, npairs, tq, ldq, p->p1y, p->fqy,
-                              twqy, s));
+  for (long long s0 = 0; s0 < total; s0 += S) {
+    const int sn = (int)(total - s0 < S ? total - s0 : S);
+    for (long long g0 = s0; g0 < s0 + sn; g0 += G) {
+      const int g = (int)(s0 + sn - g0 < G ? s0 + sn - g0 : G);
+      const int pair0 = (int)(g0 / 2);
+      const int npairs = (int)((g0 + g - 1) / 2 - g0 / 2 + 1);
+      T* fug = fu + (size_t)(g0 - s0) * plane;
+      {
+        RK_PROF("ce_cols", (double)npairs * p->qx * (p->qy / 2 + 1) * sizeof(T) +
+                               (double)npairs * p->qx * p->p1y * 2 * sizeof(T));
+        RK_CU(launch_ce_cols<T>(sl, p->qx, p->qy, seed, pair0, npairs, tq, ldq, p->p1y, p->fqy,
+                                twqy, s));
+      }
+      {
+        RK_PROF("ce_rows", (double)npairs * p->qx * p->p1y * 2 * sizeof(T) +
+                               (double)g * plane * sizeof(T));
+        RK_CU(launch_ce_rows<T>(tq, p->qx, ldq, p->p1y, fug, p->p1x, g0, g, pair0, npairs,
+                                p->fqx, twqx, s));
+      }
+      {
+        RK_PROF("site_values", (double)g * n * (p->M * sizeof(T) + 16.0) + (double)n * p->M * 8);
+        RK_CU(launch_site_values<T>(fug, p->p1x, (long long)plane, g, p->box, p->w64, p->ssd, n,
+                                    p->L, sqrt(p->tau2), seed, g0, R, p->z64,
+                                    rhs + (size_t)(g0 - s0) * n, s));
+      }
     }
     {
-      RK_PROF("ce_rows", (double)npairs * p->qx * p->p1y * 2 * sizeof(T) +
-                             (double)g * plane * sizeof(T));
-      RK_CU(launch_ce_rows<T>(tq, p->qx, ldq, p->p1y, fu, p->p1x, g0, g, pair0, npairs, p->fqx,
-                              twqx, s));
+      RK_PROF("chol_solve", (double)sn * n * 16.0 + (double)n * (double)n * 8.0);
+      RK_CU(chol_solve(p->mchol, n, rhs, sn, s));
     }
-    {
-      RK_PROF("site_values", (double)g * n * (p->M * sizeof(T) + 16.0) + (double)n * p->M * 8);
-      RK_CU(launch_site_values<T>(fu, p->p1x, (long long)plane, g, p->box, p->w64, p->ssd, n,
-                                  p->L, sqrt(p->tau2), seed, g0, R, p->z64, rhs, s));
+    for (long long g0 = s0; g0 < s0 + sn; g0 += G) {
+      const int g = (int)(s0 + sn - g0 < G ? s0 + sn - g0 : G);
+      const double* rg = rhs + (size_t)(g0 - s0) * n;
+      const T* cuse = (const T*)rg;
+      if (f32) {
+        RK_CU(launch_convert<T>(rg, cT, (size_t)g * n, s));
+        cuse = cT;
+      }
+      RK_TRY(predict_fields<T>(p, rg, cuse, g, out + (size_t)g0 * p->ny * p->nx,
+                               fu + (size_t)(g0 - s0) * plane));
     }
-    {
-      RK_PROF("chol_solve", (double)g * n * 16.0 + (double)g * n * (double)n * 8.0);
-      RK_CU(chol_solve(p->mchol, n, rhs, g, s));
-    }
-    const T* cuse = (const T*)rhs;
-    if (f32) {
-      RK_CU(launch_convert<T>(rhs, cT, (size_t)g * n, s));
-      cuse = cT;
-    }
-    RK_TRY(predict_fields<T>(p, rhs, cuse, g, out + (size_t)g0 * p->ny * p->nx, fu));
   }
   return RK_OK;
 }
@@ -519,9 +560,18 @@ rk_status ensure_adjoint(rk_plan* p) {
   RK_TRY(dalloc(&p->wd64, (size_t)p->n * p->M));
   RK_TRY(dalloc(&p->wd32, (size_t)p->n * p->M));
   RK_CU(launch_dweights(p, p->wd64, p->wd32, p->stream));
-  if (p->precision == RK_FP32 && p->nblk > 0) {
-    RK_TRY(dalloc(&p->efac_d, (size_t)p->n * p->nblk));
-    RK_CU(launch_block_factors(p->box, p->wd64, p->n, p, p->efac_d, p->stream));
+  if (p->precision == RK_FP32) {
+    std::vector<double> lam;
+    RK_TRY(lambda_host(p, lam));
+    block_for_eta(lam, p->H, p->py, kBlockEtaGrad, &p->gblk_kx, &p->gblk_ky, &p->ngblk);
+    if (p->ngblk > 0) {
+      RK_TRY(dalloc(&p->efac_g, (size_t)p->n * p->ngblk));
+      RK_TRY(dalloc(&p->efac_d, (size_t)p->n * p->ngblk));
+      RK_CU(launch_block_factors(p->box, p->w64, p->n, p, p->gblk_kx, p->gblk_ky, p->efac_g,
+                                 p->stream));
+      RK_CU(launch_block_factors(p->box, p->wd64, p->n, p, p->gblk_kx, p->gblk_ky, p->efac_d,
+                                 p->stream));
+    }
   }
   p->have_adj = true;
   return RK_OK;
@@ -535,15 +585,21 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
   const size_t plane = (size_t)p->p1y * p->p1x;
   const size_t grid = (size_t)p->ny * p->nx;
   RK_TRY(ensure_adjoint(p));
-  if (p->bw_cbar_cap < (size_t)B * n) {
-    RK_TRY(dalloc(&p->bw_cbar, (size_t)B * n));
-    p->bw_cbar_cap = (size_t)B * n;
+  // one FP64 solve for [zbar | M^{-1} c | M^{-1} K'_xx c]: the three right-hand
+  // side sets are contiguous (B x n each) and share the passes over the factor
+  const int nsets = grho ? 3 : gs2 ? 2 : 1;
+  if (p->bw_cbar_cap < (size_t)3 * B * n) {
+    RK_TRY(dalloc(&p->bw_cbar, (size_t)3 * B * n));
+    p->bw_cbar_cap = (size_t)3 * B * n;
   }
-  const bool use_blk = f32 && p->nblk > 0;
-  if (use_blk && p->bw_gblk_cap < (size_t)B * p->nblk) {
-    RK_TRY(dalloc(&p->bw_gblk, (size_t)B * p->nblk));
-    p->bw_gblk_cap = (size_t)B * p->nblk;
+  const bool use_blk = f32 && p->ngblk > 0;
+  if (use_blk && p->bw_gblk_cap < (size_t)B * p->ngblk) {
+    RK_TRY(dalloc(&p->bw_gblk, (size_t)B * p->ngblk));
+    RK_TRY(dalloc(&p->gblk, (size_t)B * p->ngblk));
+    p->bw_gblk_cap = (size_t)B * p->ngblk;
   }
+  const BlockUse gw = {p->gblk_kx, p->gblk_ky, p->ngblk, p->efac_g, p->gblk};
+  const BlockUse gwd = {p->gblk_kx, p->gblk_ky, p->ngblk, p->efac_d, p->gblk};
   const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
   const T* dlam = f32 ? (const T*)p->dlam32 : (const T*)p->dlam64;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
@@ -563,8 +619,8 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     RK_PROF("adj_cols", B * ((double)p->H * p->ny * cs + (double)p->H * p->p1y * cs));
     RK_CU(launch_cols<T>(tb, p->ldt, (long long)p->H * p->ldt, p->ny, ub, p->ldu,
                          (long long)p->H * p->ldu, p->py - (p->L - 1), p->p1y, lam, COLS_ADJ,
-                         use_blk ? p->bw_gblk : nullptr, p->blk_kx, p->blk_ky, p->nblk, B, p->H,
-                         p->fpy, twy, s));
+                         use_blk ? p->bw_gblk : nullptr, p->gblk_kx, p->gblk_ky, p->ngblk, B,
+                         p->H, p->fpy, twy, s));
   }
   {
     RK_PROF("adj_rows_inv", B * ((double)p->H * p->p1y * cs + plane * es));
@@ -574,14 +630,36 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
   }
   // cbar = A abar (+ the exact block part), zbar = M^{-1} cbar
   double* cbar = p->bw_cbar;
-  RK_CU(launch_gather<T>(abar, p->p1x, p->p1y, p->box, p->w64, n, p->L, B, cbar, s));
-  if (use_blk) {
-    const int bw = 2 * p->blk_ky + 1;
-    RK_CU(launch_block_phase(p->bw_gblk, B, p->nblk, bw, p->blk_ky, p->L - 1, p->px, p->py,
-                             p->tw64x, p->tw64y, s));
-    RK_CU(launch_block_adjoint(p->bw_gblk, B, p->nblk, bw, p->efac, n, cbar, s));
+  {
+    RK_PROF("adj_gather", (double)B * n * (p->M * es + 8.0) + (double)n * p->M * 8.0);
+    RK_CU(launch_gather<T>(abar, p->p1x, p->p1y, p->box, p->w64, n, p->L, B, cbar, s));
   }
-  RK_CU(chol_solve(p->mchol, n, cbar, B, s));
+  if (use_blk) {
+    RK_PROF("adj_block", (double)p->ngblk * n * 16.0 + (double)B * n * 8.0);
+    const int bw = 2 * p->gblk_ky + 1;
+    RK_CU(launch_block_phase(p->bw_gblk, B, p->ngblk, bw, p->gblk_ky, p->L - 1, p->px, p->py,
+                             p->tw64x, p->tw64y, s));
+    RK_CU(launch_block_adjoint(p->bw_gblk, B, p->ngblk, bw, p->efac_g, n, cbar, s));
+  }
+  double* c2 = cbar + (size_t)B * n;
+  double* c3 = cbar + (size_t)2 * B * n;
+  if (nsets >= 2)
+    RK_CU(cudaMemcpyAsync(c2, p->c64, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                          s));
+  if (nsets == 3) {
+    const size_t need = dkxx_scratch_doubles(n, B);
+    if (p->bw_dk_cap < need) {
+      RK_TRY(dalloc(&p->bw_dk, need));
+      p->bw_dk_cap = need;
+    }
+    RK_PROF("theta_dkxx", (double)n * 16.0 + (double)B * n * 16.0 + need * 16.0);
+    RK_CU(launch_matvec_dkxx(p->xy, n, p->c64, B, p->rho, p->sigma2, p->nu_code, p->bw_dk, c3,
+                             s));
+  }
+  {
+    RK_PROF("adj_solve", (double)n * n * 8.0 + (double)nsets * B * n * 16.0);
+    RK_CU(chol_solve(p->mchol, n, cbar, nsets * B, s));
+  }
   if (gz) RK_CU(cudaMemcpyAsync(gz, cbar, (size_t)B * n * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s));
   if (grho || gs2) {
@@ -594,7 +672,6 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     //   d/dlog rho     = gbar . (g_hat'(c) + g_hat_W'(c) - g_hat(M^{-1} K'_xx c)).
     const size_t need_c = (size_t)2 * B * n;
     if (p->bw_c_cap < need_c) {
-      RK_TRY(dalloc(&p->bw_c, need_c));
       RK_TRY(dalloc_bytes(&p->bw_cT, need_c * sizeof(float)));
       p->bw_c_cap = need_c;
     }
@@ -606,27 +683,22 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     T* y1 = y0 + B * grid;
     T* y2 = y1 + B * grid;
     T* y3 = y2 + B * grid;
-    double* c2 = p->bw_c;
-    double* c3 = p->bw_c + (size_t)B * n;
     float* c2f = (float*)p->bw_cT;
     float* c3f = c2f + (size_t)B * n;
     const T* cT = f32 ? (const T*)p->c32 : (const T*)p->c64;
     const T* wd = f32 ? (const T*)p->wd32 : (const T*)p->wd64;
     if (gs2) {
-      RK_CU(cudaMemcpyAsync(c2, p->c64, (size_t)B * n * sizeof(double),
-                            cudaMemcpyDeviceToDevice, s));
-      RK_CU(chol_solve(p->mchol, n, c2, B, s));
       if (f32) RK_CU(launch_convert<float>(c2, c2f, (size_t)B * n, s));
-      RK_TRY(predict_fields<T>(p, c2, f32 ? (const T*)c2f : (const T*)c2, B, y0, nullptr));
+      RK_TRY(predict_fields<T>(p, c2, f32 ? (const T*)c2f : (const T*)c2, B, y0, nullptr,
+                               nullptr, nullptr, &gw));
       RK_CU(launch_dot_rows<T, T>(gbar, y0, B, (long long)grid, p->tau2, 0, gs2, s));
     }
     if (grho) {
-      RK_CU(launch_matvec_dkxx(p->xy, n, p->c64, B, p->rho, p->sigma2, p->nu_code, c3, s));
-      RK_CU(chol_solve(p->mchol, n, c3, B, s));
       if (f32) RK_CU(launch_convert<float>(c3, c3f, (size_t)B * n, s));
-      RK_TRY(predict_fields<T>(p, p->c64, cT, B, y1, nullptr, dlam));
-      RK_TRY(predict_fields<T>(p, p->c64, cT, B, y2, nullptr, nullptr, wd, p->efac_d));
-      RK_TRY(predict_fields<T>(p, c3, f32 ? (const T*)c3f : (const T*)c3, B, y3, nullptr));
+      RK_TRY(predict_fields<T>(p, p->c64, cT, B, y1, nullptr, dlam, nullptr, &gw));
+      RK_TRY(predict_fields<T>(p, p->c64, cT, B, y2, nullptr, nullptr, wd, &gwd));
+      RK_TRY(predict_fields<T>(p, c3, f32 ? (const T*)c3f : (const T*)c3, B, y3, nullptr,
+                               nullptr, nullptr, &gw));
       RK_CU(launch_dot_rows<T, T>(gbar, y1, B, (long long)grid, 1.0, 0, grho, s));
       RK_CU(launch_dot_rows<T, T>(gbar, y2, B, (long long)grid, 1.0, 1, grho, s));
       RK_CU(launch_dot_rows<T, T>(gbar, y3, B, (long long)grid, -1.0, 1, grho, s));
@@ -806,7 +878,7 @@ rk_status rk_set_weights(rk_plan* p, int n, const int* box, const double* w) {
   RK_TRY(read_flag(p, &flag));
   if (flag & 4) return RK_ERR_INVALID_ARG;
   if (p->precision == RK_FP32 && p->nblk > 0)
-    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->efac, p->stream));
+    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, p->stream));
   p->n = n;
   return RK_OK;
 }
@@ -823,7 +895,7 @@ rk_status rk_set_sites(rk_plan* p, int n, const double* xy) {
   RK_TRY(read_flag(p, &flag));
   if (flag & 2) return RK_ERR_OBS_OUTSIDE;
   if (p->precision == RK_FP32 && p->nblk > 0)
-    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->efac, p->stream));
+    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, p->stream));
   p->n = n;
   return RK_OK;
 }
@@ -837,7 +909,7 @@ rk_status rk_set_sites_async(rk_plan* p, int n, const double* xy) {
                         p->stream));
   RK_CU(launch_weights(p->xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_sites_flag, p->stream));
   if (p->precision == RK_FP32 && p->nblk > 0)
-    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->efac, p->stream));
+    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, p->stream));
   p->n = n;
   return RK_OK;
 }
@@ -873,6 +945,7 @@ rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
     RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
     RK_CU(build_obs_cov(p->xy, n, p, p->mchol, p->stream));
     RK_CU(chol_factor(p->mchol, n, p->d_flag, p->stream));
+    RK_CU(chol_mirror(p->mchol, n, p->stream));
     int flag = 0;
     RK_TRY(read_flag(p, &flag));
     if (flag) return RK_ERR_NOT_PD;
