@@ -168,11 +168,15 @@ class Arm:
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         # one stream per cell: the cells are independent predictions
         self.streams = [torch.cuda.Stream(device=dev) for _ in self.st]
+        tori = {(p.info()["px"], p.info()["py"]) for p, _, _ in self.st}
+        self.grouped = len(tori) == 1 and len(self.st) <= 16
         self.graph = None
         torch.cuda.synchronize()
 
     def _issue(self):
-        """One step: per cell, weights (async site update), coefficients, prediction."""
+        """One step: per cell, weights (async site update) and coefficients on
+        the cell's stream; then the predictions of all cells, grouped (one
+        launch per pass, rk_predict_group) when the cells share a torus."""
         torch = self.torch
         cur = torch.cuda.current_stream()
         fork = torch.cuda.Event()
@@ -183,12 +187,15 @@ class Arm:
             with torch.cuda.stream(s):
                 p.set_sites_async(self.xy)
                 p.set_coef(c)
-                p.predict(out)
+                if not self.grouped:
+                    p.predict(out)
                 e = torch.cuda.Event()
                 e.record(s)
             joins.append(e)
         for e in joins:
             cur.wait_event(e)
+        if self.grouped:
+            self.rk.predict_group([p for p, _, _ in self.st], [o for _, _, o in self.st])
 
     def capture(self):
         """Capture one step (all cells, their streams forked and joined) in a CUDA graph."""
@@ -413,7 +420,14 @@ def run_ours(args, rank, world):
         secondary["cs512_simulate"] = measure_cs(dev, max(2, args.steps // 5), peaks)
         secondary["grad1024_backward"] = measure_backward(dev, max(2, args.steps // 5), peaks,
                                                           n=args.backward_n)
-    launches_per_cell = 7 if args.precision == "fp32" else 5
+    # our kernels per step: per cell weights (+ block factors and the FP32
+    # coefficient copy), then either per cell [block GEMM,] scatter, rows_fwd,
+    # cols, rows_inv, or the grouped passes ([block GEMM,] zero, scatter,
+    # rows_fwd, cols, rows_inv)
+    f32 = args.precision == "fp32"
+    ncell = len(main.cells)
+    per_step = ncell * (3 if f32 else 1) + (
+        (1 if f32 else 0) + 5 if main.grouped else ncell * (5 if f32 else 4))
     res = {
         "metric": METRIC, "value": value, "unit": "grid-point predictions/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -424,14 +438,17 @@ def run_ours(args, rank, world):
                    "grid": f"{main.cells[0][1]['nx']}x{main.cells[0][1]['ny']}",
                    "n": int(main.xy_np.shape[0]), "fields_per_cell": main.cells[0][2],
                    "l2": "flushed between timed steps (256 MB write)",
-                   "issue": "one stream per cell, step replayed from a CUDA graph",
+                   "issue": ("sites and coefficients on one stream per cell, the cells' "
+                             "predictions in one grouped launch per pass (rk_predict_group), "
+                             "step replayed from a CUDA graph") if main.grouped else
+                            "one stream per cell, step replayed from a CUDA graph",
                    "value_without_graph": value_nograph,
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "grid-point predictions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_cell * len(main.cells) * args.steps,
+        "gpu_launches": per_step * args.steps,
         "clocks": clocks,
         "fp64_path": fp64,
         "secondary": secondary,

@@ -175,6 +175,24 @@ rk_status rk_set_obs(rk_plan* plan, int n, const double* xy_dev, const double* z
 rk_status rk_predict(rk_plan* plan, void* out_dev);
 
 /*
+ * rk_predict_group -- rk_predict for nplans plans at once (1 <= nplans <= 16):
+ * the same steps 5-7 of Section 2.2, each pass issued as one launch over the
+ * fields of every plan, so that many small predictions (the paper's sweeps
+ * over nu and L, Section 3) fill the GPU together.
+ *   plans    host array of distinct plans, each with sites and coefficients;
+ *            all of one precision and one torus (px, py), which grids of one
+ *            size and L within a 2^a 3^b step share.
+ *   outs     host array of device pointers, outs[k] as rk_predict's out_dev
+ *            for plans[k].
+ * Work is issued on plans[0]'s stream (its side stream and events for the
+ * FP32 exact block).  Plans must not be in use on other streams meanwhile.
+ * RK_ERR_INVALID_ARG for a null or repeated plan, mixed precision or torus;
+ * RK_ERR_STATE as rk_predict.  A torus without a compile-time-specialised
+ * FFT length is predicted plan after plan on the same stream.
+ */
+rk_status rk_predict_group(rk_plan* const* plans, int nplans, void* const* outs);
+
+/*
  * rk_predict_static -- rk_predict without any device allocation.  (Not from
  * the paper: it has no counterpart there.)  Some callers cannot allocate
  * device memory at the moment they predict: a process whose device memory is

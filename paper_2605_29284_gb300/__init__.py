@@ -11,7 +11,8 @@ import torch
 
 from ._native import RK_FP32, RK_FP64, PlanInfo, RkError, check, lib, profile_enable, profile_read
 
-__all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "profile_enable", "profile_read"]
+__all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "predict_group", "profile_enable",
+           "profile_read"]
 
 
 def _ptr(t):
@@ -177,3 +178,19 @@ class Plan:
             t = torch.empty((self.B, self.n), dtype=torch.float64, device="cuda")
         self._call("rk_debug_copy", code, _ptr(t), ctypes.c_size_t(t.numel() * t.element_size()))
         return t
+
+
+def predict_group(plans, outs=None):
+    """rk_predict_group: every plan's prediction, each pass one launch for all.
+
+    plans share precision and torus; outs[k] (allocated when omitted) is
+    plans[k]'s B x ny x nx output.  Issued on the current stream."""
+    plans = list(plans)
+    if outs is None:
+        outs = [torch.empty((p.B, p.ny, p.nx), dtype=p.dtype, device="cuda") for p in plans]
+    n = len(plans)
+    harr = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+    oarr = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+    check(lib.rk_set_stream(plans[0]._h, _stream()), "rk_set_stream")
+    check(lib.rk_predict_group(harr, n, oarr), "rk_predict_group")
+    return outs

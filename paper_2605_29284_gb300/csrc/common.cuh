@@ -204,6 +204,58 @@ bool launch_rows_inv_n(const C<T>* uin, int ldu, long long ufs, int nrows, T* ou
                        long long ofs, int ocol0, int ncols, const T* add, int ald, long long afs,
                        int ar0, int ac0, int B, int N, const C<T>* tw, int H, cudaStream_t s,
                        cudaError_t* err);
+// Groups: one launch of a specialised pass over the fields of several plans
+// that share the torus (rk_predict_group).  Slot k covers units
+// [start[k], start[k + 1]) of the grid's y dimension (fields, or field
+// groups for the column pass).
+constexpr int kMaxGroup = 16;
+template <typename S>
+struct Group {
+  int n = 0;
+  int start[kMaxGroup + 1] = {0};
+  S slot[kMaxGroup];
+};
+template <typename T>
+struct RowsFwdSlot {
+  const T* in; C<T>* tout;
+  long long ifs, tfs;
+  int nrows, ncols, ild, ldt, B;
+};
+template <typename T>
+struct ColsSlot {
+  const C<T>* tin; C<T>* uout; const T* lam; double2* blk;
+  long long tfs, ufs;
+  int ldt, nrin, ldu, orow0, nrout, blk_kx, blk_ky, nblk, B;
+};
+template <typename T>
+struct RowsInvSlot {
+  const C<T>* uin; T* out; const T* add;
+  long long ufs, ofs, afs;
+  int ldu, nrows, old, ocol0, ncols, ald, ar0, ac0, B;
+};
+struct BlockGemmSlot {
+  const double* c; const double2* efac; double2* blk;
+  int n, B, nblk;
+};
+cudaError_t launch_block_gemm_group(const Group<BlockGemmSlot>& g, cudaStream_t s);
+template <typename T>
+struct ScatterSlot {
+  const int* box; const T* w; const T* c; T* cstar;
+  int n, B, L, p1x, p1y;
+};
+template <typename T>
+cudaError_t launch_scatter_group(const Group<ScatterSlot<T>>& g, cudaStream_t s);
+template <typename T>
+bool launch_rows_fwd_group(const Group<RowsFwdSlot<T>>& g, int N, const C<T>* tw, int H,
+                           cudaStream_t s, cudaError_t* err);
+template <typename T>
+bool launch_cols_group(Group<ColsSlot<T>>& g, int mode, int N, const C<T>* tw, int H,
+                       cudaStream_t s, cudaError_t* err);
+template <typename T>
+bool launch_rows_inv_group(const Group<RowsInvSlot<T>>& g, int N, const C<T>* tw, int H,
+                           cudaStream_t s, cudaError_t* err);
+// true when a specialised pass exists for length N
+bool fftn_specialised(int N);
 // true when RK_FFT_GENERIC is set in the environment: use only the generic passes
 bool fft_generic_only();
 

@@ -22,28 +22,40 @@ template <int N> struct ColVecs {
   static constexpr int min_blocks = threads <= 320 ? 3 : 2;
 };
 
+// slot of grid unit u (uniform per CTA)
+template <typename G>
+__device__ __forceinline__ int slot_of(const G& g, int u) {
+  int k = 0;
+  while (k + 1 < g.n && u >= g.start[k + 1]) ++k;
+  return k;
+}
+
 // ---------------------------------------------------------------- rows_fwd --
 template <typename T, int N>
 __global__ void __launch_bounds__(VecsPerCta<N>::value * Radix23<N>::THR)
-rows_fwd_n(const T* __restrict__ in, int nrows, int ncols, long long ifs, int ild,
-           C<T>* __restrict__ tout, int ldt, long long tfs, const C<T>* __restrict__ tw, int H) {
+rows_fwd_n(const __grid_constant__ Group<RowsFwdSlot<T>> g, const C<T>* __restrict__ tw, int H) {
   constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
-  const int f = blockIdx.y;
+  const int ks = slot_of(g, blockIdx.y);
+  const RowsFwdSlot<T>& sl = g.slot[ks];
+  const int f = blockIdx.y - g.start[ks];
+  const int nrows = sl.nrows, ncols = sl.ncols;
   const int r0 = blockIdx.x * 2 * V;
-  const T* src = in + (size_t)f * ifs;
+  if (r0 >= nrows) return;
+  const T* src = sl.in + (size_t)f * sl.ifs;
   for (int idx = threadIdx.x; idx < V * N; idx += V * THR) {
     const int v = idx / N, n = idx - v * N;
     const int ra = r0 + 2 * v, rb = ra + 1;
-    const T xa = (ra < nrows && n < ncols) ? src[(size_t)ra * ild + n] : T(0);
-    const T xb = (rb < nrows && n < ncols) ? src[(size_t)rb * ild + n] : T(0);
+    const T xa = (ra < nrows && n < ncols) ? src[(size_t)ra * sl.ild + n] : T(0);
+    const T xb = (rb < nrows && n < ncols) ? src[(size_t)rb * sl.ild + n] : T(0);
     buf[idx] = mk<T>(xa, xb);
   }
   __syncthreads();
   const int v = threadIdx.x / THR, tid = threadIdx.x - v * THR;
   fft_n<T, N, +1>(buf + v * N, tw, tid);
-  C<T>* dst = tout + (size_t)f * tfs;
+  C<T>* dst = sl.tout + (size_t)f * sl.tfs;
+  const int ldt = sl.ldt;
   constexpr int per_k = 2 * V;
   for (int idx = threadIdx.x; idx < H * per_k; idx += V * THR) {
     const int k = idx / per_k;
@@ -63,11 +75,21 @@ rows_fwd_n(const T* __restrict__ in, int nrows, int ncols, long long ifs, int il
 // -------------------------------------------------------------------- cols --
 template <typename T, int N>
 __global__ void __launch_bounds__(ColVecs<N>::threads, ColVecs<N>::min_blocks)
-cols_n(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin, C<T>* __restrict__ uout,
-       int ldu, long long ufs, int orow0, int nrout, const T* __restrict__ lam, int mode,
-       double2* __restrict__ blk, int blk_kx, int blk_ky, int nblk, int B, int H,
+cols_n(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
        const C<T>* __restrict__ tw) {
   constexpr int V = ColVecs<N>::value, THR = Radix23<N>::THR;
+  // this CTA's slot, and its field group within the slot (fields fg0,
+  // fg0 + ng, ...): lambda stays in shared memory for all of them
+  const int ks = slot_of(g, blockIdx.y);
+  const ColsSlot<T>& sl = g.slot[ks];
+  const int fg0 = blockIdx.y - g.start[ks], ng = g.start[ks + 1] - g.start[ks];
+  const C<T>* __restrict__ tin = sl.tin;
+  C<T>* __restrict__ uout = sl.uout;
+  const T* __restrict__ lam = sl.lam;
+  double2* __restrict__ blk = sl.blk;
+  const long long tfs = sl.tfs, ufs = sl.ufs;
+  const int ldt = sl.ldt, nrin = sl.nrin, ldu = sl.ldu, orow0 = sl.orow0, nrout = sl.nrout;
+  const int blk_kx = sl.blk_kx, blk_ky = sl.blk_ky, nblk = sl.nblk, B = sl.B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* bufs = reinterpret_cast<C<T>*>(smem_raw);
   T* lcols = reinterpret_cast<T*>(bufs + V * N);
@@ -92,15 +114,15 @@ cols_n(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin, C<T>* __r
       nxt[e] = (kvalid && n < nrin) ? src[n] : mk<T>(T(0), T(0));
     }
   };
-  if (blockIdx.y < B) load_col(blockIdx.y);
-  for (int f = blockIdx.y; f < B; f += gridDim.y) {
+  if (fg0 < B) load_col(fg0);
+  for (int f = fg0; f < B; f += ng) {
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
       const int n = tid + e * THR;
       if (n < N) buf[n] = nxt[e];
     }
     __syncthreads();
-    if (f + (int)gridDim.y < B) load_col(f + gridDim.y);
+    if (f + ng < B) load_col(f + ng);
     fft_n<T, N, +1>(buf, tw, tid);
     C<T>* dst = uout + (size_t)f * ufs + (size_t)k * ldu;
     if (mode == COLS_FWD_ONLY) {
@@ -156,17 +178,23 @@ cols_n(const C<T>* __restrict__ tin, int ldt, long long tfs, int nrin, C<T>* __r
 // ---------------------------------------------------------------- rows_inv --
 template <typename T, int N>
 __global__ void __launch_bounds__(VecsPerCta<N>::value * Radix23<N>::THR)
-rows_inv_n(const C<T>* __restrict__ uin, int ldu, long long ufs, int nrows, T* __restrict__ out,
-           int old, long long ofs, int ocol0, int ncols, const T* __restrict__ add, int ald,
-           long long afs, int ar0, int ac0, const C<T>* __restrict__ tw, int H) {
+rows_inv_n(const __grid_constant__ Group<RowsInvSlot<T>> g, const C<T>* __restrict__ tw, int H) {
   constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
   constexpr int per_k = 2 * V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);          // V * N
   C<T>* stage = buf + V * N;                               // H * per_k
-  const int f = blockIdx.y;
+  const int ks = slot_of(g, blockIdx.y);
+  const RowsInvSlot<T>& sl = g.slot[ks];
+  const int f = blockIdx.y - g.start[ks];
+  const int nrows = sl.nrows, ldu = sl.ldu, old = sl.old, ocol0 = sl.ocol0, ncols = sl.ncols;
+  const int ald = sl.ald, ar0 = sl.ar0, ac0 = sl.ac0;
+  T* __restrict__ out = sl.out;
+  const T* __restrict__ add = sl.add;
+  const long long ofs = sl.ofs, afs = sl.afs;
   const int r0 = blockIdx.x * 2 * V;
-  const C<T>* src = uin + (size_t)f * ufs;
+  if (r0 >= nrows) return;
+  const C<T>* src = sl.uin + (size_t)f * sl.ufs;
   for (int idx = threadIdx.x; idx < H * per_k; idx += V * THR) {
     const int k = idx / per_k, rr = idx - k * per_k;
     const int row = r0 + rr;
@@ -206,24 +234,23 @@ rows_inv_n(const C<T>* __restrict__ uin, int ldu, long long ufs, int nrows, T* _
 
 // ---------------------------------------------------------------- dispatch --
 template <typename T, int N>
-cudaError_t go_rows_fwd(const T* in, int nrows, int ncols, long long ifs, int ild, C<T>* tout,
-                        int ldt, long long tfs, int B, const C<T>* tw, int H, cudaStream_t s) {
+cudaError_t go_rows_fwd(const Group<RowsFwdSlot<T>>& g, const C<T>* tw, int H, cudaStream_t s) {
   constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
   const size_t sm = sizeof(C<T>) * V * N;
   static int smem_set = 0;
   auto kern = rows_fwd_n<T, N>;
   cudaError_t e = ensure_smem(kern, sm, smem_set);
   if (e != cudaSuccess) return e;
-  dim3 grid((nrows + 2 * V - 1) / (2 * V), B);
-  kern<<<grid, V * THR, sm, s>>>(in, nrows, ncols, ifs, ild, tout, ldt, tfs, tw, H);
+  int rows = 0;
+  for (int k = 0; k < g.n; ++k) rows = g.slot[k].nrows > rows ? g.slot[k].nrows : rows;
+  if (rows == 0 || g.start[g.n] == 0) return cudaSuccess;
+  dim3 grid((rows + 2 * V - 1) / (2 * V), g.start[g.n]);
+  kern<<<grid, V * THR, sm, s>>>(g, tw, H);
   return cudaGetLastError();
 }
 
 template <typename T, int N>
-cudaError_t go_cols(const C<T>* tin, int ldt, long long tfs, int nrin, C<T>* uout, int ldu,
-                    long long ufs, int orow0, int nrout, const T* lam, int mode, double2* blk,
-                    int blk_kx, int blk_ky, int nblk, int B, int H, const C<T>* tw,
-                    cudaStream_t s) {
+cudaError_t go_cols(Group<ColsSlot<T>>& g, int mode, int H, const C<T>* tw, cudaStream_t s) {
   constexpr int V = ColVecs<N>::value, THR = Radix23<N>::THR;
   const size_t sm = (sizeof(C<T>) + sizeof(T)) * V * N;
   static int smem_set = 0;
@@ -231,27 +258,29 @@ cudaError_t go_cols(const C<T>* tin, int ldt, long long tfs, int nrin, C<T>* uou
   cudaError_t e = ensure_smem(kern, sm, smem_set);
   if (e != cudaSuccess) return e;
   // each CTA keeps its lambda columns in shared memory for all of its fields:
-  // few field groups means lambda is read from HBM only that many times
-  const int fgroups = B < 2 ? B : 2;
-  dim3 grid((H + V - 1) / V, fgroups);
-  kern<<<grid, V * THR, sm, s>>>(tin, ldt, tfs, nrin, uout, ldu, ufs, orow0, nrout, lam, mode, blk,
-                                 blk_kx, blk_ky, nblk, B, H, tw);
+  // two field groups per slot means lambda is read from HBM only twice
+  g.start[0] = 0;
+  for (int k = 0; k < g.n; ++k)
+    g.start[k + 1] = g.start[k] + (g.slot[k].B < 2 ? g.slot[k].B : 2);
+  if (g.start[g.n] == 0) return cudaSuccess;
+  dim3 grid((H + V - 1) / V, g.start[g.n]);
+  kern<<<grid, V * THR, sm, s>>>(g, mode, H, tw);
   return cudaGetLastError();
 }
 
 template <typename T, int N>
-cudaError_t go_rows_inv(const C<T>* uin, int ldu, long long ufs, int nrows, T* out, int old,
-                        long long ofs, int ocol0, int ncols, const T* add, int ald, long long afs,
-                        int ar0, int ac0, int B, const C<T>* tw, int H, cudaStream_t s) {
+cudaError_t go_rows_inv(const Group<RowsInvSlot<T>>& g, const C<T>* tw, int H, cudaStream_t s) {
   constexpr int V = VecsPerCta<N>::value, THR = Radix23<N>::THR;
   const size_t sm = sizeof(C<T>) * (V * N + (size_t)(N / 2 + 1) * 2 * V);
   static int smem_set = 0;
   auto kern = rows_inv_n<T, N>;
   cudaError_t e = ensure_smem(kern, sm, smem_set);
   if (e != cudaSuccess) return e;
-  dim3 grid((nrows + 2 * V - 1) / (2 * V), B);
-  kern<<<grid, V * THR, sm, s>>>(uin, ldu, ufs, nrows, out, old, ofs, ocol0, ncols, add, ald, afs,
-                                 ar0, ac0, tw, H);
+  int rows = 0;
+  for (int k = 0; k < g.n; ++k) rows = g.slot[k].nrows > rows ? g.slot[k].nrows : rows;
+  if (rows == 0 || g.start[g.n] == 0) return cudaSuccess;
+  dim3 grid((rows + 2 * V - 1) / (2 * V), g.start[g.n]);
+  kern<<<grid, V * THR, sm, s>>>(g, tw, H);
   return cudaGetLastError();
 }
 
@@ -259,19 +288,59 @@ cudaError_t go_rows_inv(const C<T>* uin, int ldu, long long ufs, int nrows, T* o
 // workloads and their circulant embeddings.
 #define RK_SIZES(X) X(128) X(729) X(768) X(1024) X(1152) X(2048) X(2187) X(2304)
 
-template <typename T>
-bool launch_rows_fwd_n(const T* in, int nrows, int ncols, long long ifs, int ild, C<T>* tout,
-                       int ldt, long long tfs, int B, int N, const C<T>* tw, int H,
-                       cudaStream_t s, cudaError_t* err) {
+bool fftn_specialised(int N) {
   switch (N) {
-#define RK_CASE(NN)                                                                        \
-  case NN:                                                                                 \
-    *err = go_rows_fwd<T, NN>(in, nrows, ncols, ifs, ild, tout, ldt, tfs, B, tw, H, s); \
+#define RK_CASE(NN) case NN:
+    RK_SIZES(RK_CASE)
+#undef RK_CASE
     return true;
+    default: return false;
+  }
+}
+
+template <typename T>
+bool launch_rows_fwd_group(const Group<RowsFwdSlot<T>>& g, int N, const C<T>* tw, int H,
+                           cudaStream_t s, cudaError_t* err) {
+  switch (N) {
+#define RK_CASE(NN) case NN: *err = go_rows_fwd<T, NN>(g, tw, H, s); return true;
     RK_SIZES(RK_CASE)
 #undef RK_CASE
     default: return false;
   }
+}
+
+template <typename T>
+bool launch_cols_group(Group<ColsSlot<T>>& g, int mode, int N, const C<T>* tw, int H,
+                       cudaStream_t s, cudaError_t* err) {
+  switch (N) {
+#define RK_CASE(NN) case NN: *err = go_cols<T, NN>(g, mode, H, tw, s); return true;
+    RK_SIZES(RK_CASE)
+#undef RK_CASE
+    default: return false;
+  }
+}
+
+template <typename T>
+bool launch_rows_inv_group(const Group<RowsInvSlot<T>>& g, int N, const C<T>* tw, int H,
+                           cudaStream_t s, cudaError_t* err) {
+  switch (N) {
+#define RK_CASE(NN) case NN: *err = go_rows_inv<T, NN>(g, tw, H, s); return true;
+    RK_SIZES(RK_CASE)
+#undef RK_CASE
+    default: return false;
+  }
+}
+
+// single-plan passes: one slot
+template <typename T>
+bool launch_rows_fwd_n(const T* in, int nrows, int ncols, long long ifs, int ild, C<T>* tout,
+                       int ldt, long long tfs, int B, int N, const C<T>* tw, int H,
+                       cudaStream_t s, cudaError_t* err) {
+  Group<RowsFwdSlot<T>> g;
+  g.n = 1;
+  g.start[1] = B;
+  g.slot[0] = RowsFwdSlot<T>{in, tout, ifs, tfs, nrows, ncols, ild, ldt, B};
+  return launch_rows_fwd_group<T>(g, N, tw, H, s, err);
 }
 
 template <typename T>
@@ -279,16 +348,11 @@ bool launch_cols_n(const C<T>* tin, int ldt, long long tfs, int nrin, C<T>* uout
                    long long ufs, int orow0, int nrout, const T* lam, int mode, double2* blk,
                    int blk_kx, int blk_ky, int nblk, int B, int H, int N, const C<T>* tw,
                    cudaStream_t s, cudaError_t* err) {
-  switch (N) {
-#define RK_CASE(NN)                                                                           \
-  case NN:                                                                                    \
-    *err = go_cols<T, NN>(tin, ldt, tfs, nrin, uout, ldu, ufs, orow0, nrout, lam, mode, blk, \
-                          blk_kx, blk_ky, nblk, B, H, tw, s);                                 \
-    return true;
-    RK_SIZES(RK_CASE)
-#undef RK_CASE
-    default: return false;
-  }
+  Group<ColsSlot<T>> g;
+  g.n = 1;
+  g.slot[0] = ColsSlot<T>{tin, uout, lam, blk, tfs, ufs, ldt, nrin, ldu, orow0, nrout,
+                          blk_kx, blk_ky, nblk, B};
+  return launch_cols_group<T>(g, mode, N, tw, H, s, err);
 }
 
 template <typename T>
@@ -296,16 +360,12 @@ bool launch_rows_inv_n(const C<T>* uin, int ldu, long long ufs, int nrows, T* ou
                        long long ofs, int ocol0, int ncols, const T* add, int ald, long long afs,
                        int ar0, int ac0, int B, int N, const C<T>* tw, int H, cudaStream_t s,
                        cudaError_t* err) {
-  switch (N) {
-#define RK_CASE(NN)                                                                           \
-  case NN:                                                                                    \
-    *err = go_rows_inv<T, NN>(uin, ldu, ufs, nrows, out, old, ofs, ocol0, ncols, add, ald,   \
-                              afs, ar0, ac0, B, tw, H, s);                                    \
-    return true;
-    RK_SIZES(RK_CASE)
-#undef RK_CASE
-    default: return false;
-  }
+  Group<RowsInvSlot<T>> g;
+  g.n = 1;
+  g.start[1] = B;
+  g.slot[0] = RowsInvSlot<T>{uin, out, add, ufs, ofs, afs, ldu, nrows, old, ocol0, ncols, ald,
+                             ar0, ac0, B};
+  return launch_rows_inv_group<T>(g, N, tw, H, s, err);
 }
 
 #define RK_INST(T)                                                                             \
@@ -316,7 +376,13 @@ bool launch_rows_inv_n(const C<T>* uin, int ldu, long long ufs, int nrows, T* ou
                                  const C<T>*, cudaStream_t, cudaError_t*);                      \
   template bool launch_rows_inv_n<T>(const C<T>*, int, long long, int, T*, int, long long, int, \
                                      int, const T*, int, long long, int, int, int, int,         \
-                                     const C<T>*, int, cudaStream_t, cudaError_t*);
+                                     const C<T>*, int, cudaStream_t, cudaError_t*);             \
+  template bool launch_rows_fwd_group<T>(const Group<RowsFwdSlot<T>>&, int, const C<T>*, int,   \
+                                         cudaStream_t, cudaError_t*);                           \
+  template bool launch_cols_group<T>(Group<ColsSlot<T>>&, int, int, const C<T>*, int,           \
+                                     cudaStream_t, cudaError_t*);                               \
+  template bool launch_rows_inv_group<T>(const Group<RowsInvSlot<T>>&, int, const C<T>*, int,   \
+                                         cudaStream_t, cudaError_t*);
 RK_INST(float)
 RK_INST(double)
 

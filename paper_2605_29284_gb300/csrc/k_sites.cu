@@ -50,99 +50,122 @@ cudaError_t launch_kn_factor(double* kn, int L, double hx, double hy, double rho
 
 // ---------------------------------------------------------------- weights --
 // Steps 3-4: central box, k_i and A_i = K_N^{-1} k_i (two triangular solves
-// with the Cholesky factor), one thread per site, double throughout.  Also
-// s_i = sqrt(max(0, sigma2 - k_i^T A_i)) for conditional simulation.
-template <int W>
-__global__ void __launch_bounds__(128, 4)
-weights_kernel(const double* __restrict__ xy, int n, double x0, double x1,
-                               double y0, double y1, double hx, double hy, int nx, int ny,
-                               double rho, double sigma2, int nu_code,
-                               const double* __restrict__ kn, int* __restrict__ box,
-                               double* __restrict__ w64, float* __restrict__ w32,
-                               double* __restrict__ ssd, int* flag) {
+// with the Cholesky factor), double throughout, and s_i = sqrt(max(0, sigma2 -
+// k_i^T A_i)) for conditional simulation.
+// G lanes per site: GB300's FP64 pipe takes one warp instruction per 64
+// cycles per scheduler, so one thread per site (~M^2 dependent operations
+// each) would leave the kernel's duration to a few long instruction chains.  Lane j holds rows r = j + s G (s < S) of k_i;
+// each substitution step broadcasts the solved entry from its owner lane.
+template <int W, int G>
+__global__ void __launch_bounds__(128)
+weights_grp_kernel(const double* __restrict__ xy, int n, double x0, double x1, double y0,
+                   double y1, double hx, double hy, int nx, int ny, double rho, double sigma2,
+                   int nu_code, const double* __restrict__ kn, int* __restrict__ box,
+                   double* __restrict__ w64, float* __restrict__ w32,
+                   double* __restrict__ ssd, int* flag) {
   constexpr int M = W * W;
   constexpr int L = W / 2;
+  constexpr int S = (M + G - 1) / G;
   __shared__ double Ls[M * M];
-  __shared__ double Linv[M];     // reciprocals of the factor's diagonal
-  for (int i = threadIdx.x; i < M * M; i += blockDim.x) Ls[i] = kn[i];
-  for (int i = threadIdx.x; i < M; i += blockDim.x) Linv[i] = 1.0 / kn[i * M + i];
+  __shared__ double Linv[M];
+  for (int t = threadIdx.x; t < M * M; t += blockDim.x) Ls[t] = kn[t];
+  for (int t = threadIdx.x; t < M; t += blockDim.x) Linv[t] = 1.0 / kn[t * M + t];
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double x = xy[2 * i], y = xy[2 * i + 1];
-  if (!(x >= x0 && x <= x1 && y >= y0 && y <= y1)) {
-    atomicOr(flag, 2);
-    box[2 * i] = 0; box[2 * i + 1] = 0;
-    for (int q = 0; q < M; ++q) { w64[(size_t)i * M + q] = 0.0; w32[(size_t)i * M + q] = 0.f; }
-    ssd[i] = 0.0;
-    return;
-  }
-  const double gx = (x - x0) / hx, gy = (y - y0) / hy;
+  const int j = threadIdx.x % G;
+  const int i = blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+  const bool act = i < n;
+  const double x = act ? xy[2 * i] : x0, y = act ? xy[2 * i + 1] : y0;
+  const bool inside = x >= x0 && x <= x1 && y >= y0 && y <= y1;
+  const double gx = inside ? (x - x0) / hx : 0.0, gy = inside ? (y - y0) / hy : 0.0;
   double fx = floor(gx), fy = floor(gy);
   fx = fmin(fmax(fx, 0.0), (double)(nx - 2));
   fy = fmin(fmax(fy, 0.0), (double)(ny - 2));
-  const int ix = (int)fx, iy = (int)fy;
   const double u = gx - fx, v = gy - fy;
-  // z = k_i, then the column-oriented substitutions L y = k, L^T w = y in
-  // place.  z lives in shared memory, [q][thread] (conflict-free): FP64
-  // arithmetic, not shared-memory bandwidth, bounds this kernel.
-  extern __shared__ double zs_raw[];
-  double* z = zs_raw + threadIdx.x;
-  const int S = blockDim.x;
-#pragma unroll 4
-  for (int q = 0; q < M; ++q) {
-    const int a = q % W, b = q / W;
-    const double dx = ((double)(a - (L - 1)) - u) * hx;
-    const double dy = ((double)(b - (L - 1)) - v) * hy;
-    z[q * S] = sigma2 * matern_phi<double>(sqrt(dx * dx + dy * dy) / rho, nu_code);
+  double z[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int r = j + s * G;
+    double val = 0.0;
+    if (r < M) {
+      const int a = r % W, b = r / W;
+      const double dx = ((double)(a - (L - 1)) - u) * hx;
+      const double dy = ((double)(b - (L - 1)) - v) * hy;
+      val = sigma2 * matern_phi<double>(sqrt(dx * dx + dy * dy) / rho, nu_code);
+    }
+    z[s] = val;
   }
-  double yy = 0.0;   // |L^{-1} k_i|^2 = k_i^T K_N^{-1} k_i = k_i^T W_i
-  for (int c = 0; c < M; ++c) {
-    const double zc = z[c * S] * Linv[c];
-    z[c * S] = zc;
+  double yy = 0.0;
+#pragma unroll
+  for (int c = 0; c < M; ++c) {          // L y = k
+    const double zc = __shfl_sync(0xffffffffu, z[c / G], c % G, G) * Linv[c];
+    if (j == c % G) z[c / G] = zc;
     yy = fma(zc, zc, yy);
-#pragma unroll 4
-    for (int r = c + 1; r < M; ++r) z[r * S] = fma(-Ls[r * M + c], zc, z[r * S]);
+#pragma unroll
+    for (int s = c / G; s < S; ++s) {
+      const int r = j + s * G;
+      if (r > c && r < M) z[s] = fma(-Ls[r * M + c], zc, z[s]);
+    }
   }
-  for (int c = M - 1; c >= 0; --c) {
-    const double zc = z[c * S] * Linv[c];
-    z[c * S] = zc;
-#pragma unroll 4
-    for (int r = 0; r < c; ++r) z[r * S] = fma(-Ls[c * M + r], zc, z[r * S]);
+#pragma unroll
+  for (int c = M - 1; c >= 0; --c) {     // L^T w = y
+    const double zc = __shfl_sync(0xffffffffu, z[c / G], c % G, G) * Linv[c];
+    if (j == c % G) z[c / G] = zc;
+#pragma unroll
+    for (int s = 0; s <= c / G; ++s) {
+      const int r = j + s * G;
+      if (r < c) z[s] = fma(-Ls[c * M + r], zc, z[s]);
+    }
   }
-  for (int q = 0; q < M; ++q) {
-    const double wq = z[q * S];
-    w64[(size_t)i * M + q] = wq;
-    w32[(size_t)i * M + q] = (float)wq;
+  if (!act) return;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int r = j + s * G;
+    if (r < M) {
+      const double wq = inside ? z[s] : 0.0;
+      w64[(size_t)i * M + r] = wq;
+      w32[(size_t)i * M + r] = (float)wq;
+    }
   }
-  box[2 * i] = ix;
-  box[2 * i + 1] = iy;
-  ssd[i] = sqrt(fmax(0.0, sigma2 - yy));
+  if (j == 0) {
+    if (!inside) atomicOr(flag, 2);
+    box[2 * i] = inside ? (int)fx : 0;
+    box[2 * i + 1] = inside ? (int)fy : 0;
+    ssd[i] = inside ? sqrt(fmax(0.0, sigma2 - yy)) : 0.0;
+  }
+}
+
+// Lanes per site: about two warps per scheduler (152 SMs x 4), i.e. the
+// largest power of two G <= 2 * 608 * 32 / n, kept within [4, min(32, M)].
+// More lanes per site shorten each warp's chain of FP64 instructions but
+// spend issue slots on rows that are already solved.
+inline int weights_lanes(int n, int M) {
+  const long long target = 2LL * 152 * 4 * 32;
+  int g = 4;
+  while (g < 32 && 2 * g <= M && (long long)n * 2 * g <= target) g *= 2;
+  return g < M ? g : M;
 }
 
 cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, double* w64,
                            float* w32, double* ssd, int* flag, cudaStream_t s) {
-  const int threads = 128, blocks = (n + threads - 1) / threads;
-#define RK_W(WW)                                                                               \
-  {                                                                                            \
-    static int smem_set = 0;                                                                   \
-    const size_t sm = sizeof(double) * (WW) * (WW) * threads;                                  \
-    cudaError_t e = ensure_smem(weights_kernel<WW>, sm, smem_set);                             \
-    if (e != cudaSuccess) return e;                                                            \
-    weights_kernel<WW><<<blocks, threads, sm, s>>>(xy, n, p->x0, p->x1, p->y0, p->y1, p->hx, \
-                                                   p->hy, p->nx, p->ny, p->rho, p->sigma2,  \
-                                                   p->nu_code, p->kn_chol, box, w64, w32,   \
-                                                   ssd, flag);                              \
+  const int threads = 128;
+  const int G = weights_lanes(n, p->M);
+#define RK_WG(WW, GG)                                                                          \
+  if (G == GG) {                                                                               \
+    const int sites = threads / GG;                                                            \
+    weights_grp_kernel<WW, GG><<<(n + sites - 1) / sites, threads, 0, s>>>(                    \
+        xy, n, p->x0, p->x1, p->y0, p->y1, p->hx, p->hy, p->nx, p->ny, p->rho, p->sigma2,     \
+        p->nu_code, p->kn_chol, box, w64, w32, ssd, flag);                                     \
+    return cudaGetLastError();                                                                 \
   }
   switch (p->L) {
-    case 1: RK_W(2); break;
-    case 2: RK_W(4); break;
-    case 3: RK_W(6); break;
-    case 4: RK_W(8); break;
+    case 1: RK_WG(2, 4) break;
+    case 2: RK_WG(4, 4) RK_WG(4, 8) RK_WG(4, 16) break;
+    case 3: RK_WG(6, 4) RK_WG(6, 8) RK_WG(6, 16) RK_WG(6, 32) break;
+    case 4: RK_WG(8, 4) RK_WG(8, 8) RK_WG(8, 16) RK_WG(8, 32) break;
     default: return cudaErrorInvalidValue;
   }
-#undef RK_W
-  return cudaGetLastError();
+#undef RK_WG
+  return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------ set weights --
@@ -189,70 +212,84 @@ cudaError_t launch_set_weights(const int* box_in, const double* w_in, int n, con
 // and block frequency (kx, ky), kx in [0, KX], ky in [-KY, KY],
 //   E_i(kx, ky) = sum_{a,b} A_i[a + 2L b] exp(-2 pi i (kx (ix + a) / px + ky (iy + b) / py)),
 // so that F(c*)(kx, ky) = sum_i c_i E_i(kx, ky) exactly (c* = A^T c).
-// Layout efac[j][i], j = kx (2 KY + 1) + (ky + KY).  One thread per (site, kx).
+// Layout efac[j][i], j = kx (2 KY + 1) + (ky + KY).  A CTA takes NS sites:
+// first the row sums t_i(kx, b) = sum_a A_i[a + 2L b] exp(-2 pi i kx (ix + a) / px)
+// into shared memory, one thread per (site, kx, b), then one thread per
+// (site, kx, ky) entry, E = sum_b t_i(kx, b) exp(-2 pi i ky (iy + b) / py).
+// Twiddle indices stay below 2^31 (kx, |ky| <= 1024, torus <= 2^21).
 __global__ void block_factor_kernel(const int* __restrict__ box, const double* __restrict__ w64,
-                                    int n, int L, int px, int py, int KX, int KY,
+                                    int n, int L, int px, int py, int KX, int KY, int NS,
                                     const double2* __restrict__ twx,
                                     const double2* __restrict__ twy,
                                     double2* __restrict__ efac) {
-  const int W = 2 * L, M = W * W;
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= (long long)n * (KX + 1)) return;
-  const int i = (int)(tid % n), kx = (int)(tid / n);
-  const int ix = box[2 * i], iy = box[2 * i + 1];
-  // t[b] = sum_a A[a, b] exp(-2 pi i kx (ix + a) / px); twx[e] = exp(-2 pi i e / px)
-  double2 t[8];
-  for (int b = 0; b < W; ++b) t[b] = make_double2(0.0, 0.0);
-  for (int a = 0; a < W; ++a) {
-    const double2 e = twx[((long long)kx * (ix + a)) % px];
-    for (int b = 0; b < W; ++b) {
+  extern __shared__ double2 tsm[];        // [NS][KX + 1][2L]
+  const int W = 2 * L, M = W * W, nk = KX + 1, bw = 2 * KY + 1;
+  const int i0 = blockIdx.x * NS;
+  const int ns = min(NS, n - i0);
+  for (int e = threadIdx.x; e < ns * nk * W; e += blockDim.x) {
+    const int b = e % W, kx = (e / W) % nk, si = e / (W * nk);
+    const int i = i0 + si, ix = box[2 * i];
+    double2 t = make_double2(0.0, 0.0);
+    for (int a = 0; a < W; ++a) {
+      const double2 tw = twx[(kx * (ix + a)) % px];
       const double w = w64[(size_t)i * M + a + W * b];
-      t[b].x += w * e.x;
-      t[b].y += w * e.y;
+      t.x = fma(w, tw.x, t.x);
+      t.y = fma(w, tw.y, t.y);
     }
+    tsm[e] = t;    // e = (si * nk + kx) * W + b
   }
-  const int bw = 2 * KY + 1;
-  for (int j = 0; j < bw; ++j) {
-    const int ky = j - KY;
-    double2 e = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int e = threadIdx.x; e < nk * bw * ns; e += blockDim.x) {
+    const int si = e % ns, jj = (e / ns) % bw, kx = e / (ns * bw);
+    const int i = i0 + si, iy = box[2 * i + 1], ky = jj - KY;
+    const double2* t = tsm + (si * nk + kx) * W;
+    double2 acc = make_double2(0.0, 0.0);
     for (int b = 0; b < W; ++b) {
-      long long m = ((long long)ky * (iy + b)) % py;
+      int m = (ky * (iy + b)) % py;
       if (m < 0) m += py;
       const double2 f = twy[m];
-      // t[b] * exp(-2 pi i ky (iy + b) / py)
-      e.x += t[b].x * f.x - t[b].y * f.y;
-      e.y += t[b].x * f.y + t[b].y * f.x;
+      acc.x = fma(t[b].x, f.x, fma(-t[b].y, f.y, acc.x));
+      acc.y = fma(t[b].x, f.y, fma(t[b].y, f.x, acc.y));
     }
-    efac[((size_t)kx * bw + j) * n + i] = e;
+    efac[((size_t)kx * bw + jj) * n + i] = acc;
   }
 }
 
 cudaError_t launch_block_factors(const int* box, const double* w64, int n, const rk_plan* p,
                                  int kx, int ky, double2* efac, cudaStream_t s) {
-  const long long total = (long long)n * (kx + 1);
-  const int threads = 128;
-  const long long blocks = (total + threads - 1) / threads;
-  block_factor_kernel<<<(unsigned)blocks, threads, 0, s>>>(box, w64, n, p->L, p->px, p->py, kx,
-                                                          ky, p->tw64x, p->tw64y, efac);
+  const int W = 2 * p->L;
+  const size_t per_site = sizeof(double2) * (size_t)(kx + 1) * W;
+  // sites per CTA: two CTAs per SM at least, at most 32 KB of row sums
+  int NS = n / (2 * 152);
+  const int cap = (int)(32768 / per_site);
+  NS = NS > cap ? cap : NS;
+  NS = NS > 32 ? 32 : NS;
+  NS = NS < 1 ? 1 : NS;
+  const size_t sm = per_site * NS;
+  static int smem_set = 0;
+  cudaError_t e = ensure_smem(block_factor_kernel, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  block_factor_kernel<<<(n + NS - 1) / NS, 128, sm, s>>>(box, w64, n, p->L, p->px, p->py, kx, ky,
+                                                         NS, p->tw64x, p->tw64y, efac);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ block GEMM --
 // blk[f][j] = sum_i c[f][i] E_i(j), double.  One CTA per (j, field chunk).
-constexpr int kGemmF = 4;
+template <int F>
 __global__ void block_gemm_kernel(const double* __restrict__ c, int B, int n,
                                   const double2* __restrict__ efac, int nblk,
                                   double2* __restrict__ blk) {
   const int j = blockIdx.x;
-  const int f0 = blockIdx.y * kGemmF;
-  double ax[kGemmF], ay[kGemmF];
+  const int f0 = blockIdx.y * F;
+  double ax[F], ay[F];
 #pragma unroll
-  for (int q = 0; q < kGemmF; ++q) { ax[q] = 0.0; ay[q] = 0.0; }
+  for (int q = 0; q < F; ++q) { ax[q] = 0.0; ay[q] = 0.0; }
   const double2* e = efac + (size_t)j * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double2 ev = e[i];
 #pragma unroll
-    for (int q = 0; q < kGemmF; ++q) {
+    for (int q = 0; q < F; ++q) {
       if (f0 + q < B) {
         const double cv = c[(size_t)(f0 + q) * n + i];
         ax[q] = fma(cv, ev.x, ax[q]);
@@ -260,10 +297,10 @@ __global__ void block_gemm_kernel(const double* __restrict__ c, int B, int n,
       }
     }
   }
-  __shared__ double red[2 * kGemmF][32];
+  __shared__ double red[2 * F][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < kGemmF; ++q) {
+  for (int q = 0; q < F; ++q) {
     for (int o = 16; o > 0; o >>= 1) {
       ax[q] += __shfl_down_sync(0xffffffffu, ax[q], o);
       ay[q] += __shfl_down_sync(0xffffffffu, ay[q], o);
@@ -274,10 +311,10 @@ __global__ void block_gemm_kernel(const double* __restrict__ c, int B, int n,
   if (wid == 0) {
     const int nw = blockDim.x >> 5;
 #pragma unroll
-    for (int q = 0; q < kGemmF; ++q) {
+    for (int q = 0; q < F; ++q) {
       double sx = lane < nw ? red[2 * q][lane] : 0.0;
       double sy = lane < nw ? red[2 * q + 1][lane] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = 4; o > 0; o >>= 1) {      // nw <= 8
         sx += __shfl_down_sync(0xffffffffu, sx, o);
         sy += __shfl_down_sync(0xffffffffu, sy, o);
       }
@@ -286,10 +323,63 @@ __global__ void block_gemm_kernel(const double* __restrict__ c, int B, int n,
   }
 }
 
+// The block GEMMs of several plans in one launch (rk_predict_group): grid.y
+// runs over every plan's fields, grid.x over the largest block.
+__global__ void block_gemm_group_kernel(const __grid_constant__ Group<BlockGemmSlot> g) {
+  int ks = 0;
+  while (ks + 1 < g.n && (int)blockIdx.y >= g.start[ks + 1]) ++ks;
+  const BlockGemmSlot& sl = g.slot[ks];
+  const int j = blockIdx.x;
+  if (j >= sl.nblk) return;
+  const int f = blockIdx.y - g.start[ks], n = sl.n;
+  const double2* e = sl.efac + (size_t)j * n;
+  const double* c = sl.c + (size_t)f * n;
+  double ax = 0.0, ay = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 ev = e[i];
+    const double cv = c[i];
+    ax = fma(cv, ev.x, ax);
+    ay = fma(cv, ev.y, ay);
+  }
+  __shared__ double red[2][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_down_sync(0xffffffffu, ax, o);
+    ay += __shfl_down_sync(0xffffffffu, ay, o);
+  }
+  if (lane == 0) { red[0][wid] = ax; red[1][wid] = ay; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    double sx = lane < nw ? red[0][lane] : 0.0;
+    double sy = lane < nw ? red[1][lane] : 0.0;
+    for (int o = 4; o > 0; o >>= 1) {
+      sx += __shfl_down_sync(0xffffffffu, sx, o);
+      sy += __shfl_down_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) sl.blk[(size_t)f * sl.nblk + j] = make_double2(sx, sy);
+  }
+}
+
+cudaError_t launch_block_gemm_group(const Group<BlockGemmSlot>& g, cudaStream_t s) {
+  int most = 0;
+  for (int k = 0; k < g.n; ++k) most = g.slot[k].nblk > most ? g.slot[k].nblk : most;
+  if (g.n == 0 || most == 0 || g.start[g.n] == 0) return cudaSuccess;
+  block_gemm_group_kernel<<<dim3(most, g.start[g.n]), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// blk[f][j] = sum_i c[f][i] E_i(j), double: one CTA per (j, group of F
+// fields), F = 1, 2 or 4 by the batch, so small batches spend no FP64 issue
+// slots on empty accumulators.
 cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac, int nblk,
                               double2* blk, cudaStream_t s) {
-  dim3 grid(nblk, (B + kGemmF - 1) / kGemmF);
-  block_gemm_kernel<<<grid, 256, 0, s>>>(c, B, n, efac, nblk, blk);
+  if (nblk <= 0 || B <= 0) return cudaSuccess;
+  const int F = B >= 4 ? 4 : B >= 2 ? 2 : 1;
+  dim3 grid(nblk, (B + F - 1) / F);
+  if (F == 4) block_gemm_kernel<4><<<grid, 256, 0, s>>>(c, B, n, efac, nblk, blk);
+  else if (F == 2) block_gemm_kernel<2><<<grid, 256, 0, s>>>(c, B, n, efac, nblk, blk);
+  else block_gemm_kernel<1><<<grid, 256, 0, s>>>(c, B, n, efac, nblk, blk);
   return cudaGetLastError();
 }
 
@@ -322,6 +412,53 @@ cudaError_t launch_scatter(const int* box, const T* w, const T* c, int n, int B,
   return cudaGetLastError();
 }
 
+// The scatter of several plans in one launch (rk_predict_group): slot k
+// covers fields [start[k], start[k + 1]) of grid.y.  zero_group_kernel
+// clears every slot's c* first (grid.y = slot).
+template <typename T>
+__global__ void scatter_group_kernel(const __grid_constant__ Group<ScatterSlot<T>> g) {
+  int ks = 0;
+  while (ks + 1 < g.n && (int)blockIdx.y >= g.start[ks + 1]) ++ks;
+  const ScatterSlot<T>& sl = g.slot[ks];
+  const int f = blockIdx.y - g.start[ks];
+  const int W = 2 * sl.L, M = W * W;
+  const long long total = (long long)sl.n * M;
+  T* cs = sl.cstar + (size_t)f * sl.p1y * sl.p1x;
+  const T* cf = sl.c + (size_t)f * sl.n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / M), q = (int)(t - (long long)i * M);
+    const int a = q % W, b = q / W;
+    const int px = sl.box[2 * i] + a, py = sl.box[2 * i + 1] + b;
+    atomicAdd(cs + (size_t)py * sl.p1x + px, sl.w[t] * cf[i]);
+  }
+}
+
+template <typename T>
+__global__ void zero_group_kernel(const __grid_constant__ Group<ScatterSlot<T>> g) {
+  const ScatterSlot<T>& sl = g.slot[blockIdx.y];
+  const size_t count = (size_t)sl.B * sl.p1y * sl.p1x;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+       t += (size_t)gridDim.x * blockDim.x)
+    sl.cstar[t] = T(0);
+}
+
+template <typename T>
+cudaError_t launch_scatter_group(const Group<ScatterSlot<T>>& g, cudaStream_t s) {
+  long long most = 0;
+  for (int k = 0; k < g.n; ++k) {
+    const long long t = (long long)g.slot[k].n * (2 * g.slot[k].L) * (2 * g.slot[k].L);
+    most = t > most ? t : most;
+  }
+  if (g.n == 0 || g.start[g.n] == 0) return cudaSuccess;
+  zero_group_kernel<T><<<dim3(128, g.n), 256, 0, s>>>(g);
+  long long blocks = (most + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  scatter_group_kernel<T><<<dim3((unsigned)blocks, g.start[g.n]), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void convert_kernel(const double* __restrict__ src, T* __restrict__ dst, size_t count) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
@@ -339,6 +476,8 @@ template cudaError_t launch_scatter<float>(const int*, const float*, const float
                                            float*, int, int, cudaStream_t);
 template cudaError_t launch_scatter<double>(const int*, const double*, const double*, int, int,
                                             int, double*, int, int, cudaStream_t);
+template cudaError_t launch_scatter_group<float>(const Group<ScatterSlot<float>>&, cudaStream_t);
+template cudaError_t launch_scatter_group<double>(const Group<ScatterSlot<double>>&, cudaStream_t);
 template cudaError_t launch_convert<float>(const double*, float*, size_t, cudaStream_t);
 template cudaError_t launch_convert<double>(const double*, double*, size_t, cudaStream_t);
 

@@ -407,6 +407,91 @@ rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* 
   return RK_OK;
 }
 
+// Steps 5-7 for several plans sharing the torus, each pass one launch over
+// all of their fields: the block GEMMs on the first plan's side stream, the
+// zeroing and scatter, rows_fwd, cols and rows_inv on its stream.
+template <typename T>
+rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
+  rk_plan* p0 = plans[0];
+  cudaStream_t s = p0->stream;
+  const bool f32 = sizeof(T) == sizeof(float);
+  bool any_blk = false;
+  double sc_b = 0, rf_b = 0, co_b = 0, ri_b = 0, bg_b = 0;
+  Group<ScatterSlot<T>> gs;
+  Group<RowsFwdSlot<T>> gf;
+  Group<ColsSlot<T>> gc;
+  Group<RowsInvSlot<T>> gi;
+  Group<BlockGemmSlot> gb;
+  gs.n = gf.n = gc.n = gi.n = gb.n = np;
+  for (int k = 0; k < np; ++k) {
+    rk_plan* p = plans[k];
+    const int B = p->B;
+    const size_t plane = (size_t)p->p1y * p->p1x;
+    const bool blk = f32 && p->nblk > 0;
+    any_blk = any_blk || blk;
+    const T* w = f32 ? (const T*)p->w32 : (const T*)p->w64;
+    const T* cT = f32 ? (const T*)p->c32 : (const T*)p->c64;
+    const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
+    gs.slot[k] = ScatterSlot<T>{p->box, w, cT, (T*)p->cstar, p->n, B, p->L, p->p1x, p->p1y};
+    gf.slot[k] = RowsFwdSlot<T>{(const T*)p->cstar, (C<T>*)p->tbuf, (long long)plane,
+                                (long long)p->H * p->ldt, p->p1y, p->p1x, p->p1x, p->ldt, B};
+    gc.slot[k] = ColsSlot<T>{(const C<T>*)p->tbuf, (C<T>*)p->ubuf, lam, blk ? p->blk : nullptr,
+                             (long long)p->H * p->ldt, (long long)p->H * p->ldu, p->ldt, p->p1y,
+                             p->ldu, p->L - 1, p->ny, p->blk_kx, p->blk_ky, p->nblk, B};
+    gi.slot[k] = RowsInvSlot<T>{(const C<T>*)p->ubuf, (T*)outs[k], nullptr,
+                                (long long)p->H * p->ldu, (long long)p->ny * p->nx, 0, p->ldu,
+                                p->ny, p->nx, p->L - 1, p->nx, 0, 0, 0, B};
+    gb.slot[k] = BlockGemmSlot{p->c64, p->efac, p->blk, p->n, B, blk ? p->nblk : 0};
+    gb.start[k + 1] = gb.start[k] + B;
+    gs.start[k + 1] = gs.start[k] + B;
+    gf.start[k + 1] = gf.start[k] + B;
+    gi.start[k + 1] = gi.start[k] + B;
+    const double es = sizeof(T), cs = 2.0 * es, nM = (double)p->n * p->M;
+    sc_b += B * (plane * es + nM * 2 * es + p->n * es) + nM * es + p->n * 8.0;
+    rf_b += B * (plane * es + (double)p->H * p->p1y * cs);
+    co_b += B * ((double)p->H * p->p1y * cs + (double)p->H * p->ny * cs) + (double)p->H * p->py * es;
+    ri_b += B * ((double)p->H * p->ny * cs + (double)p->ny * p->nx * es);
+    if (blk) bg_b += (double)p->nblk * p->n * 16.0 + B * (p->n * 8.0 + p->nblk * 16.0);
+  }
+  const C<T>* twx = f32 ? (const C<T>*)p0->tw32x : (const C<T>*)p0->tw64x;
+  const C<T>* twy = f32 ? (const C<T>*)p0->tw32y : (const C<T>*)p0->tw64y;
+  cudaError_t err = cudaSuccess;
+  if (any_blk) {
+    RK_CU(cudaEventRecord(p0->ev_fork, s));
+    RK_CU(cudaStreamWaitEvent(p0->side, p0->ev_fork, 0));
+    cudaStream_t s_main = s;
+    {
+      cudaStream_t s = p0->side;
+      RK_PROF("block_gemm", bg_b);
+      RK_CU(launch_block_gemm_group(gb, s));
+    }
+    RK_CU(cudaEventRecord(p0->ev_join, p0->side));
+    (void)s_main;
+  }
+  {
+    RK_PROF("scatter", sc_b);
+    RK_CU(launch_scatter_group<T>(gs, s));
+  }
+  {
+    RK_PROF("rows_fwd", rf_b);
+    if (!launch_rows_fwd_group<T>(gf, p0->px, twx, p0->H, s, &err)) return RK_ERR_INVALID_ARG;
+    RK_CU(err);
+  }
+  if (any_blk) RK_CU(cudaStreamWaitEvent(s, p0->ev_join, 0));
+  {
+    RK_PROF("cols", co_b);
+    if (!launch_cols_group<T>(gc, COLS_CONV, p0->py, twy, p0->H, s, &err))
+      return RK_ERR_INVALID_ARG;
+    RK_CU(err);
+  }
+  {
+    RK_PROF("rows_inv", ri_b);
+    if (!launch_rows_inv_group<T>(gi, p0->px, twx, p0->H, s, &err)) return RK_ERR_INVALID_ARG;
+    RK_CU(err);
+  }
+  return RK_OK;
+}
+
 template <typename T>
 rk_status predict_impl(rk_plan* p, T* out) {
   const T* cT = sizeof(T) == sizeof(float) ? (const T*)p->c32 : (const T*)p->c64;
@@ -971,6 +1056,36 @@ rk_status rk_predict(rk_plan* p, void* out) {
   if (p->n == 0 || !p->have_coef) return RK_ERR_STATE;
   if (p->precision == RK_FP64) return predict_impl<double>(p, (double*)out);
   return predict_impl<float>(p, (float*)out);
+}
+
+rk_status rk_predict_group(rk_plan* const* plans, int nplans, void* const* outs) {
+  if (!plans || !outs || nplans < 1 || nplans > kMaxGroup) return RK_ERR_INVALID_ARG;
+  rk_plan* p0 = plans[0];
+  if (!p0) return RK_ERR_INVALID_ARG;
+  for (int k = 0; k < nplans; ++k) {
+    const rk_plan* p = plans[k];
+    if (!p || !outs[k]) return RK_ERR_INVALID_ARG;
+    if (p->n == 0 || !p->have_coef) return RK_ERR_STATE;
+    if (p->precision != p0->precision || p->px != p0->px || p->py != p0->py)
+      return RK_ERR_INVALID_ARG;
+    for (int j = 0; j < k; ++j)
+      if (plans[j] == p) return RK_ERR_INVALID_ARG;     // one plan's scratch, twice
+  }
+  if (fft_generic_only() || !fftn_specialised(p0->px) || !fftn_specialised(p0->py)) {
+    // no specialised pass for this torus: the plans one after another
+    for (int k = 0; k < nplans; ++k) {
+      rk_plan* p = plans[k];
+      cudaStream_t keep = p->stream;
+      p->stream = p0->stream;
+      const rk_status st = p->precision == RK_FP64 ? predict_impl<double>(p, (double*)outs[k])
+                                                   : predict_impl<float>(p, (float*)outs[k]);
+      p->stream = keep;
+      if (st != RK_OK) return st;
+    }
+    return RK_OK;
+  }
+  if (p0->precision == RK_FP64) return predict_group_impl<double>(plans, nplans, outs);
+  return predict_group_impl<float>(plans, nplans, outs);
 }
 
 rk_status rk_predict_host(rk_plan* p, int n, const double* xy_host, int B, const double* c_host,

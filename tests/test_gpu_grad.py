@@ -112,11 +112,13 @@ def test_autograd_gradcheck_fp64(rk):
 
     try:
         # the scatter accumulates with float atomics, so repeated backward calls
-        # agree to rounding, not bit for bit
+        # agree to rounding, not bit for bit; the theta-gradients contract
+        # predictions of M^{-1} c = M^{-2} z (tau^2 = 1e-4: cond(M)^2 ~ 1e8
+        # amplifies those last-bit differences), hence an absolute 1e-8
         # eps = 1e-4: with 1e-6 the rounding of the neighbourhood solve in the
         # re-created plans (cond K_N ~ 1e6 here) dominates the difference quotient
         assert torch.autograd.gradcheck(f, (z, lr, ls), eps=1e-4, atol=1e-5, rtol=1e-4,
-                                        fast_mode=True, nondet_tol=1e-10)
+                                        fast_mode=True, nondet_tol=1e-8)
     finally:
         clear_cache()
 

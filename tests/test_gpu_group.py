@@ -1,0 +1,94 @@
+"""rk_predict_group: several plans' predictions in one launch per pass.
+
+The grouped passes run the single-plan kernels' arithmetic with per-plan
+descriptors, so every plan's output must equal its own rk_predict (FP32 up
+to the order of the scatter's atomic additions), and through it the oracle.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import case, rel_err  # noqa: E402
+from oracle import rapid  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def rk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_29284_gb300 as m
+    return m
+
+
+def _plans(rk, m, ext, cells, prec, n=400, B=1, seed=31):
+    plans, coefs = [], []
+    for k, (nu, L) in enumerate(cells):
+        th = (nu, 0.15, 1.0)
+        xy, z, c, g = case(n, m, m, ext, *th, 1e-3, L, seed=seed + k, B=B)
+        p = rk.Plan(m, m, ext, *th, 1e-3, L, precision=prec)
+        p.set_sites(torch.from_numpy(xy).cuda())
+        p.set_coef(torch.from_numpy(np.atleast_2d(c)).cuda())
+        plans.append(p)
+        coefs.append((xy, c, g, th))
+    return plans, coefs
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp64", 1e-13)])
+def test_group_equals_single_plans_on_paper_cells(rk, prec, tol):
+    # the nine cells of the 350^2 paper configuration share the 729^2 torus
+    ext = (0.0, 1.6, 0.0, 1.0)
+    cells = [(nu, L) for nu in (0.5, 1.5, 2.5) for L in (1, 2, 3)]
+    plans, coefs = _plans(rk, 350, ext, cells, prec, n=1368)
+    try:
+        assert len({(p.info()["px"], p.info()["py"]) for p in plans}) == 1
+        single = [p.predict().double().cpu().numpy() for p in plans]
+        for _ in range(2):
+            outs = rk.predict_group(plans)
+            torch.cuda.synchronize()
+            for o, s in zip(outs, single):
+                assert rel_err(o.double().cpu().numpy(), s) <= tol
+        # and the first cell against the oracle's FFT steps
+        xy, c, g, th = coefs[0]
+        ref = rapid.predict(xy, c, g, *th, method="fft")
+        assert rel_err(outs[0].double().cpu().numpy(), ref) <= (2e-5 if prec == "fp32" else 1e-12)
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_group_with_batches_and_unspecialised_torus(rk):
+    # B = 3 fields per plan; and a 40 x 40 grid whose 81-point torus has no
+    # compile-time FFT (the plans then run one after another)
+    ext = (0.0, 1.0, 0.0, 1.0)
+    for m, cells in ((350, [(1.5, 2), (2.5, 1)]), (40, [(1.5, 2), (0.5, 2)])):
+        plans, _ = _plans(rk, m, ext, cells, "fp32", n=300, B=3)
+        try:
+            single = [p.predict().double().cpu().numpy() for p in plans]
+            outs = rk.predict_group(plans)
+            for o, s in zip(outs, single):
+                assert o.shape == (3, m, m)
+                assert rel_err(o.double().cpu().numpy(), s) <= 1e-6
+        finally:
+            for p in plans:
+                p.close()
+
+
+def test_group_rejects_bad_groups(rk):
+    ext = (0.0, 1.6, 0.0, 1.0)
+    a, _ = _plans(rk, 350, ext, [(1.5, 2)], "fp32")
+    b, _ = _plans(rk, 350, ext, [(1.5, 2)], "fp64")
+    c, _ = _plans(rk, 200, ext, [(1.5, 2)], "fp32")
+    empty = rk.Plan(350, 350, ext, 1.5, 0.15, 1.0, 1e-3, 2)
+    try:
+        for group in ([a[0], b[0]], [a[0], c[0]], [a[0], a[0]]):
+            with pytest.raises(rk.RkError) as e:
+                rk.predict_group(group, [torch.empty((1, 350, 350), device="cuda")] * len(group))
+            assert e.value.name == "RK_ERR_INVALID_ARG"
+        with pytest.raises(rk.RkError) as e:
+            rk.predict_group([a[0], empty], [torch.empty((1, 350, 350), device="cuda")] * 2)
+        assert e.value.name == "RK_ERR_STATE"
+    finally:
+        for p in a + b + c + [empty]:
+            p.close()
