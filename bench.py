@@ -308,7 +308,7 @@ def measure_cs(dev, steps, peaks, R=None):
         total += a.elapsed_time(b)
     rk.profile_enable(False)
     prof = rk.profile_read()
-    roof, kernels = roofline(prof, steps, peaks)
+    roof, kernels = roofline(prof, steps, peaks, "cs512")
     info = p.info()
     p.close()
     sec = total / steps / 1e3
@@ -360,18 +360,64 @@ def measure_backward(dev, steps, peaks, n=None):
                        "range": w["rho"], "L": w["L"], "tau2": w["tau2"]}}
 
 
-def roofline(prof, steps, peaks):
+# GB300's FP64 peak from its unit counts and clock: 152 SMs x 2070 MHz x
+# 4 FP64 operations per clock per SM (two fused multiply-adds) = 1.26 TFLOP/s,
+# NVIDIA's nominal 1.25 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel, the
+# workload it was taken on and a digest of the sources it was built from; the
+# bench reports it only while those sources are unchanged (profiles/ has the
+# captures and commands)
+TRAFFIC = {}
+
+
+def _sources_digest(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2605_29284_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, workload):
+    t = TRAFFIC.get(kernel)
+    if not t or t["workload"] != workload:
+        return None
+    try:
+        return t["bytes_per_launch"] if _sources_digest(t["sources"]) == t["digest"] else None
+    except OSError:
+        return None
+
+
+def roofline(prof, steps, peaks, workload=None):
+    """The dominant kernel's roofline (by time): HBM-bound passes as algorithmic
+    bytes per second against the measured copy bandwidth, FP64-bound passes as
+    algorithmic FP64 operations per second against the FP64 peak."""
     hbm = peaks.get("hbm_gbs")
     src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    dname, (dl, dms, dbytes) = max(prof.items(), key=lambda kv: kv[1][1])
-    achieved = dbytes / (dms / 1e3) / 1e9
-    kernels = {k: {"launches": v[0], "ms_per_step": v[1] / steps,
-                   "GBps": v[2] / (v[1] / 1e3) / 1e9 if v[1] > 0 else None,
-                   "bytes_per_launch": v[2] / v[0]}
-               for k, v in prof.items()}
-    return ({"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-             "frac": achieved / hbm, "traffic": None, "peak_source": src}, kernels)
+    dname, (dl, dms, dbytes, dflops) = max(prof.items(), key=lambda kv: kv[1][1])
+    kernels = {}
+    for k, v in prof.items():
+        e = {"launches": v[0], "ms_per_step": v[1] / steps,
+             "GBps": v[2] / (v[1] / 1e3) / 1e9 if v[1] > 0 else None,
+             "bytes_per_launch": v[2] / v[0]}
+        if v[3] > 0:
+            e["fp64_TFLOPs"] = v[3] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None
+        kernels[k] = e
+    traffic = _traffic(dname, workload)
+    if dflops > 0:
+        achieved = dflops / (dms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dname, "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": traffic, "peak_source": "nominal FP64 (152 SMs x 2070 MHz x 4)"}
+    else:
+        achieved = dbytes / (dms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic, "peak_source": src}
+    return roof, kernels
 
 
 def run_ours(args, rank, world):
@@ -391,7 +437,7 @@ def run_ours(args, rank, world):
     clocks = sampler.stop()
     value = main.points * args.steps * world / (total_ms / 1e3)
     value_nograph = main.points * args.steps * world / (prof_ms / 1e3)
-    roof, kernels = roofline(prof, args.steps, peaks)
+    roof, kernels = roofline(prof, args.steps, peaks, args.workload)
     main.graph = None
     e2e_value, h2d, d2h = main.e2e(max(3, args.steps // 2), 2)
     fp64 = None
@@ -410,7 +456,7 @@ def run_ours(args, rank, world):
         a = Arm("grad1024", args.precision, dev, solve=False)
         k = max(3, args.steps // 2)
         ms, pr = a.timed(k, 2, world, profile=True)
-        r2, k2 = roofline(pr, k, peaks)
+        r2, k2 = roofline(pr, k, peaks, "grad1024")
         secondary["grad1024_forward"] = {
             "value": a.points * k * world / (ms / 1e3), "unit": "grid-point predictions/s",
             "ms_per_step": ms / k, "roofline": r2, "kernels": k2,
@@ -420,13 +466,12 @@ def run_ours(args, rank, world):
         secondary["cs512_simulate"] = measure_cs(dev, max(2, args.steps // 5), peaks)
         secondary["grad1024_backward"] = measure_backward(dev, max(2, args.steps // 5), peaks,
                                                           n=args.backward_n)
-    # our kernels per step: per cell weights (+ block factors and the FP32
-    # coefficient copy), then either per cell [block GEMM,] scatter, rows_fwd,
-    # cols, rows_inv, or the grouped passes ([block GEMM,] zero, scatter,
-    # rows_fwd, cols, rows_inv)
+    # our kernels per step: per cell weights (+ block factors), then either
+    # per cell [block GEMM,] scatter, rows_fwd, cols, rows_inv, or the grouped
+    # passes ([block GEMM,] zero, scatter, rows_fwd, cols, rows_inv)
     f32 = args.precision == "fp32"
     ncell = len(main.cells)
-    per_step = ncell * (3 if f32 else 1) + (
+    per_step = ncell * (2 if f32 else 1) + (
         (1 if f32 else 0) + 5 if main.grouped else ncell * (5 if f32 else 4))
     res = {
         "metric": METRIC, "value": value, "unit": "grid-point predictions/s",

@@ -272,13 +272,16 @@ rk_status rk_debug_copy(rk_plan* plan, int what, void* dst_dev, size_t bytes);
  * (the bytes its inputs and outputs occupy, as stated in the library's design
  * notes) are recorded.  rk_profile_read synchronises the recorded events and
  * fills up to max entries (one per kernel name) with launches, total
- * milliseconds and total algorithmic bytes; it returns the number of entries.
+ * milliseconds, total algorithmic bytes and, for passes bound by FP64
+ * arithmetic, total algorithmic FP64 operations (adds and multiplies, a fused
+ * multiply-add counting two); it returns the number of entries.
  */
 typedef struct {
   char name[32];
   int launches;
   double total_ms;
   double bytes;
+  double flops;   /* algorithmic FP64 operations of FP64-bound passes, else 0 */
 } rk_profile_entry;
 rk_status rk_profile_enable(int on);
 int rk_profile_read(rk_profile_entry* out, int max);

@@ -34,7 +34,8 @@ class PlanInfo(ctypes.Structure):
 
 class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int),
-                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("flops", ctypes.c_double)]
 
 
 def _load():
@@ -91,8 +92,8 @@ def profile_enable(on=True):
 
 
 def profile_read():
-    """{kernel: (launches, total_ms, algorithmic_bytes)} since the last read."""
+    """{kernel: (launches, total_ms, algorithmic_bytes, fp64_flops)} since the last read."""
     buf = (ProfileEntry * 64)()
     k = lib.rk_profile_read(buf, 64)
-    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes)
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes, buf[i].flops)
             for i in range(k)}

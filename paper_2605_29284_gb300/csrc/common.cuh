@@ -42,7 +42,7 @@ __device__ __forceinline__ T matern_phi(T d, int nu_code) {
   T e = exp(-d);
   if (nu_code == 0) return e;
   if (nu_code == 1) return (T(1) + d) * e;
-  return (T(1) + d + d * d / T(3)) * e;
+  return (T(1) + d + d * d * T(1.0 / 3.0)) * e;   // a multiply: FP64 division is a long sequence
 }
 // -t phi'(t): derivative of phi(d / rho) with respect to log rho.
 // nu = 1/2: t e^-t; 3/2: t^2 e^-t; 5/2: (t^2 / 3)(1 + t) e^-t.
@@ -51,7 +51,7 @@ __device__ __forceinline__ T matern_dlogrho(T t, int nu_code) {
   T e = exp(-t);
   if (nu_code == 0) return t * e;
   if (nu_code == 1) return t * t * e;
-  return (t * t / T(3)) * (T(1) + t) * e;
+  return (t * t * T(1.0 / 3.0)) * (T(1) + t) * e;
 }
 
 // Raises a kernel's dynamic shared-memory limit when a launch needs more than
@@ -120,7 +120,6 @@ struct rk_plan {
   // coefficients
   int B = 0, B_cap = 0, n_cap_coef = 0;
   double* c64 = nullptr;       // B x n
-  float* c32 = nullptr;        // B x n
   double* z64 = nullptr;       // B x n data (after rk_solve_coef)
   bool have_coef = false, have_chol = false;
   // Cholesky factor of M = K_xx + tau2 I (n x n lower, column-major), double
@@ -156,8 +155,6 @@ struct rk_plan {
   double* bw_cbar = nullptr; size_t bw_cbar_cap = 0; // 3 x B x n: zbar, M^-1 c, M^-1 K' c
   void* bw_y = nullptr; size_t bw_y_bytes = 0;       // 3 x B x ny x nx
   double2* bw_gblk = nullptr; size_t bw_gblk_cap = 0;
-  size_t bw_c_cap = 0;                               // capacity of bw_cT (values)
-  void* bw_cT = nullptr;                              // their float copies
   bool have_adj = false;
   // device staging for rk_predict_host
   double* h_xy = nullptr; size_t h_xy_cap = 0;
@@ -240,7 +237,7 @@ struct BlockGemmSlot {
 cudaError_t launch_block_gemm_group(const Group<BlockGemmSlot>& g, cudaStream_t s);
 template <typename T>
 struct ScatterSlot {
-  const int* box; const T* w; const T* c; T* cstar;
+  const int* box; const T* w; const double* c; T* cstar;
   int n, B, L, p1x, p1y;
 };
 template <typename T>
@@ -280,11 +277,8 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
 cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac, int nblk,
                               double2* blk, cudaStream_t s);
 template <typename T>
-cudaError_t launch_scatter(const int* box, const T* w, const T* c, int n, int B, int L,
+cudaError_t launch_scatter(const int* box, const T* w, const double* c, int n, int B, int L,
                            T* cstar, int p1x, int p1y, cudaStream_t s);
-template <typename T>
-cudaError_t launch_convert(const double* src, T* dst, size_t count, cudaStream_t s);
-
 // dense FP64 Cholesky of M = K_xx + tau2 I and solves
 cudaError_t build_obs_cov(const double* xy, int n, const rk_plan* p, double* a, cudaStream_t s);
 cudaError_t chol_factor(double* a, int n, int* flag, cudaStream_t s);

@@ -57,7 +57,7 @@ cudaError_t launch_kn_factor(double* kn, int L, double hx, double hy, double rho
 // each) would leave the kernel's duration to a few long instruction chains.  Lane j holds rows r = j + s G (s < S) of k_i;
 // each substitution step broadcasts the solved entry from its owner lane.
 template <int W, int G>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(64)
 weights_grp_kernel(const double* __restrict__ xy, int n, double x0, double x1, double y0,
                    double y1, double hx, double hy, int nx, int ny, double rho, double sigma2,
                    int nu_code, const double* __restrict__ kn, int* __restrict__ box,
@@ -81,6 +81,7 @@ weights_grp_kernel(const double* __restrict__ xy, int n, double x0, double x1, d
   fx = fmin(fmax(fx, 0.0), (double)(nx - 2));
   fy = fmin(fmax(fy, 0.0), (double)(ny - 2));
   const double u = gx - fx, v = gy - fy;
+  const double inv_rho = 1.0 / rho;
   double z[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
@@ -90,7 +91,7 @@ weights_grp_kernel(const double* __restrict__ xy, int n, double x0, double x1, d
       const int a = r % W, b = r / W;
       const double dx = ((double)(a - (L - 1)) - u) * hx;
       const double dy = ((double)(b - (L - 1)) - v) * hy;
-      val = sigma2 * matern_phi<double>(sqrt(dx * dx + dy * dy) / rho, nu_code);
+      val = sigma2 * matern_phi<double>(sqrt(dx * dx + dy * dy) * inv_rho, nu_code);
     }
     z[s] = val;
   }
@@ -147,7 +148,9 @@ inline int weights_lanes(int n, int M) {
 
 cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, double* w64,
                            float* w32, double* ssd, int* flag, cudaStream_t s) {
-  const int threads = 128;
+  // two warps per CTA: a site's FP64 chain is long, so finer CTAs spread
+  // the warps evenly over the schedulers
+  const int threads = 64;
   const int G = weights_lanes(n, p->M);
 #define RK_WG(WW, GG)                                                                          \
   if (G == GG) {                                                                               \
@@ -230,11 +233,14 @@ __global__ void block_factor_kernel(const int* __restrict__ box, const double* _
     const int b = e % W, kx = (e / W) % nk, si = e / (W * nk);
     const int i = i0 + si, ix = box[2 * i];
     double2 t = make_double2(0.0, 0.0);
+    int m = (kx * ix) % px;                 // kx (ix + a) mod px, stepped by kx
     for (int a = 0; a < W; ++a) {
-      const double2 tw = twx[(kx * (ix + a)) % px];
+      const double2 tw = twx[m];
       const double w = w64[(size_t)i * M + a + W * b];
       t.x = fma(w, tw.x, t.x);
       t.y = fma(w, tw.y, t.y);
+      m += kx;
+      m = m >= px ? m - px : m;
     }
     tsm[e] = t;    // e = (si * nk + kx) * W + b
   }
@@ -244,9 +250,10 @@ __global__ void block_factor_kernel(const int* __restrict__ box, const double* _
     const int i = i0 + si, iy = box[2 * i + 1], ky = jj - KY;
     const double2* t = tsm + (si * nk + kx) * W;
     double2 acc = make_double2(0.0, 0.0);
-    for (int b = 0; b < W; ++b) {
-      int m = (ky * (iy + b)) % py;
-      if (m < 0) m += py;
+    int m = (ky * iy) % py;                 // ky (iy + b) mod py, stepped by ky
+    m = m < 0 ? m + py : m;
+    const int step = ky < 0 ? ky + py : ky;
+    for (int b = 0; b < W; ++b, m = (m + step >= py ? m + step - py : m + step)) {
       const double2 f = twy[m];
       acc.x = fma(t[b].x, f.x, fma(-t[b].y, f.y, acc.x));
       acc.y = fma(t[b].x, f.y, fma(t[b].y, f.x, acc.y));
@@ -387,7 +394,7 @@ cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac
 // Step 5: c*[f][iy + b][ix + a] += A_i[a + 2L b] c[f][i] on the padded grid.
 template <typename T>
 __global__ void scatter_kernel(const int* __restrict__ box, const T* __restrict__ w,
-                               const T* __restrict__ c, int n, int B, int L,
+                               const double* __restrict__ c, int n, int B, int L,
                                T* __restrict__ cstar, int p1x, int p1y) {
   const int W = 2 * L, M = W * W;
   const long long total = (long long)n * M;
@@ -397,13 +404,13 @@ __global__ void scatter_kernel(const int* __restrict__ box, const T* __restrict_
     const int i = (int)(t / M), q = (int)(t - (long long)i * M);
     const int a = q % W, b = q / W;
     const int px = box[2 * i] + a, py = box[2 * i + 1] + b;
-    atomicAdd(cstar + ((size_t)f * p1y + py) * p1x + px, w[t] * c[(size_t)f * n + i]);
+    atomicAdd(cstar + ((size_t)f * p1y + py) * p1x + px, w[t] * (T)c[(size_t)f * n + i]);
   }
 }
 
 template <typename T>
-cudaError_t launch_scatter(const int* box, const T* w, const T* c, int n, int B, int L, T* cstar,
-                           int p1x, int p1y, cudaStream_t s) {
+cudaError_t launch_scatter(const int* box, const T* w, const double* c, int n, int B, int L,
+                           T* cstar, int p1x, int p1y, cudaStream_t s) {
   const long long total = (long long)n * (2 * L) * (2 * L);
   long long blocks = (total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
@@ -424,13 +431,13 @@ __global__ void scatter_group_kernel(const __grid_constant__ Group<ScatterSlot<T
   const int W = 2 * sl.L, M = W * W;
   const long long total = (long long)sl.n * M;
   T* cs = sl.cstar + (size_t)f * sl.p1y * sl.p1x;
-  const T* cf = sl.c + (size_t)f * sl.n;
+  const double* cf = sl.c + (size_t)f * sl.n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t / M), q = (int)(t - (long long)i * M);
     const int a = q % W, b = q / W;
     const int px = sl.box[2 * i] + a, py = sl.box[2 * i + 1] + b;
-    atomicAdd(cs + (size_t)py * sl.p1x + px, sl.w[t] * cf[i]);
+    atomicAdd(cs + (size_t)py * sl.p1x + px, sl.w[t] * (T)cf[i]);
   }
 }
 
@@ -459,26 +466,11 @@ cudaError_t launch_scatter_group(const Group<ScatterSlot<T>>& g, cudaStream_t s)
   return cudaGetLastError();
 }
 
-template <typename T>
-__global__ void convert_kernel(const double* __restrict__ src, T* __restrict__ dst, size_t count) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
-       i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = (T)src[i];
-}
-
-template <typename T>
-cudaError_t launch_convert(const double* src, T* dst, size_t count, cudaStream_t s) {
-  convert_kernel<T><<<256, 256, 0, s>>>(src, dst, count);
-  return cudaGetLastError();
-}
-
-template cudaError_t launch_scatter<float>(const int*, const float*, const float*, int, int, int,
+template cudaError_t launch_scatter<float>(const int*, const float*, const double*, int, int, int,
                                            float*, int, int, cudaStream_t);
 template cudaError_t launch_scatter<double>(const int*, const double*, const double*, int, int,
                                             int, double*, int, int, cudaStream_t);
 template cudaError_t launch_scatter_group<float>(const Group<ScatterSlot<float>>&, cudaStream_t);
 template cudaError_t launch_scatter_group<double>(const Group<ScatterSlot<double>>&, cudaStream_t);
-template cudaError_t launch_convert<float>(const double*, float*, size_t, cudaStream_t);
-template cudaError_t launch_convert<double>(const double*, double*, size_t, cudaStream_t);
 
 }  // namespace rk

@@ -46,13 +46,12 @@ static rk_status predict_static(rk_plan* p, T* out, unsigned char* base) {
   C<T>* ub = (C<T>*)(base + cstar_b + t_b);
   double2* blk = (double2*)(base + cstar_b + t_b + u_b);
   const T* w = f32 ? (const T*)p->w32 : (const T*)p->w64;
-  const T* c = f32 ? (const T*)p->c32 : (const T*)p->c64;
   const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
   const C<T>* twy = f32 ? (const C<T>*)p->tw32y : (const C<T>*)p->tw64y;
   // c* accumulates by atomics, so it must start at zero on every call
   if (cudaMemsetAsync(cstar, 0, (size_t)B * plane * sizeof(T), s) != cudaSuccess ||
-      launch_scatter<T>(p->box, w, c, p->n, B, p->L, cstar, p->p1x, p->p1y, s) != cudaSuccess ||
+      launch_scatter<T>(p->box, w, p->c64, p->n, B, p->L, cstar, p->p1x, p->p1y, s) != cudaSuccess ||
       launch_rows_fwd<T>(cstar, p->p1y, p->p1x, (long long)plane, p->p1x, tb, p->ldt,
                          (long long)p->H * p->ldt, B, p->fpx, twx, p->H, s) != cudaSuccess)
     return RK_ERR_CUDA;

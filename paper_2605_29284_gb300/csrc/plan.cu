@@ -137,7 +137,7 @@ rk_status dalloc_bytes(void** p, size_t bytes) {
 struct ProfRec {
   const char* name;
   cudaEvent_t a, b;
-  double bytes;
+  double bytes, flops;
 };
 bool g_prof_on = false;
 std::vector<ProfRec> g_prof;
@@ -146,10 +146,12 @@ struct ProfScope {
   ProfRec rec;
   cudaStream_t s;
   bool on;
-  ProfScope(const char* name, double bytes, cudaStream_t st) : s(st), on(g_prof_on) {
+  ProfScope(const char* name, double bytes, double flops, cudaStream_t st)
+      : s(st), on(g_prof_on) {
     if (!on) return;
     rec.name = name;
     rec.bytes = bytes;
+    rec.flops = flops;
     cudaEventCreate(&rec.a);
     cudaEventCreate(&rec.b);
     cudaEventRecord(rec.a, s);
@@ -160,7 +162,12 @@ struct ProfScope {
     g_prof.push_back(rec);
   }
 };
-#define RK_PROF(name, bytes) ProfScope prof_scope_##__LINE__(name, (double)(bytes), s)
+// RK_PROF: a memory-bound pass (algorithmic bytes); RK_PROF64: an FP64-bound
+// pass, also with its algorithmic FP64 operations (one per add or multiply,
+// two per fused multiply-add, none for the exponentials and square roots)
+#define RK_PROF(name, bytes) ProfScope prof_scope_##__LINE__(name, (double)(bytes), 0.0, s)
+#define RK_PROF64(name, bytes, flops) \
+  ProfScope prof_scope_##__LINE__(name, (double)(bytes), (double)(flops), s)
 
 rk_status read_flag(rk_plan* p, int* value) {
   RK_CU(cudaMemcpyAsync(value, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
@@ -273,11 +280,11 @@ rk_status choose_block(rk_plan* p) {
 void free_plan(rk_plan* p) {
   void* bufs[] = {p->tw64x, p->tw64y, p->tw32x, p->tw32y, p->lam64, p->lam32, p->dlam64,
                   p->dlam32, p->kn_chol, p->kn_dlog, p->box, p->w64, p->w32, p->ssd, p->efac,
-                  p->c64, p->c32, p->z64, p->mchol, p->cstar, p->tbuf, p->ubuf, p->blk,
+                  p->c64, p->z64, p->mchol, p->cstar, p->tbuf, p->ubuf, p->blk,
                   p->d_flag, p->tw64qx, p->tw64qy, p->tw32qx, p->tw32qy, p->ce_sqrt64,
                   p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_c, p->h_out, p->xy, p->wd64,
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
-                  p->bw_cT, p->efac_g, p->gblk, p->bw_dk};
+                  p->efac_g, p->gblk, p->bw_dk};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
@@ -313,7 +320,6 @@ rk_status ensure_field_scratch(rk_plan* p, int B) {
 rk_status ensure_coef(rk_plan* p, int B) {
   if (B > p->B_cap || p->n > p->n_cap_coef) {
     RK_TRY(dalloc(&p->c64, (size_t)B * p->n));
-    RK_TRY(dalloc(&p->c32, (size_t)B * p->n));
     RK_TRY(dalloc(&p->z64, (size_t)B * p->n));
     p->B_cap = B;
     p->n_cap_coef = p->n;
@@ -321,13 +327,8 @@ rk_status ensure_coef(rk_plan* p, int B) {
   return ensure_field_scratch(p, B);
 }
 
-// c32 from c64 and the exact block (FP32 plans)
 rk_status finish_coef(rk_plan* p, int B) {
   p->B = B;
-  if (p->precision == RK_FP32) {
-    if (launch_convert<float>(p->c64, p->c32, (size_t)B * p->n, p->stream) != cudaSuccess)
-      return RK_ERR_CUDA;
-  }
   p->have_coef = true;
   return RK_OK;
 }
@@ -340,11 +341,11 @@ struct BlockUse {
   double2* blk;
 };
 
-// Steps 5-7 for nf fields with coefficients c64 (double) and cT (plan
-// precision; may equal c64 for RK_FP64 plans); out[f] (+ addend window).
-// FP32 plans use the forward block unless bu names another one.
+// Steps 5-7 for nf fields with coefficients c64 (double; the FP32 scatter
+// rounds each one as it reads it); out[f] (+ addend window).  FP32 plans use
+// the forward block unless bu names another one.
 template <typename T>
-rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* out,
+rk_status predict_fields(rk_plan* p, const double* c64, int nf, T* out,
                          const T* addend, const T* lam_override = nullptr,
                          const T* w_override = nullptr, const BlockUse* bu = nullptr) {
   const int B = nf;
@@ -372,7 +373,8 @@ rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* 
     cudaStream_t s_main = s;
     {
       cudaStream_t s = p->side;
-      RK_PROF("block_gemm", (double)bk.nblk * p->n * 16.0 + B * (p->n * 8.0 + bk.nblk * 16.0));
+      RK_PROF64("block_gemm", (double)bk.nblk * p->n * 16.0 + B * (p->n * 8.0 + bk.nblk * 16.0),
+                4.0 * B * p->n * bk.nblk);
       RK_CU(launch_block_gemm(c64, B, p->n, bk.efac, bk.nblk, bk.blk, s));
     }
     RK_CU(cudaEventRecord(p->ev_join, p->side));
@@ -381,7 +383,7 @@ rk_status predict_fields(rk_plan* p, const double* c64, const T* cT, int nf, T* 
   {
     RK_PROF("scatter", B * (plane * es + nM * 2 * es + p->n * es) + nM * es + p->n * 8.0);
     RK_CU(cudaMemsetAsync(cstar, 0, (size_t)B * plane * sizeof(T), s));
-    RK_CU(launch_scatter<T>(p->box, w, cT, p->n, B, p->L, cstar, p->p1x, p->p1y, s));
+    RK_CU(launch_scatter<T>(p->box, w, c64, p->n, B, p->L, cstar, p->p1x, p->p1y, s));
   }
   {
     RK_PROF("rows_fwd", B * (plane * es + (double)p->H * p->p1y * cs));
@@ -416,7 +418,7 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
   cudaStream_t s = p0->stream;
   const bool f32 = sizeof(T) == sizeof(float);
   bool any_blk = false;
-  double sc_b = 0, rf_b = 0, co_b = 0, ri_b = 0, bg_b = 0;
+  double sc_b = 0, rf_b = 0, co_b = 0, ri_b = 0, bg_b = 0, bg_f = 0;
   Group<ScatterSlot<T>> gs;
   Group<RowsFwdSlot<T>> gf;
   Group<ColsSlot<T>> gc;
@@ -430,9 +432,8 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
     const bool blk = f32 && p->nblk > 0;
     any_blk = any_blk || blk;
     const T* w = f32 ? (const T*)p->w32 : (const T*)p->w64;
-    const T* cT = f32 ? (const T*)p->c32 : (const T*)p->c64;
     const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
-    gs.slot[k] = ScatterSlot<T>{p->box, w, cT, (T*)p->cstar, p->n, B, p->L, p->p1x, p->p1y};
+    gs.slot[k] = ScatterSlot<T>{p->box, w, p->c64, (T*)p->cstar, p->n, B, p->L, p->p1x, p->p1y};
     gf.slot[k] = RowsFwdSlot<T>{(const T*)p->cstar, (C<T>*)p->tbuf, (long long)plane,
                                 (long long)p->H * p->ldt, p->p1y, p->p1x, p->p1x, p->ldt, B};
     gc.slot[k] = ColsSlot<T>{(const C<T>*)p->tbuf, (C<T>*)p->ubuf, lam, blk ? p->blk : nullptr,
@@ -451,7 +452,10 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
     rf_b += B * (plane * es + (double)p->H * p->p1y * cs);
     co_b += B * ((double)p->H * p->p1y * cs + (double)p->H * p->ny * cs) + (double)p->H * p->py * es;
     ri_b += B * ((double)p->H * p->ny * cs + (double)p->ny * p->nx * es);
-    if (blk) bg_b += (double)p->nblk * p->n * 16.0 + B * (p->n * 8.0 + p->nblk * 16.0);
+    if (blk) {
+      bg_b += (double)p->nblk * p->n * 16.0 + B * (p->n * 8.0 + p->nblk * 16.0);
+      bg_f += 4.0 * B * p->n * p->nblk;
+    }
   }
   const C<T>* twx = f32 ? (const C<T>*)p0->tw32x : (const C<T>*)p0->tw64x;
   const C<T>* twy = f32 ? (const C<T>*)p0->tw32y : (const C<T>*)p0->tw64y;
@@ -462,7 +466,7 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
     cudaStream_t s_main = s;
     {
       cudaStream_t s = p0->side;
-      RK_PROF("block_gemm", bg_b);
+      RK_PROF64("block_gemm", bg_b, bg_f);
       RK_CU(launch_block_gemm_group(gb, s));
     }
     RK_CU(cudaEventRecord(p0->ev_join, p0->side));
@@ -494,8 +498,7 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
 
 template <typename T>
 rk_status predict_impl(rk_plan* p, T* out) {
-  const T* cT = sizeof(T) == sizeof(float) ? (const T*)p->c32 : (const T*)p->c64;
-  return predict_fields<T>(p, p->c64, cT, p->B, out, (const T*)nullptr);
+  return predict_fields<T>(p, p->c64, p->B, out, (const T*)nullptr);
 }
 
 // ---------------------------------------------------- conditional simulation --
@@ -571,9 +574,8 @@ rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
   const size_t fu_b = (size_t)S * plane * sizeof(T);
   const size_t tq_b = (size_t)maxpairs * p->qx * ldq * 2 * sizeof(T);
   const size_t rhs_b = (size_t)S * n * sizeof(double);
-  const size_t c32_b = (size_t)G * n * sizeof(T);
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t need = al(fu_b) + al(tq_b) + al(rhs_b) + al(c32_b);
+  const size_t need = al(fu_b) + al(tq_b) + al(rhs_b);
   if (p->cs_bytes < need) {
     RK_TRY(dalloc_bytes(&p->cs_buf, need));
     p->cs_bytes = need;
@@ -583,7 +585,6 @@ rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
   T* fu = (T*)base;
   C<T>* tq = (C<T>*)(base + al(fu_b));
   double* rhs = (double*)(base + al(fu_b) + al(tq_b));
-  T* cT = (T*)(base + al(fu_b) + al(tq_b) + al(rhs_b));
   const bool f32 = sizeof(T) == sizeof(float);
   const T* sl = f32 ? (const T*)p->ce_sqrt32 : (const T*)p->ce_sqrt64;
   const C<T>* twqx = f32 ? (const C<T>*)p->tw32qx : (const C<T>*)p->tw64qx;
@@ -615,18 +616,14 @@ rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
       }
     }
     {
-      RK_PROF("chol_solve", (double)sn * n * 16.0 + (double)n * (double)n * 8.0);
+      RK_PROF64("chol_solve", (double)sn * n * 16.0 + (double)n * (double)n * 8.0,
+                2.0 * n * (double)n * sn);
       RK_CU(chol_solve(p->mchol, n, rhs, sn, s));
     }
     for (long long g0 = s0; g0 < s0 + sn; g0 += G) {
       const int g = (int)(s0 + sn - g0 < G ? s0 + sn - g0 : G);
       const double* rg = rhs + (size_t)(g0 - s0) * n;
-      const T* cuse = (const T*)rg;
-      if (f32) {
-        RK_CU(launch_convert<T>(rg, cT, (size_t)g * n, s));
-        cuse = cT;
-      }
-      RK_TRY(predict_fields<T>(p, rg, cuse, g, out + (size_t)g0 * p->ny * p->nx,
+      RK_TRY(predict_fields<T>(p, rg, g, out + (size_t)g0 * p->ny * p->nx,
                                fu + (size_t)(g0 - s0) * plane));
     }
   }
@@ -737,12 +734,14 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
       RK_TRY(dalloc(&p->bw_dk, need));
       p->bw_dk_cap = need;
     }
-    RK_PROF("theta_dkxx", (double)n * 16.0 + (double)B * n * 16.0 + need * 16.0);
+    RK_PROF64("theta_dkxx", (double)n * 16.0 + (double)B * n * 16.0 + need * 16.0,
+              2.0 * n * (double)n * B);
     RK_CU(launch_matvec_dkxx(p->xy, n, p->c64, B, p->rho, p->sigma2, p->nu_code, p->bw_dk, c3,
                              s));
   }
   {
-    RK_PROF("adj_solve", (double)n * n * 8.0 + (double)nsets * B * n * 16.0);
+    RK_PROF64("adj_solve", (double)n * n * 8.0 + (double)nsets * B * n * 16.0,
+              2.0 * n * (double)n * nsets * B);
     RK_CU(chol_solve(p->mchol, n, cbar, nsets * B, s));
   }
   if (gz) RK_CU(cudaMemcpyAsync(gz, cbar, (size_t)B * n * sizeof(double),
@@ -755,11 +754,6 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     //                  = tau^2 gbar . g_hat(M^{-1} c),
     //   zbar^T K'_xx c = gbar . g_hat(M^{-1} K'_xx c),
     //   d/dlog rho     = gbar . (g_hat'(c) + g_hat_W'(c) - g_hat(M^{-1} K'_xx c)).
-    const size_t need_c = (size_t)2 * B * n;
-    if (p->bw_c_cap < need_c) {
-      RK_TRY(dalloc_bytes(&p->bw_cT, need_c * sizeof(float)));
-      p->bw_c_cap = need_c;
-    }
     if (p->bw_y_bytes < 4 * B * grid * sizeof(T)) {
       RK_TRY(dalloc_bytes(&p->bw_y, 4 * B * grid * sizeof(T)));
       p->bw_y_bytes = 4 * B * grid * sizeof(T);
@@ -768,22 +762,15 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     T* y1 = y0 + B * grid;
     T* y2 = y1 + B * grid;
     T* y3 = y2 + B * grid;
-    float* c2f = (float*)p->bw_cT;
-    float* c3f = c2f + (size_t)B * n;
-    const T* cT = f32 ? (const T*)p->c32 : (const T*)p->c64;
     const T* wd = f32 ? (const T*)p->wd32 : (const T*)p->wd64;
     if (gs2) {
-      if (f32) RK_CU(launch_convert<float>(c2, c2f, (size_t)B * n, s));
-      RK_TRY(predict_fields<T>(p, c2, f32 ? (const T*)c2f : (const T*)c2, B, y0, nullptr,
-                               nullptr, nullptr, &gw));
+      RK_TRY(predict_fields<T>(p, c2, B, y0, nullptr, nullptr, nullptr, &gw));
       RK_CU(launch_dot_rows<T, T>(gbar, y0, B, (long long)grid, p->tau2, 0, gs2, s));
     }
     if (grho) {
-      if (f32) RK_CU(launch_convert<float>(c3, c3f, (size_t)B * n, s));
-      RK_TRY(predict_fields<T>(p, p->c64, cT, B, y1, nullptr, dlam, nullptr, &gw));
-      RK_TRY(predict_fields<T>(p, p->c64, cT, B, y2, nullptr, nullptr, wd, &gwd));
-      RK_TRY(predict_fields<T>(p, c3, f32 ? (const T*)c3f : (const T*)c3, B, y3, nullptr,
-                               nullptr, nullptr, &gw));
+      RK_TRY(predict_fields<T>(p, p->c64, B, y1, nullptr, dlam, nullptr, &gw));
+      RK_TRY(predict_fields<T>(p, p->c64, B, y2, nullptr, nullptr, wd, &gwd));
+      RK_TRY(predict_fields<T>(p, c3, B, y3, nullptr, nullptr, nullptr, &gw));
       RK_CU(launch_dot_rows<T, T>(gbar, y1, B, (long long)grid, 1.0, 0, grho, s));
       RK_CU(launch_dot_rows<T, T>(gbar, y2, B, (long long)grid, 1.0, 1, grho, s));
       RK_CU(launch_dot_rows<T, T>(gbar, y3, B, (long long)grid, -1.0, 1, grho, s));
@@ -906,6 +893,7 @@ int rk_profile_read(rk_profile_entry* out, int max) {
     out[k].launches += 1;
     out[k].total_ms += ms;
     out[k].bytes += r.bytes;
+    out[k].flops += r.flops;
   }
   g_prof.clear();
   return count;
@@ -992,9 +980,17 @@ rk_status rk_set_sites_async(rk_plan* p, int n, const double* xy) {
   p->xy_valid = true;
   RK_CU(cudaMemcpyAsync(p->xy, xy, (size_t)2 * n * sizeof(double), cudaMemcpyDeviceToDevice,
                         p->stream));
-  RK_CU(launch_weights(p->xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_sites_flag, p->stream));
-  if (p->precision == RK_FP32 && p->nblk > 0)
-    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, p->stream));
+  cudaStream_t s = p->stream;
+  {
+    RK_PROF64("weights", (double)n * (16.0 + 12.0 * p->M + 16.0) + 8.0 * p->M * p->M,
+              (double)n * (2.0 * p->M * p->M + 10.0 * p->M));
+    RK_CU(launch_weights(p->xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_sites_flag, s));
+  }
+  if (p->precision == RK_FP32 && p->nblk > 0) {
+    RK_PROF64("block_factors", (double)n * (8.0 * p->M + 8.0 + 16.0 * p->nblk),
+              (double)n * (4.0 * (p->blk_kx + 1) * p->M + 8.0 * p->nblk * 2 * p->L));
+    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, s));
+  }
   p->n = n;
   return RK_OK;
 }
