@@ -31,14 +31,9 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64
   }
 }
 
-// (xi, eta) for element `index` of sub-stream `sub` in `stream`
+// Box-Muller on the words (wa, wb)
 template <typename T>
-__device__ __forceinline__ void normal_pair(uint64_t index, uint64_t sub, uint64_t stream,
-                                            uint64_t seed, T& xi, T& eta) {
-  uint64_t c[4] = {index >> 1, sub, stream, 0ull};
-  philox4x64_10(c, seed, 0ull);
-  const uint64_t wa = (index & 1) ? c[2] : c[0];
-  const uint64_t wb = (index & 1) ? c[3] : c[1];
+__device__ __forceinline__ void box_muller(uint64_t wa, uint64_t wb, T& xi, T& eta) {
   if (sizeof(T) == sizeof(double)) {
     const double u1 = ((double)(wa >> 11) + 0.5) * 0x1.0p-53;
     const double u2 = ((double)(wb >> 11) + 0.5) * 0x1.0p-53;
@@ -59,6 +54,15 @@ __device__ __forceinline__ void normal_pair(uint64_t index, uint64_t sub, uint64
   }
 }
 
+// (xi, eta) for element `index` of sub-stream `sub` in `stream`
+template <typename T>
+__device__ __forceinline__ void normal_pair(uint64_t index, uint64_t sub, uint64_t stream,
+                                            uint64_t seed, T& xi, T& eta) {
+  uint64_t c[4] = {index >> 1, sub, stream, 0ull};
+  philox4x64_10(c, seed, 0ull);
+  box_muller<T>((index & 1) ? c[2] : c[0], (index & 1) ? c[3] : c[1], xi, eta);
+}
+
 // ------------------------------------------------------------ CE columns --
 // Column kx of pair p: noise times sqrt(lambda / (qx qy)), forward FFT along
 // y, rows [0, nkeep) written to tq[(p - pair0) * qx + kx][0..nkeep).
@@ -74,11 +78,23 @@ ce_cols_kernel(const T* __restrict__ sqrtlam, int qx, int qy, unsigned long long
   const int pair = pair0 + blockIdx.y;
   const int kxh = kx < qx - kx ? kx : qx - kx;
   const T* sl = sqrtlam + (size_t)kxh * qy;
-  for (int ky = threadIdx.x; ky < qy; ky += blockDim.x) {
-    T xi, eta;
-    normal_pair<T>((uint64_t)kx * qy + ky, (uint64_t)pair, 1ull, seed, xi, eta);
-    const T s = sl[ky];
-    bufa[ky] = mk<T>(s * xi, s * eta);
+  // one Philox call serves the torus indices 2m and 2m + 1 (words 0-1 and
+  // 2-3): each thread takes such a pair of this column's indices
+  const uint64_t kbase = (uint64_t)kx * qy;
+  for (uint64_t kk = (kbase & ~1ull) + 2ull * threadIdx.x; kk < kbase + qy;
+       kk += 2ull * blockDim.x) {
+    uint64_t c[4] = {kk >> 1, (uint64_t)pair, 1ull, 0ull};
+    philox4x64_10(c, seed, 0ull);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t k = kk + h;
+      if (k < kbase || k >= kbase + qy) continue;
+      const int ky = (int)(k - kbase);
+      T xi, eta;
+      box_muller<T>(c[2 * h], c[2 * h + 1], xi, eta);
+      const T s = sl[ky];
+      bufa[ky] = mk<T>(s * xi, s * eta);
+    }
   }
   __syncthreads();
   C<T>* res = fft_smem<T>(bufa, bufb, qy, 1, fpy, twy, +1);

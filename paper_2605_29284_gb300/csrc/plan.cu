@@ -14,7 +14,14 @@ namespace {
 
 // Fraction of the spectral peak above which a frequency belongs to the exact
 // low-frequency block of RK_FP32 plans, and the block's size limit.
+// The forward block holds the frequencies where lambda > eta max(lambda).
+// For nu >= 3/2 (spectra decaying like |k|^-4 or faster) eta = 1e-2; for the
+// exponential kernel (nu = 1/2, |k|^-3) the FP32 transform's noise is far
+// less concentrated by lambda (measured in the oracle's FP32 emulation: 0.8 to
+// 8e-6 of max|g| with no block at all), and eta = 1e-1 keeps its block at
+// tens of entries instead of hundreds.
 constexpr double kBlockEta = 1e-2;
+constexpr double kBlockEtaExp = 1e-1;
 constexpr double kBlockEtaGrad = 1e-4;
 constexpr int kBlockMax = 1024;
 // largest torus length per dimension (shared-memory limit of the FFT passes)
@@ -273,7 +280,8 @@ rk_status lambda_host(rk_plan* p, std::vector<double>& lam) {
 rk_status choose_block(rk_plan* p) {
   std::vector<double> lam;
   RK_TRY(lambda_host(p, lam));
-  block_for_eta(lam, p->H, p->py, kBlockEta, &p->blk_kx, &p->blk_ky, &p->nblk);
+  block_for_eta(lam, p->H, p->py, p->nu_code == 0 ? kBlockEtaExp : kBlockEta, &p->blk_kx,
+                &p->blk_ky, &p->nblk);
   return RK_OK;
 }
 
