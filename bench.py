@@ -73,6 +73,26 @@ def workload_cells(name):
     return w, xy, cells
 
 
+def max_over_ranks(x, device):
+    """MAX of x over the ranks of the default process group (x when alone):
+    the replicas' timed region ends when the slowest one does."""
+    import torch
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_config(name, world=1):
+    """The workload part of the JSON line's config (both arms)."""
+    w, xy, cells = workload_cells(name)
+    return {"workload": name, "cells": [c[0] for c in cells],
+            "grid": f"{cells[0][1]['nx']}x{cells[0][1]['ny']}", "n": int(xy.shape[0]),
+            "fields_per_cell": cells[0][2], "parallelism": f"replicas x{world}"}
+
+
 # -------------------------------------------------------------------- clocks --
 
 class ClockSampler:
@@ -245,10 +265,8 @@ class Arm:
             prof = rk.profile_read()
         torch.cuda.synchronize()
         if world > 1:
-            t = torch.tensor([total], device=self.dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
-        return total, prof
+            torch.distributed.barrier()
+        return max_over_ranks(total, self.dev), prof
 
     def e2e(self, steps, warmup):
         """The same prediction through rk_predict_host: host inputs in, host output out."""
@@ -369,7 +387,11 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # workload it was taken on and a digest of the sources it was built from; the
 # bench reports it only while those sources are unchanged (profiles/ has the
 # captures and commands)
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/cols_grad1024.md: ncu --set full, one launch (16 fields, P = 2187)
+    "cols": {"workload": "grad1024", "bytes_per_launch": 163313664 + 103914496,
+             "sources": ["k_fftn.cu", "fftn.cuh", "fft.cuh"], "digest": "978821fdb35b3e20"},
+}
 
 
 def _sources_digest(files):
@@ -479,16 +501,13 @@ def run_ours(args, rank, world):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": "synthetic (seeded sites and data; see synth)",
-        "config": {"workload": args.workload, "cells": [c[0] for c in main.cells],
-                   "grid": f"{main.cells[0][1]['nx']}x{main.cells[0][1]['ny']}",
-                   "n": int(main.xy_np.shape[0]), "fields_per_cell": main.cells[0][2],
+        "config": {**workload_config(args.workload, world),
                    "l2": "flushed between timed steps (256 MB write)",
                    "issue": ("sites and coefficients on one stream per cell, the cells' "
                              "predictions in one grouped launch per pass (rk_predict_group), "
                              "step replayed from a CUDA graph") if main.grouped else
                             "one stream per cell, step replayed from a CUDA graph",
-                   "value_without_graph": value_nograph,
-                   "parallelism": f"replicas x{world}"},
+                   "value_without_graph": value_nograph},
         "roofline": roof,
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "grid-point predictions/s",
@@ -545,10 +564,15 @@ def main():
             return 0
         cb = cpu_oracle_rate(args.workload, budget_s=max(10.0, 2.0 * args.steps),
                              steps=args.steps)
+        cfg = workload_config(args.workload, 1)
+        w, _, cells = workload_cells(args.workload)
+        points = sum(kw["nx"] * kw["ny"] * B for _, kw, B in cells)
         res = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": points / cb["value"] * 1e3,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic", "config": {"workload": args.workload},
+               "data": "synthetic (seeded sites and data; see synth)",
+               "config": {**cfg, "issue": "the FP64 CPU oracle on the host cores (sampled)"},
                "cpu_baseline": cb,
                "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": 0}}

@@ -213,7 +213,8 @@ rk_status rk_predict_group(rk_plan* const* plans, int nplans, void* const* outs)
  * before any stream capture.  Every call shares the one array and the array
  * keeps the last call's contents, so calls that overlap on the GPU (on
  * different streams or host threads) race and must be serialised by the
- * caller; the accumulation buffer is cleared at the start of every call.
+ * caller; the scatter writes every element of c* on every call, so nothing
+ * carries over from one call to the next.
  */
 rk_status rk_predict_static(rk_plan* plan, void* out_dev);
 

@@ -70,3 +70,22 @@ def test_simulate_needs_solved_coefficients(rk):
         with pytest.raises(rk.RkError) as e:
             p.simulate(4, 1)
         assert e.value.name == "RK_ERR_STATE"
+
+
+def test_realisations_on_a_compile_time_torus(rk):
+    # a 512 x 512 grid whose embedding lands on a torus length with its own
+    # compile-time FFT (the CE passes for 1152 ... 2304): parity as above
+    ext = (0.0, 1.0, 0.0, 1.0)
+    m, n, R, L = 512, 300, 3, 2
+    th, tau2, seed = (0.5, 0.05, 1.0), 1e-2, 777
+    xy = synth.sites_uniform(n, ext, 91)
+    z = synth.normals((1, n), 92)
+    g = rapid.Grid(m, m, ext, L)
+    qx, qy, _ = cs.ce_spectrum(g, *th)
+    assert qx in (1152, 1296, 1536, 1728, 1944, 2304) and qy == qx
+    ref = cs.simulate(xy, z, g, *th, tau2, R, seed)
+    with rk.Plan(m, m, ext, *th, tau2, L, precision="fp32") as p:
+        p.set_obs(torch.from_numpy(xy).cuda(), torch.from_numpy(z).cuda())
+        out = p.simulate(R, seed).double().cpu().numpy()
+        assert (p.info()["qx"], p.info()["qy"]) == (qx, qy)
+    assert rel_err(out, ref) <= 2e-5

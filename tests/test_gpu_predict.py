@@ -234,3 +234,19 @@ def test_async_site_update_matches_and_latches_outside_sites(rk):
         with pytest.raises(rk.RkError) as e:
             p.set_sites_async(torch.from_numpy(np.vstack([xy, xy])).cuda())   # would grow
         assert e.value.name == "RK_ERR_STATE"
+
+
+def test_repeated_site_updates(rk):
+    # the site order behind the tiled scatter (built for n >= 4096; smaller
+    # sets are scanned whole per tile) is rebuilt on every update: updates in
+    # a row across both regimes each predict correctly
+    ext = (0.0, 1.0, 0.0, 1.0)
+    th, tau2 = (1.5, 0.2, 1.0), 1e-3
+    cases = [case(n, 70, 60, ext, *th, tau2, 2, seed=101 + n) for n in (5000, 250, 5000, 4100)]
+    with rk.Plan(70, 60, ext, *th, tau2, 2, precision="fp32") as p:
+        for xy, z, c, g in cases:
+            p.set_sites(torch.from_numpy(xy).cuda())
+            p.set_coef(torch.from_numpy(c).cuda())
+            out = p.predict().double().cpu().numpy()
+            ref = rapid.predict(xy, c, g, *th, method="fft")
+            assert rel_err(out, ref) <= TOL["fp32"]
