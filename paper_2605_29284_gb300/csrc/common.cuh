@@ -117,6 +117,14 @@ struct rk_plan {
   float* w32 = nullptr;        // n x M
   double* ssd = nullptr;       // n: sqrt(max(0, sigma2 - k_i^T W_i)) (CS)
   double2* efac = nullptr;     // n x nblk Fourier factors of A_i on the block
+  // sites ordered by the 32 x 32 tile of the padded grid holding their box
+  // corner (the tiled scatter): tile_start[tiles + 1], site_order[n]; built
+  // only for n >= kTileSortMin (fewer sites scatter with global atomics)
+  int tiles_x = 0, tiles_y = 0;
+  int* tile_start = nullptr;
+  int* tile_count = nullptr;   // sites per tile (zero between updates)
+  int* tile_cursor = nullptr;  // placement cursors of tile_fill
+  int* site_order = nullptr;
   // coefficients
   int B = 0, B_cap = 0, n_cap_coef = 0;
   double* c64 = nullptr;       // B x n
@@ -136,6 +144,10 @@ struct rk_plan {
   // side stream for the FP64 block GEMM, which runs beside the FP32 row pass
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the block factors of a site update also run on the side stream (only
+  // the block GEMM needs them): ev_wfork marks the weights on the plan's
+  // stream, ev_sites the factors' completion on the side stream
+  cudaEvent_t ev_wfork = nullptr, ev_sites = nullptr;
   // conditional simulation state
   int qx = 0, qy = 0;
   rk::FftPlan fqx, fqy;
@@ -206,6 +218,7 @@ bool launch_rows_inv_n(const C<T>* uin, int ldu, long long ufs, int nrows, T* ou
 // [start[k], start[k + 1]) of the grid's y dimension (fields, or field
 // groups for the column pass).
 constexpr int kMaxGroup = 16;
+constexpr int kTileSortMin = 4096;
 template <typename S>
 struct Group {
   int n = 0;
@@ -238,10 +251,13 @@ cudaError_t launch_block_gemm_group(const Group<BlockGemmSlot>& g, cudaStream_t 
 template <typename T>
 struct ScatterSlot {
   const int* box; const T* w; const double* c; T* cstar;
-  int n, B, L, p1x, p1y;
+  const int* tstart; const int* order;
+  int n, B, L, p1x, p1y, ntx, nty;
 };
 template <typename T>
-cudaError_t launch_scatter_group(const Group<ScatterSlot<T>>& g, cudaStream_t s);
+ScatterSlot<T> scatter_slot(const rk_plan* p, const T* w, const double* c, int B, T* cstar);
+template <typename T>
+cudaError_t launch_scatter_group(Group<ScatterSlot<T>>& g, cudaStream_t s);
 template <typename T>
 bool launch_rows_fwd_group(const Group<RowsFwdSlot<T>>& g, int N, const C<T>* tw, int H,
                            cudaStream_t s, cudaError_t* err);
@@ -277,8 +293,9 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
 cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac, int nblk,
                               double2* blk, cudaStream_t s);
 template <typename T>
-cudaError_t launch_scatter(const int* box, const T* w, const double* c, int n, int B, int L,
-                           T* cstar, int p1x, int p1y, cudaStream_t s);
+cudaError_t launch_scatter(const rk_plan* p, const T* w, const double* c, int B, T* cstar,
+                           cudaStream_t s);
+cudaError_t launch_tile_sites(const int* box, int n, rk_plan* p, bool counted, cudaStream_t s);
 // dense FP64 Cholesky of M = K_xx + tau2 I and solves
 cudaError_t build_obs_cov(const double* xy, int n, const rk_plan* p, double* a, cudaStream_t s);
 cudaError_t chol_factor(double* a, int n, int* flag, cudaStream_t s);

@@ -11,6 +11,7 @@
 //             (i >> 1, t, 2, 0), words (0, 1) for even i, (2, 3) for odd i.
 #include "common.cuh"
 #include "fft.cuh"
+#include "fftn.cuh"
 
 namespace rk {
 
@@ -171,10 +172,128 @@ __global__ void site_values_kernel(const T* __restrict__ fu, int p1x, long long 
   }
 }
 
+// ------------------------------------ CE passes at compile-time lengths --
+// The same two passes for the torus lengths of the workloads' embeddings,
+// with the compile-time FFT of fftn.cuh: V vectors of length N per CTA.
+template <int N>
+struct CeVecs {
+  static constexpr int thr = Radix23<N>::THR;
+  static constexpr int value = thr >= 256 ? 1 : 512 / thr;
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(CeVecs<N>::value * Radix23<N>::THR)
+ce_cols_n(const T* __restrict__ sqrtlam, int qx, unsigned long long seed, int pair0,
+          C<T>* __restrict__ tq, int ldq, int nkeep, const C<T>* __restrict__ twy) {
+  constexpr int V = CeVecs<N>::value, THR = Radix23<N>::THR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int v = threadIdx.x / THR, tid = threadIdx.x - v * THR;
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw) + v * N;
+  const int kx = blockIdx.x * V + v;
+  const int pair = pair0 + blockIdx.y;
+  const bool valid = kx < qx;
+  if (valid) {
+    const int kxh = kx < qx - kx ? kx : qx - kx;
+    const T* sl = sqrtlam + (size_t)kxh * N;
+    const uint64_t kbase = (uint64_t)kx * N;
+    for (uint64_t kk = (kbase & ~1ull) + 2ull * tid; kk < kbase + N; kk += 2ull * THR) {
+      uint64_t c[4] = {kk >> 1, (uint64_t)pair, 1ull, 0ull};
+      philox4x64_10(c, seed, 0ull);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint64_t k = kk + h;
+        if (k < kbase || k >= kbase + N) continue;
+        const int ky = (int)(k - kbase);
+        T xi, eta;
+        box_muller<T>(c[2 * h], c[2 * h + 1], xi, eta);
+        const T sv = sl[ky];
+        buf[ky] = mk<T>(sv * xi, sv * eta);
+      }
+    }
+  }
+  __syncthreads();
+  fft_n<T, N, +1>(buf, twy, tid);
+  if (valid) {
+    C<T>* dst = tq + ((size_t)blockIdx.y * qx + kx) * ldq;
+    for (int r = tid; r < nkeep; r += THR) dst[r] = buf[r];
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(CeVecs<N>::value * Radix23<N>::THR)
+ce_rows_n(const C<T>* __restrict__ tq, int ldq, int nrows, T* __restrict__ fu, int p1x,
+          long long t0, int treal, int pair0, const C<T>* __restrict__ twx) {
+  constexpr int V = CeVecs<N>::value, THR = Radix23<N>::THR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* bufs = reinterpret_cast<C<T>*>(smem_raw);
+  const int r0 = blockIdx.x * V;
+  const int pl = blockIdx.y;
+  const C<T>* src = tq + (size_t)pl * N * ldq;
+  // rows r0 .. r0 + V - 1 of the column spectra: element (kx, row) at kx * ldq + row
+  for (int idx = threadIdx.x; idx < V * N; idx += V * THR) {
+    const int kx = idx / V, vv = idx - kx * V;
+    const int row = r0 + vv;
+    bufs[vv * N + kx] = row < nrows ? src[(size_t)kx * ldq + row] : mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  const int v = threadIdx.x / THR, tid = threadIdx.x - v * THR;
+  fft_n<T, N, +1>(bufs + v * N, twx, tid);
+  const long long pair = pair0 + pl;
+  for (int idx = threadIdx.x; idx < V * 2 * p1x; idx += V * THR) {
+    const int vv = idx / (2 * p1x), rem = idx - vv * 2 * p1x;
+    const int part = rem / p1x, px = rem - part * p1x;
+    const int row = r0 + vv;
+    if (row >= nrows) continue;
+    const long long j = 2 * pair + part - t0;
+    if (j < 0 || j >= treal) continue;
+    const C<T> z = bufs[vv * N + px];
+    fu[((size_t)j * nrows + row) * p1x + px] = part ? z.y : z.x;
+  }
+}
+
+#define RK_CE_SIZES(X) X(1152) X(1296) X(1536) X(1728) X(1944) X(2304)
+
+template <typename T, int N>
+cudaError_t go_ce_cols(const T* sqrtlam, int qx, unsigned long long seed, int pair0, int npairs,
+                       C<T>* tq, int ldq, int nkeep, const C<T>* twy, cudaStream_t s) {
+  constexpr int V = CeVecs<N>::value, THR = Radix23<N>::THR;
+  const size_t sm = sizeof(C<T>) * V * N;
+  static int smem_set = 0;
+  auto kern = ce_cols_n<T, N>;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((qx + V - 1) / V, npairs), V * THR, sm, s>>>(sqrtlam, qx, seed, pair0, tq, ldq,
+                                                            nkeep, twy);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t go_ce_rows(const C<T>* tq, int ldq, int nrows, T* fu, int p1x, long long t0,
+                       int treal, int pair0, int npairs, const C<T>* twx, cudaStream_t s) {
+  constexpr int V = CeVecs<N>::value, THR = Radix23<N>::THR;
+  const size_t sm = sizeof(C<T>) * V * N;
+  static int smem_set = 0;
+  auto kern = ce_rows_n<T, N>;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((nrows + V - 1) / V, npairs), V * THR, sm, s>>>(tq, ldq, nrows, fu, p1x, t0, treal,
+                                                               pair0, twx);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_ce_cols(const T* sqrtlam, int qx, int qy, unsigned long long seed, int pair0,
                            int npairs, C<T>* tq, int ldq, int nkeep, const FftPlan& fpy,
                            const C<T>* twy, cudaStream_t s) {
+  if (sizeof(T) == sizeof(float) && !fft_generic_only()) {
+    switch (qy) {
+#define RK_CASE(NN) \
+  case NN: return go_ce_cols<T, NN>(sqrtlam, qx, seed, pair0, npairs, tq, ldq, nkeep, twy, s);
+      RK_CE_SIZES(RK_CASE)
+#undef RK_CASE
+      default: break;
+    }
+  }
   const size_t sm = sizeof(C<T>) * 2 * qy;
   auto kern = ce_cols_kernel<T>;
   static int smem_set = 0;
@@ -188,6 +307,16 @@ template <typename T>
 cudaError_t launch_ce_rows(const C<T>* tq, int qx, int ldq, int nrows, T* fu, int p1x,
                            long long t0, int treal, int pair0, int npairs, const FftPlan& fpx,
                            const C<T>* twx, cudaStream_t s) {
+  if (sizeof(T) == sizeof(float) && !fft_generic_only()) {
+    switch (qx) {
+#define RK_CASE(NN)                                                                         \
+  case NN:                                                                                  \
+    return go_ce_rows<T, NN>(tq, ldq, nrows, fu, p1x, t0, treal, pair0, npairs, twx, s);
+      RK_CE_SIZES(RK_CASE)
+#undef RK_CASE
+      default: break;
+    }
+  }
   const size_t sm = sizeof(C<T>) * 2 * kCeRows * qx;
   auto kern = ce_rows_kernel<T>;
   static int smem_set = 0;

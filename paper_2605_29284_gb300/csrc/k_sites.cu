@@ -62,7 +62,7 @@ weights_grp_kernel(const double* __restrict__ xy, int n, double x0, double x1, d
                    double y1, double hx, double hy, int nx, int ny, double rho, double sigma2,
                    int nu_code, const double* __restrict__ kn, int* __restrict__ box,
                    double* __restrict__ w64, float* __restrict__ w32,
-                   double* __restrict__ ssd, int* flag) {
+                   double* __restrict__ ssd, int* flag, int* __restrict__ tcount, int ntx) {
   constexpr int M = W * W;
   constexpr int L = W / 2;
   constexpr int S = (M + G - 1) / G;
@@ -129,9 +129,11 @@ weights_grp_kernel(const double* __restrict__ xy, int n, double x0, double x1, d
   }
   if (j == 0) {
     if (!inside) atomicOr(flag, 2);
-    box[2 * i] = inside ? (int)fx : 0;
-    box[2 * i + 1] = inside ? (int)fy : 0;
+    const int bx = inside ? (int)fx : 0, by = inside ? (int)fy : 0;
+    box[2 * i] = bx;
+    box[2 * i + 1] = by;
     ssd[i] = inside ? sqrt(fmax(0.0, sigma2 - yy)) : 0.0;
+    if (tcount) atomicAdd(tcount + (by / 32) * ntx + bx / 32, 1);   // sites per scatter tile
   }
 }
 
@@ -157,7 +159,8 @@ cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, 
     const int sites = threads / GG;                                                            \
     weights_grp_kernel<WW, GG><<<(n + sites - 1) / sites, threads, 0, s>>>(                    \
         xy, n, p->x0, p->x1, p->y0, p->y1, p->hx, p->hy, p->nx, p->ny, p->rho, p->sigma2,     \
-        p->nu_code, p->kn_chol, box, w64, w32, ssd, flag);                                     \
+        p->nu_code, p->kn_chol, box, w64, w32, ssd, flag,                                      \
+        n >= kTileSortMin ? p->tile_count : nullptr, p->tiles_x);                              \
     return cudaGetLastError();                                                                 \
   }
   switch (p->L) {
@@ -391,59 +394,141 @@ cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac
 }
 
 // --------------------------------------------------------------- scatter --
-// Step 5: c*[f][iy + b][ix + a] += A_i[a + 2L b] c[f][i] on the padded grid.
-template <typename T>
-__global__ void scatter_kernel(const int* __restrict__ box, const T* __restrict__ w,
-                               const double* __restrict__ c, int n, int B, int L,
-                               T* __restrict__ cstar, int p1x, int p1y) {
-  const int W = 2 * L, M = W * W;
-  const long long total = (long long)n * M;
-  const int f = blockIdx.y;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t / M), q = (int)(t - (long long)i * M);
-    const int a = q % W, b = q / W;
-    const int px = box[2 * i] + a, py = box[2 * i + 1] + b;
-    atomicAdd(cstar + ((size_t)f * p1y + py) * p1x + px, w[t] * (T)c[(size_t)f * n + i]);
+// Step 5: c*[f][iy + b][ix + a] += A_i[a + 2L b] c[f][i] on the padded grid,
+// tile by tile.  The padded grid is cut into 32 x 32 tiles and the sites are
+// ordered by the tile holding their box corner (ix, iy) (rk_set_sites builds
+// this order for n >= kTileSortMin: tile_count, tile_scan, tile_fill; fewer
+// sites scatter with global atomics after a zeroing pass).  A site's footprint
+// (2L <= 8) reaches at most the next tile in x and y, so the CTA of tile
+// (tx, ty) takes the sites of tiles (tx, ty), (tx - 1, ty), (tx, ty - 1) and
+// (tx - 1, ty - 1), accumulates what lands in its tile in shared memory, and
+// writes the whole tile: no global atomics and no zeroing pass.
+constexpr int kTile = 32;
+
+__global__ void tile_count_kernel(const int* __restrict__ box, int n, int ntx,
+                                  int* __restrict__ count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(count + (box[2 * i + 1] / kTile) * ntx + box[2 * i] / kTile, 1);
+}
+
+// exclusive scan of count into start[0..nt]; count and cursor are left at
+// zero (one CTA)
+__global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ count, int nt,
+                                                         int* __restrict__ start,
+                                                         int* __restrict__ cursor) {
+  __shared__ int part[1024];
+  const int per = (nt + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per, b1 = min(nt, b0 + per);
+  int sum = 0;
+  for (int t = b0; t < b1; ++t) sum += count[t];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {     // inclusive Hillis-Steele scan
+    const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - sum;
+  for (int t = b0; t < b1; ++t) {
+    start[t] = run;
+    run += count[t];
+    count[t] = 0;
+    cursor[t] = 0;
+  }
+  if (threadIdx.x == blockDim.x - 1) start[nt] = part[threadIdx.x];
+}
+
+__global__ void tile_fill_kernel(const int* __restrict__ box, int n, int ntx,
+                                 const int* __restrict__ start, int* __restrict__ cursor,
+                                 int* __restrict__ order) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int h = (box[2 * i + 1] / kTile) * ntx + box[2 * i] / kTile;
+    const int at = start[h] + atomicAdd(cursor + h, 1);
+    if (at < n) order[at] = i;      // always true when the counts are consistent
   }
 }
 
-template <typename T>
-cudaError_t launch_scatter(const int* box, const T* w, const double* c, int n, int B, int L,
-                           T* cstar, int p1x, int p1y, cudaStream_t s) {
-  const long long total = (long long)n * (2 * L) * (2 * L);
-  long long blocks = (total + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  dim3 grid((unsigned)blocks, B);
-  scatter_kernel<T><<<grid, 256, 0, s>>>(box, w, c, n, B, L, cstar, p1x, p1y);
+// The counts come from the weights kernel (or tile_count_kernel for
+// caller-supplied boxes); the scan turns them into tile starts and zeroes
+// them and the cursors, so the next update starts from zero; the fill places
+// the sites.
+cudaError_t launch_tile_sites(const int* box, int n, rk_plan* p, bool counted, cudaStream_t s) {
+  if (n < kTileSortMin) return cudaSuccess;      // the scatter scans all sites per tile
+  const int nt = p->tiles_x * p->tiles_y;
+  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  if (!counted) tile_count_kernel<<<blocks, 256, 0, s>>>(box, n, p->tiles_x, p->tile_count);
+  tile_scan_kernel<<<1, 1024, 0, s>>>(p->tile_count, nt, p->tile_start, p->tile_cursor);
+  tile_fill_kernel<<<blocks, 256, 0, s>>>(box, n, p->tiles_x, p->tile_start, p->tile_cursor,
+                                          p->site_order);
   return cudaGetLastError();
 }
 
-// The scatter of several plans in one launch (rk_predict_group): slot k
-// covers fields [start[k], start[k + 1]) of grid.y.  zero_group_kernel
-// clears every slot's c* first (grid.y = slot).
+// fields per CTA: the accumulators of FB fields share one pass over the sites
+constexpr int kScF = 4;
+
 template <typename T>
-__global__ void scatter_group_kernel(const __grid_constant__ Group<ScatterSlot<T>> g) {
-  int ks = 0;
-  while (ks + 1 < g.n && (int)blockIdx.y >= g.start[ks + 1]) ++ks;
-  const ScatterSlot<T>& sl = g.slot[ks];
-  const int f = blockIdx.y - g.start[ks];
+__device__ __forceinline__ void scatter_tile(const ScatterSlot<T>& sl, int tile, int f0,
+                                             T (*acc)[kTile * kTile]) {
   const int W = 2 * sl.L, M = W * W;
-  const long long total = (long long)sl.n * M;
-  T* cs = sl.cstar + (size_t)f * sl.p1y * sl.p1x;
-  const double* cf = sl.c + (size_t)f * sl.n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t / M), q = (int)(t - (long long)i * M);
-    const int a = q % W, b = q / W;
-    const int px = sl.box[2 * i] + a, py = sl.box[2 * i + 1] + b;
-    atomicAdd(cs + (size_t)py * sl.p1x + px, sl.w[t] * (T)cf[i]);
+  const int nf = min(kScF, sl.B - f0);
+  for (int e = threadIdx.x; e < kScF * kTile * kTile; e += blockDim.x) (&acc[0][0])[e] = T(0);
+  __syncthreads();
+  const int tx = tile % sl.ntx, ty = tile / sl.ntx;
+  const int x0 = tx * kTile, y0 = ty * kTile;
+  for (int d = 0; d < 4; ++d) {
+    const int hx = tx - (d & 1), hy = ty - (d >> 1);
+    if (hx < 0 || hy < 0) continue;
+    const int h = hy * sl.ntx + hx;
+    const int s0 = sl.tstart[h], cnt = sl.tstart[h + 1] - s0;
+    for (int e = threadIdx.x; e < cnt * M; e += blockDim.x) {
+      const int i = sl.order[s0 + e / M], q = e % M;
+      const int px = sl.box[2 * i] + q % W - x0, py = sl.box[2 * i + 1] + q / W - y0;
+      if ((unsigned)px >= (unsigned)kTile || (unsigned)py >= (unsigned)kTile) continue;
+      const T wv = sl.w[(size_t)i * M + q];
+      for (int f = 0; f < nf; ++f)
+        atomicAdd(&acc[f][py * kTile + px], wv * (T)sl.c[(size_t)(f0 + f) * sl.n + i]);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nf * kTile * kTile; e += blockDim.x) {
+    const int f = e / (kTile * kTile), r = e - f * kTile * kTile;
+    const int gx = x0 + r % kTile, gy = y0 + r / kTile;
+    if (gx < sl.p1x && gy < sl.p1y)
+      sl.cstar[((size_t)(f0 + f) * sl.p1y + gy) * sl.p1x + gx] = acc[f][r];
+  }
+}
+
+// Few sites (no order built): block b of the grid's x dimension takes a
+// contiguous run of sites and adds their footprints to c* with global
+// atomics; c* was zeroed first (zero_kernel).
+template <typename T>
+__device__ __forceinline__ void scatter_atomic(const ScatterSlot<T>& sl, int b, int nb, int f0) {
+  const int W = 2 * sl.L, M = W * W;
+  const int nf = min(kScF, sl.B - f0);
+  const int per = (sl.n + nb - 1) / nb, i0 = b * per, i1 = min(sl.n, i0 + per);
+  for (int e = threadIdx.x; e < (i1 - i0) * M; e += blockDim.x) {
+    const int i = i0 + e / M, q = e % M;
+    const int px = sl.box[2 * i] + q % W, py = sl.box[2 * i + 1] + q / W;
+    const T wv = sl.w[(size_t)i * M + q];
+    for (int f = 0; f < nf; ++f)
+      atomicAdd(sl.cstar + ((size_t)(f0 + f) * sl.p1y + py) * sl.p1x + px,
+                wv * (T)sl.c[(size_t)(f0 + f) * sl.n + i]);
   }
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) scatter_kernel(const ScatterSlot<T> sl) {
+  __shared__ T acc[kScF][kTile * kTile];
+  if (sl.tstart == nullptr) scatter_atomic<T>(sl, blockIdx.x, gridDim.x, blockIdx.y * kScF);
+  else scatter_tile<T>(sl, blockIdx.x, blockIdx.y * kScF, acc);
+}
+
+// zeroes c* of the slots that scatter with atomics (grid.y = slot)
+template <typename T>
 __global__ void zero_group_kernel(const __grid_constant__ Group<ScatterSlot<T>> g) {
   const ScatterSlot<T>& sl = g.slot[blockIdx.y];
+  if (sl.tstart != nullptr) return;
   const size_t count = (size_t)sl.B * sl.p1y * sl.p1x;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
        t += (size_t)gridDim.x * blockDim.x)
@@ -451,26 +536,68 @@ __global__ void zero_group_kernel(const __grid_constant__ Group<ScatterSlot<T>> 
 }
 
 template <typename T>
-cudaError_t launch_scatter_group(const Group<ScatterSlot<T>>& g, cudaStream_t s) {
-  long long most = 0;
-  for (int k = 0; k < g.n; ++k) {
-    const long long t = (long long)g.slot[k].n * (2 * g.slot[k].L) * (2 * g.slot[k].L);
-    most = t > most ? t : most;
+ScatterSlot<T> scatter_slot(const rk_plan* p, const T* w, const double* c, int B, T* cstar) {
+  const bool sorted = p->n >= kTileSortMin;
+  return ScatterSlot<T>{p->box, w, c, cstar, sorted ? p->tile_start : nullptr,
+                        sorted ? p->site_order : nullptr, p->n, B, p->L,
+                        p->p1x, p->p1y, p->tiles_x, p->tiles_y};
+}
+
+template <typename T>
+cudaError_t launch_scatter(const rk_plan* p, const T* w, const double* c, int B, T* cstar,
+                           cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const ScatterSlot<T> sl = scatter_slot<T>(p, w, c, B, cstar);
+  if (sl.tstart == nullptr) {
+    const cudaError_t e = cudaMemsetAsync(cstar, 0, sizeof(T) * B * p->p1y * p->p1x, s);
+    if (e != cudaSuccess) return e;
   }
-  if (g.n == 0 || g.start[g.n] == 0) return cudaSuccess;
-  zero_group_kernel<T><<<dim3(128, g.n), 256, 0, s>>>(g);
-  long long blocks = (most + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  if (blocks < 1) blocks = 1;
-  scatter_group_kernel<T><<<dim3((unsigned)blocks, g.start[g.n]), 256, 0, s>>>(g);
+  dim3 grid(p->tiles_x * p->tiles_y, (B + kScF - 1) / kScF);
+  scatter_kernel<T><<<grid, 256, 0, s>>>(sl);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_scatter<float>(const int*, const float*, const double*, int, int, int,
-                                           float*, int, int, cudaStream_t);
-template cudaError_t launch_scatter<double>(const int*, const double*, const double*, int, int,
-                                            int, double*, int, int, cudaStream_t);
-template cudaError_t launch_scatter_group<float>(const Group<ScatterSlot<float>>&, cudaStream_t);
-template cudaError_t launch_scatter_group<double>(const Group<ScatterSlot<double>>&, cudaStream_t);
+// The scatter of several plans in one launch (rk_predict_group): slot k
+// covers field groups [start[k], start[k + 1]) of grid.y, grid.x its tiles.
+template <typename T>
+__global__ void __launch_bounds__(256)
+scatter_group_kernel(const __grid_constant__ Group<ScatterSlot<T>> g) {
+  __shared__ T acc[kScF][kTile * kTile];
+  int ks = 0;
+  while (ks + 1 < g.n && (int)blockIdx.y >= g.start[ks + 1]) ++ks;
+  const ScatterSlot<T>& sl = g.slot[ks];
+  const int nt = sl.ntx * sl.nty;
+  if ((int)blockIdx.x >= nt) return;
+  if (sl.tstart == nullptr) scatter_atomic<T>(sl, blockIdx.x, nt, (blockIdx.y - g.start[ks]) * kScF);
+  else scatter_tile<T>(sl, blockIdx.x, (blockIdx.y - g.start[ks]) * kScF, acc);
+}
+
+template <typename T>
+cudaError_t launch_scatter_group(Group<ScatterSlot<T>>& g, cudaStream_t s) {
+  int tiles = 0;
+  g.start[0] = 0;
+  for (int k = 0; k < g.n; ++k) {
+    const int t = g.slot[k].ntx * g.slot[k].nty;
+    tiles = t > tiles ? t : tiles;
+    g.start[k + 1] = g.start[k] + (g.slot[k].B + kScF - 1) / kScF;
+  }
+  if (g.n == 0 || g.start[g.n] == 0) return cudaSuccess;
+  bool any_atomic = false;
+  for (int k = 0; k < g.n; ++k) any_atomic = any_atomic || g.slot[k].tstart == nullptr;
+  if (any_atomic) zero_group_kernel<T><<<dim3(64, g.n), 256, 0, s>>>(g);
+  scatter_group_kernel<T><<<dim3(tiles, g.start[g.n]), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_scatter<float>(const rk_plan*, const float*, const double*, int,
+                                           float*, cudaStream_t);
+template cudaError_t launch_scatter<double>(const rk_plan*, const double*, const double*, int,
+                                            double*, cudaStream_t);
+template cudaError_t launch_scatter_group<float>(Group<ScatterSlot<float>>&, cudaStream_t);
+template cudaError_t launch_scatter_group<double>(Group<ScatterSlot<double>>&, cudaStream_t);
+template ScatterSlot<float> scatter_slot<float>(const rk_plan*, const float*, const double*, int,
+                                                float*);
+template ScatterSlot<double> scatter_slot<double>(const rk_plan*, const double*, const double*,
+                                                 int, double*);
 
 }  // namespace rk

@@ -49,14 +49,15 @@ static rk_status predict_static(rk_plan* p, T* out, unsigned char* base) {
   const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
   const C<T>* twy = f32 ? (const C<T>*)p->tw32y : (const C<T>*)p->tw64y;
-  // c* accumulates by atomics, so it must start at zero on every call
-  if (cudaMemsetAsync(cstar, 0, (size_t)B * plane * sizeof(T), s) != cudaSuccess ||
-      launch_scatter<T>(p->box, w, p->c64, p->n, B, p->L, cstar, p->p1x, p->p1y, s) != cudaSuccess ||
+  // the tiled scatter writes every element of c*, so nothing needs clearing
+  if (launch_scatter<T>(p, w, p->c64, B, cstar, s) != cudaSuccess ||
       launch_rows_fwd<T>(cstar, p->p1y, p->p1x, (long long)plane, p->p1x, tb, p->ldt,
                          (long long)p->H * p->ldt, B, p->fpx, twx, p->H, s) != cudaSuccess)
     return RK_ERR_CUDA;
   const bool use_blk = f32 && p->nblk > 0;
-  if (use_blk && launch_block_gemm(p->c64, B, p->n, p->efac, p->nblk, blk, s) != cudaSuccess)
+  // the block factors of the last site update were computed on the side stream
+  if (use_blk && (cudaStreamWaitEvent(s, p->ev_sites, 0) != cudaSuccess ||
+                  launch_block_gemm(p->c64, B, p->n, p->efac, p->nblk, blk, s) != cudaSuccess))
     return RK_ERR_CUDA;
   if (launch_cols<T>(tb, p->ldt, (long long)p->H * p->ldt, p->p1y, ub, p->ldu,
                      (long long)p->H * p->ldu, p->L - 1, p->ny, lam, COLS_CONV,

@@ -292,11 +292,14 @@ void free_plan(rk_plan* p) {
                   p->d_flag, p->tw64qx, p->tw64qy, p->tw32qx, p->tw32qy, p->ce_sqrt64,
                   p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_c, p->h_out, p->xy, p->wd64,
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
-                  p->efac_g, p->gblk, p->bw_dk};
+                  p->efac_g, p->gblk, p->bw_dk, p->tile_start,
+                  p->tile_count, p->tile_cursor, p->site_order};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->ev_wfork) cudaEventDestroy(p->ev_wfork);
+  if (p->ev_sites) cudaEventDestroy(p->ev_sites);
   if (p->side) cudaStreamDestroy(p->side);
 }
 
@@ -390,8 +393,7 @@ rk_status predict_fields(rk_plan* p, const double* c64, int nf, T* out,
   }
   {
     RK_PROF("scatter", B * (plane * es + nM * 2 * es + p->n * es) + nM * es + p->n * 8.0);
-    RK_CU(cudaMemsetAsync(cstar, 0, (size_t)B * plane * sizeof(T), s));
-    RK_CU(launch_scatter<T>(p->box, w, c64, p->n, B, p->L, cstar, p->p1x, p->p1y, s));
+    RK_CU(launch_scatter<T>(p, w, c64, B, cstar, s));
   }
   {
     RK_PROF("rows_fwd", B * (plane * es + (double)p->H * p->p1y * cs));
@@ -441,7 +443,7 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
     any_blk = any_blk || blk;
     const T* w = f32 ? (const T*)p->w32 : (const T*)p->w64;
     const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
-    gs.slot[k] = ScatterSlot<T>{p->box, w, p->c64, (T*)p->cstar, p->n, B, p->L, p->p1x, p->p1y};
+    gs.slot[k] = scatter_slot<T>(p, w, p->c64, B, (T*)p->cstar);
     gf.slot[k] = RowsFwdSlot<T>{(const T*)p->cstar, (C<T>*)p->tbuf, (long long)plane,
                                 (long long)p->H * p->ldt, p->p1y, p->p1x, p->p1x, p->ldt, B};
     gc.slot[k] = ColsSlot<T>{(const C<T>*)p->tbuf, (C<T>*)p->ubuf, lam, blk ? p->blk : nullptr,
@@ -452,7 +454,6 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
                                 p->ny, p->nx, p->L - 1, p->nx, 0, 0, 0, B};
     gb.slot[k] = BlockGemmSlot{p->c64, p->efac, p->blk, p->n, B, blk ? p->nblk : 0};
     gb.start[k + 1] = gb.start[k] + B;
-    gs.start[k + 1] = gs.start[k] + B;
     gf.start[k + 1] = gf.start[k] + B;
     gi.start[k + 1] = gi.start[k] + B;
     const double es = sizeof(T), cs = 2.0 * es, nM = (double)p->n * p->M;
@@ -471,6 +472,8 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
   if (any_blk) {
     RK_CU(cudaEventRecord(p0->ev_fork, s));
     RK_CU(cudaStreamWaitEvent(p0->side, p0->ev_fork, 0));
+    for (int k = 1; k < np; ++k)   // block factors ran on each plan's own side stream
+      RK_CU(cudaStreamWaitEvent(p0->side, plans[k]->ev_sites, 0));
     cudaStream_t s_main = s;
     {
       cudaStream_t s = p0->side;
@@ -846,9 +849,20 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
   do {
     if ((st = dalloc(&p->d_flag, 1)) != RK_OK) break;
     if ((st = dalloc(&p->d_sites_flag, 1)) != RK_OK) break;
+    p->tiles_x = (p->p1x + 31) / 32;
+    p->tiles_y = (p->p1y + 31) / 32;
+    if ((st = dalloc(&p->tile_start, (size_t)p->tiles_x * p->tiles_y + 1)) != RK_OK) break;
+    if ((st = dalloc(&p->tile_count, (size_t)p->tiles_x * p->tiles_y)) != RK_OK) break;
+    if ((st = dalloc(&p->tile_cursor, (size_t)p->tiles_x * p->tiles_y)) != RK_OK) break;
+    if (cudaMemset(p->tile_count, 0, sizeof(int) * p->tiles_x * p->tiles_y) != cudaSuccess) {
+      st = RK_ERR_CUDA;
+      break;
+    }
     if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_wfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_sites, cudaEventDisableTiming) != cudaSuccess) {
       st = RK_ERR_CUDA;
       break;
     }
@@ -932,13 +946,32 @@ rk_status rk_plan_get_info(const rk_plan* p, rk_plan_info* info) {
   return RK_OK;
 }
 
+// The block factors of the sites just weighted (FP32 plans), on the side
+// stream after the weights; the block GEMM, which runs on that stream too,
+// is the only consumer (rk_predict_static and groups wait on ev_sites).
+rk_status launch_site_factors(rk_plan* p, int n) {
+  if (p->precision != RK_FP32 || p->nblk == 0) return RK_OK;
+  RK_CU(cudaEventRecord(p->ev_wfork, p->stream));
+  RK_CU(cudaStreamWaitEvent(p->side, p->ev_wfork, 0));
+  {
+    cudaStream_t s = p->side;
+    RK_PROF64("block_factors", (double)n * (8.0 * p->M + 8.0 + 16.0 * p->nblk),
+              (double)n * (4.0 * (p->blk_kx + 1) * p->M + 8.0 * p->nblk * 2 * p->L));
+    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, s));
+  }
+  RK_CU(cudaEventRecord(p->ev_sites, p->side));
+  return RK_OK;
+}
+
 rk_status ensure_sites(rk_plan* p, int n) {
   if (n > p->n_cap) {
+    RK_CU(cudaStreamSynchronize(p->side));   // the side stream may still read the old buffers
     RK_TRY(dalloc(&p->xy, (size_t)2 * n));
     RK_TRY(dalloc(&p->box, (size_t)2 * n));
     RK_TRY(dalloc(&p->w64, (size_t)n * p->M));
     RK_TRY(dalloc(&p->w32, (size_t)n * p->M));
     RK_TRY(dalloc(&p->ssd, (size_t)n));
+    RK_TRY(dalloc(&p->site_order, (size_t)n));
     if (p->precision == RK_FP32 && p->nblk > 0) RK_TRY(dalloc(&p->efac, (size_t)n * p->nblk));
     p->n_cap = n;
   }
@@ -958,8 +991,8 @@ rk_status rk_set_weights(rk_plan* p, int n, const int* box, const double* w) {
   int flag = 0;
   RK_TRY(read_flag(p, &flag));
   if (flag & 4) return RK_ERR_INVALID_ARG;
-  if (p->precision == RK_FP32 && p->nblk > 0)
-    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, p->stream));
+  RK_CU(launch_tile_sites(p->box, n, p, false, p->stream));
+  RK_TRY(launch_site_factors(p, n));
   p->n = n;
   return RK_OK;
 }
@@ -972,11 +1005,11 @@ rk_status rk_set_sites(rk_plan* p, int n, const double* xy) {
                         p->stream));
   RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
   RK_CU(launch_weights(p->xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_flag, p->stream));
+  RK_CU(launch_tile_sites(p->box, n, p, true, p->stream));   // clears the weights' counts
   int flag = 0;
   RK_TRY(read_flag(p, &flag));
   if (flag & 2) return RK_ERR_OBS_OUTSIDE;
-  if (p->precision == RK_FP32 && p->nblk > 0)
-    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, p->stream));
+  RK_TRY(launch_site_factors(p, n));
   p->n = n;
   return RK_OK;
 }
@@ -994,11 +1027,11 @@ rk_status rk_set_sites_async(rk_plan* p, int n, const double* xy) {
               (double)n * (2.0 * p->M * p->M + 10.0 * p->M));
     RK_CU(launch_weights(p->xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_sites_flag, s));
   }
-  if (p->precision == RK_FP32 && p->nblk > 0) {
-    RK_PROF64("block_factors", (double)n * (8.0 * p->M + 8.0 + 16.0 * p->nblk),
-              (double)n * (4.0 * (p->blk_kx + 1) * p->M + 8.0 * p->nblk * 2 * p->L));
-    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, s));
+  {
+    RK_PROF("tile_sites", (double)n * 24.0);
+    RK_CU(launch_tile_sites(p->box, n, p, true, s));
   }
+  RK_TRY(launch_site_factors(p, n));
   p->n = n;
   return RK_OK;
 }
