@@ -49,6 +49,8 @@ def parse():
                     help="skip the 1024^2, conditional-simulation and adjoint measurements")
     ap.add_argument("--backward-n", type=int, default=None,
                     help="sites for the adjoint measurement (default: the workload's 20000)")
+    ap.add_argument("--secondary-only", choices=["cs512", "grad1024_backward"], default=None,
+                    help="run one secondary measurement alone and print it (for profiling)")
     return ap.parse_args()
 
 
@@ -194,10 +196,18 @@ class Arm:
         torch.cuda.synchronize()
 
     def _issue(self):
-        """One step: per cell, weights (async site update) and coefficients on
-        the cell's stream; then the predictions of all cells, grouped (one
-        launch per pass, rk_predict_group) when the cells share a torus."""
+        """One step: every cell's weights (site update), coefficients and
+        prediction.  Cells sharing a torus go as groups (rk_set_sites_group:
+        one weights launch per L; rk_predict_group: one launch per pass);
+        otherwise one stream per cell."""
         torch = self.torch
+        if self.grouped:
+            plans = [p for p, _, _ in self.st]
+            self.rk.set_sites_group(plans, [self.xy] * len(plans))
+            for p, c, _ in self.st:
+                p.set_coef(c)
+            self.rk.predict_group(plans, [o for _, _, o in self.st])
+            return
         cur = torch.cuda.current_stream()
         fork = torch.cuda.Event()
         fork.record(cur)
@@ -207,15 +217,12 @@ class Arm:
             with torch.cuda.stream(s):
                 p.set_sites_async(self.xy)
                 p.set_coef(c)
-                if not self.grouped:
-                    p.predict(out)
+                p.predict(out)
                 e = torch.cuda.Event()
                 e.record(s)
             joins.append(e)
         for e in joins:
             cur.wait_event(e)
-        if self.grouped:
-            self.rk.predict_group([p for p, _, _ in self.st], [o for _, _, o in self.st])
 
     def capture(self):
         """Capture one step (all cells, their streams forked and joined) in a CUDA graph."""
@@ -488,13 +495,21 @@ def run_ours(args, rank, world):
         secondary["cs512_simulate"] = measure_cs(dev, max(2, args.steps // 5), peaks)
         secondary["grad1024_backward"] = measure_backward(dev, max(2, args.steps // 5), peaks,
                                                           n=args.backward_n)
-    # our kernels per step: per cell weights (+ block factors), then either
-    # per cell [block GEMM,] scatter, rows_fwd, cols, rows_inv, or the grouped
-    # passes ([block GEMM,] zero, scatter, rows_fwd, cols, rows_inv)
+    # our kernels per step.  Sites: weights, the scatter order for n >= 4096
+    # (scan, fill), FP32 block factors; prediction: FP32 block GEMM, a zeroing
+    # pass when a cell scatters with atomics (n < 4096), scatter, rows_fwd,
+    # cols, rows_inv.  Grouped: one weights launch per L and one launch for
+    # each other pass over all cells.
     f32 = args.precision == "fp32"
     ncell = len(main.cells)
-    per_step = ncell * (2 if f32 else 1) + (
-        (1 if f32 else 0) + 5 if main.grouped else ncell * (5 if f32 else 4))
+    nsite = int(main.xy_np.shape[0])
+    order = 2 if nsite >= 4096 else 0
+    zero = 0 if nsite >= 4096 else 1
+    if main.grouped:
+        nL = len({kw["L"] for _, kw, _ in main.cells})
+        per_step = nL + ncell * order + (2 if f32 else 0) + zero + 4
+    else:
+        per_step = ncell * (1 + order + (2 if f32 else 0) + 4)
     res = {
         "metric": METRIC, "value": value, "unit": "grid-point predictions/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -503,9 +518,10 @@ def run_ours(args, rank, world):
         "data": "synthetic (seeded sites and data; see synth)",
         "config": {**workload_config(args.workload, world),
                    "l2": "flushed between timed steps (256 MB write)",
-                   "issue": ("sites and coefficients on one stream per cell, the cells' "
-                             "predictions in one grouped launch per pass (rk_predict_group), "
-                             "step replayed from a CUDA graph") if main.grouped else
+                   "issue": ("the cells' site updates grouped (rk_set_sites_group: one "
+                             "weights launch per L), their predictions grouped "
+                             "(rk_predict_group: one launch per pass), step replayed from a "
+                             "CUDA graph") if main.grouped else
                             "one stream per cell, step replayed from a CUDA graph",
                    "value_without_graph": value_nograph},
         "roofline": roof,
@@ -581,6 +597,18 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.secondary_only:
+        import torch
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        torch.cuda.set_device(dev)
+        peaks = _load_peaks()
+        if args.secondary_only == "cs512":
+            out = measure_cs(dev, args.steps, peaks)
+        else:
+            out = measure_backward(dev, args.steps, peaks, n=args.backward_n)
+        if rank == 0:
+            print(json.dumps({"secondary": args.secondary_only, **out}))
+        return 0
     res = run_ours(args, rank, world)
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"] = cpu_oracle_rate(args.workload)

@@ -128,6 +128,26 @@ rk_status rk_set_sites(rk_plan* plan, int n, const double* xy_dev);
 rk_status rk_set_sites_async(rk_plan* plan, int n, const double* xy_dev);
 
 /*
+ * rk_set_sites_group -- rk_set_sites_async for nplans plans at once (1 <=
+ * nplans <= 16): the weights of steps 3-4 (Section 2.2) in one launch per
+ * neighbourhood size L over all the plans' sites, and the FP32 plans' block
+ * factors in one launch, so that the plans of a sweep (Section 3) fill the
+ * GPU together.
+ *   plans   host array of distinct plans
+ *   n       host array, n[k] sites for plans[k] (at most what earlier
+ *           rk_set_sites calls sized: no allocation here)
+ *   xy      host array of device pointers, xy[k] n[k] x 2 doubles
+ * Issued on plans[0]'s stream (block factors on its side stream); no host
+ * synchronisation: sites outside the extent are latched per plan and
+ * reported by that plan's rk_check_sites once plans[0]'s stream has passed
+ * this call (rk_check_sites synchronises only its own plan's stream).
+ * Plans must not be in use on other streams meanwhile.  RK_ERR_INVALID_ARG for null or
+ * repeated plans, RK_ERR_STATE when n[k] exceeds a plan's sized capacity.
+ */
+rk_status rk_set_sites_group(rk_plan* const* plans, int nplans, const int* n,
+                             const double* const* xy);
+
+/*
  * rk_check_sites -- synchronises with the plan's stream and returns
  * RK_ERR_OBS_OUTSIDE if any site given to rk_set_sites_async since the last
  * check lay outside the extent, RK_OK otherwise; clears the latch.

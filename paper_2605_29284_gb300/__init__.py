@@ -12,7 +12,7 @@ import torch
 from ._native import RK_FP32, RK_FP64, PlanInfo, RkError, check, lib, profile_enable, profile_read
 
 __all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "predict_group", "profile_enable",
-           "profile_read"]
+           "profile_read", "set_sites_group"]
 
 
 def _ptr(t):
@@ -194,3 +194,21 @@ def predict_group(plans, outs=None):
     check(lib.rk_set_stream(plans[0]._h, _stream()), "rk_set_stream")
     check(lib.rk_predict_group(harr, n, oarr), "rk_predict_group")
     return outs
+
+
+def set_sites_group(plans, xys):
+    """rk_set_sites_group: the plans' site updates, weights in one launch per L.
+
+    xys[k] (device, n_k x 2 doubles) goes to plans[k], whose buffers an
+    earlier set_sites sized.  Issued on the current stream; no host sync."""
+    plans = list(plans)
+    xys = [_dev_f64(x) for x in xys]
+    n = len(plans)
+    harr = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+    narr = (ctypes.c_int * n)(*[int(x.shape[0]) for x in xys])
+    xarr = (ctypes.c_void_p * n)(*[_ptr(x) for x in xys])
+    check(lib.rk_set_stream(plans[0]._h, _stream()), "rk_set_stream")
+    check(lib.rk_set_sites_group(harr, n, narr, xarr), "rk_set_sites_group")
+    for p, x in zip(plans, xys):
+        p.n = int(x.shape[0])
+        p._xy = x

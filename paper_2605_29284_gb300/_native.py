@@ -66,6 +66,7 @@ _SIGS = {
     "rk_predict_host": [_vp, _int, _vp, _int, _vp, _vp],
     "rk_predict_static": [_vp, _vp],
     "rk_predict_group": [ctypes.POINTER(_vp), _int, ctypes.POINTER(_vp)],
+    "rk_set_sites_group": [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_vp)],
     "rk_simulate": [_vp, _int, ctypes.c_ulonglong, _vp],
     "rk_predict_backward": [_vp, _vp, _vp, _vp, _vp],
     "rk_debug_copy": [_vp, _int, _vp, ctypes.c_size_t],

@@ -243,6 +243,22 @@ struct RowsInvSlot {
   long long ufs, ofs, afs;
   int ldu, nrows, old, ocol0, ncols, ald, ar0, ac0, B;
 };
+struct WeightsSlot {
+  const double* xy; const double* kn;
+  int* box; double* w64; float* w32; double* ssd; int* flag; int* tcount;
+  int n, nx, ny, ntx, nu_code, L;
+  double x0, x1, y0, y1, hx, hy, rho, sigma2;
+};
+WeightsSlot weights_slot(const double* xy, int n, const rk_plan* p, int* box, double* w64,
+                         float* w32, double* ssd, int* flag);
+cudaError_t launch_weights_group(Group<WeightsSlot>& g, cudaStream_t s);
+struct BlockFactorSlot {
+  const int* box; const double* w64; const double2* twx; const double2* twy; double2* efac;
+  int n, L, px, py, KX, KY, NS;
+};
+BlockFactorSlot block_factor_slot(const int* box, const double* w64, int n, const rk_plan* p,
+                                  int kx, int ky, double2* efac);
+cudaError_t launch_block_factors_group(Group<BlockFactorSlot>& g, cudaStream_t s);
 struct BlockGemmSlot {
   const double* c; const double2* efac; double2* blk;
   int n, B, nblk;

@@ -56,23 +56,30 @@ cudaError_t launch_kn_factor(double* kn, int L, double hx, double hy, double rho
 // cycles per scheduler, so one thread per site (~M^2 dependent operations
 // each) would leave the kernel's duration to a few long instruction chains.  Lane j holds rows r = j + s G (s < S) of k_i;
 // each substitution step broadcasts the solved entry from its owner lane.
+// One CTA's sites of one plan (slot sl, CTA cta of that plan's share);
+// Ls / Linv: shared memory for the factor and its diagonal's reciprocals.
 template <int W, int G>
-__global__ void __launch_bounds__(64)
-weights_grp_kernel(const double* __restrict__ xy, int n, double x0, double x1, double y0,
-                   double y1, double hx, double hy, int nx, int ny, double rho, double sigma2,
-                   int nu_code, const double* __restrict__ kn, int* __restrict__ box,
-                   double* __restrict__ w64, float* __restrict__ w32,
-                   double* __restrict__ ssd, int* flag, int* __restrict__ tcount, int ntx) {
+__device__ __forceinline__ void weights_cta(const WeightsSlot& sl, int cta, double* Ls,
+                                            double* Linv) {
   constexpr int M = W * W;
   constexpr int L = W / 2;
   constexpr int S = (M + G - 1) / G;
-  __shared__ double Ls[M * M];
-  __shared__ double Linv[M];
+  const double* __restrict__ xy = sl.xy;
+  const double* __restrict__ kn = sl.kn;
+  int* __restrict__ box = sl.box;
+  double* __restrict__ w64 = sl.w64;
+  float* __restrict__ w32 = sl.w32;
+  double* __restrict__ ssd = sl.ssd;
+  int* __restrict__ tcount = sl.tcount;
+  const int n = sl.n, nx = sl.nx, ny = sl.ny, ntx = sl.ntx, nu_code = sl.nu_code;
+  const double x0 = sl.x0, x1 = sl.x1, y0 = sl.y0, y1 = sl.y1, hx = sl.hx, hy = sl.hy;
+  const double rho = sl.rho, sigma2 = sl.sigma2;
+  int* flag = sl.flag;
   for (int t = threadIdx.x; t < M * M; t += blockDim.x) Ls[t] = kn[t];
   for (int t = threadIdx.x; t < M; t += blockDim.x) Linv[t] = 1.0 / kn[t * M + t];
   __syncthreads();
   const int j = threadIdx.x % G;
-  const int i = blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+  const int i = cta * (blockDim.x / G) + threadIdx.x / G;
   const bool act = i < n;
   const double x = act ? xy[2 * i] : x0, y = act ? xy[2 * i + 1] : y0;
   const bool inside = x >= x0 && x <= x1 && y >= y0 && y <= y1;
@@ -137,6 +144,32 @@ weights_grp_kernel(const double* __restrict__ xy, int n, double x0, double x1, d
   }
 }
 
+// One launch for one plan or several (rk_set_sites_group) with L <= 3,
+// whatever their L: slot k covers CTAs [start[k], start[k + 1]) and runs the
+// variant for its L with G lanes per site (G capped at M for L = 1).  L = 4
+// (M = 64) has a kernel of its own: its register needs would cap the others'
+// occupancy.
+template <int G, int LMAX>
+__global__ void __launch_bounds__(64)
+weights_grp_kernel(const __grid_constant__ Group<WeightsSlot> g) {
+  constexpr int MM = 4 * LMAX * LMAX;
+  __shared__ double Ls[MM * MM];
+  __shared__ double Linv[MM];
+  int ks = 0;
+  while (ks + 1 < g.n && (int)blockIdx.x >= g.start[ks + 1]) ++ks;
+  const WeightsSlot& sl = g.slot[ks];
+  const int cta = blockIdx.x - g.start[ks];
+  if constexpr (LMAX == 4) {
+    weights_cta<8, G>(sl, cta, Ls, Linv);
+  } else {
+    switch (sl.L) {
+      case 1: weights_cta<2, (G < 4 ? G : 4)>(sl, cta, Ls, Linv); break;
+      case 2: weights_cta<4, G>(sl, cta, Ls, Linv); break;
+      default: weights_cta<6, G>(sl, cta, Ls, Linv); break;
+    }
+  }
+}
+
 // Lanes per site: about two warps per scheduler (152 SMs x 4), i.e. the
 // largest power of two G <= 2 * 608 * 32 / n, kept within [4, min(32, M)].
 // More lanes per site shorten each warp's chain of FP64 instructions but
@@ -148,30 +181,63 @@ inline int weights_lanes(int n, int M) {
   return g < M ? g : M;
 }
 
-cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, double* w64,
-                           float* w32, double* ssd, int* flag, cudaStream_t s) {
+WeightsSlot weights_slot(const double* xy, int n, const rk_plan* p, int* box, double* w64,
+                         float* w32, double* ssd, int* flag) {
+  return WeightsSlot{xy, p->kn_chol, box, w64, w32, ssd, flag,
+                     n >= kTileSortMin ? p->tile_count : nullptr,
+                     n, p->nx, p->ny, p->tiles_x, p->nu_code, p->L,
+                     p->x0, p->x1, p->y0, p->y1, p->hx, p->hy, p->rho, p->sigma2};
+}
+
+// One launch over g's slots (any mix of L); g.start is filled here (in CTAs).
+// G from the total site count and the largest neighbourhood.
+template <int LMAX>
+cudaError_t launch_weights_slots(Group<WeightsSlot>& g, cudaStream_t s) {
   // two warps per CTA: a site's FP64 chain is long, so finer CTAs spread
   // the warps evenly over the schedulers
   const int threads = 64;
-  const int G = weights_lanes(n, p->M);
-#define RK_WG(WW, GG)                                                                          \
-  if (G == GG) {                                                                               \
-    const int sites = threads / GG;                                                            \
-    weights_grp_kernel<WW, GG><<<(n + sites - 1) / sites, threads, 0, s>>>(                    \
-        xy, n, p->x0, p->x1, p->y0, p->y1, p->hx, p->hy, p->nx, p->ny, p->rho, p->sigma2,     \
-        p->nu_code, p->kn_chol, box, w64, w32, ssd, flag,                                      \
-        n >= kTileSortMin ? p->tile_count : nullptr, p->tiles_x);                              \
-    return cudaGetLastError();                                                                 \
+  long long total = 0;
+  int Mmax = 0;
+  for (int k = 0; k < g.n; ++k) {
+    total += g.slot[k].n;
+    const int M = 4 * g.slot[k].L * g.slot[k].L;
+    Mmax = M > Mmax ? M : Mmax;
   }
-  switch (p->L) {
-    case 1: RK_WG(2, 4) break;
-    case 2: RK_WG(4, 4) RK_WG(4, 8) RK_WG(4, 16) break;
-    case 3: RK_WG(6, 4) RK_WG(6, 8) RK_WG(6, 16) RK_WG(6, 32) break;
-    case 4: RK_WG(8, 4) RK_WG(8, 8) RK_WG(8, 16) RK_WG(8, 32) break;
-    default: return cudaErrorInvalidValue;
+  if (g.n == 0 || total == 0) return cudaSuccess;
+  const int G = weights_lanes(total > 0x7fffffff ? 0x7fffffff : (int)total, Mmax);
+  g.start[0] = 0;
+  for (int k = 0; k < g.n; ++k) {
+    const int gk = g.slot[k].L == 1 && G > 4 ? 4 : G;
+    g.start[k + 1] = g.start[k] + (g.slot[k].n + threads / gk - 1) / (threads / gk);
   }
-#undef RK_WG
-  return cudaErrorInvalidValue;
+  switch (G) {
+    case 4: weights_grp_kernel<4, LMAX><<<g.start[g.n], threads, 0, s>>>(g); break;
+    case 8: weights_grp_kernel<8, LMAX><<<g.start[g.n], threads, 0, s>>>(g); break;
+    case 16: weights_grp_kernel<16, LMAX><<<g.start[g.n], threads, 0, s>>>(g); break;
+    default: weights_grp_kernel<32, LMAX><<<g.start[g.n], threads, 0, s>>>(g); break;
+  }
+  return cudaGetLastError();
+}
+
+// g's slots split into L <= 3 (one launch) and L = 4 (one launch)
+cudaError_t launch_weights_group(Group<WeightsSlot>& g, cudaStream_t s) {
+  Group<WeightsSlot> a, b;
+  for (int k = 0; k < g.n; ++k) {
+    if (g.slot[k].L == 4) b.slot[b.n++] = g.slot[k];
+    else a.slot[a.n++] = g.slot[k];
+  }
+  cudaError_t e = launch_weights_slots<3>(a, s);
+  if (e != cudaSuccess) return e;
+  return launch_weights_slots<4>(b, s);
+}
+
+cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, double* w64,
+                           float* w32, double* ssd, int* flag, cudaStream_t s) {
+  if (p->L < 1 || p->L > 4) return cudaErrorInvalidValue;
+  Group<WeightsSlot> g;
+  g.n = 1;
+  g.slot[0] = weights_slot(xy, n, p, box, w64, w32, ssd, flag);
+  return launch_weights_group(g, s);
 }
 
 // ------------------------------------------------------------ set weights --
@@ -223,14 +289,19 @@ cudaError_t launch_set_weights(const int* box_in, const double* w_in, int n, con
 // into shared memory, one thread per (site, kx, b), then one thread per
 // (site, kx, ky) entry, E = sum_b t_i(kx, b) exp(-2 pi i ky (iy + b) / py).
 // Twiddle indices stay below 2^31 (kx, |ky| <= 1024, torus <= 2^21).
-__global__ void block_factor_kernel(const int* __restrict__ box, const double* __restrict__ w64,
-                                    int n, int L, int px, int py, int KX, int KY, int NS,
-                                    const double2* __restrict__ twx,
-                                    const double2* __restrict__ twy,
-                                    double2* __restrict__ efac) {
+__global__ void block_factor_kernel(const __grid_constant__ Group<BlockFactorSlot> g) {
   extern __shared__ double2 tsm[];        // [NS][KX + 1][2L]
-  const int W = 2 * L, M = W * W, nk = KX + 1, bw = 2 * KY + 1;
-  const int i0 = blockIdx.x * NS;
+  int ks = 0;
+  while (ks + 1 < g.n && (int)blockIdx.x >= g.start[ks + 1]) ++ks;
+  const BlockFactorSlot& sl = g.slot[ks];
+  const int* __restrict__ box = sl.box;
+  const double* __restrict__ w64 = sl.w64;
+  const double2* __restrict__ twx = sl.twx;
+  const double2* __restrict__ twy = sl.twy;
+  double2* __restrict__ efac = sl.efac;
+  const int n = sl.n, px = sl.px, py = sl.py, KY = sl.KY, NS = sl.NS;
+  const int W = 2 * sl.L, M = W * W, nk = sl.KX + 1, bw = 2 * KY + 1;
+  const int i0 = (blockIdx.x - g.start[ks]) * NS;
   const int ns = min(NS, n - i0);
   for (int e = threadIdx.x; e < ns * nk * W; e += blockDim.x) {
     const int b = e % W, kx = (e / W) % nk, si = e / (W * nk);
@@ -265,8 +336,8 @@ __global__ void block_factor_kernel(const int* __restrict__ box, const double* _
   }
 }
 
-cudaError_t launch_block_factors(const int* box, const double* w64, int n, const rk_plan* p,
-                                 int kx, int ky, double2* efac, cudaStream_t s) {
+BlockFactorSlot block_factor_slot(const int* box, const double* w64, int n, const rk_plan* p,
+                                  int kx, int ky, double2* efac) {
   const int W = 2 * p->L;
   const size_t per_site = sizeof(double2) * (size_t)(kx + 1) * W;
   // sites per CTA: two CTAs per SM at least, at most 32 KB of row sums
@@ -275,13 +346,32 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
   NS = NS > cap ? cap : NS;
   NS = NS > 32 ? 32 : NS;
   NS = NS < 1 ? 1 : NS;
-  const size_t sm = per_site * NS;
+  return BlockFactorSlot{box, w64, p->tw64x, p->tw64y, efac, n, p->L, p->px, p->py, kx, ky, NS};
+}
+
+cudaError_t launch_block_factors_group(Group<BlockFactorSlot>& g, cudaStream_t s) {
+  size_t sm = 0;
+  g.start[0] = 0;
+  for (int k = 0; k < g.n; ++k) {
+    const BlockFactorSlot& sl = g.slot[k];
+    const size_t b = sizeof(double2) * (size_t)(sl.KX + 1) * 2 * sl.L * sl.NS;
+    sm = b > sm ? b : sm;
+    g.start[k + 1] = g.start[k] + (sl.n + sl.NS - 1) / sl.NS;
+  }
+  if (g.n == 0 || g.start[g.n] == 0) return cudaSuccess;
   static int smem_set = 0;
   cudaError_t e = ensure_smem(block_factor_kernel, sm, smem_set);
   if (e != cudaSuccess) return e;
-  block_factor_kernel<<<(n + NS - 1) / NS, 128, sm, s>>>(box, w64, n, p->L, p->px, p->py, kx, ky,
-                                                         NS, p->tw64x, p->tw64y, efac);
+  block_factor_kernel<<<g.start[g.n], 128, sm, s>>>(g);
   return cudaGetLastError();
+}
+
+cudaError_t launch_block_factors(const int* box, const double* w64, int n, const rk_plan* p,
+                                 int kx, int ky, double2* efac, cudaStream_t s) {
+  Group<BlockFactorSlot> g;
+  g.n = 1;
+  g.slot[0] = block_factor_slot(box, w64, n, p, kx, ky, efac);
+  return launch_block_factors_group(g, s);
 }
 
 // ------------------------------------------------------------ block GEMM --

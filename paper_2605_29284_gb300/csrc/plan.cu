@@ -381,6 +381,7 @@ rk_status predict_fields(rk_plan* p, const double* c64, int nf, T* out,
   if (use_blk) {
     RK_CU(cudaEventRecord(p->ev_fork, s));
     RK_CU(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+    RK_CU(cudaStreamWaitEvent(p->side, p->ev_sites, 0));   // factors from a grouped update
     cudaStream_t s_main = s;
     {
       cudaStream_t s = p->side;
@@ -1033,6 +1034,67 @@ rk_status rk_set_sites_async(rk_plan* p, int n, const double* xy) {
   }
   RK_TRY(launch_site_factors(p, n));
   p->n = n;
+  return RK_OK;
+}
+
+rk_status rk_set_sites_group(rk_plan* const* plans, int nplans, const int* n,
+                            const double* const* xy) {
+  if (!plans || !n || !xy || nplans < 1 || nplans > kMaxGroup || !plans[0])
+    return RK_ERR_INVALID_ARG;
+  for (int k = 0; k < nplans; ++k) {
+    if (!plans[k] || !xy[k] || n[k] < 1) return RK_ERR_INVALID_ARG;
+    for (int j = 0; j < k; ++j)
+      if (plans[j] == plans[k]) return RK_ERR_INVALID_ARG;
+    if (n[k] > plans[k]->n_cap) return RK_ERR_STATE;
+  }
+  rk_plan* p0 = plans[0];
+  cudaStream_t s = p0->stream;
+  double wb = 0, wf = 0, fb = 0, ff = 0;
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    RK_TRY(ensure_sites(p, n[k]));   // no growth: only resets the derived state
+    p->xy_valid = true;
+    RK_CU(cudaMemcpyAsync(p->xy, xy[k], (size_t)2 * n[k] * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s));
+    wb += (double)n[k] * (16.0 + 12.0 * p->M + 16.0) + 8.0 * p->M * p->M;
+    wf += (double)n[k] * (2.0 * p->M * p->M + 10.0 * p->M);
+    if (p->precision == RK_FP32 && p->nblk > 0) {
+      fb += (double)n[k] * (8.0 * p->M + 8.0 + 16.0 * p->nblk);
+      ff += (double)n[k] * (4.0 * (p->blk_kx + 1) * p->M + 8.0 * p->nblk * 2 * p->L);
+    }
+  }
+  {
+    RK_PROF64("weights", wb, wf);
+    Group<WeightsSlot> g;               // one launch for every plan, whatever its L
+    for (int k = 0; k < nplans; ++k) {
+      rk_plan* p = plans[k];
+      g.slot[g.n++] = weights_slot(p->xy, n[k], p, p->box, p->w64, p->w32, p->ssd,
+                                   p->d_sites_flag);
+    }
+    RK_CU(launch_weights_group(g, s));
+  }
+  {
+    RK_PROF("tile_sites", 0.0);
+    for (int k = 0; k < nplans; ++k) RK_CU(launch_tile_sites(plans[k]->box, n[k], plans[k], true, s));
+  }
+  Group<BlockFactorSlot> gf;
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    if (p->precision == RK_FP32 && p->nblk > 0)
+      gf.slot[gf.n++] = block_factor_slot(p->box, p->w64, n[k], p, p->blk_kx, p->blk_ky, p->efac);
+  }
+  if (gf.n > 0) {
+    // on the first plan's side stream; every plan's ev_sites marks the result
+    RK_CU(cudaEventRecord(p0->ev_wfork, s));
+    RK_CU(cudaStreamWaitEvent(p0->side, p0->ev_wfork, 0));
+    {
+      cudaStream_t s = p0->side;
+      RK_PROF64("block_factors", fb, ff);
+      RK_CU(launch_block_factors_group(gf, s));
+    }
+    for (int k = 0; k < nplans; ++k) RK_CU(cudaEventRecord(plans[k]->ev_sites, p0->side));
+  }
+  for (int k = 0; k < nplans; ++k) plans[k]->n = n[k];
   return RK_OK;
 }
 

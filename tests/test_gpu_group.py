@@ -92,3 +92,37 @@ def test_group_rejects_bad_groups(rk):
     finally:
         for p in a + b + c + [empty]:
             p.close()
+
+
+def test_grouped_site_updates_equal_single_updates(rk):
+    # rk_set_sites_group (weights per L in one launch, block factors in one)
+    # against each plan's own rk_set_sites: the same predictions; an outside
+    # site is latched for its plan only
+    ext = (0.0, 1.6, 0.0, 1.0)
+    cells = [(nu, L) for nu in (0.5, 2.5) for L in (1, 2, 3)]
+    plans, coefs = _plans(rk, 350, ext, cells, "fp32", n=1368)
+    try:
+        single = [p.predict().double().cpu().numpy() for p in plans]
+        xys = [torch.from_numpy(xy).cuda() for xy, _, _, _ in coefs]
+        rk.set_sites_group(plans, xys)
+        for p, (xy, c, g, th) in zip(plans, coefs):
+            p.set_coef(torch.from_numpy(np.atleast_2d(c)).cuda())
+        outs = rk.predict_group(plans)
+        torch.cuda.synchronize()
+        for p, o, s in zip(plans, outs, single):
+            p.check_sites()
+            assert rel_err(o.double().cpu().numpy(), s) <= 1e-6
+        bad = coefs[4][0].copy()
+        bad[7] = (1.7, 0.5)
+        rk.set_sites_group(plans, xys[:4] + [torch.from_numpy(bad).cuda()] + xys[5:])
+        torch.cuda.synchronize()
+        for k, p in enumerate(plans):
+            if k == 4:
+                with pytest.raises(rk.RkError) as e:
+                    p.check_sites()
+                assert e.value.name == "RK_ERR_OBS_OUTSIDE"
+            else:
+                p.check_sites()
+    finally:
+        for p in plans:
+            p.close()
