@@ -396,8 +396,16 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # captures and commands)
 TRAFFIC = {
     # profiles/cols_grad1024.md: ncu --set full, one launch (16 fields, P = 2187)
-    "cols": {"workload": "grad1024", "bytes_per_launch": 163313664 + 103914496,
-             "sources": ["k_fftn.cu", "fftn.cuh", "fft.cuh"], "digest": "978821fdb35b3e20"},
+    ("cols", "grad1024"): {"bytes_per_launch": 163313664 + 103914496,
+                           "sources": ["k_fftn.cu", "fftn.cuh", "fft.cuh"],
+                           "digest": "978821fdb35b3e20"},
+    # profiles/cols_paper350.md: the grouped column pass of the nine cells
+    ("cols", "paper350"): {"bytes_per_launch": 19767552 + 697600,
+                           "sources": ["k_fftn.cu", "fftn.cuh", "fft.cuh"],
+                           "digest": "978821fdb35b3e20"},
+    # profiles/weights_paper350.md: the grouped weights launch of the nine cells
+    ("weights", "paper350"): {"bytes_per_launch": 383488, "sources": ["k_sites.cu", "common.cuh"],
+                              "digest": "ee65bbd4135356c9"},
 }
 
 
@@ -411,8 +419,8 @@ def _sources_digest(files):
 
 
 def _traffic(kernel, workload):
-    t = TRAFFIC.get(kernel)
-    if not t or t["workload"] != workload:
+    t = TRAFFIC.get((kernel, workload))
+    if not t:
         return None
     try:
         return t["bytes_per_launch"] if _sources_digest(t["sources"]) == t["digest"] else None
