@@ -276,19 +276,31 @@ class Arm:
         return max_over_ranks(total, self.dev), prof
 
     def e2e(self, steps, warmup):
-        """The same prediction through rk_predict_host: host inputs in, host output out."""
+        """The same step through the host-buffer API (rk_predict_host_group, or
+        rk_predict_host per cell): sites and coefficients copied in from pinned
+        host memory, the grids copied back, inside the timed region."""
         torch = self.torch
-        c_host = [c.cpu().numpy() for _, c, _ in self.st]
+        xy = torch.from_numpy(self.xy_np).pin_memory().numpy()
+        cs = [c.cpu().pin_memory().numpy() for _, c, _ in self.st]
+        outs = [torch.empty(tuple(o.shape), dtype=o.dtype, pin_memory=True).numpy()
+                for _, _, o in self.st]
+        plans = [p for p, _, _ in self.st]
+
+        def once():
+            if self.grouped:
+                self.rk.predict_host_group(plans, [xy] * len(plans), cs, outs)
+            else:
+                for p, c, o in zip(plans, cs, outs):
+                    p.predict_host(xy, c, o)
+
         for _ in range(warmup):
-            for (p, c, out), ch in zip(self.st, c_host):
-                p.predict_host(self.xy_np, ch)
+            once()
         acc = 0.0
         for _ in range(steps):
             self.flush.zero_()
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            for (p, c, out), ch in zip(self.st, c_host):
-                p.predict_host(self.xy_np, ch)
+            once()
             acc += time.perf_counter() - t1
         n = self.xy_np.shape[0]
         esz = 4 if self.st[0][0].dtype == torch.float32 else 8
@@ -389,6 +401,11 @@ def measure_backward(dev, steps, peaks, n=None):
 # 4 FP64 operations per clock per SM (two fused multiply-adds) = 1.26 TFLOP/s,
 # NVIDIA's nominal 1.25 TFLOP/s
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+# double-float on the FP32 pipe: 152 SMs x 128 lanes x 2070 MHz FP32
+# instructions per second, 15 of them per double-float multiply-add (the
+# library's df_fma: product, its error, two cross terms, TwoSum, FastTwoSum),
+# 2 operations per multiply-add = 5.4 TFLOP/s of FP64-precision-equivalent work
+DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 15 * 2 / 1e12
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel, the
 # workload it was taken on and a digest of the sources it was built from; the
@@ -435,21 +452,27 @@ def roofline(prof, steps, peaks, workload=None):
     hbm = peaks.get("hbm_gbs")
     src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    dname, (dl, dms, dbytes, dflops) = max(prof.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms, dbytes, dflops, dpipe) = max(prof.items(), key=lambda kv: kv[1][1])
     kernels = {}
     for k, v in prof.items():
         e = {"launches": v[0], "ms_per_step": v[1] / steps,
              "GBps": v[2] / (v[1] / 1e3) / 1e9 if v[1] > 0 else None,
              "bytes_per_launch": v[2] / v[0]}
         if v[3] > 0:
-            e["fp64_TFLOPs"] = v[3] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None
+            key = "fp64_TFLOPs" if v[4] == 64 else "double_float_TFLOPs"
+            e[key] = v[3] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None
         kernels[k] = e
     traffic = _traffic(dname, workload)
     if dflops > 0:
         achieved = dflops / (dms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": dname, "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": traffic, "peak_source": "nominal FP64 (152 SMs x 2070 MHz x 4)"}
+        if dpipe == 64:
+            peak, src = FP64_PEAK_TFLOPS, "nominal FP64 (152 SMs x 2070 MHz x 4)"
+        else:
+            peak, src = DF_PEAK_TFLOPS, ("double-float on the FP32 pipe (152 SMs x 128 lanes x "
+                                         "2070 MHz / 15 instructions x 2)")
+        roof = {"bound": "alu", "kernel": dname, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": src}
     else:
         achieved = dbytes / (dms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,

@@ -240,13 +240,32 @@ rk_status rk_predict_static(rk_plan* plan, void* out_dev);
 
 /*
  * rk_predict_host -- the same prediction called with host buffers: copies
- * xy_host (n x 2 doubles) and c_host (B x n doubles) to the device, runs
- * rk_set_sites, rk_set_coef and rk_predict, and copies the B x ny x nx
- * result back into out_host (float or double per the plan precision).
- * Synchronises with the stream before returning.
+ * xy_host (n x 2 doubles) and c_host (B x n doubles) to the device, updates
+ * the sites and coefficients, predicts, and copies the B x ny x nx result
+ * back into out_host (float or double per the plan precision).  One
+ * synchronisation with the stream, at the end; host buffers may be pageable,
+ * pinned ones let the copies overlap.  RK_ERR_OBS_OUTSIDE (after the copies)
+ * when a site lies outside the extent: that site then carried no weight.
  */
 rk_status rk_predict_host(rk_plan* plan, int n, const double* xy_host, int B,
                           const double* c_host, void* out_host);
+
+/*
+ * rk_predict_host_group -- rk_predict_host for nplans plans at once (1 <=
+ * nplans <= 16, distinct, one precision, one torus): the copies in, the
+ * grouped site update (rk_set_sites_group), the coefficients, the grouped
+ * prediction (rk_predict_group) and the copies out, issued on plans[0]'s
+ * stream with one synchronisation at the end.
+ *   n[k], xy_host[k]   sites of plans[k] (host, n[k] x 2 doubles)
+ *   B[k], c_host[k]    its coefficients (host, B[k] x n[k] doubles)
+ *   out_host[k]        its result (host, B[k] x ny x nx, plan precision)
+ * Device buffers grow on first use.  RK_ERR_OBS_OUTSIDE when any plan saw a
+ * site outside its extent (its latch is cleared); the other errors as for
+ * rk_set_sites_group and rk_predict_group.
+ */
+rk_status rk_predict_host_group(rk_plan* const* plans, int nplans, const int* n,
+                                const double* const* xy_host, const int* B,
+                                const double* const* c_host, void* const* out_host);
 
 /*
  * rk_simulate -- conditional simulation (Section 1: unconditional draw, then
@@ -293,8 +312,9 @@ rk_status rk_debug_copy(rk_plan* plan, int what, void* dst_dev, size_t bytes);
  * (the bytes its inputs and outputs occupy, as stated in the library's design
  * notes) are recorded.  rk_profile_read synchronises the recorded events and
  * fills up to max entries (one per kernel name) with launches, total
- * milliseconds, total algorithmic bytes and, for passes bound by FP64
- * arithmetic, total algorithmic FP64 operations (adds and multiplies, a fused
+ * milliseconds, total algorithmic bytes and, for passes bound by arithmetic
+ * at FP64 precision (on the FP64 pipe, or in double-float on the FP32 pipe:
+ * the pipe field), total algorithmic operations (adds and multiplies, a fused
  * multiply-add counting two); it returns the number of entries.
  */
 typedef struct {
@@ -302,7 +322,8 @@ typedef struct {
   int launches;
   double total_ms;
   double bytes;
-  double flops;   /* algorithmic FP64 operations of FP64-bound passes, else 0 */
+  double flops;   /* algorithmic FP64-precision operations of arithmetic-bound passes, else 0 */
+  int pipe;       /* 0: memory-bound pass; 64: FP64 pipe; 2: double-float on the FP32 pipe */
 } rk_profile_entry;
 rk_status rk_profile_enable(int on);
 int rk_profile_read(rk_profile_entry* out, int max);

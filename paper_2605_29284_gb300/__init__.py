@@ -11,8 +11,8 @@ import torch
 
 from ._native import RK_FP32, RK_FP64, PlanInfo, RkError, check, lib, profile_enable, profile_read
 
-__all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "predict_group", "profile_enable",
-           "profile_read", "set_sites_group"]
+__all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "predict_group",
+           "predict_host_group", "profile_enable", "profile_read", "set_sites_group"]
 
 
 def _ptr(t):
@@ -134,12 +134,14 @@ class Plan:
         self._call("rk_predict", _ptr(out))
         return out
 
-    def predict_host(self, xy, c):
-        """Prediction from host (numpy) inputs to a host result (rk_predict_host)."""
+    def predict_host(self, xy, c, out=None):
+        """Prediction from host (numpy) inputs to a host result (rk_predict_host);
+        out (B x ny x nx, plan precision, e.g. a pinned buffer) is filled if given."""
         xy = np.ascontiguousarray(xy, dtype=np.float64)
         c = np.ascontiguousarray(np.atleast_2d(c), dtype=np.float64)
         npdt = np.float64 if self.precision == RK_FP64 else np.float32
-        out = np.empty((c.shape[0], self.ny, self.nx), dtype=npdt)
+        if out is None:
+            out = np.empty((c.shape[0], self.ny, self.nx), dtype=npdt)
         self._call("rk_predict_host", int(xy.shape[0]), xy.ctypes.data_as(ctypes.c_void_p),
                    int(c.shape[0]), c.ctypes.data_as(ctypes.c_void_p),
                    out.ctypes.data_as(ctypes.c_void_p))
@@ -212,3 +214,31 @@ def set_sites_group(plans, xys):
     for p, x in zip(plans, xys):
         p.n = int(x.shape[0])
         p._xy = x
+
+
+def predict_host_group(plans, xys, cs, outs=None):
+    """rk_predict_host_group: host sites and coefficients in, host grids out,
+    for several plans with one synchronisation.  xys[k] (n_k x 2) and cs[k]
+    (B_k x n_k) are numpy arrays (pinned memory lets the copies overlap);
+    outs[k] (B_k x ny x nx, plan precision) are filled (allocated if None)."""
+    plans = list(plans)
+    xys = [np.ascontiguousarray(x, dtype=np.float64) for x in xys]
+    cs = [np.ascontiguousarray(np.atleast_2d(c), dtype=np.float64) for c in cs]
+    if outs is None:
+        outs = [np.empty((c.shape[0], p.ny, p.nx),
+                         dtype=np.float64 if p.precision == RK_FP64 else np.float32)
+                for p, c in zip(plans, cs)]
+    k = len(plans)
+    vp = ctypes.c_void_p
+    harr = (vp * k)(*[p._h.value for p in plans])
+    narr = (ctypes.c_int * k)(*[int(x.shape[0]) for x in xys])
+    barr = (ctypes.c_int * k)(*[int(c.shape[0]) for c in cs])
+    xarr = (vp * k)(*[x.ctypes.data for x in xys])
+    carr = (vp * k)(*[c.ctypes.data for c in cs])
+    oarr = (vp * k)(*[o.ctypes.data for o in outs])
+    check(lib.rk_set_stream(plans[0]._h, _stream()), "rk_set_stream")
+    check(lib.rk_predict_host_group(harr, k, narr, xarr, barr, carr, oarr),
+          "rk_predict_host_group")
+    for p, x, c in zip(plans, xys, cs):
+        p.n, p.B = x.shape[0], c.shape[0]
+    return outs

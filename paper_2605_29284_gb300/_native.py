@@ -35,7 +35,7 @@ class PlanInfo(ctypes.Structure):
 class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int),
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double),
-                ("flops", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("pipe", ctypes.c_int)]
 
 
 def _load():
@@ -67,6 +67,8 @@ _SIGS = {
     "rk_predict_static": [_vp, _vp],
     "rk_predict_group": [ctypes.POINTER(_vp), _int, ctypes.POINTER(_vp)],
     "rk_set_sites_group": [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_vp)],
+    "rk_predict_host_group": [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_vp),
+                              ctypes.POINTER(_int), ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "rk_simulate": [_vp, _int, ctypes.c_ulonglong, _vp],
     "rk_predict_backward": [_vp, _vp, _vp, _vp, _vp],
     "rk_debug_copy": [_vp, _int, _vp, ctypes.c_size_t],
@@ -93,8 +95,10 @@ def profile_enable(on=True):
 
 
 def profile_read():
-    """{kernel: (launches, total_ms, algorithmic_bytes, fp64_flops)} since the last read."""
+    """{kernel: (launches, total_ms, algorithmic_bytes, flops, pipe)} since the last read
+    (pipe 0: memory-bound, 64: FP64, 2: double-float on the FP32 pipe)."""
     buf = (ProfileEntry * 64)()
     k = lib.rk_profile_read(buf, 64)
-    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes, buf[i].flops)
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes, buf[i].flops,
+                                   buf[i].pipe)
             for i in range(k)}

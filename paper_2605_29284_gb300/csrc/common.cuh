@@ -133,6 +133,8 @@ struct rk_plan {
   // Cholesky factor of M = K_xx + tau2 I (n x n lower, column-major), double
   double* mchol = nullptr;
   size_t mchol_cap = 0;
+  float2* mchol_df = nullptr;  // RK_FP32 plans: the factor as double-float pairs
+  size_t mchol_df_cap = 0;
   // scratch for prediction, sized for B_cap fields (and realisations)
   void* cstar = nullptr; size_t cstar_bytes = 0;     // B x p1y x p1x (plan precision)
   void* tbuf = nullptr; size_t tbuf_bytes = 0;       // B x H x ldt complex
@@ -141,6 +143,7 @@ struct rk_plan {
   int ldt = 0, ldu = 0;
   int* d_flag = nullptr;                             // device status flag
   int* d_sites_flag = nullptr;                       // latch of rk_set_sites_async
+  int* h_flag = nullptr;                             // pinned host copy of the latch
   // side stream for the FP64 block GEMM, which runs beside the FP32 row pass
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -170,7 +173,6 @@ struct rk_plan {
   bool have_adj = false;
   // device staging for rk_predict_host
   double* h_xy = nullptr; size_t h_xy_cap = 0;
-  double* h_c = nullptr; size_t h_c_cap = 0;
   void* h_out = nullptr; size_t h_out_cap = 0;
 };
 
@@ -316,7 +318,10 @@ cudaError_t launch_tile_sites(const int* box, int n, rk_plan* p, bool counted, c
 cudaError_t build_obs_cov(const double* xy, int n, const rk_plan* p, double* a, cudaStream_t s);
 cudaError_t chol_factor(double* a, int n, int* flag, cudaStream_t s);
 cudaError_t chol_mirror(double* a, int n, cudaStream_t s);
-cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s);
+// adf (double-float copy of the mirrored factor) selects double-float updates
+cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
+                       const float2* adf = nullptr);
+cudaError_t chol_split(const double* a, int n, float2* adf, cudaStream_t s);
 
 // conditional simulation
 template <typename T>

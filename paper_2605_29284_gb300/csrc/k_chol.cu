@@ -4,6 +4,7 @@
 // linear systems").  Column-major storage, a[j * n + i] = M(i, j); only the
 // lower triangle is used.  Right-looking blocked algorithm with 32 x 32 tiles.
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace rk {
 
@@ -231,7 +232,58 @@ __global__ void __launch_bounds__(SU) solve_update_kernel(const double* __restri
     if (f < nf) x[(size_t)(f0 + f) * n + r] -= acc[f];
 }
 
-cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s) {
+// The same update with the factor as double-float pairs (adf, written by
+// chol_split) and double-float accumulation on the FP32 pipe: ~48-bit
+// products and sums instead of FP64, for RK_FP32 plans, whose outputs need
+// far less (the diagonal substitutions stay FP64).
+template <bool FWD>
+__global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __restrict__ adf, int n,
+                                                             int k, double* x, int B) {
+  __shared__ float2 Xs[SB][SF];
+  const int nb = min(SB, n - k);
+  const int f0 = blockIdx.y * SF;
+  const int nf = min(SF, B - f0);
+  for (int t = threadIdx.x; t < SB * SF; t += blockDim.x) {
+    const int f = t / SB, c = t % SB;
+    const dfl v = df_make((c < nb && f < nf) ? x[(size_t)(f0 + f) * n + k + c] : 0.0);
+    Xs[c][f] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  const int r = (FWD ? k + nb : 0) + blockIdx.x * SU + threadIdx.x;
+  if (r >= (FWD ? n : k)) return;
+  dfl acc[SF];
+#pragma unroll
+  for (int f = 0; f < SF; ++f) acc[f] = {0.f, 0.f};
+  const float2* col = adf + (size_t)k * n + r;
+#pragma unroll 8
+  for (int c = 0; c < nb; ++c) {
+    const float2 l2 = __ldg(col + (size_t)c * n);
+    const dfl l = {l2.x, l2.y};
+#pragma unroll
+    for (int f = 0; f < SF; ++f) acc[f] = df_fma(l, {Xs[c][f].x, Xs[c][f].y}, acc[f]);
+  }
+#pragma unroll
+  for (int f = 0; f < SF; ++f)
+    if (f < nf) x[(size_t)(f0 + f) * n + r] -= df_double(acc[f]);
+}
+
+// adf = a as double-float pairs (the mirrored factor, both triangles)
+__global__ void chol_split_kernel(const double* __restrict__ a, size_t count,
+                                  float2* __restrict__ adf) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const dfl v = df_make(a[t]);
+    adf[t] = make_float2(v.hi, v.lo);
+  }
+}
+
+cudaError_t chol_split(const double* a, int n, float2* adf, cudaStream_t s) {
+  chol_split_kernel<<<2048, 256, 0, s>>>(a, (size_t)n * n, adf);
+  return cudaGetLastError();
+}
+
+cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
+                       const float2* adf) {
   if (n <= 0 || B <= 0) return cudaSuccess;
   const int dgrid = (B + 3) / 4;              // four warps (right-hand sides) per CTA
   const int fblocks = (B + SF - 1) / SF;
@@ -239,14 +291,20 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s)
     const int nb = n - k < SB ? n - k : SB;
     solve_diag_kernel<true><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     const int rest = n - k - nb;
-    if (rest > 0)
-      solve_update_kernel<true><<<dim3((rest + SU - 1) / SU, fblocks), SU, 0, s>>>(a, n, k, x, B);
+    if (rest > 0) {
+      const dim3 grid((rest + SU - 1) / SU, fblocks);
+      if (adf) solve_update_df_kernel<true><<<grid, SU, 0, s>>>(adf, n, k, x, B);
+      else solve_update_kernel<true><<<grid, SU, 0, s>>>(a, n, k, x, B);
+    }
   }
   const int last = ((n - 1) / SB) * SB;
   for (int k = last; k >= 0; k -= SB) {
     solve_diag_kernel<false><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
-    if (k > 0)
-      solve_update_kernel<false><<<dim3((k + SU - 1) / SU, fblocks), SU, 0, s>>>(a, n, k, x, B);
+    if (k > 0) {
+      const dim3 grid((k + SU - 1) / SU, fblocks);
+      if (adf) solve_update_df_kernel<false><<<grid, SU, 0, s>>>(adf, n, k, x, B);
+      else solve_update_kernel<false><<<grid, SU, 0, s>>>(a, n, k, x, B);
+    }
   }
   return cudaGetLastError();
 }

@@ -145,6 +145,7 @@ struct ProfRec {
   const char* name;
   cudaEvent_t a, b;
   double bytes, flops;
+  int pipe;
 };
 bool g_prof_on = false;
 std::vector<ProfRec> g_prof;
@@ -153,12 +154,13 @@ struct ProfScope {
   ProfRec rec;
   cudaStream_t s;
   bool on;
-  ProfScope(const char* name, double bytes, double flops, cudaStream_t st)
+  ProfScope(const char* name, double bytes, double flops, int pipe, cudaStream_t st)
       : s(st), on(g_prof_on) {
     if (!on) return;
     rec.name = name;
     rec.bytes = bytes;
     rec.flops = flops;
+    rec.pipe = pipe;
     cudaEventCreate(&rec.a);
     cudaEventCreate(&rec.b);
     cudaEventRecord(rec.a, s);
@@ -171,10 +173,13 @@ struct ProfScope {
 };
 // RK_PROF: a memory-bound pass (algorithmic bytes); RK_PROF64: an FP64-bound
 // pass, also with its algorithmic FP64 operations (one per add or multiply,
-// two per fused multiply-add, none for the exponentials and square roots)
-#define RK_PROF(name, bytes) ProfScope prof_scope_##__LINE__(name, (double)(bytes), 0.0, s)
+// two per fused multiply-add, none for the exponentials and square roots);
+// RK_PROFDF: the same operations carried out in double-float on the FP32 pipe
+#define RK_PROF(name, bytes) ProfScope prof_scope_##__LINE__(name, (double)(bytes), 0.0, 0, s)
 #define RK_PROF64(name, bytes, flops) \
-  ProfScope prof_scope_##__LINE__(name, (double)(bytes), (double)(flops), s)
+  ProfScope prof_scope_##__LINE__(name, (double)(bytes), (double)(flops), 64, s)
+#define RK_PROFDF(name, bytes, flops) \
+  ProfScope prof_scope_##__LINE__(name, (double)(bytes), (double)(flops), 2, s)
 
 rk_status read_flag(rk_plan* p, int* value) {
   RK_CU(cudaMemcpyAsync(value, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
@@ -290,12 +295,14 @@ void free_plan(rk_plan* p) {
                   p->dlam32, p->kn_chol, p->kn_dlog, p->box, p->w64, p->w32, p->ssd, p->efac,
                   p->c64, p->z64, p->mchol, p->cstar, p->tbuf, p->ubuf, p->blk,
                   p->d_flag, p->tw64qx, p->tw64qy, p->tw32qx, p->tw32qy, p->ce_sqrt64,
-                  p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_c, p->h_out, p->xy, p->wd64,
+                  p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_out, p->xy, p->wd64,
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
                   p->efac_g, p->gblk, p->bw_dk, p->tile_start,
-                  p->tile_count, p->tile_cursor, p->site_order};
+                  p->tile_count, p->tile_cursor, p->site_order,
+                  p->mchol_df};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (p->h_flag) cudaFreeHost(p->h_flag);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->ev_wfork) cudaEventDestroy(p->ev_wfork);
@@ -576,6 +583,7 @@ constexpr int kCsSolve = 512;    // right-hand sides per FP64 solve
 template <typename T>
 rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
   cudaStream_t s = p->stream;
+  const float2* sdf = sizeof(T) == sizeof(float) ? p->mchol_df : nullptr;
   const int n = p->n;
   const long long total = (long long)p->B * R;
   const int G = total < kCsChunk ? (int)total : kCsChunk;
@@ -627,7 +635,11 @@ rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
                                     rhs + (size_t)(g0 - s0) * n, s));
       }
     }
-    {
+    if (sdf) {   // double-float updates on the FP32 pipe
+      RK_PROFDF("chol_solve", (double)sn * n * 16.0 + (double)n * (double)n * 8.0,
+                2.0 * n * (double)n * sn);
+      RK_CU(chol_solve(p->mchol, n, rhs, sn, s, sdf));
+    } else {
       RK_PROF64("chol_solve", (double)sn * n * 16.0 + (double)n * (double)n * 8.0,
                 2.0 * n * (double)n * sn);
       RK_CU(chol_solve(p->mchol, n, rhs, sn, s));
@@ -674,6 +686,7 @@ rk_status ensure_adjoint(rk_plan* p) {
 template <typename T>
 rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, double* gs2) {
   cudaStream_t s = p->stream;
+  const float2* sdf = sizeof(T) == sizeof(float) ? p->mchol_df : nullptr;
   const int B = p->B, n = p->n;
   const bool f32 = sizeof(T) == sizeof(float);
   const size_t plane = (size_t)p->p1y * p->p1x;
@@ -751,7 +764,11 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     RK_CU(launch_matvec_dkxx(p->xy, n, p->c64, B, p->rho, p->sigma2, p->nu_code, p->bw_dk, c3,
                              s));
   }
-  {
+  if (sdf) {   // double-float updates on the FP32 pipe
+    RK_PROFDF("adj_solve", (double)n * n * 8.0 + (double)nsets * B * n * 16.0,
+              2.0 * n * (double)n * nsets * B);
+    RK_CU(chol_solve(p->mchol, n, cbar, nsets * B, s, sdf));
+  } else {
     RK_PROF64("adj_solve", (double)n * n * 8.0 + (double)nsets * B * n * 16.0,
               2.0 * n * (double)n * nsets * B);
     RK_CU(chol_solve(p->mchol, n, cbar, nsets * B, s));
@@ -850,6 +867,11 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
   do {
     if ((st = dalloc(&p->d_flag, 1)) != RK_OK) break;
     if ((st = dalloc(&p->d_sites_flag, 1)) != RK_OK) break;
+    if (cudaMallocHost((void**)&p->h_flag, sizeof(int)) != cudaSuccess) {
+      p->h_flag = nullptr;
+      st = RK_ERR_OOM;
+      break;
+    }
     p->tiles_x = (p->p1x + 31) / 32;
     p->tiles_y = (p->p1y + 31) / 32;
     if ((st = dalloc(&p->tile_start, (size_t)p->tiles_x * p->tiles_y + 1)) != RK_OK) break;
@@ -917,6 +939,7 @@ int rk_profile_read(rk_profile_entry* out, int max) {
     out[k].total_ms += ms;
     out[k].bytes += r.bytes;
     out[k].flops += r.flops;
+    out[k].pipe = r.pipe;
   }
   g_prof.clear();
   return count;
@@ -1130,6 +1153,13 @@ rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
     RK_CU(build_obs_cov(p->xy, n, p, p->mchol, p->stream));
     RK_CU(chol_factor(p->mchol, n, p->d_flag, p->stream));
     RK_CU(chol_mirror(p->mchol, n, p->stream));
+    if (p->precision == RK_FP32) {
+      if (p->mchol_df_cap < (size_t)n * n) {
+        RK_TRY(dalloc(&p->mchol_df, (size_t)n * n));
+        p->mchol_df_cap = (size_t)n * n;
+      }
+      RK_CU(chol_split(p->mchol, n, p->mchol_df, p->stream));
+    }
     int flag = 0;
     RK_TRY(read_flag(p, &flag));
     if (flag) return RK_ERR_NOT_PD;
@@ -1139,7 +1169,8 @@ rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
                         p->stream));
   RK_CU(cudaMemcpyAsync(p->c64, z, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice,
                         p->stream));
-  RK_CU(chol_solve(p->mchol, n, p->c64, B, p->stream));
+  RK_CU(chol_solve(p->mchol, n, p->c64, B, p->stream,
+                   p->precision == RK_FP32 ? p->mchol_df : nullptr));
   RK_TRY(finish_coef(p, B));
   RK_CU(cudaStreamSynchronize(p->stream));
   return RK_OK;
@@ -1187,33 +1218,80 @@ rk_status rk_predict_group(rk_plan* const* plans, int nplans, void* const* outs)
   return predict_group_impl<float>(plans, nplans, outs);
 }
 
+rk_status rk_predict_host_group(rk_plan* const* plans, int nplans, const int* n,
+                                const double* const* xy_host, const int* B,
+                                const double* const* c_host, void* const* out_host) {
+  if (!plans || !n || !xy_host || !B || !c_host || !out_host || nplans < 1 ||
+      nplans > kMaxGroup || !plans[0])
+    return RK_ERR_INVALID_ARG;
+  for (int k = 0; k < nplans; ++k) {
+    if (!plans[k] || n[k] < 1 || B[k] < 1 || !xy_host[k] || !c_host[k] || !out_host[k])
+      return RK_ERR_INVALID_ARG;
+    if (plans[k]->precision != plans[0]->precision) return RK_ERR_INVALID_ARG;
+    for (int j = 0; j < k; ++j)
+      if (plans[j] == plans[k]) return RK_ERR_INVALID_ARG;
+  }
+  rk_plan* p0 = plans[0];
+  cudaStream_t s = p0->stream;
+  const double* xy_dev[kMaxGroup];
+  void* out_dev[kMaxGroup];
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    // capacities first (the only allocations, on growth)
+    if (n[k] > p->n_cap) {
+      RK_TRY(ensure_sites(p, n[k]));
+      p->n = 0;
+    }
+    if (p->h_xy_cap < (size_t)2 * n[k]) {
+      RK_TRY(dalloc(&p->h_xy, (size_t)2 * n[k]));
+      p->h_xy_cap = (size_t)2 * n[k];
+    }
+    const size_t esz = p->precision == RK_FP64 ? sizeof(double) : sizeof(float);
+    const size_t out_bytes = (size_t)B[k] * p->ny * p->nx * esz;
+    if (p->h_out_cap < out_bytes) {
+      RK_TRY(dalloc_bytes(&p->h_out, out_bytes));
+      p->h_out_cap = out_bytes;
+    }
+    RK_CU(cudaMemcpyAsync(p->h_xy, xy_host[k], (size_t)2 * n[k] * sizeof(double),
+                          cudaMemcpyHostToDevice, s));
+    xy_dev[k] = p->h_xy;
+    out_dev[k] = p->h_out;
+  }
+  RK_TRY(rk_set_sites_group(plans, nplans, n, xy_dev));
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    RK_TRY(ensure_coef(p, B[k]));
+    RK_CU(cudaMemcpyAsync(p->c64, c_host[k], (size_t)B[k] * n[k] * sizeof(double),
+                          cudaMemcpyHostToDevice, s));
+    RK_TRY(finish_coef(p, B[k]));
+  }
+  RK_TRY(rk_predict_group(plans, nplans, out_dev));
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    const size_t esz = p->precision == RK_FP64 ? sizeof(double) : sizeof(float);
+    RK_CU(cudaMemcpyAsync(out_host[k], p->h_out, (size_t)B[k] * p->ny * p->nx * esz,
+                          cudaMemcpyDeviceToHost, s));
+    RK_CU(cudaMemcpyAsync(p->h_flag, p->d_sites_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
+  RK_CU(cudaStreamSynchronize(s));   // the one synchronisation of the call
+  bool outside = false;
+  for (int k = 0; k < nplans; ++k) {
+    if (*plans[k]->h_flag & 2) {
+      outside = true;
+      RK_CU(cudaMemsetAsync(plans[k]->d_sites_flag, 0, sizeof(int), s));
+    }
+  }
+  return outside ? RK_ERR_OBS_OUTSIDE : RK_OK;
+}
+
 rk_status rk_predict_host(rk_plan* p, int n, const double* xy_host, int B, const double* c_host,
                           void* out_host) {
-  if (!p || n < 1 || B < 1 || !xy_host || !c_host || !out_host) return RK_ERR_INVALID_ARG;
-  const size_t esz = p->precision == RK_FP64 ? sizeof(double) : sizeof(float);
-  const size_t out_bytes = (size_t)B * p->ny * p->nx * esz;
-  if (p->h_xy_cap < (size_t)2 * n) {
-    RK_TRY(dalloc(&p->h_xy, (size_t)2 * n));
-    p->h_xy_cap = (size_t)2 * n;
-  }
-  if (p->h_c_cap < (size_t)B * n) {
-    RK_TRY(dalloc(&p->h_c, (size_t)B * n));
-    p->h_c_cap = (size_t)B * n;
-  }
-  if (p->h_out_cap < out_bytes) {
-    RK_TRY(dalloc_bytes(&p->h_out, out_bytes));
-    p->h_out_cap = out_bytes;
-  }
-  RK_CU(cudaMemcpyAsync(p->h_xy, xy_host, (size_t)2 * n * sizeof(double), cudaMemcpyHostToDevice,
-                        p->stream));
-  RK_CU(cudaMemcpyAsync(p->h_c, c_host, (size_t)B * n * sizeof(double), cudaMemcpyHostToDevice,
-                        p->stream));
-  RK_TRY(rk_set_sites(p, n, p->h_xy));
-  RK_TRY(rk_set_coef(p, B, p->h_c));
-  RK_TRY(rk_predict(p, p->h_out));
-  RK_CU(cudaMemcpyAsync(out_host, p->h_out, out_bytes, cudaMemcpyDeviceToHost, p->stream));
-  RK_CU(cudaStreamSynchronize(p->stream));
-  return RK_OK;
+  if (!p) return RK_ERR_INVALID_ARG;
+  rk_plan* plans[1] = {p};
+  const double* xy[1] = {xy_host};
+  const double* c[1] = {c_host};
+  void* out[1] = {out_host};
+  return rk_predict_host_group(plans, 1, &n, xy, &B, c, out);
 }
 
 rk_status rk_debug_copy(rk_plan* p, int what, void* dst, size_t bytes) {

@@ -126,3 +126,31 @@ def test_grouped_site_updates_equal_single_updates(rk):
     finally:
         for p in plans:
             p.close()
+
+
+def test_host_group_equals_device_group(rk):
+    # rk_predict_host_group (host buffers in and out, one synchronisation)
+    # against the device-side grouped calls; and the single-plan host call
+    ext = (0.0, 1.6, 0.0, 1.0)
+    cells = [(1.5, 1), (1.5, 3), (2.5, 2)]
+    plans, coefs = _plans(rk, 350, ext, cells, "fp32", n=700, B=2)
+    try:
+        dev = [p.predict().double().cpu().numpy() for p in plans]
+        xys = [xy for xy, _, _, _ in coefs]
+        cs = [np.atleast_2d(c) for _, c, _, _ in coefs]
+        outs = rk.predict_host_group(plans, xys, cs)
+        for o, d in zip(outs, dev):
+            assert o.shape == (2, 350, 350)
+            assert rel_err(o.astype(np.float64), d) <= 1e-6
+        one = plans[1].predict_host(xys[1], cs[1])
+        assert rel_err(one.astype(np.float64), dev[1]) <= 1e-6
+        bad = xys[2].copy()
+        bad[0] = (-0.5, 0.5)
+        with pytest.raises(rk.RkError) as e:
+            rk.predict_host_group(plans, xys[:2] + [bad], cs)
+        assert e.value.name == "RK_ERR_OBS_OUTSIDE"
+        outs = rk.predict_host_group(plans, xys, cs)      # the latch was cleared
+        assert rel_err(outs[0].astype(np.float64), dev[0]) <= 1e-6
+    finally:
+        for p in plans:
+            p.close()
