@@ -105,6 +105,7 @@ struct rk_plan {
   double* dlam64 = nullptr; float* dlam32 = nullptr;   // d lambda / d log rho (adjoint)
   // neighbourhood covariance factor (M x M lower Cholesky, double)
   double* kn_chol = nullptr;
+  float2* kn_df = nullptr;     // RK_FP32: kn_chol / sigma as float pairs (M x M), then sigma / L_qq
   double* kn_dlog = nullptr;   // d K_N / d log rho (adjoint)
   // exact low-frequency block (FP32 plans)
   int blk_kx = -1, blk_ky = -1, nblk = 0;
@@ -116,7 +117,10 @@ struct rk_plan {
   double* w64 = nullptr;       // n x M
   float* w32 = nullptr;        // n x M
   double* ssd = nullptr;       // n: sqrt(max(0, sigma2 - k_i^T W_i)) (CS)
-  double2* efac = nullptr;     // n x nblk Fourier factors of A_i on the block
+  float2* wdf = nullptr;       // RK_FP32: n x M, the weights as double-float pairs
+  double2* efac = nullptr;     // RK_FP32: n x nblk Fourier factors of A_i on the block
+  float4* twdfx = nullptr;     // RK_FP32: the px and py twiddles as double-float pairs
+  float4* twdfy = nullptr;     //   (re.hi, re.lo, im.hi, im.lo)
   // sites ordered by the 32 x 32 tile of the padded grid holding their box
   // corner (the tiled scatter): tile_start[tiles + 1], site_order[n]; built
   // only for n >= kTileSortMin (fewer sites scatter with global atomics)
@@ -246,14 +250,17 @@ struct RowsInvSlot {
   int ldu, nrows, old, ocol0, ncols, ald, ar0, ac0, B;
 };
 struct WeightsSlot {
-  const double* xy; const double* kn;
-  int* box; double* w64; float* w32; double* ssd; int* flag; int* tcount;
-  int n, nx, ny, ntx, nu_code, L;
+  const double* xy; const double* kn; const float2* kn_df;
+  int* box; double* w64; float* w32; float2* wdf; double* ssd; int* flag; int* tcount;
+  int n, nx, ny, ntx, nu_code, L, dfw;   // dfw: double-float variant (RK_FP32 plans)
   double x0, x1, y0, y1, hx, hy, rho, sigma2;
+  double hxr, hyr, sigma;                // hx / rho, hy / rho, sqrt(sigma2)
+  float2 hxr_df, hyr_df;                 // hx / rho, hy / rho as float pairs
 };
 WeightsSlot weights_slot(const double* xy, int n, const rk_plan* p, int* box, double* w64,
                          float* w32, double* ssd, int* flag);
 cudaError_t launch_weights_group(Group<WeightsSlot>& g, cudaStream_t s);
+cudaError_t launch_kn_split(const double* kn, int M, double sigma2, float2* out, cudaStream_t s);
 struct BlockFactorSlot {
   const int* box; const double* w64; const double2* twx; const double2* twy; double2* efac;
   int n, L, px, py, KX, KY, NS;
@@ -261,6 +268,14 @@ struct BlockFactorSlot {
 BlockFactorSlot block_factor_slot(const int* box, const double* w64, int n, const rk_plan* p,
                                   int kx, int ky, double2* efac);
 cudaError_t launch_block_factors_group(Group<BlockFactorSlot>& g, cudaStream_t s);
+// the forward block of RK_FP32 plans, in double-float
+struct BlockFactorDfSlot {
+  const int* box; const float2* wdf; const float4* twx; const float4* twy; double2* efac;
+  int n, L, px, py, KX, KY, NS;
+};
+BlockFactorDfSlot block_factor_df_slot(const rk_plan* p, int n);
+cudaError_t launch_block_factors_df_group(Group<BlockFactorDfSlot>& g, cudaStream_t s);
+cudaError_t launch_block_factors_df(const rk_plan* p, int n, cudaStream_t s);
 struct BlockGemmSlot {
   const double* c; const double2* efac; double2* blk;
   int n, B, nblk;

@@ -53,6 +53,58 @@ __device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) {
 
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
 
+// a * b
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, pe));
+  return fast_two_sum(p, pe);
+}
+
+// sqrt(a) for a >= 0: the rounded single-precision root s, then one Newton
+// step s + (a - s^2) / (2 s) with a - s^2 formed exactly (s^2 = p + pe by the
+// FMA product error; a.hi - p is exact by Sterbenz's lemma).
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+  if (!(a.hi > 0.f)) return {0.f, 0.f};
+  const float s = __fsqrt_rn(a.hi);
+  const float p = __fmul_rn(s, s);
+  const float pe = __fmaf_rn(s, s, -p);
+  const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
+  return fast_two_sum(s, __fmul_rn(res, __fdividef(0.5f, s)));
+}
+
+// e^{-d} for d >= 0 (0 beyond d = 80, below 2^-115): Cody and Waite's
+// reduction d = k ln 2 + r, |r| <= ln(2) / 2 + rounding, so e^{-d} = 2^{-k}
+// e^{-r}, and the Taylor series of e^{-r} to degree 12 (remainder below
+// 0.35^13 / 13! < 2e-16) by Horner's rule: degrees 8-12, which stay below
+// 6e-9, in single precision, degrees 0-7 in double-float.  The error stays
+// within a few 1e-15 absolute (ln 2 held to about 2^-48 gives a relative
+// error growing like 2^-48 k, on a value below 2^-k).
+__device__ __forceinline__ dfl df_exp_neg(dfl d) {
+  if (!(d.hi <= 80.f)) return {0.f, 0.f};
+  constexpr double kLn2 = 0.69314718055994530942;
+  constexpr float kLn2Hi = (float)kLn2;
+  constexpr float kLn2Lo = (float)(kLn2 - (double)kLn2Hi);
+  const float k = rintf(d.hi * 1.44269504f);
+  const dfl r = df_fma({-k, 0.f}, {kLn2Hi, kLn2Lo}, d);
+  const dfl nr = df_neg(r);
+  float t = (float)(1.0 / 479001600.0);                        // 1 / 12!
+  t = __fmaf_rn(t, nr.hi, (float)(1.0 / 39916800.0));
+  t = __fmaf_rn(t, nr.hi, (float)(1.0 / 3628800.0));
+  t = __fmaf_rn(t, nr.hi, (float)(1.0 / 362880.0));
+  t = __fmaf_rn(t, nr.hi, (float)(1.0 / 40320.0));               // 1 / 8!
+  constexpr double c[8] = {1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720,
+                           1.0 / 5040};
+  dfl e = {t, 0.f};
+#pragma unroll
+  for (int j = 7; j >= 0; --j) {
+    const float ch = (float)c[j];
+    e = df_fma(e, nr, {ch, (float)(c[j] - (double)ch)});
+  }
+  const float sc = __int_as_float((127 - (int)k) << 23);         // 2^{-k}, k in [0, 116]
+  return {e.hi * sc, e.lo * sc};
+}
+
 // complex double-float: (re.hi, re.lo, im.hi, im.lo) in a float4
 __device__ __forceinline__ float4 cdf_pack(dfl re, dfl im) {
   return make_float4(re.hi, re.lo, im.hi, im.lo);

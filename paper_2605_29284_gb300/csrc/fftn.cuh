@@ -82,7 +82,9 @@ struct Radix23 {
   static constexpr int THR = (A >= 3) ? N / 8 : N / maxr();
 };
 
-template <typename T, int N, int THR, int R, int NS, int DIR>
+// TWS_SH: the twiddle table is in shared memory (plain loads) rather than
+// global memory (read-only loads).
+template <typename T, int N, int THR, int R, int NS, int DIR, bool TW_SH>
 __device__ __forceinline__ void stage_n(C<T>* __restrict__ buf, const C<T>* __restrict__ tw,
                                         int tid) {
   constexpr int NB = N / R;
@@ -101,7 +103,7 @@ __device__ __forceinline__ void stage_n(C<T>* __restrict__ buf, const C<T>* __re
         const int k = j % NS;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const C<T> w = __ldg(tw + r * k * TWS);
+          const C<T> w = TW_SH ? tw[r * k * TWS] : __ldg(tw + r * k * TWS);
           const C<T> x = buf[j + r * NB];
           a[it][r] = DIR > 0 ? cmul<T>(x, w) : cmulc<T>(x, w);
         }
@@ -123,21 +125,22 @@ __device__ __forceinline__ void stage_n(C<T>* __restrict__ buf, const C<T>* __re
   __syncthreads();
 }
 
-template <typename T, int N, int THR, int S, int DIR>
+template <typename T, int N, int THR, int S, int DIR, bool TW_SH>
 __device__ __forceinline__ void fft_stages(C<T>* buf, const C<T>* tw, int tid) {
   using P = Radix23<N>;
   if constexpr (S < P::S) {
-    stage_n<T, N, THR, P::radix(S), P::span(S), DIR>(buf, tw, tid);
-    fft_stages<T, N, THR, S + 1, DIR>(buf, tw, tid);
+    stage_n<T, N, THR, P::radix(S), P::span(S), DIR, TW_SH>(buf, tw, tid);
+    fft_stages<T, N, THR, S + 1, DIR, TW_SH>(buf, tw, tid);
   }
 }
 
 // In-place transform of one length-N vector by THR threads (tid in [0, THR)),
 // forward for DIR = +1 (exp(-2 pi i jk / N)), unnormalised inverse for -1.
-// All threads of the CTA must call it (it synchronises the CTA).
-template <typename T, int N, int DIR>
+// All threads of the CTA must call it (it synchronises the CTA).  TW_SH: tw
+// points to a copy of the table in shared memory.
+template <typename T, int N, int DIR, bool TW_SH = false>
 __device__ __forceinline__ void fft_n(C<T>* buf, const C<T>* tw, int tid) {
-  fft_stages<T, N, Radix23<N>::THR, 0, DIR>(buf, tw, tid);
+  fft_stages<T, N, Radix23<N>::THR, 0, DIR, TW_SH>(buf, tw, tid);
 }
 
 }  // namespace rk

@@ -267,6 +267,53 @@ __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __res
     if (f < nf) x[(size_t)(f0 + f) * n + r] -= df_double(acc[f]);
 }
 
+// The diagonal-block substitution in double-float (RK_FP32 plans): the same
+// lane layout as solve_diag_kernel, FP32 instructions instead of FP64 ones on
+// the sequential chain of the block.
+__device__ __forceinline__ dfl shfl_df(dfl v, int src) {
+  return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+template <bool FWD>
+__global__ void solve_diag_df_kernel(const float2* __restrict__ adf, const double* __restrict__ a,
+                                     int n, int k, double* x, int B) {
+  __shared__ float2 Ls[SB * SB];            // Ls[c * SB + r] = adf[(k + c) n + k + r]
+  __shared__ float2 rd[SB];                 // 1 / L(k + c, k + c) as a pair
+  const int nb = min(SB, n - k);
+#pragma unroll 8
+  for (int t = threadIdx.x; t < nb * SB; t += blockDim.x) {
+    const int c = t / SB, r = t % SB;
+    Ls[t] = r < nb ? adf[(size_t)(k + c) * n + k + r] : make_float2(0.f, 0.f);
+  }
+  if (threadIdx.x < nb) {
+    const dfl v = df_make(1.0 / a[(size_t)(k + threadIdx.x) * n + k + threadIdx.x]);
+    rd[threadIdx.x] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (f >= B) return;
+  double* xf = x + (size_t)f * n + k;
+  dfl v0 = df_make(lane < nb ? xf[lane] : 0.0);
+  dfl v1 = df_make(lane + 32 < nb ? xf[lane + 32] : 0.0);
+  const dfl zero = {0.f, 0.f};
+  for (int step = 0; step < nb; ++step) {
+    const int c = FWD ? step : nb - 1 - step;
+    const float2* col = Ls + c * SB;
+    const dfl l0 = {col[lane].x, col[lane].y};
+    const dfl l1 = {col[lane + 32].x, col[lane + 32].y};
+    const dfl own = shfl_df(c < 32 ? v0 : v1, c & 31);
+    const dfl xc = df_fma(own, {rd[c].x, rd[c].y}, zero);
+    if (lane == (c & 31)) {
+      if (c < 32) v0 = xc; else v1 = xc;
+    }
+    if (FWD ? (lane > c) : (lane < c)) v0 = df_fma(df_neg(l0), xc, v0);
+    if (FWD ? (lane + 32 > c) : (lane + 32 < c)) v1 = df_fma(df_neg(l1), xc, v1);
+  }
+  if (lane < nb) xf[lane] = df_double(v0);
+  if (lane + 32 < nb) xf[lane + 32] = df_double(v1);
+}
+
 // adf = a as double-float pairs (the mirrored factor, both triangles)
 __global__ void chol_split_kernel(const double* __restrict__ a, size_t count,
                                   float2* __restrict__ adf) {
@@ -289,7 +336,8 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
   const int fblocks = (B + SF - 1) / SF;
   for (int k = 0; k < n; k += SB) {
     const int nb = n - k < SB ? n - k : SB;
-    solve_diag_kernel<true><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
+    if (adf) solve_diag_df_kernel<true><<<dgrid, 128, 0, s>>>(adf, a, n, k, x, B);
+    else solve_diag_kernel<true><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     const int rest = n - k - nb;
     if (rest > 0) {
       const dim3 grid((rest + SU - 1) / SU, fblocks);
@@ -299,7 +347,8 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
   }
   const int last = ((n - 1) / SB) * SB;
   for (int k = last; k >= 0; k -= SB) {
-    solve_diag_kernel<false><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
+    if (adf) solve_diag_df_kernel<false><<<dgrid, 128, 0, s>>>(adf, a, n, k, x, B);
+    else solve_diag_kernel<false><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     if (k > 0) {
       const dim3 grid((k + SU - 1) / SU, fblocks);
       if (adf) solve_update_df_kernel<false><<<grid, SU, 0, s>>>(adf, n, k, x, B);

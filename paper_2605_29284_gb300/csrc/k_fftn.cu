@@ -22,6 +22,38 @@ template <int N> struct ColVecs {
   static constexpr int min_blocks = threads <= 320 ? 3 : 2;
 };
 
+// Shared memory of the column pass: the working columns, the lambda columns,
+// then while two CTAs still fit an SM (113 KB each): a copy of the twiddle
+// table, and a second set of column buffers (the next field's columns land
+// while the current ones are transformed).
+template <typename T, int N> struct ColBuffers {
+  static constexpr size_t kFit = 113 * 1024;
+  static constexpr size_t cols = sizeof(C<T>) * ColVecs<N>::value * N;
+  static constexpr size_t lams = sizeof(T) * ColVecs<N>::value * N;
+  static constexpr size_t table = sizeof(C<T>) * N;
+  static constexpr bool tw_sh = cols + lams + table <= kFit;
+  static constexpr int value = cols * 2 + lams + (tw_sh ? table : 0) <= kFit ? 2 : 1;
+  static constexpr size_t bytes = cols * value + lams + (tw_sh ? table : 0);
+};
+
+// Asynchronous global -> shared copy of one element (cp.async; 4, 8 or 16
+// bytes, both addresses aligned to that size); zero fill when !ok, reading
+// nothing from src.
+template <typename E>
+__device__ __forceinline__ void cp_async_zfill(E* dst, const E* src, bool ok) {
+  static_assert(sizeof(E) == 4 || sizeof(E) == 8 || sizeof(E) == 16, "cp.async size");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src),
+               "n"((int)sizeof(E)), "r"(ok ? (int)sizeof(E) : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // slot of grid unit u (uniform per CTA)
 template <typename G>
 __device__ __forceinline__ int slot_of(const G& g, int u) {
@@ -90,40 +122,50 @@ cols_n(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
   const long long tfs = sl.tfs, ufs = sl.ufs;
   const int ldt = sl.ldt, nrin = sl.nrin, ldu = sl.ldu, orow0 = sl.orow0, nrout = sl.nrout;
   const int blk_kx = sl.blk_kx, blk_ky = sl.blk_ky, nblk = sl.nblk, B = sl.B;
+  // shared memory: the working columns, the next field's columns (when two
+  // CTAs still fit an SM with both; ColBuffers) and the lambda columns
+  constexpr int NBUF = ColBuffers<T, N>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool TW_SH = ColBuffers<T, N>::tw_sh;
   C<T>* bufs = reinterpret_cast<C<T>*>(smem_raw);
-  T* lcols = reinterpret_cast<T*>(bufs + V * N);
+  C<T>* tws = bufs + NBUF * V * N;                         // N twiddles when TW_SH
+  T* lcols = reinterpret_cast<T*>(tws + (TW_SH ? N : 0));
+  const C<T>* twf = TW_SH ? tws : tw;
   const int v = threadIdx.x / THR, tid = threadIdx.x - v * THR;
   const int k = blockIdx.x * V + v;           // this group's column
   const bool kvalid = k < H;
-  C<T>* buf = bufs + v * N;
   T* lcol = lcols + v * N;
-  if (mode != COLS_FWD_ONLY && kvalid)
-    for (int n = tid; n < N; n += THR) lcol[n] = lam[(size_t)k * N + n];
   const bool use_blk = blk != nullptr && kvalid && k <= blk_kx;
   const int bw = 2 * blk_ky + 1;
-  // software pipeline over this CTA's fields: the next field's column is
-  // loaded into registers while the current one is transformed
-  constexpr int PER = (N + THR - 1) / THR;
-  C<T> nxt[PER];
-  auto load_col = [&](int f) {
-    const C<T>* src = tin + (size_t)f * tfs + (size_t)k * ldt;
-#pragma unroll
-    for (int e = 0; e < PER; ++e) {
-      const int n = tid + e * THR;
-      nxt[e] = (kvalid && n < nrin) ? src[n] : mk<T>(T(0), T(0));
+  // a field's column goes to shared memory by asynchronous copies (zero
+  // filled below nrin), issued a field ahead when there are two buffers
+  auto issue_col = [&](int f, C<T>* dstb) {
+    const C<T>* src = tin + (size_t)f * tfs + (size_t)(kvalid ? k : 0) * ldt;
+    for (int n = tid; n < N; n += THR) {
+      const bool ok = kvalid && n < nrin;
+      cp_async_zfill(dstb + n, ok ? src + n : src, ok);
     }
   };
-  if (fg0 < B) load_col(fg0);
-  for (int f = fg0; f < B; f += ng) {
-#pragma unroll
-    for (int e = 0; e < PER; ++e) {
-      const int n = tid + e * THR;
-      if (n < N) buf[n] = nxt[e];
-    }
+  if (mode != COLS_FWD_ONLY && kvalid) {
+    const T* lsrc = lam + (size_t)k * N;
+    for (int n = tid; n < N; n += THR) cp_async_zfill(lcol + n, lsrc + n, true);
+  }
+  if constexpr (TW_SH)
+    for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async_zfill(tws + n, tw + n, true);
+  if (fg0 < B) issue_col(fg0, bufs + v * N);
+  cp_async_commit();
+  int it = 0;
+  for (int f = fg0; f < B; f += ng, ++it) {
+    C<T>* buf = bufs + ((NBUF == 2 ? (it & 1) : 0) * V + v) * N;
+    cp_async_wait_all();
     __syncthreads();
-    if (f + ng < B) load_col(f + ng);
-    fft_n<T, N, +1>(buf, tw, tid);
+    if (f + ng < B) {
+      if constexpr (NBUF == 2) {
+        issue_col(f + ng, bufs + ((1 - (it & 1)) * V + v) * N);
+        cp_async_commit();
+      }
+    }
+    fft_n<T, N, +1, TW_SH>(buf, twf, tid);
     C<T>* dst = uout + (size_t)f * ufs + (size_t)k * ldu;
     if (mode == COLS_FWD_ONLY) {
       if (kvalid)
@@ -133,6 +175,10 @@ cols_n(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
           dst[n] = buf[r];
         }
       __syncthreads();
+      if constexpr (NBUF == 1) {
+        if (f + ng < B) issue_col(f + ng, buf);
+        cp_async_commit();
+      }
       continue;
     }
     if (mode == COLS_CONV) {
@@ -164,7 +210,7 @@ cols_n(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
       }
     }
     __syncthreads();
-    fft_n<T, N, -1>(buf, tw, tid);
+    fft_n<T, N, -1, TW_SH>(buf, twf, tid);
     if (kvalid)
       for (int n = tid; n < nrout; n += THR) {
         int r = orow0 + n;
@@ -172,6 +218,10 @@ cols_n(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
         dst[n] = buf[r];
       }
     __syncthreads();
+    if constexpr (NBUF == 1) {
+      if (f + ng < B) issue_col(f + ng, buf);
+      cp_async_commit();
+    }
   }
 }
 
@@ -252,7 +302,7 @@ cudaError_t go_rows_fwd(const Group<RowsFwdSlot<T>>& g, const C<T>* tw, int H, c
 template <typename T, int N>
 cudaError_t go_cols(Group<ColsSlot<T>>& g, int mode, int H, const C<T>* tw, cudaStream_t s) {
   constexpr int V = ColVecs<N>::value, THR = Radix23<N>::THR;
-  const size_t sm = (sizeof(C<T>) + sizeof(T)) * V * N;
+  const size_t sm = ColBuffers<T, N>::bytes;
   static int smem_set = 0;
   auto kern = cols_n<T, N>;
   cudaError_t e = ensure_smem(kern, sm, smem_set);

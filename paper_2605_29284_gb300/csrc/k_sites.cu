@@ -1,6 +1,9 @@
 // Per-site work of the rapid predictor (Section 2.2, algorithm steps 1, 3,
 // 4, 5 and Eq. "weights"), and the exact low-frequency block of F(c*).
+#include <cmath>
+
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace rk {
 
@@ -45,6 +48,23 @@ __global__ void kn_factor_kernel(double* out, int L, double hx, double hy, doubl
 cudaError_t launch_kn_factor(double* kn, int L, double hx, double hy, double rho, double sigma2,
                              int nu_code, int* flag, cudaStream_t s) {
   kn_factor_kernel<<<1, 256, 0, s>>>(kn, L, hx, hy, rho, sigma2, nu_code, flag);
+  return cudaGetLastError();
+}
+
+// The factor for the double-float weights (RK_FP32 plans), once per plan:
+// out[q] = kn[q] / sigma (q < M^2) and out[M^2 + q] = sigma / L_qq, as float pairs.
+__global__ void kn_split_kernel(const double* __restrict__ kn, int M, double sigma2,
+                                float2* __restrict__ out) {
+  const double sigma = sqrt(sigma2);
+  for (int t = threadIdx.x; t < M * M + M; t += blockDim.x) {
+    const double v = t < M * M ? kn[t] / sigma : sigma / kn[(t - M * M) * (M + 1)];
+    const dfl d = df_make(v);
+    out[t] = make_float2(d.hi, d.lo);
+  }
+}
+
+cudaError_t launch_kn_split(const double* kn, int M, double sigma2, float2* out, cudaStream_t s) {
+  kn_split_kernel<<<1, 256, 0, s>>>(kn, M, sigma2, out);
   return cudaGetLastError();
 }
 
@@ -144,12 +164,142 @@ __device__ __forceinline__ void weights_cta(const WeightsSlot& sl, int cta, doub
   }
 }
 
+// The same steps for RK_FP32 plans in double-float arithmetic on the FP32
+// pipe (64x the FP64 rate on GB300; about 2^-47 relative per operation).  The
+// quantities are taken in units of sigma2: phi = k_i / sigma2 and the factor
+// L / sigma of K_N / sigma2, so A_i = (K_N / sigma2)^{-1} phi is unchanged and
+// s_i = sigma sqrt(max(0, 1 - phi^T A_i)).  Rounding of this order keeps the
+// residual K_N A_i - k_i near 1e-13 sigma2 |A_i|, far below what single-
+// precision scatter and transforms resolve.
+__device__ __forceinline__ dfl matern_phi_df(dfl d, int nu_code) {
+  const dfl e = df_exp_neg(d);
+  const dfl one = {1.f, 0.f};
+  if (nu_code == 0) return e;
+  if (nu_code == 1) return df_mul(df_add(one, d), e);
+  constexpr double kThird = 1.0 / 3.0;
+  constexpr float kThirdHi = (float)kThird;
+  const dfl third = {kThirdHi, (float)(kThird - (double)kThirdHi)};
+  return df_mul(df_fma(d, df_fma(d, third, one), one), e);   // 1 + d + d^2 / 3
+}
+
+__device__ __forceinline__ dfl shfl_dfl(dfl v, int src, int width) {
+  return {__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width)};
+}
+
+// The G lanes of a site (one warp holds whole sites, G divides 32) keep the
+// site's vector in shared memory, so the substitution loops stay rolled: a
+// fully unrolled double-float substitution outgrows the instruction cache.
+// Step c: every lane forms the pivot z_c / L_cc from shared memory, updates
+// its own rows r = j + s G, and after a warp barrier the pivot's owner stores it.
+template <int W, int G>
+__device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, float2* Ls,
+                                               float2* Linv) {
+  constexpr int M = W * W;
+  constexpr int L = W / 2;
+  constexpr int S = (M + G - 1) / G;
+  constexpr int SITES = 64 / G;          // blockDim.x == 64
+  __shared__ float2 Zs[SITES * M];
+  const double* __restrict__ xy = sl.xy;
+  const float2* __restrict__ kdf = sl.kn_df;
+  const int n = sl.n, nx = sl.nx, ny = sl.ny, ntx = sl.ntx, nu_code = sl.nu_code;
+  const double x0 = sl.x0, x1 = sl.x1, y0 = sl.y0, y1 = sl.y1, hx = sl.hx, hy = sl.hy;
+  for (int t = threadIdx.x; t < M * M; t += blockDim.x) Ls[t] = kdf[t];
+  for (int t = threadIdx.x; t < M; t += blockDim.x) Linv[t] = kdf[M * M + t];
+  __syncthreads();
+  const int j = threadIdx.x % G, q = threadIdx.x / G;
+  const int i = cta * SITES + q;
+  float2* z = Zs + q * M;
+  const bool act = i < n;
+  // the box and the offsets in double, by the site's first lane only (the
+  // FP64 pipe is 1/64 of the FP32 one), then shared with its other lanes
+  int bx = 0, by = 0, in = 0;
+  dfl nu = {0.f, 0.f}, nv = {0.f, 0.f};
+  if (j == 0) {
+    const double x = act ? xy[2 * i] : x0, y = act ? xy[2 * i + 1] : y0;
+    const bool inside = x >= x0 && x <= x1 && y >= y0 && y <= y1;
+    const double gx = inside ? (x - x0) / hx : 0.0, gy = inside ? (y - y0) / hy : 0.0;
+    double fx = floor(gx), fy = floor(gy);
+    fx = fmin(fmax(fx, 0.0), (double)(nx - 2));
+    fy = fmin(fmax(fy, 0.0), (double)(ny - 2));
+    nu = df_neg(df_make(gx - fx));
+    nv = df_neg(df_make(gy - fy));
+    bx = inside ? (int)fx : 0;
+    by = inside ? (int)fy : 0;
+    in = inside;
+  }
+  const bool inside = __shfl_sync(0xffffffffu, in, 0, G) != 0;
+  nu = shfl_dfl(nu, 0, G);
+  nv = shfl_dfl(nv, 0, G);
+  const dfl hxr = {sl.hxr_df.x, sl.hxr_df.y}, hyr = {sl.hyr_df.x, sl.hyr_df.y};
+#pragma unroll 1
+  for (int r = j; r < M; r += G) {
+    const int a = r % W, b = r / W;
+    const dfl dx = df_mul(df_add({(float)(a - (L - 1)), 0.f}, nu), hxr);
+    const dfl dy = df_mul(df_add({(float)(b - (L - 1)), 0.f}, nv), hyr);
+    const dfl v = matern_phi_df(df_sqrt(df_fma(dx, dx, df_mul(dy, dy))), nu_code);
+    z[r] = make_float2(v.hi, v.lo);
+  }
+  __syncwarp();
+  dfl yy = {0.f, 0.f};
+#pragma unroll 1
+  for (int c = 0; c < M; ++c) {          // L y = phi
+    const float2 zv = z[c], li = Linv[c];
+    const dfl zc = df_mul({zv.x, zv.y}, {li.x, li.y});
+    yy = df_fma(zc, zc, yy);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int r = j + s * G;
+      if (r > c && r < M) {
+        const float2 l = Ls[r * M + c], zr = z[r];
+        const dfl u = df_fma({-l.x, -l.y}, zc, {zr.x, zr.y});
+        z[r] = make_float2(u.hi, u.lo);
+      }
+    }
+    __syncwarp();
+    if (j == c % G) z[c] = make_float2(zc.hi, zc.lo);
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int c = M - 1; c >= 0; --c) {     // L^T w = y
+    const float2 zv = z[c], li = Linv[c];
+    const dfl wc = df_mul({zv.x, zv.y}, {li.x, li.y});
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int r = j + s * G;
+      if (r < c) {
+        const float2 l = Ls[c * M + r], zr = z[r];
+        const dfl u = df_fma({-l.x, -l.y}, wc, {zr.x, zr.y});
+        z[r] = make_float2(u.hi, u.lo);
+      }
+    }
+    __syncwarp();
+    if (j == c % G) z[c] = make_float2(wc.hi, wc.lo);
+  }
+  __syncwarp();
+  if (!act) return;
+  for (int r = j; r < M; r += G) {
+    const float2 wv = inside ? z[r] : make_float2(0.f, 0.f);
+    sl.w64[(size_t)i * M + r] = (double)wv.x + (double)wv.y;
+    sl.w32[(size_t)i * M + r] = wv.x;
+    sl.wdf[(size_t)i * M + r] = wv;
+  }
+  if (j == 0) {
+    if (!inside) atomicOr(sl.flag, 2);
+    sl.box[2 * i] = bx;
+    sl.box[2 * i + 1] = by;
+    const dfl rest = df_add({1.f, 0.f}, df_neg(yy));
+    sl.ssd[i] = inside ? sl.sigma * sqrt(fmax(0.0, df_double(rest))) : 0.0;
+    if (sl.tcount) atomicAdd(sl.tcount + (by / 32) * ntx + bx / 32, 1);
+  }
+}
+
 // One launch for one plan or several (rk_set_sites_group) with L <= 3,
 // whatever their L: slot k covers CTAs [start[k], start[k + 1]) and runs the
 // variant for its L with G lanes per site (G capped at M for L = 1).  L = 4
 // (M = 64) has a kernel of its own: its register needs would cap the others'
 // occupancy.
-template <int G, int LMAX>
+// DF selects the double-float variant (every slot of the launch has dfw set).
+template <int G, int LMAX, bool DF>
 __global__ void __launch_bounds__(64)
 weights_grp_kernel(const __grid_constant__ Group<WeightsSlot> g) {
   constexpr int MM = 4 * LMAX * LMAX;
@@ -159,7 +309,19 @@ weights_grp_kernel(const __grid_constant__ Group<WeightsSlot> g) {
   while (ks + 1 < g.n && (int)blockIdx.x >= g.start[ks + 1]) ++ks;
   const WeightsSlot& sl = g.slot[ks];
   const int cta = blockIdx.x - g.start[ks];
-  if constexpr (LMAX == 4) {
+  if constexpr (DF) {
+    float2* Lf = reinterpret_cast<float2*>(Ls);
+    float2* Lif = reinterpret_cast<float2*>(Linv);
+    if constexpr (LMAX == 4) {
+      weights_cta_df<8, G>(sl, cta, Lf, Lif);
+    } else {
+      switch (sl.L) {
+        case 1: weights_cta_df<2, (G < 4 ? G : 4)>(sl, cta, Lf, Lif); break;
+        case 2: weights_cta_df<4, G>(sl, cta, Lf, Lif); break;
+        default: weights_cta_df<6, G>(sl, cta, Lf, Lif); break;
+      }
+    }
+  } else if constexpr (LMAX == 4) {
     weights_cta<8, G>(sl, cta, Ls, Linv);
   } else {
     switch (sl.L) {
@@ -170,28 +332,40 @@ weights_grp_kernel(const __grid_constant__ Group<WeightsSlot> g) {
   }
 }
 
-// Lanes per site: about two warps per scheduler (152 SMs x 4), i.e. the
-// largest power of two G <= 2 * 608 * 32 / n, kept within [4, min(32, M)].
+// Lanes per site: about two warps per scheduler (152 SMs x 4; eight for the
+// double-float variant), i.e. the largest power of two G <= 2 * 608 * 32 / n
+// (8 * 608 * 32 / n), kept within [4, min(32, M)].
 // More lanes per site shorten each warp's chain of FP64 instructions but
 // spend issue slots on rows that are already solved.
-inline int weights_lanes(int n, int M) {
-  const long long target = 2LL * 152 * 4 * 32;
+inline int weights_lanes(int n, int M, bool df) {
+  // the double-float variant's steps are short and its sites' vectors live in
+  // shared memory: more lanes per site pay there (about four warps per scheduler)
+  const long long target = (df ? 8LL : 2LL) * 152 * 4 * 32;
   int g = 4;
   while (g < 32 && 2 * g <= M && (long long)n * 2 * g <= target) g *= 2;
   return g < M ? g : M;
 }
 
+// v as the float nearest it and the float nearest the remainder (host side)
+static float2 float_pair(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 WeightsSlot weights_slot(const double* xy, int n, const rk_plan* p, int* box, double* w64,
                          float* w32, double* ssd, int* flag) {
-  return WeightsSlot{xy, p->kn_chol, box, w64, w32, ssd, flag,
+  return WeightsSlot{xy, p->kn_chol, p->kn_df, box, w64, w32, p->wdf, ssd, flag,
                      n >= kTileSortMin ? p->tile_count : nullptr,
                      n, p->nx, p->ny, p->tiles_x, p->nu_code, p->L,
-                     p->x0, p->x1, p->y0, p->y1, p->hx, p->hy, p->rho, p->sigma2};
+                     p->precision == RK_FP32 && p->kn_df != nullptr && p->wdf != nullptr,
+                     p->x0, p->x1, p->y0, p->y1, p->hx, p->hy, p->rho, p->sigma2,
+                     p->hx / p->rho, p->hy / p->rho, std::sqrt(p->sigma2),
+                     float_pair(p->hx / p->rho), float_pair(p->hy / p->rho)};
 }
 
 // One launch over g's slots (any mix of L); g.start is filled here (in CTAs).
 // G from the total site count and the largest neighbourhood.
-template <int LMAX>
+template <int LMAX, bool DF>
 cudaError_t launch_weights_slots(Group<WeightsSlot>& g, cudaStream_t s) {
   // two warps per CTA: a site's FP64 chain is long, so finer CTAs spread
   // the warps evenly over the schedulers
@@ -204,31 +378,34 @@ cudaError_t launch_weights_slots(Group<WeightsSlot>& g, cudaStream_t s) {
     Mmax = M > Mmax ? M : Mmax;
   }
   if (g.n == 0 || total == 0) return cudaSuccess;
-  const int G = weights_lanes(total > 0x7fffffff ? 0x7fffffff : (int)total, Mmax);
+  const int G = weights_lanes(total > 0x7fffffff ? 0x7fffffff : (int)total, Mmax, DF);
   g.start[0] = 0;
   for (int k = 0; k < g.n; ++k) {
     const int gk = g.slot[k].L == 1 && G > 4 ? 4 : G;
     g.start[k + 1] = g.start[k] + (g.slot[k].n + threads / gk - 1) / (threads / gk);
   }
   switch (G) {
-    case 4: weights_grp_kernel<4, LMAX><<<g.start[g.n], threads, 0, s>>>(g); break;
-    case 8: weights_grp_kernel<8, LMAX><<<g.start[g.n], threads, 0, s>>>(g); break;
-    case 16: weights_grp_kernel<16, LMAX><<<g.start[g.n], threads, 0, s>>>(g); break;
-    default: weights_grp_kernel<32, LMAX><<<g.start[g.n], threads, 0, s>>>(g); break;
+    case 4: weights_grp_kernel<4, LMAX, DF><<<g.start[g.n], threads, 0, s>>>(g); break;
+    case 8: weights_grp_kernel<8, LMAX, DF><<<g.start[g.n], threads, 0, s>>>(g); break;
+    case 16: weights_grp_kernel<16, LMAX, DF><<<g.start[g.n], threads, 0, s>>>(g); break;
+    default: weights_grp_kernel<32, LMAX, DF><<<g.start[g.n], threads, 0, s>>>(g); break;
   }
   return cudaGetLastError();
 }
 
-// g's slots split into L <= 3 (one launch) and L = 4 (one launch)
+// g's slots split by variant (double or double-float) and by L <= 3 or L = 4:
+// at most four launches, one for a group of plans of one precision and L <= 3
 cudaError_t launch_weights_group(Group<WeightsSlot>& g, cudaStream_t s) {
-  Group<WeightsSlot> a, b;
+  Group<WeightsSlot> part[4];
   for (int k = 0; k < g.n; ++k) {
-    if (g.slot[k].L == 4) b.slot[b.n++] = g.slot[k];
-    else a.slot[a.n++] = g.slot[k];
+    Group<WeightsSlot>& q = part[(g.slot[k].L == 4 ? 1 : 0) + (g.slot[k].dfw ? 2 : 0)];
+    q.slot[q.n++] = g.slot[k];
   }
-  cudaError_t e = launch_weights_slots<3>(a, s);
-  if (e != cudaSuccess) return e;
-  return launch_weights_slots<4>(b, s);
+  cudaError_t e = launch_weights_slots<3, false>(part[0], s);
+  if (e == cudaSuccess) e = launch_weights_slots<4, false>(part[1], s);
+  if (e == cudaSuccess) e = launch_weights_slots<3, true>(part[2], s);
+  if (e == cudaSuccess) e = launch_weights_slots<4, true>(part[3], s);
+  return e;
 }
 
 cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, double* w64,
@@ -246,7 +423,7 @@ cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, 
 __global__ void set_weights_kernel(const int* __restrict__ box_in, const double* __restrict__ w_in,
                                    int n, int M, int nx, int ny, int* __restrict__ box,
                                    double* __restrict__ w64, float* __restrict__ w32,
-                                   double* __restrict__ ssd, int* flag) {
+                                   float2* __restrict__ wdf, double* __restrict__ ssd, int* flag) {
   const long long total = (long long)n * M;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -265,6 +442,10 @@ __global__ void set_weights_kernel(const int* __restrict__ box_in, const double*
     const double w = w_in[t];
     w64[t] = w;
     w32[t] = (float)w;
+    if (wdf) {
+      const dfl d = df_make(w);
+      wdf[t] = make_float2(d.hi, d.lo);
+    }
   }
 }
 
@@ -275,7 +456,7 @@ cudaError_t launch_set_weights(const int* box_in, const double* w_in, int n, con
   long long blocks = (total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   set_weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(box_in, w_in, n, p->M, p->nx, p->ny, box,
-                                                      w64, w32, ssd, flag);
+                                                      w64, w32, p->wdf, ssd, flag);
   return cudaGetLastError();
 }
 
@@ -372,6 +553,101 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
   g.n = 1;
   g.slot[0] = block_factor_slot(box, w64, n, p, kx, ky, efac);
   return launch_block_factors_group(g, s);
+}
+
+// The forward block of RK_FP32 plans in double-float on the FP32 pipe: the
+// same two stages as block_factor_kernel, from the weights' float pairs and
+// double-float twiddles (re.hi, re.lo, im.hi, im.lo); E_i is stored in double
+// for the FP64 block GEMM.  The block only has to be far more accurate than
+// the single-precision transforms it corrects; double-float (about 2^-47 per
+// operation) is, and runs at 64x the FP64 rate.
+__device__ __forceinline__ void cdf_fma(dfl ar, dfl ai, dfl br, dfl bi, dfl& cr, dfl& ci) {
+  cr = df_fma(ar, br, df_fma(df_neg(ai), bi, cr));
+  ci = df_fma(ar, bi, df_fma(ai, br, ci));
+}
+
+__global__ void block_factor_df_kernel(const __grid_constant__ Group<BlockFactorDfSlot> g) {
+  extern __shared__ float4 tsm4[];        // [NS][KX + 1][2L]
+  int ks = 0;
+  while (ks + 1 < g.n && (int)blockIdx.x >= g.start[ks + 1]) ++ks;
+  const BlockFactorDfSlot& sl = g.slot[ks];
+  const int* __restrict__ box = sl.box;
+  const float2* __restrict__ wdf = sl.wdf;
+  const float4* __restrict__ twx = sl.twx;
+  const float4* __restrict__ twy = sl.twy;
+  double2* __restrict__ efac = sl.efac;
+  const int n = sl.n, px = sl.px, py = sl.py, KY = sl.KY, NS = sl.NS;
+  const int W = 2 * sl.L, M = W * W, nk = sl.KX + 1, bw = 2 * KY + 1;
+  const int i0 = (blockIdx.x - g.start[ks]) * NS;
+  const int ns = min(NS, n - i0);
+  for (int e = threadIdx.x; e < ns * nk * W; e += blockDim.x) {
+    const int b = e % W, kx = (e / W) % nk, si = e / (W * nk);
+    const int i = i0 + si, ix = box[2 * i];
+    dfl tr = {0.f, 0.f}, ti = {0.f, 0.f};
+    int m = (kx * ix) % px;                 // kx (ix + a) mod px, stepped by kx
+    for (int a = 0; a < W; ++a) {
+      const float4 tw = twx[m];
+      const float2 wv = wdf[(size_t)i * M + a + W * b];
+      const dfl w = {wv.x, wv.y};
+      tr = df_fma(w, {tw.x, tw.y}, tr);
+      ti = df_fma(w, {tw.z, tw.w}, ti);
+      m += kx;
+      m = m >= px ? m - px : m;
+    }
+    tsm4[e] = make_float4(tr.hi, tr.lo, ti.hi, ti.lo);    // e = (si * nk + kx) * W + b
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nk * bw * ns; e += blockDim.x) {
+    const int si = e % ns, jj = (e / ns) % bw, kx = e / (ns * bw);
+    const int i = i0 + si, iy = box[2 * i + 1], ky = jj - KY;
+    const float4* t = tsm4 + (si * nk + kx) * W;
+    dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
+    int m = (ky * iy) % py;                 // ky (iy + b) mod py, stepped by ky
+    m = m < 0 ? m + py : m;
+    const int step = ky < 0 ? ky + py : ky;
+    for (int b = 0; b < W; ++b, m = (m + step >= py ? m + step - py : m + step)) {
+      const float4 f = twy[m], tb = t[b];
+      cdf_fma({tb.x, tb.y}, {tb.z, tb.w}, {f.x, f.y}, {f.z, f.w}, ar, ai);
+    }
+    efac[((size_t)kx * bw + jj) * n + i] = make_double2(df_double(ar), df_double(ai));
+  }
+}
+
+BlockFactorDfSlot block_factor_df_slot(const rk_plan* p, int n) {
+  const int W = 2 * p->L;
+  const size_t per_site = sizeof(float4) * (size_t)(p->blk_kx + 1) * W;
+  // sites per CTA: four CTAs per SM at least, at most 32 KB of row sums
+  int NS = n / (4 * 152);
+  const int cap = (int)(32768 / per_site);
+  NS = NS > cap ? cap : NS;
+  NS = NS > 32 ? 32 : NS;
+  NS = NS < 1 ? 1 : NS;
+  return BlockFactorDfSlot{p->box, p->wdf, p->twdfx, p->twdfy, p->efac, n, p->L, p->px,
+                           p->py, p->blk_kx, p->blk_ky, NS};
+}
+
+cudaError_t launch_block_factors_df_group(Group<BlockFactorDfSlot>& g, cudaStream_t s) {
+  size_t sm = 0;
+  g.start[0] = 0;
+  for (int k = 0; k < g.n; ++k) {
+    const BlockFactorDfSlot& sl = g.slot[k];
+    const size_t b = sizeof(float4) * (size_t)(sl.KX + 1) * 2 * sl.L * sl.NS;
+    sm = b > sm ? b : sm;
+    g.start[k + 1] = g.start[k] + (sl.n + sl.NS - 1) / sl.NS;
+  }
+  if (g.n == 0 || g.start[g.n] == 0) return cudaSuccess;
+  static int smem_set = 0;
+  cudaError_t e = ensure_smem(block_factor_df_kernel, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  block_factor_df_kernel<<<g.start[g.n], 128, sm, s>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_factors_df(const rk_plan* p, int n, cudaStream_t s) {
+  Group<BlockFactorDfSlot> g;
+  g.n = 1;
+  g.slot[0] = block_factor_df_slot(p, n);
+  return launch_block_factors_df_group(g, s);
 }
 
 // ------------------------------------------------------------ block GEMM --

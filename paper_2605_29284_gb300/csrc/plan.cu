@@ -198,6 +198,22 @@ rk_status upload_twiddles(int n, double2** t64, float2** t32) {
   return RK_OK;
 }
 
+// The same table as double-float pairs (re.hi, re.lo, im.hi, im.lo): the
+// double values split into a float and the float nearest their remainder.
+rk_status upload_twiddles_df(int n, float4** tdf) {
+  std::vector<double2> h64;
+  std::vector<float2> h32;
+  make_twiddles(n, h64, h32);
+  std::vector<float4> h(n);
+  for (int e = 0; e < n; ++e) {
+    const float ch = (float)h64[e].x, sh = (float)h64[e].y;
+    h[e] = make_float4(ch, (float)(h64[e].x - (double)ch), sh, (float)(h64[e].y - (double)sh));
+  }
+  RK_TRY(dalloc(tdf, n));
+  RK_CU(cudaMemcpy(*tdf, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+  return RK_OK;
+}
+
 // Half spectrum (H x py, unscaled) of the symmetric torus base on a
 // tx x ty torus: kind 0 = phi, 1 = d/dlog rho.  *lam is allocated here.
 rk_status spectrum_raw(rk_plan* p, int tx, int ty, const FftPlan& fx, const FftPlan& fy,
@@ -293,13 +309,14 @@ rk_status choose_block(rk_plan* p) {
 void free_plan(rk_plan* p) {
   void* bufs[] = {p->tw64x, p->tw64y, p->tw32x, p->tw32y, p->lam64, p->lam32, p->dlam64,
                   p->dlam32, p->kn_chol, p->kn_dlog, p->box, p->w64, p->w32, p->ssd, p->efac,
+                  p->wdf, p->twdfx, p->twdfy,
                   p->c64, p->z64, p->mchol, p->cstar, p->tbuf, p->ubuf, p->blk,
                   p->d_flag, p->tw64qx, p->tw64qy, p->tw32qx, p->tw32qy, p->ce_sqrt64,
                   p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_out, p->xy, p->wd64,
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
                   p->efac_g, p->gblk, p->bw_dk, p->tile_start,
                   p->tile_count, p->tile_cursor, p->site_order,
-                  p->mchol_df};
+                  p->mchol_df, p->kn_df};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_flag) cudaFreeHost(p->h_flag);
@@ -892,6 +909,9 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
     if (cudaMemset(p->d_sites_flag, 0, sizeof(int)) != cudaSuccess) { st = RK_ERR_CUDA; break; }
     if ((st = upload_twiddles(p->px, &p->tw64x, &p->tw32x)) != RK_OK) break;
     if ((st = upload_twiddles(p->py, &p->tw64y, &p->tw32y)) != RK_OK) break;
+    if (precision == RK_FP32 && ((st = upload_twiddles_df(p->px, &p->twdfx)) != RK_OK ||
+                                 (st = upload_twiddles_df(p->py, &p->twdfy)) != RK_OK))
+      break;
     if ((st = compute_spectrum(p, 0, &p->lam64, &p->lam32)) != RK_OK) break;
     if (precision == RK_FP32 && (st = choose_block(p)) != RK_OK) break;
     if ((st = dalloc(&p->kn_chol, (size_t)p->M * p->M)) != RK_OK) break;
@@ -900,6 +920,13 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
                          p->stream) != cudaSuccess) {
       st = RK_ERR_CUDA;
       break;
+    }
+    if (precision == RK_FP32) {
+      if ((st = dalloc(&p->kn_df, (size_t)p->M * p->M + p->M)) != RK_OK) break;
+      if (launch_kn_split(p->kn_chol, p->M, p->sigma2, p->kn_df, p->stream) != cudaSuccess) {
+        st = RK_ERR_CUDA;
+        break;
+      }
     }
     int flag = 0;
     if ((st = read_flag(p, &flag)) != RK_OK) break;
@@ -979,9 +1006,9 @@ rk_status launch_site_factors(rk_plan* p, int n) {
   RK_CU(cudaStreamWaitEvent(p->side, p->ev_wfork, 0));
   {
     cudaStream_t s = p->side;
-    RK_PROF64("block_factors", (double)n * (8.0 * p->M + 8.0 + 16.0 * p->nblk),
+    RK_PROFDF("block_factors", (double)n * (8.0 * p->M + 8.0 + 16.0 * p->nblk),
               (double)n * (4.0 * (p->blk_kx + 1) * p->M + 8.0 * p->nblk * 2 * p->L));
-    RK_CU(launch_block_factors(p->box, p->w64, n, p, p->blk_kx, p->blk_ky, p->efac, s));
+    RK_CU(launch_block_factors_df(p, n, s));
   }
   RK_CU(cudaEventRecord(p->ev_sites, p->side));
   return RK_OK;
@@ -996,7 +1023,9 @@ rk_status ensure_sites(rk_plan* p, int n) {
     RK_TRY(dalloc(&p->w32, (size_t)n * p->M));
     RK_TRY(dalloc(&p->ssd, (size_t)n));
     RK_TRY(dalloc(&p->site_order, (size_t)n));
-    if (p->precision == RK_FP32 && p->nblk > 0) RK_TRY(dalloc(&p->efac, (size_t)n * p->nblk));
+    if (p->precision == RK_FP32) RK_TRY(dalloc(&p->wdf, (size_t)n * p->M));
+    if (p->precision == RK_FP32 && p->nblk > 0)
+      RK_TRY(dalloc(&p->efac, (size_t)n * p->nblk));
     p->n_cap = n;
   }
   p->n = 0;
@@ -1100,11 +1129,10 @@ rk_status rk_set_sites_group(rk_plan* const* plans, int nplans, const int* n,
     RK_PROF("tile_sites", 0.0);
     for (int k = 0; k < nplans; ++k) RK_CU(launch_tile_sites(plans[k]->box, n[k], plans[k], true, s));
   }
-  Group<BlockFactorSlot> gf;
+  Group<BlockFactorDfSlot> gf;
   for (int k = 0; k < nplans; ++k) {
     rk_plan* p = plans[k];
-    if (p->precision == RK_FP32 && p->nblk > 0)
-      gf.slot[gf.n++] = block_factor_slot(p->box, p->w64, n[k], p, p->blk_kx, p->blk_ky, p->efac);
+    if (p->precision == RK_FP32 && p->nblk > 0) gf.slot[gf.n++] = block_factor_df_slot(p, n[k]);
   }
   if (gf.n > 0) {
     // on the first plan's side stream; every plan's ev_sites marks the result
@@ -1112,8 +1140,8 @@ rk_status rk_set_sites_group(rk_plan* const* plans, int nplans, const int* n,
     RK_CU(cudaStreamWaitEvent(p0->side, p0->ev_wfork, 0));
     {
       cudaStream_t s = p0->side;
-      RK_PROF64("block_factors", fb, ff);
-      RK_CU(launch_block_factors_group(gf, s));
+      RK_PROFDF("block_factors", fb, ff);
+      RK_CU(launch_block_factors_df_group(gf, s));
     }
     for (int k = 0; k < nplans; ++k) RK_CU(cudaEventRecord(plans[k]->ev_sites, p0->side));
   }

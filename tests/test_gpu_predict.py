@@ -55,6 +55,9 @@ def _check_weights(w, xy, g, th):
     assert res <= 1e-13 * np.abs(KN).max() * max(1.0, np.abs(w).max()) * g.M
 
 
+WTOL = {"fp64": 1e-10, "fp32": 1e-8}
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_tiny_workload_against_direct_sum(rk, prec):
     # n = 200 uniform sites, 64 x 64 grid, nu = 1.5, range 0.2, tau^2 = 1e-4, L = 2
@@ -65,7 +68,10 @@ def test_tiny_workload_against_direct_sum(rk, prec):
     assert rel_err(out, ref) <= TOL[prec]
     ix, iy, W = rapid.weights(xy, g, *th)
     assert np.array_equal(box[:, 0], ix) and np.array_equal(box[:, 1], iy)
-    assert np.abs(w - W).max() <= 1e-10 * np.abs(W).max()
+    # RK_FP32 plans solve for the weights in double-float arithmetic (unit
+    # roundoff 2^-47, 64x that of double); the forward error scales with
+    # cond(K_N), the residual (checked next) with the unit roundoff alone
+    assert np.abs(w - W).max() <= WTOL[prec] * np.abs(W).max()
     _check_weights(w, xy, g, th)
     assert info["px"] == rapid.torus_size(64, 2) and info["py"] == rapid.torus_size(64, 2)
 
