@@ -198,14 +198,13 @@ class Arm:
     def _issue(self):
         """One step: every cell's weights (site update), coefficients and
         prediction.  Cells sharing a torus go as groups (rk_set_sites_group:
-        one weights launch per L; rk_predict_group: one launch per pass);
-        otherwise one stream per cell."""
+        one weights launch per L; rk_set_coef_group: one copy launch;
+        rk_predict_group: one launch per pass); otherwise one stream per cell."""
         torch = self.torch
         if self.grouped:
             plans = [p for p, _, _ in self.st]
             self.rk.set_sites_group(plans, [self.xy] * len(plans))
-            for p, c, _ in self.st:
-                p.set_coef(c)
+            self.rk.set_coef_group(plans, [c for _, c, _ in self.st])
             self.rk.predict_group(plans, [o for _, _, o in self.st])
             return
         cur = torch.cuda.current_stream()

@@ -173,6 +173,18 @@ rk_status rk_set_weights(rk_plan* plan, int n, const int* box_dev, const double*
 rk_status rk_set_coef(rk_plan* plan, int B, const double* c_dev);
 
 /*
+ * rk_set_coef_group -- rk_set_coef for nplans plans at once (1 <= nplans <=
+ * 16, distinct, each with sites set): one copy launch for all of them, on
+ * plans[0]'s stream.  B[k], c_dev[k]: plans[k]'s field count and device
+ * coefficients (B[k] x n doubles, n its site count).  Buffers grow on first
+ * use (an allocation, so size them before any stream capture).
+ * RK_ERR_INVALID_ARG for null, repeated or out-of-range arguments,
+ * RK_ERR_STATE for a plan without sites.
+ */
+rk_status rk_set_coef_group(rk_plan* const* plans, int nplans, const int* B,
+                            const double* const* c_dev);
+
+/*
  * rk_solve_coef -- Eq. (3) without covariates: c = M^{-1} z for B fields,
  * M = K_xx + tau2 I (Section 2), by a double-precision Cholesky factorisation
  * of M on the device and two triangular solves.  The factor is kept for

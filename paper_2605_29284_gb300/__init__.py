@@ -12,7 +12,8 @@ import torch
 from ._native import RK_FP32, RK_FP64, PlanInfo, RkError, check, lib, profile_enable, profile_read
 
 __all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "predict_group",
-           "predict_host_group", "profile_enable", "profile_read", "set_sites_group"]
+           "predict_host_group", "profile_enable", "profile_read", "set_coef_group",
+           "set_sites_group"]
 
 
 def _ptr(t):
@@ -214,6 +215,22 @@ def set_sites_group(plans, xys):
     for p, x in zip(plans, xys):
         p.n = int(x.shape[0])
         p._xy = x
+
+
+def set_coef_group(plans, cs):
+    """rk_set_coef_group: every plan's coefficients (device, B_k x n_k
+    doubles) copied in one launch.  Issued on the current stream."""
+    plans = list(plans)
+    cs = [_dev_f64(c) for c in cs]
+    cs = [c.unsqueeze(0) if c.dim() == 1 else c for c in cs]
+    k = len(plans)
+    harr = (ctypes.c_void_p * k)(*[p._h.value for p in plans])
+    barr = (ctypes.c_int * k)(*[int(c.shape[0]) for c in cs])
+    carr = (ctypes.c_void_p * k)(*[_ptr(c) for c in cs])
+    check(lib.rk_set_stream(plans[0]._h, _stream()), "rk_set_stream")
+    check(lib.rk_set_coef_group(harr, k, barr, carr), "rk_set_coef_group")
+    for p, c in zip(plans, cs):
+        p.B = int(c.shape[0])
 
 
 def predict_host_group(plans, xys, cs, outs=None):

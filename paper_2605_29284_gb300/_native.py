@@ -67,6 +67,7 @@ _SIGS = {
     "rk_predict_static": [_vp, _vp],
     "rk_predict_group": [ctypes.POINTER(_vp), _int, ctypes.POINTER(_vp)],
     "rk_set_sites_group": [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_vp)],
+    "rk_set_coef_group": [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_vp)],
     "rk_predict_host_group": [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_vp),
                               ctypes.POINTER(_int), ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "rk_simulate": [_vp, _int, ctypes.c_ulonglong, _vp],

@@ -118,6 +118,7 @@ struct rk_plan {
   float* w32 = nullptr;        // n x M
   double* ssd = nullptr;       // n: sqrt(max(0, sigma2 - k_i^T W_i)) (CS)
   float2* wdf = nullptr;       // RK_FP32: n x M, the weights as double-float pairs
+  bool w64_stale = false;      // w64 not yet formed from wdf (ensure_w64)
   double2* efac = nullptr;     // RK_FP32: n x nblk Fourier factors of A_i on the block
   float4* twdfx = nullptr;     // RK_FP32: the px and py twiddles as double-float pairs
   float4* twdfy = nullptr;     //   (re.hi, re.lo, im.hi, im.lo)
@@ -250,7 +251,8 @@ struct RowsInvSlot {
   int ldu, nrows, old, ocol0, ncols, ald, ar0, ac0, B;
 };
 struct WeightsSlot {
-  const double* xy; const double* kn; const float2* kn_df;
+  const double* xy; double* xy_out;      // xy_out: the plan's copy, written when xy is not it
+  const double* kn; const float2* kn_df;
   int* box; double* w64; float* w32; float2* wdf; double* ssd; int* flag; int* tcount;
   int n, nx, ny, ntx, nu_code, L, dfw;   // dfw: double-float variant (RK_FP32 plans)
   double x0, x1, y0, y1, hx, hy, rho, sigma2;
@@ -261,6 +263,11 @@ WeightsSlot weights_slot(const double* xy, int n, const rk_plan* p, int* box, do
                          float* w32, double* ssd, int* flag);
 cudaError_t launch_weights_group(Group<WeightsSlot>& g, cudaStream_t s);
 cudaError_t launch_kn_split(const double* kn, int M, double sigma2, float2* out, cudaStream_t s);
+cudaError_t launch_convert_weights(const float2* wdf, size_t count, double* w64, cudaStream_t s);
+struct CopySlot {
+  const double* src; double* dst; long long count;
+};
+cudaError_t launch_copy_group(Group<CopySlot>& g, cudaStream_t s);
 struct BlockFactorSlot {
   const int* box; const double* w64; const double2* twx; const double2* twy; double2* efac;
   int n, L, px, py, KX, KY, NS;
@@ -337,6 +344,7 @@ cudaError_t chol_mirror(double* a, int n, cudaStream_t s);
 cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
                        const float2* adf = nullptr);
 cudaError_t chol_split(const double* a, int n, float2* adf, cudaStream_t s);
+cudaError_t chol_invert_diag_df(const double* a, int n, float2* adf, cudaStream_t s);
 
 // conditional simulation
 template <typename T>

@@ -267,51 +267,93 @@ __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __res
     if (f < nf) x[(size_t)(f0 + f) * n + r] -= df_double(acc[f]);
 }
 
-// The diagonal-block substitution in double-float (RK_FP32 plans): the same
-// lane layout as solve_diag_kernel, FP32 instructions instead of FP64 ones on
-// the sequential chain of the block.
-__device__ __forceinline__ dfl shfl_df(dfl v, int src) {
-  return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
-}
+// RK_FP32 plans: the diagonal blocks of the double-float factor hold the
+// inverses of L's diagonal blocks instead (chol_invert_diag_df), so a block
+// step of the solve is the product x_k <- L_kk^{-1} x_k (forward) or
+// L_kk^{-T} x_k (backward): 64-term sums in parallel instead of a 64-step
+// substitution chain.  adf[(k + c) n + k + r] holds L_kk^{-1}(r, c) for
+// r >= c and its mirror L_kk^{-1}(c, r) for r < c, so in both directions
+// the thread of row r reads column c of the block at row r; the block is
+// staged in shared memory first (coalesced loads, conflict-free reads).
+constexpr int kDiagRhs = 4;     // right-hand sides per CTA of the block product
 
 template <bool FWD>
-__global__ void solve_diag_df_kernel(const float2* __restrict__ adf, const double* __restrict__ a,
-                                     int n, int k, double* x, int B) {
-  __shared__ float2 Ls[SB * SB];            // Ls[c * SB + r] = adf[(k + c) n + k + r]
-  __shared__ float2 rd[SB];                 // 1 / L(k + c, k + c) as a pair
+__global__ void __launch_bounds__(SB * kDiagRhs)
+solve_diag_inv_df_kernel(const float2* __restrict__ adf, int n, int k, double* x, int B) {
+  __shared__ float2 Ts[SB * SB];            // Ts[c * SB + r] = adf[(k + c) n + k + r]
+  __shared__ float2 xs[kDiagRhs][SB];
   const int nb = min(SB, n - k);
-#pragma unroll 8
+#pragma unroll 4
   for (int t = threadIdx.x; t < nb * SB; t += blockDim.x) {
     const int c = t / SB, r = t % SB;
-    Ls[t] = r < nb ? adf[(size_t)(k + c) * n + k + r] : make_float2(0.f, 0.f);
+    Ts[t] = r < nb ? adf[(size_t)(k + c) * n + k + r] : make_float2(0.f, 0.f);
   }
-  if (threadIdx.x < nb) {
-    const dfl v = df_make(1.0 / a[(size_t)(k + threadIdx.x) * n + k + threadIdx.x]);
-    rd[threadIdx.x] = make_float2(v.hi, v.lo);
+  const int r = threadIdx.x % SB, fl = threadIdx.x / SB;
+  const int f = blockIdx.x * kDiagRhs + fl;
+  const bool live = f < B;
+  double* xf = x + (size_t)(live ? f : 0) * n + k;
+  const dfl v = df_make(live && r < nb ? xf[r] : 0.0);
+  xs[fl][r] = make_float2(v.hi, v.lo);
+  __syncthreads();
+  if (!live || r >= nb) return;
+  dfl acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+  const int c0 = FWD ? 0 : r, c1 = FWD ? r + 1 : nb;     // L^{-1}: c <= r; L^{-T}: c >= r
+  int c = c0;
+  for (; c + 1 < c1; c += 2) {
+    const float2 l0 = Ts[c * SB + r], l1 = Ts[(c + 1) * SB + r];
+    const float2 x0 = xs[fl][c], x1 = xs[fl][c + 1];
+    acc0 = df_fma({l0.x, l0.y}, {x0.x, x0.y}, acc0);
+    acc1 = df_fma({l1.x, l1.y}, {x1.x, x1.y}, acc1);
+  }
+  if (c < c1) {
+    const float2 l0 = Ts[c * SB + r];
+    const float2 x0 = xs[fl][c];
+    acc0 = df_fma({l0.x, l0.y}, {x0.x, x0.y}, acc0);
+  }
+  xf[r] = df_double(df_add(acc0, acc1));
+}
+
+// The inverses of the factor's diagonal blocks (SB x SB, lower triangular),
+// in double from a's lower triangle, written into adf's diagonal blocks as
+// float pairs, both triangles (the mirror as above).  One CTA per block,
+// thread j forms column j by forward substitution on L_kk x = e_j.
+__global__ void __launch_bounds__(SB) chol_invert_diag_kernel(const double* __restrict__ a, int n,
+                                                             float2* __restrict__ adf) {
+  extern __shared__ double tinv_sm[];
+  double* T = tinv_sm;                  // [SB][SB + 1]: T[i * (SB + 1) + c] = L_kk(i, c)
+  double* X = tinv_sm + SB * (SB + 1);  // [SB][SB + 1]: X[i * (SB + 1) + j] = L_kk^{-1}(i, j)
+  const int k = blockIdx.x * SB;
+  const int nb = min(SB, n - k);
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int c = t / nb, i = t % nb;
+    T[i * (SB + 1) + c] = i >= c ? a[(size_t)(k + c) * n + k + i] : 0.0;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (f >= B) return;
-  double* xf = x + (size_t)f * n + k;
-  dfl v0 = df_make(lane < nb ? xf[lane] : 0.0);
-  dfl v1 = df_make(lane + 32 < nb ? xf[lane + 32] : 0.0);
-  const dfl zero = {0.f, 0.f};
-  for (int step = 0; step < nb; ++step) {
-    const int c = FWD ? step : nb - 1 - step;
-    const float2* col = Ls + c * SB;
-    const dfl l0 = {col[lane].x, col[lane].y};
-    const dfl l1 = {col[lane + 32].x, col[lane + 32].y};
-    const dfl own = shfl_df(c < 32 ? v0 : v1, c & 31);
-    const dfl xc = df_fma(own, {rd[c].x, rd[c].y}, zero);
-    if (lane == (c & 31)) {
-      if (c < 32) v0 = xc; else v1 = xc;
+  const int j = threadIdx.x;
+  if (j < nb) {
+    for (int i = 0; i < j; ++i) X[i * (SB + 1) + j] = 0.0;
+    for (int i = j; i < nb; ++i) {
+      double s = i == j ? 1.0 : 0.0;
+      for (int q = j; q < i; ++q) s = fma(-T[i * (SB + 1) + q], X[q * (SB + 1) + j], s);
+      X[i * (SB + 1) + j] = s / T[i * (SB + 1) + i];
     }
-    if (FWD ? (lane > c) : (lane < c)) v0 = df_fma(df_neg(l0), xc, v0);
-    if (FWD ? (lane + 32 > c) : (lane + 32 < c)) v1 = df_fma(df_neg(l1), xc, v1);
   }
-  if (lane < nb) xf[lane] = df_double(v0);
-  if (lane + 32 < nb) xf[lane + 32] = df_double(v1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int c = t / nb, r = t % nb;
+    const double v = r >= c ? X[r * (SB + 1) + c] : X[c * (SB + 1) + r];
+    const dfl d = df_make(v);
+    adf[(size_t)(k + c) * n + k + r] = make_float2(d.hi, d.lo);
+  }
+}
+
+cudaError_t chol_invert_diag_df(const double* a, int n, float2* adf, cudaStream_t s) {
+  const size_t sm = sizeof(double) * 2 * SB * (SB + 1);
+  static int smem_set = 0;
+  cudaError_t e = ensure_smem(chol_invert_diag_kernel, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  chol_invert_diag_kernel<<<(n + SB - 1) / SB, SB, sm, s>>>(a, n, adf);
+  return cudaGetLastError();
 }
 
 // adf = a as double-float pairs (the mirrored factor, both triangles)
@@ -333,10 +375,11 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
                        const float2* adf) {
   if (n <= 0 || B <= 0) return cudaSuccess;
   const int dgrid = (B + 3) / 4;              // four warps (right-hand sides) per CTA
+  const int igrid = (B + kDiagRhs - 1) / kDiagRhs;
   const int fblocks = (B + SF - 1) / SF;
   for (int k = 0; k < n; k += SB) {
     const int nb = n - k < SB ? n - k : SB;
-    if (adf) solve_diag_df_kernel<true><<<dgrid, 128, 0, s>>>(adf, a, n, k, x, B);
+    if (adf) solve_diag_inv_df_kernel<true><<<igrid, SB * kDiagRhs, 0, s>>>(adf, n, k, x, B);
     else solve_diag_kernel<true><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     const int rest = n - k - nb;
     if (rest > 0) {
@@ -347,7 +390,7 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
   }
   const int last = ((n - 1) / SB) * SB;
   for (int k = last; k >= 0; k -= SB) {
-    if (adf) solve_diag_df_kernel<false><<<dgrid, 128, 0, s>>>(adf, a, n, k, x, B);
+    if (adf) solve_diag_inv_df_kernel<false><<<igrid, SB * kDiagRhs, 0, s>>>(adf, n, k, x, B);
     else solve_diag_kernel<false><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     if (k > 0) {
       const dim3 grid((k + SU - 1) / SU, fblocks);

@@ -155,6 +155,10 @@ __device__ __forceinline__ void weights_cta(const WeightsSlot& sl, int cta, doub
     }
   }
   if (j == 0) {
+    if (sl.xy_out) {                      // the plan's copy of the sites
+      sl.xy_out[2 * i] = x;
+      sl.xy_out[2 * i + 1] = y;
+    }
     if (!inside) atomicOr(flag, 2);
     const int bx = inside ? (int)fx : 0, by = inside ? (int)fy : 0;
     box[2 * i] = bx;
@@ -182,54 +186,59 @@ __device__ __forceinline__ dfl matern_phi_df(dfl d, int nu_code) {
   return df_mul(df_fma(d, df_fma(d, third, one), one), e);   // 1 + d + d^2 / 3
 }
 
-__device__ __forceinline__ dfl shfl_dfl(dfl v, int src, int width) {
-  return {__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width)};
-}
-
 // The G lanes of a site (one warp holds whole sites, G divides 32) keep the
 // site's vector in shared memory, so the substitution loops stay rolled: a
 // fully unrolled double-float substitution outgrows the instruction cache.
 // Step c: every lane forms the pivot z_c / L_cc from shared memory, updates
 // its own rows r = j + s G, and after a warp barrier the pivot's owner stores it.
+constexpr int kWeightsDfThreads = 128;
+
 template <int W, int G>
 __device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, float2* Ls,
                                                float2* Linv) {
   constexpr int M = W * W;
   constexpr int L = W / 2;
   constexpr int S = (M + G - 1) / G;
-  constexpr int SITES = 64 / G;          // blockDim.x == 64
+  constexpr int SITES = kWeightsDfThreads / G;   // <= 32
   __shared__ float2 Zs[SITES * M];
+  __shared__ int sbox[2 * SITES], sin[SITES];
+  __shared__ float2 suv[2 * SITES];
   const double* __restrict__ xy = sl.xy;
   const float2* __restrict__ kdf = sl.kn_df;
   const int n = sl.n, nx = sl.nx, ny = sl.ny, ntx = sl.ntx, nu_code = sl.nu_code;
   const double x0 = sl.x0, x1 = sl.x1, y0 = sl.y0, y1 = sl.y1, hx = sl.hx, hy = sl.hy;
   for (int t = threadIdx.x; t < M * M; t += blockDim.x) Ls[t] = kdf[t];
   for (int t = threadIdx.x; t < M; t += blockDim.x) Linv[t] = kdf[M * M + t];
-  __syncthreads();
-  const int j = threadIdx.x % G, q = threadIdx.x / G;
-  const int i = cta * SITES + q;
-  float2* z = Zs + q * M;
-  const bool act = i < n;
-  // the box and the offsets in double, by the site's first lane only (the
-  // FP64 pipe is 1/64 of the FP32 one), then shared with its other lanes
-  int bx = 0, by = 0, in = 0;
-  dfl nu = {0.f, 0.f}, nv = {0.f, 0.f};
-  if (j == 0) {
+  // the boxes and offsets in double, one lane per site of the CTA in the
+  // first warp: the FP64 pipe takes a warp instruction whatever its active
+  // lanes, so the other warps issue none
+  if (threadIdx.x < SITES) {
+    const int i = cta * SITES + threadIdx.x;
+    const bool act = i < n;
     const double x = act ? xy[2 * i] : x0, y = act ? xy[2 * i + 1] : y0;
+    if (act && sl.xy_out) {               // the plan's copy of the sites
+      sl.xy_out[2 * i] = x;
+      sl.xy_out[2 * i + 1] = y;
+    }
     const bool inside = x >= x0 && x <= x1 && y >= y0 && y <= y1;
     const double gx = inside ? (x - x0) / hx : 0.0, gy = inside ? (y - y0) / hy : 0.0;
     double fx = floor(gx), fy = floor(gy);
     fx = fmin(fmax(fx, 0.0), (double)(nx - 2));
     fy = fmin(fmax(fy, 0.0), (double)(ny - 2));
-    nu = df_neg(df_make(gx - fx));
-    nv = df_neg(df_make(gy - fy));
-    bx = inside ? (int)fx : 0;
-    by = inside ? (int)fy : 0;
-    in = inside;
+    const dfl u = df_neg(df_make(gx - fx)), v = df_neg(df_make(gy - fy));
+    suv[2 * threadIdx.x] = make_float2(u.hi, u.lo);
+    suv[2 * threadIdx.x + 1] = make_float2(v.hi, v.lo);
+    sbox[2 * threadIdx.x] = inside ? (int)fx : 0;
+    sbox[2 * threadIdx.x + 1] = inside ? (int)fy : 0;
+    sin[threadIdx.x] = inside;
   }
-  const bool inside = __shfl_sync(0xffffffffu, in, 0, G) != 0;
-  nu = shfl_dfl(nu, 0, G);
-  nv = shfl_dfl(nv, 0, G);
+  __syncthreads();
+  const int j = threadIdx.x % G, q = threadIdx.x / G;
+  const int i = cta * SITES + q;
+  float2* z = Zs + q * M;
+  const bool act = i < n;
+  const bool inside = sin[q] != 0;
+  const dfl nu = {suv[2 * q].x, suv[2 * q].y}, nv = {suv[2 * q + 1].x, suv[2 * q + 1].y};
   const dfl hxr = {sl.hxr_df.x, sl.hxr_df.y}, hyr = {sl.hyr_df.x, sl.hyr_df.y};
 #pragma unroll 1
   for (int r = j; r < M; r += G) {
@@ -240,12 +249,10 @@ __device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, f
     z[r] = make_float2(v.hi, v.lo);
   }
   __syncwarp();
-  dfl yy = {0.f, 0.f};
 #pragma unroll 1
   for (int c = 0; c < M; ++c) {          // L y = phi
     const float2 zv = z[c], li = Linv[c];
     const dfl zc = df_mul({zv.x, zv.y}, {li.x, li.y});
-    yy = df_fma(zc, zc, yy);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const int r = j + s * G;
@@ -259,6 +266,16 @@ __device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, f
     if (j == c % G) z[c] = make_float2(zc.hi, zc.lo);
   }
   __syncwarp();
+  // phi^T A_i = |y|^2: each lane's rows, then a sum over the site's lanes
+  dfl yy = {0.f, 0.f};
+  for (int r = j; r < M; r += G) {
+    const float2 yv = z[r];
+    yy = df_fma({yv.x, yv.y}, {yv.x, yv.y}, yy);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+    yy = df_add(yy, {__shfl_xor_sync(0xffffffffu, yy.hi, o, G),
+                     __shfl_xor_sync(0xffffffffu, yy.lo, o, G)});
 #pragma unroll 1
   for (int c = M - 1; c >= 0; --c) {     // L^T w = y
     const float2 zv = z[c], li = Linv[c];
@@ -277,13 +294,15 @@ __device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, f
   }
   __syncwarp();
   if (!act) return;
+  // the double copy of the weights is formed on demand (convert_weights):
+  // the forward path reads the float pairs and the floats only
   for (int r = j; r < M; r += G) {
     const float2 wv = inside ? z[r] : make_float2(0.f, 0.f);
-    sl.w64[(size_t)i * M + r] = (double)wv.x + (double)wv.y;
     sl.w32[(size_t)i * M + r] = wv.x;
     sl.wdf[(size_t)i * M + r] = wv;
   }
   if (j == 0) {
+    const int bx = sbox[2 * q], by = sbox[2 * q + 1];
     if (!inside) atomicOr(sl.flag, 2);
     sl.box[2 * i] = bx;
     sl.box[2 * i + 1] = by;
@@ -298,9 +317,17 @@ __device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, f
 // variant for its L with G lanes per site (G capped at M for L = 1).  L = 4
 // (M = 64) has a kernel of its own: its register needs would cap the others'
 // occupancy.
+// Lanes per site of the double-float variant for neighbourhood size L, from
+// the launch's G: 4 for L = 1, G for L = 2, 2G (at most 32) for L >= 3, whose
+// 2M-step substitution chains are the longest: more lanes per site keep
+// more of them in flight and shorten each step.
+constexpr int df_lanes(int L, int G) {
+  return L == 1 ? 4 : L == 2 ? G : (2 * G > 32 ? 32 : 2 * G);
+}
+
 // DF selects the double-float variant (every slot of the launch has dfw set).
 template <int G, int LMAX, bool DF>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(DF ? kWeightsDfThreads : 64)
 weights_grp_kernel(const __grid_constant__ Group<WeightsSlot> g) {
   constexpr int MM = 4 * LMAX * LMAX;
   __shared__ double Ls[MM * MM];
@@ -313,12 +340,12 @@ weights_grp_kernel(const __grid_constant__ Group<WeightsSlot> g) {
     float2* Lf = reinterpret_cast<float2*>(Ls);
     float2* Lif = reinterpret_cast<float2*>(Linv);
     if constexpr (LMAX == 4) {
-      weights_cta_df<8, G>(sl, cta, Lf, Lif);
+      weights_cta_df<8, df_lanes(4, G)>(sl, cta, Lf, Lif);
     } else {
       switch (sl.L) {
-        case 1: weights_cta_df<2, (G < 4 ? G : 4)>(sl, cta, Lf, Lif); break;
-        case 2: weights_cta_df<4, G>(sl, cta, Lf, Lif); break;
-        default: weights_cta_df<6, G>(sl, cta, Lf, Lif); break;
+        case 1: weights_cta_df<2, df_lanes(1, G)>(sl, cta, Lf, Lif); break;
+        case 2: weights_cta_df<4, df_lanes(2, G)>(sl, cta, Lf, Lif); break;
+        default: weights_cta_df<6, df_lanes(3, G)>(sl, cta, Lf, Lif); break;
       }
     }
   } else if constexpr (LMAX == 4) {
@@ -354,7 +381,8 @@ static float2 float_pair(double v) {
 
 WeightsSlot weights_slot(const double* xy, int n, const rk_plan* p, int* box, double* w64,
                          float* w32, double* ssd, int* flag) {
-  return WeightsSlot{xy, p->kn_chol, p->kn_df, box, w64, w32, p->wdf, ssd, flag,
+  return WeightsSlot{xy, xy == p->xy ? nullptr : p->xy, p->kn_chol, p->kn_df, box, w64, w32,
+                     p->wdf, ssd, flag,
                      n >= kTileSortMin ? p->tile_count : nullptr,
                      n, p->nx, p->ny, p->tiles_x, p->nu_code, p->L,
                      p->precision == RK_FP32 && p->kn_df != nullptr && p->wdf != nullptr,
@@ -368,8 +396,9 @@ WeightsSlot weights_slot(const double* xy, int n, const rk_plan* p, int* box, do
 template <int LMAX, bool DF>
 cudaError_t launch_weights_slots(Group<WeightsSlot>& g, cudaStream_t s) {
   // two warps per CTA: a site's FP64 chain is long, so finer CTAs spread
-  // the warps evenly over the schedulers
-  const int threads = 64;
+  // the warps evenly over the schedulers (four for the double-float variant,
+  // whose first warp forms every site's box in double)
+  const int threads = DF ? kWeightsDfThreads : 64;
   long long total = 0;
   int Mmax = 0;
   for (int k = 0; k < g.n; ++k) {
@@ -378,14 +407,18 @@ cudaError_t launch_weights_slots(Group<WeightsSlot>& g, cudaStream_t s) {
     Mmax = M > Mmax ? M : Mmax;
   }
   if (g.n == 0 || total == 0) return cudaSuccess;
-  const int G = weights_lanes(total > 0x7fffffff ? 0x7fffffff : (int)total, Mmax, DF);
+  int G = weights_lanes(total > 0x7fffffff ? 0x7fffffff : (int)total, Mmax, DF);
+  // the double-float L = 4 variant keeps at most 16 sites' vectors (M = 64)
+  // beside the factor in its 48 KB of static shared memory
+  constexpr int Gmin = (DF && LMAX == 4) ? 8 : 4;
+  G = G < Gmin ? Gmin : G;
   g.start[0] = 0;
   for (int k = 0; k < g.n; ++k) {
-    const int gk = g.slot[k].L == 1 && G > 4 ? 4 : G;
+    const int gk = DF ? df_lanes(g.slot[k].L, G) : (g.slot[k].L == 1 && G > 4 ? 4 : G);
     g.start[k + 1] = g.start[k] + (g.slot[k].n + threads / gk - 1) / (threads / gk);
   }
   switch (G) {
-    case 4: weights_grp_kernel<4, LMAX, DF><<<g.start[g.n], threads, 0, s>>>(g); break;
+    case 4: weights_grp_kernel<Gmin, LMAX, DF><<<g.start[g.n], threads, 0, s>>>(g); break;
     case 8: weights_grp_kernel<8, LMAX, DF><<<g.start[g.n], threads, 0, s>>>(g); break;
     case 16: weights_grp_kernel<16, LMAX, DF><<<g.start[g.n], threads, 0, s>>>(g); break;
     default: weights_grp_kernel<32, LMAX, DF><<<g.start[g.n], threads, 0, s>>>(g); break;
@@ -415,6 +448,49 @@ cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, 
   g.n = 1;
   g.slot[0] = weights_slot(xy, n, p, box, w64, w32, ssd, flag);
   return launch_weights_group(g, s);
+}
+
+// The double copy of weights held as float pairs (RK_FP32 plans).
+__global__ void convert_weights_kernel(const float2* __restrict__ wdf, size_t count,
+                                       double* __restrict__ w64) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = wdf[t];
+    w64[t] = (double)v.x + (double)v.y;
+  }
+}
+
+cudaError_t launch_convert_weights(const float2* wdf, size_t count, double* w64, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  size_t blocks = (count + 255) / 256;
+  blocks = blocks > 1216 ? 1216 : blocks;
+  convert_weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(wdf, count, w64);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- coefficients --
+// Several plans' coefficient copies (rk_set_coef_group) in one launch: slot k
+// covers CTAs [start[k], start[k + 1]).
+__global__ void copy_group_kernel(const __grid_constant__ Group<CopySlot> g) {
+  int ks = 0;
+  while (ks + 1 < g.n && (int)blockIdx.x >= g.start[ks + 1]) ++ks;
+  const CopySlot& sl = g.slot[ks];
+  const long long ctas = g.start[ks + 1] - g.start[ks];
+  for (long long t = (blockIdx.x - g.start[ks]) * (long long)blockDim.x + threadIdx.x;
+       t < sl.count; t += ctas * blockDim.x)
+    sl.dst[t] = sl.src[t];
+}
+
+cudaError_t launch_copy_group(Group<CopySlot>& g, cudaStream_t s) {
+  g.start[0] = 0;
+  for (int k = 0; k < g.n; ++k) {
+    long long c = (g.slot[k].count + 1023) / 1024;
+    c = c < 1 ? 1 : c > 256 ? 256 : c;
+    g.start[k + 1] = g.start[k] + (int)c;
+  }
+  if (g.n == 0) return cudaSuccess;
+  copy_group_kernel<<<g.start[g.n], 256, 0, s>>>(g);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ set weights --

@@ -180,6 +180,9 @@ struct ProfScope {
   ProfScope prof_scope_##__LINE__(name, (double)(bytes), (double)(flops), 64, s)
 #define RK_PROFDF(name, bytes, flops) \
   ProfScope prof_scope_##__LINE__(name, (double)(bytes), (double)(flops), 2, s)
+// the pipe chosen at run time: 64 (FP64) or 2 (double-float)
+#define RK_PROFP(name, bytes, flops, pipe) \
+  ProfScope prof_scope_##__LINE__(name, (double)(bytes), (double)(flops), (pipe), s)
 
 rk_status read_flag(rk_plan* p, int* value) {
   RK_CU(cudaMemcpyAsync(value, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
@@ -365,6 +368,16 @@ rk_status ensure_coef(rk_plan* p, int B) {
 rk_status finish_coef(rk_plan* p, int B) {
   p->B = B;
   p->have_coef = true;
+  return RK_OK;
+}
+
+// RK_FP32 plans' weights come as float pairs (and floats); the double copy,
+// which the adjoint, conditional simulation and rk_debug_copy read, is formed
+// from the pairs on first use after a site update.
+rk_status ensure_w64(rk_plan* p) {
+  if (!p->w64_stale) return RK_OK;
+  RK_CU(launch_convert_weights(p->wdf, (size_t)p->n * p->M, p->w64, p->stream));
+  p->w64_stale = false;
   return RK_OK;
 }
 
@@ -599,6 +612,7 @@ constexpr int kCsSolve = 512;    // right-hand sides per FP64 solve
 // prediction of every c_r with f_u,r added in the last pass.
 template <typename T>
 rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
+  RK_TRY(ensure_w64(p));
   cudaStream_t s = p->stream;
   const float2* sdf = sizeof(T) == sizeof(float) ? p->mchol_df : nullptr;
   const int n = p->n;
@@ -674,6 +688,7 @@ rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
 // ------------------------------------------------------------------ adjoint --
 rk_status ensure_adjoint(rk_plan* p) {
   if (p->have_adj) return RK_OK;
+  RK_TRY(ensure_w64(p));
   if (!p->dlam64) RK_TRY(compute_spectrum(p, 1, &p->dlam64, &p->dlam32));
   if (!p->kn_dlog) {
     RK_TRY(dalloc(&p->kn_dlog, (size_t)p->M * p->M));
@@ -1041,6 +1056,7 @@ rk_status rk_set_weights(rk_plan* p, int n, const int* box, const double* w) {
   p->xy_valid = false;
   RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
   RK_CU(launch_set_weights(box, w, n, p, p->box, p->w64, p->w32, p->ssd, p->d_flag, p->stream));
+  p->w64_stale = false;
   int flag = 0;
   RK_TRY(read_flag(p, &flag));
   if (flag & 4) return RK_ERR_INVALID_ARG;
@@ -1054,10 +1070,10 @@ rk_status rk_set_sites(rk_plan* p, int n, const double* xy) {
   if (!p || n < 1 || !xy) return RK_ERR_INVALID_ARG;
   RK_TRY(ensure_sites(p, n));
   p->xy_valid = true;
-  RK_CU(cudaMemcpyAsync(p->xy, xy, (size_t)2 * n * sizeof(double), cudaMemcpyDeviceToDevice,
-                        p->stream));
   RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
-  RK_CU(launch_weights(p->xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_flag, p->stream));
+  // the weights kernel reads xy and writes the plan's copy of it
+  RK_CU(launch_weights(xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_flag, p->stream));
+  p->w64_stale = p->precision == RK_FP32;
   RK_CU(launch_tile_sites(p->box, n, p, true, p->stream));   // clears the weights' counts
   int flag = 0;
   RK_TRY(read_flag(p, &flag));
@@ -1072,13 +1088,12 @@ rk_status rk_set_sites_async(rk_plan* p, int n, const double* xy) {
   if (n > p->n_cap) return RK_ERR_STATE;
   RK_TRY(ensure_sites(p, n));   // no growth: only resets the derived state
   p->xy_valid = true;
-  RK_CU(cudaMemcpyAsync(p->xy, xy, (size_t)2 * n * sizeof(double), cudaMemcpyDeviceToDevice,
-                        p->stream));
   cudaStream_t s = p->stream;
   {
-    RK_PROF64("weights", (double)n * (16.0 + 12.0 * p->M + 16.0) + 8.0 * p->M * p->M,
-              (double)n * (2.0 * p->M * p->M + 10.0 * p->M));
-    RK_CU(launch_weights(p->xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_sites_flag, s));
+    RK_PROFP("weights", (double)n * (16.0 + 12.0 * p->M + 16.0) + 8.0 * p->M * p->M,
+             (double)n * (2.0 * p->M * p->M + 10.0 * p->M), p->precision == RK_FP32 ? 2 : 64);
+    RK_CU(launch_weights(xy, n, p, p->box, p->w64, p->w32, p->ssd, p->d_sites_flag, s));
+    p->w64_stale = p->precision == RK_FP32;
   }
   {
     RK_PROF("tile_sites", (double)n * 24.0);
@@ -1102,12 +1117,12 @@ rk_status rk_set_sites_group(rk_plan* const* plans, int nplans, const int* n,
   rk_plan* p0 = plans[0];
   cudaStream_t s = p0->stream;
   double wb = 0, wf = 0, fb = 0, ff = 0;
+  bool all32 = true;
   for (int k = 0; k < nplans; ++k) {
     rk_plan* p = plans[k];
     RK_TRY(ensure_sites(p, n[k]));   // no growth: only resets the derived state
     p->xy_valid = true;
-    RK_CU(cudaMemcpyAsync(p->xy, xy[k], (size_t)2 * n[k] * sizeof(double),
-                          cudaMemcpyDeviceToDevice, s));
+    all32 = all32 && p->precision == RK_FP32;
     wb += (double)n[k] * (16.0 + 12.0 * p->M + 16.0) + 8.0 * p->M * p->M;
     wf += (double)n[k] * (2.0 * p->M * p->M + 10.0 * p->M);
     if (p->precision == RK_FP32 && p->nblk > 0) {
@@ -1116,14 +1131,15 @@ rk_status rk_set_sites_group(rk_plan* const* plans, int nplans, const int* n,
     }
   }
   {
-    RK_PROF64("weights", wb, wf);
+    RK_PROFP("weights", wb, wf, all32 ? 2 : 64);
     Group<WeightsSlot> g;               // one launch for every plan, whatever its L
     for (int k = 0; k < nplans; ++k) {
       rk_plan* p = plans[k];
-      g.slot[g.n++] = weights_slot(p->xy, n[k], p, p->box, p->w64, p->w32, p->ssd,
+      g.slot[g.n++] = weights_slot(xy[k], n[k], p, p->box, p->w64, p->w32, p->ssd,
                                    p->d_sites_flag);
     }
     RK_CU(launch_weights_group(g, s));
+    for (int k = 0; k < nplans; ++k) plans[k]->w64_stale = plans[k]->precision == RK_FP32;
   }
   {
     RK_PROF("tile_sites", 0.0);
@@ -1167,6 +1183,27 @@ rk_status rk_set_coef(rk_plan* p, int B, const double* c) {
   return finish_coef(p, B);
 }
 
+rk_status rk_set_coef_group(rk_plan* const* plans, int nplans, const int* B,
+                           const double* const* c) {
+  if (!plans || !B || !c || nplans < 1 || nplans > kMaxGroup || !plans[0])
+    return RK_ERR_INVALID_ARG;
+  for (int k = 0; k < nplans; ++k) {
+    if (!plans[k] || B[k] < 1 || !c[k]) return RK_ERR_INVALID_ARG;
+    if (plans[k]->n == 0) return RK_ERR_STATE;
+    for (int j = 0; j < k; ++j)
+      if (plans[j] == plans[k]) return RK_ERR_INVALID_ARG;
+  }
+  Group<CopySlot> g;
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    RK_TRY(ensure_coef(p, B[k]));
+    g.slot[g.n++] = CopySlot{c[k], p->c64, (long long)B[k] * p->n};
+  }
+  RK_CU(launch_copy_group(g, plans[0]->stream));
+  for (int k = 0; k < nplans; ++k) RK_TRY(finish_coef(plans[k], B[k]));
+  return RK_OK;
+}
+
 rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
   if (!p || B < 1 || !z) return RK_ERR_INVALID_ARG;
   if (p->n == 0 || !p->xy_valid) return RK_ERR_STATE;
@@ -1187,6 +1224,7 @@ rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
         p->mchol_df_cap = (size_t)n * n;
       }
       RK_CU(chol_split(p->mchol, n, p->mchol_df, p->stream));
+      RK_CU(chol_invert_diag_df(p->mchol, n, p->mchol_df, p->stream));
     }
     int flag = 0;
     RK_TRY(read_flag(p, &flag));
@@ -1329,7 +1367,11 @@ rk_status rk_debug_copy(rk_plan* p, int what, void* dst, size_t bytes) {
   size_t need = 0;
   switch (what) {
     case 0: src = p->box; need = (size_t)2 * p->n * sizeof(int); break;
-    case 1: src = p->w64; need = (size_t)p->n * p->M * sizeof(double); break;
+    case 1:
+      RK_TRY(ensure_w64(p));
+      src = p->w64;
+      need = (size_t)p->n * p->M * sizeof(double);
+      break;
     case 2:
       src = p->precision == RK_FP64 ? (const void*)p->lam64 : (const void*)p->lam32;
       need = (size_t)p->H * p->py * esz;

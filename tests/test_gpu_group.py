@@ -105,8 +105,8 @@ def test_grouped_site_updates_equal_single_updates(rk):
         single = [p.predict().double().cpu().numpy() for p in plans]
         xys = [torch.from_numpy(xy).cuda() for xy, _, _, _ in coefs]
         rk.set_sites_group(plans, xys)
-        for p, (xy, c, g, th) in zip(plans, coefs):
-            p.set_coef(torch.from_numpy(np.atleast_2d(c)).cuda())
+        rk.set_coef_group(plans, [torch.from_numpy(np.atleast_2d(c)).cuda()
+                                  for _, c, _, _ in coefs])
         outs = rk.predict_group(plans)
         torch.cuda.synchronize()
         for p, o, s in zip(plans, outs, single):
@@ -123,6 +123,36 @@ def test_grouped_site_updates_equal_single_updates(rk):
                 assert e.value.name == "RK_ERR_OBS_OUTSIDE"
             else:
                 p.check_sites()
+    finally:
+        for p in plans:
+            p.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp64", 1e-12)])
+def test_grouped_updates_keep_the_plans_sites_and_coefficients(rk, prec, tol):
+    # the weights kernel writes each plan's copy of its sites (no separate
+    # copy) and rk_set_coef_group copies every plan's coefficients in one
+    # launch: a later rk_solve_coef (which builds M from the plan's sites)
+    # and prediction equal a fresh plan given the same data
+    ext = (0.0, 1.6, 0.0, 1.0)
+    cells = [(0.5, 1), (1.5, 2), (2.5, 3)]
+    plans, coefs = _plans(rk, 120, ext, cells, prec, n=300)
+    new_xy = [np.ascontiguousarray(xy[::-1]) for xy, _, _, _ in coefs]   # new site order
+    try:
+        rk.set_sites_group(plans, [torch.from_numpy(x).cuda() for x in new_xy])
+        cs = [torch.from_numpy(np.atleast_2d(c)[:, ::-1].copy()).cuda() for _, c, _, _ in coefs]
+        rk.set_coef_group(plans, cs)
+        got = [o.double().cpu().numpy() for o in rk.predict_group(plans)]
+        for k, (p, (xy, c, g, th)) in enumerate(zip(plans, coefs)):
+            with rk.Plan(120, 120, ext, *th, 1e-3, g.L, precision=prec) as q:
+                q.set_sites(torch.from_numpy(new_xy[k]).cuda())
+                q.set_coef(cs[k])
+                assert rel_err(got[k], q.predict().double().cpu().numpy()) <= tol
+                z = torch.from_numpy(np.atleast_2d(np.sin(7 * new_xy[k][:, 0]))).cuda()
+                p.solve_coef(z)
+                q.solve_coef(z)
+                assert rel_err(p.predict().double().cpu().numpy(),
+                               q.predict().double().cpu().numpy()) <= tol
     finally:
         for p in plans:
             p.close()
