@@ -345,6 +345,8 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
                        const float2* adf = nullptr);
 cudaError_t chol_split(const double* a, int n, float2* adf, cudaStream_t s);
 cudaError_t chol_invert_diag_df(const double* a, int n, float2* adf, cudaStream_t s);
+// doubles split into float pairs (hi, lo)
+cudaError_t launch_split_pairs(const double* src, size_t count, float2* dst, cudaStream_t s);
 
 // conditional simulation
 template <typename T>
@@ -376,6 +378,9 @@ template <typename Ta, typename Tb>
 cudaError_t launch_dot_rows(const Ta* a, const Tb* b, int B, long long len, double scale,
                             int accumulate, double* out, cudaStream_t s);
 size_t dkxx_scratch_doubles(int n, int B);
+cudaError_t launch_matvec_dkxx_df(const double* xy, int n, const double* c, int B, double rho,
+                                  double sigma2, int nu_code, double* scratch, double* out,
+                                  cudaStream_t s);
 cudaError_t launch_matvec_dkxx(const double* xy, int n, const double* c, int B, double rho,
                                double sigma2, int nu_code, double* part, double* out,
                                cudaStream_t s);

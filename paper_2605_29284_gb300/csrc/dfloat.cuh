@@ -20,7 +20,22 @@ __device__ __forceinline__ dfl df_make(double d) {
   return {h, (float)(d - (double)h)};
 }
 
-__device__ __forceinline__ double df_double(dfl a) { return (double)a.hi + (double)a.lo; }
+// float -> double from the IEEE 754 encodings (binary32 -> binary64: the
+// exponent rebiased by 1023 - 127, the significand moved up 52 - 23 bits):
+// exact for normal floats; zeros and subnormals give a signed zero,
+// infinities and NaNs keep their class.  Integer instructions only: the
+// conversion instruction runs on GB300's FP64 pipe (1/64 of the FP32 rate).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned ed = e == 0u ? 0u : e == 0xffu ? 0x7ffu : e + 896u;
+  const unsigned m = e == 0u ? 0u : (u & 0x7fffffu);
+  const unsigned hi = (u & 0x80000000u) | (ed << 20) | (m >> 3);
+  return __hiloint2double((int)hi, (int)(m << 29));
+}
+
+// hi + lo in double: one FP64 addition
+__device__ __forceinline__ double df_double(dfl a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -108,6 +123,30 @@ __device__ __forceinline__ dfl df_exp_neg(dfl d) {
 // complex double-float: (re.hi, re.lo, im.hi, im.lo) in a float4
 __device__ __forceinline__ float4 cdf_pack(dfl re, dfl im) {
   return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+// The Matern closed forms of phi (nu = 1/2, 3/2, 5/2; see matern_phi) and of
+// -t phi'(t) (see matern_dlogrho) in double-float, for d, t >= 0.
+__device__ __forceinline__ dfl matern_phi_df(dfl d, int nu_code) {
+  const dfl e = df_exp_neg(d);
+  const dfl one = {1.f, 0.f};
+  if (nu_code == 0) return e;
+  if (nu_code == 1) return df_mul(df_add(one, d), e);
+  constexpr double kThird = 1.0 / 3.0;
+  constexpr float kThirdHi = (float)kThird;
+  const dfl third = {kThirdHi, (float)(kThird - (double)kThirdHi)};
+  return df_mul(df_fma(d, df_fma(d, third, one), one), e);   // 1 + d + d^2 / 3
+}
+
+__device__ __forceinline__ dfl matern_dlogrho_df(dfl t, int nu_code) {
+  const dfl e = df_exp_neg(t);
+  if (nu_code == 0) return df_mul(t, e);
+  const dfl t2e = df_mul(df_mul(t, t), e);
+  if (nu_code == 1) return t2e;
+  constexpr double kThird = 1.0 / 3.0;
+  constexpr float kThirdHi = (float)kThird;
+  const dfl third = {kThirdHi, (float)(kThird - (double)kThirdHi)};
+  return df_mul(df_mul(t2e, third), df_add({1.f, 0.f}, t));   // (t^2 / 3)(1 + t) e^-t
 }
 
 }  // namespace rk

@@ -6,6 +6,7 @@
 //   d/dlog rho     = gbar . (K'_gg A^T c + K_gg A'^T c) - zbar^T K'_xx c,
 // where ' is d / dlog rho and A' has rows W_i' = K_N^{-1} (k_i' - K_N' W_i).
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace rk {
 
@@ -299,9 +300,124 @@ __global__ void dkxx_reduce_kernel(const double* __restrict__ part, int n, int B
   out[(size_t)f * n + i] = acc;
 }
 
+// RK_FP32 plans: the same product in double-float on the FP32 pipe (the
+// entries' exponentials and the sums are FP64 work otherwise, at 1/64 of the
+// FP32 rate): sites and coefficients split into float pairs first, partial
+// vectors as pairs, summed in the same fixed order.
+__global__ void __launch_bounds__(256) matvec_dkxx_df_kernel(const float2* __restrict__ xydf,
+                                                             int n, const float2* __restrict__ cdf,
+                                                             int B, float2 inv_rho, float2 sigma2,
+                                                             int nu_code,
+                                                             float2* __restrict__ part) {
+  __shared__ float2 Ks[kDT][kDT + 1];
+  __shared__ float2 xi[kDT], yi[kDT], xj[kDT], yj[kDT];
+  __shared__ float2 cI[kDF][kDT], cJ[kDF][kDT];
+  const int tile = blockIdx.x;
+  int J = (int)((sqrtf(8.0f * tile + 1.0f) - 1.0f) * 0.5f);   // tiles (I, J), I <= J
+  while ((J + 1) * (J + 2) / 2 <= tile) ++J;
+  while (J * (J + 1) / 2 > tile) --J;
+  const int I = tile - J * (J + 1) / 2;
+  const int i0 = I * kDT, j0 = J * kDT;
+  const float2 zero = make_float2(0.f, 0.f);
+  if (threadIdx.x < kDT) {
+    const int t = threadIdx.x;
+    xi[t] = i0 + t < n ? xydf[2 * (i0 + t)] : zero;
+    yi[t] = i0 + t < n ? xydf[2 * (i0 + t) + 1] : zero;
+    xj[t] = j0 + t < n ? xydf[2 * (j0 + t)] : zero;
+    yj[t] = j0 + t < n ? xydf[2 * (j0 + t) + 1] : zero;
+  }
+  __syncthreads();
+  const dfl ir = {inv_rho.x, inv_rho.y}, s2 = {sigma2.x, sigma2.y};
+  for (int e = threadIdx.x; e < kDT * kDT; e += blockDim.x) {
+    const int a = e / kDT, b = e % kDT;
+    dfl v = {0.f, 0.f};
+    if (i0 + a < n && j0 + b < n) {
+      const dfl dx = df_add({xi[a].x, xi[a].y}, {-xj[b].x, -xj[b].y});
+      const dfl dy = df_add({yi[a].x, yi[a].y}, {-yj[b].x, -yj[b].y});
+      const dfl t = df_mul(df_sqrt(df_fma(dx, dx, df_mul(dy, dy))), ir);
+      v = df_mul(s2, matern_dlogrho_df(t, nu_code));
+    }
+    Ks[a][b] = make_float2(v.hi, v.lo);
+  }
+  const bool diag = I == J;
+  for (int f0 = 0; f0 < B; f0 += kDF) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kDF * kDT; e += blockDim.x) {
+      const int f = e / kDT, t = e % kDT;
+      const bool fo = f0 + f < B;
+      cI[f][t] = fo && i0 + t < n ? cdf[(size_t)(f0 + f) * n + i0 + t] : zero;
+      cJ[f][t] = fo && j0 + t < n ? cdf[(size_t)(f0 + f) * n + j0 + t] : zero;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * kDF * kDT; e += blockDim.x) {
+      const bool rows = e < kDF * kDT;
+      const int ee = rows ? e : e - kDF * kDT;
+      const int f = ee / kDT, t = ee % kDT;
+      if (f0 + f >= B || (!rows && diag)) continue;
+      dfl acc = {0.f, 0.f};
+      if (rows) {
+#pragma unroll 4
+        for (int b = 0; b < kDT; ++b) {
+          const float2 k = Ks[t][b], x = cJ[f][b];
+          acc = df_fma({k.x, k.y}, {x.x, x.y}, acc);
+        }
+      } else {
+#pragma unroll 4
+        for (int a = 0; a < kDT; ++a) {
+          const float2 k = Ks[a][t], x = cI[f][a];
+          acc = df_fma({k.x, k.y}, {x.x, x.y}, acc);
+        }
+      }
+      part[(((size_t)tile * 2 + (rows ? 0 : 1)) * B + f0 + f) * kDT + t] =
+          make_float2(acc.hi, acc.lo);
+    }
+  }
+}
+
+__global__ void dkxx_reduce_df_kernel(const float2* __restrict__ part, int n, int B, int T,
+                                      double* __restrict__ out) {
+  const int K = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
+  const int i = K * kDT + t;
+  if (i >= n) return;
+  dfl acc = {0.f, 0.f};
+  for (int J = K; J < T; ++J) {
+    const size_t tile = (size_t)J * (J + 1) / 2 + K;
+    const float2 v = part[((tile * 2 + 0) * B + f) * kDT + t];
+    acc = df_add(acc, {v.x, v.y});
+  }
+  for (int I = 0; I < K; ++I) {
+    const size_t tile = (size_t)K * (K + 1) / 2 + I;
+    const float2 v = part[((tile * 2 + 1) * B + f) * kDT + t];
+    acc = df_add(acc, {v.x, v.y});
+  }
+  out[(size_t)f * n + i] = df_double(acc);
+}
+
+// partial vectors (and, for the double-float product, the split sites and
+// coefficients after them), in doubles
 size_t dkxx_scratch_doubles(int n, int B) {
   const size_t T = (size_t)(n + kDT - 1) / kDT;
-  return T * (T + 1) / 2 * 2 * (size_t)B * kDT;
+  return T * (T + 1) / 2 * 2 * (size_t)B * kDT + 2 * (size_t)n + (size_t)B * n;
+}
+
+cudaError_t launch_matvec_dkxx_df(const double* xy, int n, const double* c, int B, double rho,
+                                  double sigma2, int nu_code, double* scratch, double* out,
+                                  cudaStream_t s) {
+  const int T = (n + kDT - 1) / kDT;
+  const size_t tiles = (size_t)T * (T + 1) / 2;
+  float2* part = reinterpret_cast<float2*>(scratch);
+  float2* xydf = part + tiles * 2 * (size_t)B * kDT;
+  float2* cdf = xydf + 2 * (size_t)n;
+  cudaError_t e = launch_split_pairs(xy, 2 * (size_t)n, xydf, s);
+  if (e == cudaSuccess) e = launch_split_pairs(c, (size_t)B * n, cdf, s);
+  if (e != cudaSuccess) return e;
+  const double ir = 1.0 / rho;
+  const float irh = (float)ir, s2h = (float)sigma2;
+  matvec_dkxx_df_kernel<<<(unsigned)tiles, 256, 0, s>>>(
+      xydf, n, cdf, B, make_float2(irh, (float)(ir - (double)irh)),
+      make_float2(s2h, (float)(sigma2 - (double)s2h)), nu_code, part);
+  dkxx_reduce_df_kernel<<<dim3(T, B), kDT, 0, s>>>(part, n, B, T, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_matvec_dkxx(const double* xy, int n, const double* c, int B, double rho,

@@ -371,6 +371,14 @@ cudaError_t chol_split(const double* a, int n, float2* adf, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_split_pairs(const double* src, size_t count, float2* dst, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  size_t blocks = (count + 255) / 256;
+  blocks = blocks > 2048 ? 2048 : blocks;
+  chol_split_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, count, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
                        const float2* adf) {
   if (n <= 0 || B <= 0) return cudaSuccess;

@@ -175,22 +175,12 @@ __device__ __forceinline__ void weights_cta(const WeightsSlot& sl, int cta, doub
 // s_i = sigma sqrt(max(0, 1 - phi^T A_i)).  Rounding of this order keeps the
 // residual K_N A_i - k_i near 1e-13 sigma2 |A_i|, far below what single-
 // precision scatter and transforms resolve.
-__device__ __forceinline__ dfl matern_phi_df(dfl d, int nu_code) {
-  const dfl e = df_exp_neg(d);
-  const dfl one = {1.f, 0.f};
-  if (nu_code == 0) return e;
-  if (nu_code == 1) return df_mul(df_add(one, d), e);
-  constexpr double kThird = 1.0 / 3.0;
-  constexpr float kThirdHi = (float)kThird;
-  const dfl third = {kThirdHi, (float)(kThird - (double)kThirdHi)};
-  return df_mul(df_fma(d, df_fma(d, third, one), one), e);   // 1 + d + d^2 / 3
-}
-
 // The G lanes of a site (one warp holds whole sites, G divides 32) keep the
 // site's vector in shared memory, so the substitution loops stay rolled: a
 // fully unrolled double-float substitution outgrows the instruction cache.
-// Step c: every lane forms the pivot z_c / L_cc from shared memory, updates
-// its own rows r = j + s G, and after a warp barrier the pivot's owner stores it.
+// A step takes two pivots: every lane solves them from shared memory,
+// updates its own rows r = j + s G, and after a warp barrier the pivots'
+// owners store them.
 constexpr int kWeightsDfThreads = 128;
 
 template <int W, int G>
@@ -249,21 +239,27 @@ __device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, f
     z[r] = make_float2(v.hi, v.lo);
   }
   __syncwarp();
+  // two pivots per step (M = 4 L^2 is even): rows c and c + 1 are solved
+  // from the shared vector by every lane, then each lane removes both from
+  // its rows below them, one warp barrier per pair
 #pragma unroll 1
-  for (int c = 0; c < M; ++c) {          // L y = phi
-    const float2 zv = z[c], li = Linv[c];
-    const dfl zc = df_mul({zv.x, zv.y}, {li.x, li.y});
+  for (int c = 0; c < M; c += 2) {       // L y = phi
+    const float2 v0 = z[c], v1 = z[c + 1], i0 = Linv[c], i1 = Linv[c + 1];
+    const float2 l10 = Ls[(c + 1) * M + c];
+    const dfl y0 = df_mul({v0.x, v0.y}, {i0.x, i0.y});
+    const dfl y1 = df_mul(df_fma({-l10.x, -l10.y}, y0, {v1.x, v1.y}), {i1.x, i1.y});
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const int r = j + s * G;
-      if (r > c && r < M) {
-        const float2 l = Ls[r * M + c], zr = z[r];
-        const dfl u = df_fma({-l.x, -l.y}, zc, {zr.x, zr.y});
+      if (r > c + 1 && r < M) {
+        const float2 la = Ls[r * M + c], lb = Ls[r * M + c + 1], zr = z[r];
+        const dfl u = df_fma({-lb.x, -lb.y}, y1, df_fma({-la.x, -la.y}, y0, {zr.x, zr.y}));
         z[r] = make_float2(u.hi, u.lo);
       }
     }
     __syncwarp();
-    if (j == c % G) z[c] = make_float2(zc.hi, zc.lo);
+    if (j == c % G) z[c] = make_float2(y0.hi, y0.lo);
+    if (j == (c + 1) % G) z[c + 1] = make_float2(y1.hi, y1.lo);
   }
   __syncwarp();
   // phi^T A_i = |y|^2: each lane's rows, then a sum over the site's lanes
@@ -277,20 +273,23 @@ __device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, f
     yy = df_add(yy, {__shfl_xor_sync(0xffffffffu, yy.hi, o, G),
                      __shfl_xor_sync(0xffffffffu, yy.lo, o, G)});
 #pragma unroll 1
-  for (int c = M - 1; c >= 0; --c) {     // L^T w = y
-    const float2 zv = z[c], li = Linv[c];
-    const dfl wc = df_mul({zv.x, zv.y}, {li.x, li.y});
+  for (int c = M - 1; c > 0; c -= 2) {   // L^T w = y, rows c and c - 1 per step
+    const float2 v0 = z[c], v1 = z[c - 1], i0 = Linv[c], i1 = Linv[c - 1];
+    const float2 l01 = Ls[c * M + c - 1];
+    const dfl w0 = df_mul({v0.x, v0.y}, {i0.x, i0.y});
+    const dfl w1 = df_mul(df_fma({-l01.x, -l01.y}, w0, {v1.x, v1.y}), {i1.x, i1.y});
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const int r = j + s * G;
-      if (r < c) {
-        const float2 l = Ls[c * M + r], zr = z[r];
-        const dfl u = df_fma({-l.x, -l.y}, wc, {zr.x, zr.y});
+      if (r < c - 1) {
+        const float2 la = Ls[c * M + r], lb = Ls[(c - 1) * M + r], zr = z[r];
+        const dfl u = df_fma({-lb.x, -lb.y}, w1, df_fma({-la.x, -la.y}, w0, {zr.x, zr.y}));
         z[r] = make_float2(u.hi, u.lo);
       }
     }
     __syncwarp();
-    if (j == c % G) z[c] = make_float2(wc.hi, wc.lo);
+    if (j == c % G) z[c] = make_float2(w0.hi, w0.lo);
+    if (j == (c - 1) % G) z[c - 1] = make_float2(w1.hi, w1.lo);
   }
   __syncwarp();
   if (!act) return;
@@ -318,12 +317,9 @@ __device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, f
 // (M = 64) has a kernel of its own: its register needs would cap the others'
 // occupancy.
 // Lanes per site of the double-float variant for neighbourhood size L, from
-// the launch's G: 4 for L = 1, G for L = 2, 2G (at most 32) for L >= 3, whose
-// 2M-step substitution chains are the longest: more lanes per site keep
-// more of them in flight and shorten each step.
-constexpr int df_lanes(int L, int G) {
-  return L == 1 ? 4 : L == 2 ? G : (2 * G > 32 ? 32 : 2 * G);
-}
+// the launch's G: 4 for L = 1 (M = 4), G otherwise.  (2G for L >= 3 doubled
+// the warps in flight but also the per-step instructions, and was slower.)
+constexpr int df_lanes(int L, int G) { return L == 1 ? 4 : G; }
 
 // DF selects the double-float variant (every slot of the launch has dfw set).
 template <int G, int LMAX, bool DF>
@@ -456,7 +452,7 @@ __global__ void convert_weights_kernel(const float2* __restrict__ wdf, size_t co
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
        t += (size_t)gridDim.x * blockDim.x) {
     const float2 v = wdf[t];
-    w64[t] = (double)v.x + (double)v.y;
+    w64[t] = df_double({v.x, v.y});
   }
 }
 
@@ -637,67 +633,99 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
 // for the FP64 block GEMM.  The block only has to be far more accurate than
 // the single-precision transforms it corrects; double-float (about 2^-47 per
 // operation) is, and runs at 64x the FP64 rate.
-__device__ __forceinline__ void cdf_fma(dfl ar, dfl ai, dfl br, dfl bi, dfl& cr, dfl& ci) {
-  cr = df_fma(ar, br, df_fma(df_neg(ai), bi, cr));
-  ci = df_fma(ar, bi, df_fma(ai, br, ci));
+// Threads: NS sites per CTA (a power of two, the fastest index, so the
+// factors' writes coalesce) times 128 / NS lanes over a site's (kx, b) and
+// (kx, ky) pairs; W = 2L is a compile-time constant, so the pair indices
+// split cheaply.  NS = 16 unless the row sums (NS (KX + 1) W float4) would
+// pass 96 KB of shared memory.
+constexpr int kBfThreads = 128;
+constexpr int kBfSites = 16;
+
+template <int W>
+__device__ __forceinline__ void block_factor_df_cta(const BlockFactorDfSlot& sl, int cta,
+                                                    float4* tsm) {
+  constexpr int M = W * W;
+  const int* __restrict__ box = sl.box;
+  const float2* __restrict__ wdf = sl.wdf;
+  double2* __restrict__ efac = sl.efac;
+  const int n = sl.n, px = sl.px, py = sl.py, KY = sl.KY;
+  const int nk = sl.KX + 1, nky = KY + 1, bw = 2 * KY + 1;
+  const int NS = sl.NS, lanes = kBfThreads / NS;
+  const float4* __restrict__ twx = sl.twx;
+  const float4* __restrict__ twy = sl.twy;
+  const int si = threadIdx.x & (NS - 1), lane = threadIdx.x / NS;
+  const int i = cta * NS + si;
+  const bool live = i < n;
+  const int ix = live ? box[2 * i] : 0, iy = live ? box[2 * i + 1] : 0;
+  // stage 1: t(kx, b) = sum_a A_i[a + W b] e^{-2 pi i kx (ix + a) / px}
+  for (int p = lane; p < nk * W; p += lanes) {
+    const int kx = p / W, b = p - kx * W;
+    dfl tr = {0.f, 0.f}, ti = {0.f, 0.f};
+    if (live) {
+      int m = (kx * ix) % px;               // kx (ix + a) mod px, stepped by kx
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        const float4 tw = twx[m];
+        const float2 wv = wdf[(size_t)i * M + a + W * b];
+        const dfl w = {wv.x, wv.y};
+        tr = df_fma(w, {tw.x, tw.y}, tr);
+        ti = df_fma(w, {tw.z, tw.w}, ti);
+        m += kx;
+        m = m >= px ? m - px : m;
+      }
+    }
+    tsm[(si * nk + kx) * W + b] = make_float4(tr.hi, tr.lo, ti.hi, ti.lo);
+  }
+  __syncthreads();
+  if (!live) return;
+  // stage 2, ky and -ky together: with t = tr + i ti and f = e^{-2 pi i ky
+  // (iy + b) / py}, e^{+2 pi i ...} = conj(f), so from A = sum tr fr,
+  // B = sum ti fi, C = sum tr fi, D = sum ti fr:  E(ky) = (A - B) + i (C + D)
+  // and E(-ky) = (A + B) + i (D - C): four real products per term for both
+  for (int q = lane; q < nk * nky; q += lanes) {
+    const int kx = q / nky, ky = q - kx * nky;
+    const float4* t = tsm + (si * nk + kx) * W;
+    dfl A = {0.f, 0.f}, Bs = {0.f, 0.f}, Cs = {0.f, 0.f}, D = {0.f, 0.f};
+    int m = (ky * iy) % py;                 // ky (iy + b) mod py, stepped by ky
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      const float4 f = twy[m], tb = t[b];
+      const dfl fr = {f.x, f.y}, fi = {f.z, f.w}, tr = {tb.x, tb.y}, ti = {tb.z, tb.w};
+      A = df_fma(tr, fr, A);
+      Bs = df_fma(ti, fi, Bs);
+      Cs = df_fma(tr, fi, Cs);
+      D = df_fma(ti, fr, D);
+      m += ky;
+      m = m >= py ? m - py : m;
+    }
+    double2* out = efac + (size_t)kx * bw * n + i;
+    out[(size_t)(KY + ky) * n] = make_double2(df_double(df_add(A, df_neg(Bs))),
+                                             df_double(df_add(Cs, D)));
+    if (ky > 0)
+      out[(size_t)(KY - ky) * n] = make_double2(df_double(df_add(A, Bs)),
+                                               df_double(df_add(D, df_neg(Cs))));
+  }
 }
 
-__global__ void block_factor_df_kernel(const __grid_constant__ Group<BlockFactorDfSlot> g) {
-  extern __shared__ float4 tsm4[];        // [NS][KX + 1][2L]
+__global__ void __launch_bounds__(kBfThreads)
+block_factor_df_kernel(const __grid_constant__ Group<BlockFactorDfSlot> g) {
+  extern __shared__ float4 tsm4[];        // [kBfSites][KX + 1][2L]
   int ks = 0;
   while (ks + 1 < g.n && (int)blockIdx.x >= g.start[ks + 1]) ++ks;
   const BlockFactorDfSlot& sl = g.slot[ks];
-  const int* __restrict__ box = sl.box;
-  const float2* __restrict__ wdf = sl.wdf;
-  const float4* __restrict__ twx = sl.twx;
-  const float4* __restrict__ twy = sl.twy;
-  double2* __restrict__ efac = sl.efac;
-  const int n = sl.n, px = sl.px, py = sl.py, KY = sl.KY, NS = sl.NS;
-  const int W = 2 * sl.L, M = W * W, nk = sl.KX + 1, bw = 2 * KY + 1;
-  const int i0 = (blockIdx.x - g.start[ks]) * NS;
-  const int ns = min(NS, n - i0);
-  for (int e = threadIdx.x; e < ns * nk * W; e += blockDim.x) {
-    const int b = e % W, kx = (e / W) % nk, si = e / (W * nk);
-    const int i = i0 + si, ix = box[2 * i];
-    dfl tr = {0.f, 0.f}, ti = {0.f, 0.f};
-    int m = (kx * ix) % px;                 // kx (ix + a) mod px, stepped by kx
-    for (int a = 0; a < W; ++a) {
-      const float4 tw = twx[m];
-      const float2 wv = wdf[(size_t)i * M + a + W * b];
-      const dfl w = {wv.x, wv.y};
-      tr = df_fma(w, {tw.x, tw.y}, tr);
-      ti = df_fma(w, {tw.z, tw.w}, ti);
-      m += kx;
-      m = m >= px ? m - px : m;
-    }
-    tsm4[e] = make_float4(tr.hi, tr.lo, ti.hi, ti.lo);    // e = (si * nk + kx) * W + b
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nk * bw * ns; e += blockDim.x) {
-    const int si = e % ns, jj = (e / ns) % bw, kx = e / (ns * bw);
-    const int i = i0 + si, iy = box[2 * i + 1], ky = jj - KY;
-    const float4* t = tsm4 + (si * nk + kx) * W;
-    dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
-    int m = (ky * iy) % py;                 // ky (iy + b) mod py, stepped by ky
-    m = m < 0 ? m + py : m;
-    const int step = ky < 0 ? ky + py : ky;
-    for (int b = 0; b < W; ++b, m = (m + step >= py ? m + step - py : m + step)) {
-      const float4 f = twy[m], tb = t[b];
-      cdf_fma({tb.x, tb.y}, {tb.z, tb.w}, {f.x, f.y}, {f.z, f.w}, ar, ai);
-    }
-    efac[((size_t)kx * bw + jj) * n + i] = make_double2(df_double(ar), df_double(ai));
+  const int cta = blockIdx.x - g.start[ks];
+  switch (sl.L) {
+    case 1: block_factor_df_cta<2>(sl, cta, tsm4); break;
+    case 2: block_factor_df_cta<4>(sl, cta, tsm4); break;
+    case 3: block_factor_df_cta<6>(sl, cta, tsm4); break;
+    default: block_factor_df_cta<8>(sl, cta, tsm4); break;
   }
 }
 
 BlockFactorDfSlot block_factor_df_slot(const rk_plan* p, int n) {
-  const int W = 2 * p->L;
-  const size_t per_site = sizeof(float4) * (size_t)(p->blk_kx + 1) * W;
-  // sites per CTA: four CTAs per SM at least, at most 32 KB of row sums
-  int NS = n / (4 * 152);
-  const int cap = (int)(32768 / per_site);
-  NS = NS > cap ? cap : NS;
-  NS = NS > 32 ? 32 : NS;
-  NS = NS < 1 ? 1 : NS;
+  const size_t per_site = sizeof(float4) * (size_t)(p->blk_kx + 1) * 2 * p->L;
+  int NS = kBfSites;
+  while (NS > 1 && NS * per_site > 96 * 1024) NS /= 2;
   return BlockFactorDfSlot{p->box, p->wdf, p->twdfx, p->twdfy, p->efac, n, p->L, p->px,
                            p->py, p->blk_kx, p->blk_ky, NS};
 }
@@ -715,7 +743,7 @@ cudaError_t launch_block_factors_df_group(Group<BlockFactorDfSlot>& g, cudaStrea
   static int smem_set = 0;
   cudaError_t e = ensure_smem(block_factor_df_kernel, sm, smem_set);
   if (e != cudaSuccess) return e;
-  block_factor_df_kernel<<<g.start[g.n], 128, sm, s>>>(g);
+  block_factor_df_kernel<<<g.start[g.n], kBfThreads, sm, s>>>(g);
   return cudaGetLastError();
 }
 

@@ -791,10 +791,14 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
       RK_TRY(dalloc(&p->bw_dk, need));
       p->bw_dk_cap = need;
     }
-    RK_PROF64("theta_dkxx", (double)n * 16.0 + (double)B * n * 16.0 + need * 16.0,
-              2.0 * n * (double)n * B);
-    RK_CU(launch_matvec_dkxx(p->xy, n, p->c64, B, p->rho, p->sigma2, p->nu_code, p->bw_dk, c3,
-                             s));
+    RK_PROFP("theta_dkxx", (double)n * 16.0 + (double)B * n * 16.0 + need * 16.0,
+             2.0 * n * (double)n * B, f32 ? 2 : 64);
+    if (f32)
+      RK_CU(launch_matvec_dkxx_df(p->xy, n, p->c64, B, p->rho, p->sigma2, p->nu_code, p->bw_dk,
+                                  c3, s));
+    else
+      RK_CU(launch_matvec_dkxx(p->xy, n, p->c64, B, p->rho, p->sigma2, p->nu_code, p->bw_dk, c3,
+                               s));
   }
   if (sdf) {   // double-float updates on the FP32 pipe
     RK_PROFDF("adj_solve", (double)n * n * 8.0 + (double)nsets * B * n * 16.0,
