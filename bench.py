@@ -412,16 +412,17 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 15 * 2 / 1e12
 # captures and commands)
 TRAFFIC = {
     # profiles/cols_grad1024.md: ncu --set full, one launch (16 fields, P = 2187)
-    ("cols", "grad1024"): {"bytes_per_launch": 163313664 + 103914496,
+    ("cols", "grad1024"): {"bytes_per_launch": 163149568 + 98872832,
                            "sources": ["k_fftn.cu", "fftn.cuh", "fft.cuh"],
-                           "digest": "978821fdb35b3e20"},
+                           "digest": "52d5115a63d8320e"},
     # profiles/cols_paper350.md: the grouped column pass of the nine cells
-    ("cols", "paper350"): {"bytes_per_launch": 19767552 + 697600,
+    ("cols", "paper350"): {"bytes_per_launch": 18885120 + 0,
                            "sources": ["k_fftn.cu", "fftn.cuh", "fft.cuh"],
-                           "digest": "978821fdb35b3e20"},
-    # profiles/weights_paper350.md: the grouped weights launch of the nine cells
-    ("weights", "paper350"): {"bytes_per_launch": 383488, "sources": ["k_sites.cu", "common.cuh"],
-                              "digest": "ee65bbd4135356c9"},
+                           "digest": "52d5115a63d8320e"},
+    # profiles/weights_paper350.md: the grouped double-float weights of the nine cells
+    ("weights", "paper350"): {"bytes_per_launch": 132864 + 0,
+                              "sources": ["k_sites.cu", "common.cuh", "dfloat.cuh"],
+                              "digest": "185c28e71c340cb3"},
 }
 
 

@@ -267,7 +267,10 @@ rk_status rk_predict_host(rk_plan* plan, int n, const double* xy_host, int B,
  * nplans <= 16, distinct, one precision, one torus): the copies in, the
  * grouped site update (rk_set_sites_group), the coefficients, the grouped
  * prediction (rk_predict_group) and the copies out, issued on plans[0]'s
- * stream with one synchronisation at the end.
+ * stream with one synchronisation at the end.  When every host buffer is
+ * page-locked, the call's stream work is also captured as a CUDA graph (held
+ * by plans[0]) and later calls with the same plans, sizes and pointers replay
+ * it, as long as no plan buffer has been allocated or released meanwhile.
  *   n[k], xy_host[k]   sites of plans[k] (host, n[k] x 2 doubles)
  *   B[k], c_host[k]    its coefficients (host, B[k] x n[k] doubles)
  *   out_host[k]        its result (host, B[k] x ny x nx, plan precision)

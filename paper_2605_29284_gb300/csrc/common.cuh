@@ -86,6 +86,9 @@ struct DevBuf {
   size_t n = 0;
 };
 
+// at most this many plans in one grouped call
+constexpr int kMaxGroup = 16;
+
 }  // namespace rk
 
 struct rk_plan {
@@ -149,6 +152,7 @@ struct rk_plan {
   int* d_flag = nullptr;                             // device status flag
   int* d_sites_flag = nullptr;                       // latch of rk_set_sites_async
   int* h_flag = nullptr;                             // pinned host copy of the latch
+  int* h_flag_dev = nullptr;                         // its device-side address
   // side stream for the FP64 block GEMM, which runs beside the FP32 row pass
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -179,6 +183,14 @@ struct rk_plan {
   // device staging for rk_predict_host
   double* h_xy = nullptr; size_t h_xy_cap = 0;
   void* h_out = nullptr; size_t h_out_cap = 0;
+  // rk_predict_host_group with page-locked host buffers, captured once as a
+  // CUDA graph (on the group's first plan) and replayed while the key (the
+  // plans, sizes, host pointers and the allocation epoch) is unchanged
+  cudaGraphExec_t hg_exec = nullptr;
+  cudaStream_t hg_stream = nullptr;                  // the capture's stream
+  uint64_t id = 0;                                   // unique per plan of the process
+  uint64_t hg_key[2 + 6 * rk::kMaxGroup] = {0};
+  int hg_len = 0;
 };
 
 namespace rk {
@@ -224,7 +236,6 @@ bool launch_rows_inv_n(const C<T>* uin, int ldu, long long ufs, int nrows, T* ou
 // that share the torus (rk_predict_group).  Slot k covers units
 // [start[k], start[k + 1]) of the grid's y dimension (fields, or field
 // groups for the column pass).
-constexpr int kMaxGroup = 16;
 constexpr int kTileSortMin = 4096;
 template <typename S>
 struct Group {
@@ -268,6 +279,10 @@ struct CopySlot {
   const double* src; double* dst; long long count;
 };
 cudaError_t launch_copy_group(Group<CopySlot>& g, cudaStream_t s);
+struct FlagSlot {
+  const int* src; int* dst;
+};
+cudaError_t launch_flag_group(const Group<FlagSlot>& g, cudaStream_t s);
 struct BlockFactorSlot {
   const int* box; const double* w64; const double2* twx; const double2* twy; double2* efac;
   int n, L, px, py, KX, KY, NS;

@@ -32,6 +32,17 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64
   }
 }
 
+// The uniform ((w >> 11) + 1/2) 2^-53 in float, within one unit in the last
+// place.  With v = w >> 11 = hi 2^21 + lo (hi < 2^32, lo < 2^21):
+// lo 2^-53 + 2^-54 is exact in float, and a fused multiply-add adds hi 2^-32
+// (hi itself rounded to 24 bits when it is longer).  Only 32-bit integer
+// conversions: the 64-bit one runs on GB300's FP64 pipe.
+__device__ __forceinline__ float uniform_f32(uint64_t w) {
+  const uint64_t v = w >> 11;
+  const float lo = fmaf((float)(unsigned)(v & 0x1fffffu), 0x1.0p-53f, 0x1.0p-54f);
+  return fmaf((float)(unsigned)(v >> 21), 0x1.0p-32f, lo);
+}
+
 // Box-Muller on the words (wa, wb)
 template <typename T>
 __device__ __forceinline__ void box_muller(uint64_t wa, uint64_t wb, T& xi, T& eta) {
@@ -44,9 +55,7 @@ __device__ __forceinline__ void box_muller(uint64_t wa, uint64_t wb, T& xi, T& e
     xi = (T)(r * co);
     eta = (T)(r * s);
   } else {
-    // the same uniforms rounded to float (relative error 2^-24)
-    const float u1 = fmaf((float)(wa >> 11), 0x1.0p-53f, 0x1.0p-54f);
-    const float u2 = fmaf((float)(wb >> 11), 0x1.0p-53f, 0x1.0p-54f);
+    const float u1 = uniform_f32(wa), u2 = uniform_f32(wb);
     const float r = sqrtf(-2.0f * logf(u1));
     float s, co;
     sincospif(2.0f * u2, &s, &co);

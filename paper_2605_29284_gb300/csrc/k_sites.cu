@@ -489,6 +489,19 @@ cudaError_t launch_copy_group(Group<CopySlot>& g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Several plans' site latches copied out in one launch (rk_predict_host_group:
+// dst is page-locked host memory the GPU writes directly).
+__global__ void flag_group_kernel(const __grid_constant__ Group<FlagSlot> g) {
+  const int k = threadIdx.x;
+  if (k < g.n) *g.slot[k].dst = *g.slot[k].src;
+}
+
+cudaError_t launch_flag_group(const Group<FlagSlot>& g, cudaStream_t s) {
+  if (g.n == 0) return cudaSuccess;
+  flag_group_kernel<<<1, 32, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ set weights --
 // Copies caller weights into the plan (double and float) and checks the box
 // indices; flag bit 4 marks an index out of range.
@@ -777,29 +790,24 @@ __global__ void block_gemm_kernel(const double* __restrict__ c, int B, int n,
       }
     }
   }
-  __shared__ double red[2 * F][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // the sum over the CTA through shared memory: warp v adds value v's 256
+  // partial sums (8 per lane, then 5 shuffle steps), so the FP64 additions
+  // of the reduction are ~3x fewer than a shuffle tree in every warp
+  __shared__ double red[2 * F][256];
 #pragma unroll
   for (int q = 0; q < F; ++q) {
-    for (int o = 16; o > 0; o >>= 1) {
-      ax[q] += __shfl_down_sync(0xffffffffu, ax[q], o);
-      ay[q] += __shfl_down_sync(0xffffffffu, ay[q], o);
-    }
-    if (lane == 0) { red[2 * q][wid] = ax[q]; red[2 * q + 1][wid] = ay[q]; }
+    red[2 * q][threadIdx.x] = ax[q];
+    red[2 * q + 1][threadIdx.x] = ay[q];
   }
   __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int q = 0; q < F; ++q) {
-      double sx = lane < nw ? red[2 * q][lane] : 0.0;
-      double sy = lane < nw ? red[2 * q + 1][lane] : 0.0;
-      for (int o = 4; o > 0; o >>= 1) {      // nw <= 8
-        sx += __shfl_down_sync(0xffffffffu, sx, o);
-        sy += __shfl_down_sync(0xffffffffu, sy, o);
-      }
-      if (lane == 0 && f0 + q < B) blk[(size_t)(f0 + q) * nblk + j] = make_double2(sx, sy);
-    }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int v = wid; v < 2 * F; v += blockDim.x >> 5) {
+    double sv = 0.0;
+    for (int t = lane; t < blockDim.x; t += 32) sv += red[v][t];
+    for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
+    const int q = v >> 1;
+    if (lane == 0 && f0 + q < B)
+      reinterpret_cast<double*>(blk + (size_t)(f0 + q) * nblk + j)[v & 1] = sv;
   }
 }
 
@@ -821,23 +829,18 @@ __global__ void block_gemm_group_kernel(const __grid_constant__ Group<BlockGemmS
     ax = fma(cv, ev.x, ax);
     ay = fma(cv, ev.y, ay);
   }
-  __shared__ double red[2][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    ax += __shfl_down_sync(0xffffffffu, ax, o);
-    ay += __shfl_down_sync(0xffffffffu, ay, o);
-  }
-  if (lane == 0) { red[0][wid] = ax; red[1][wid] = ay; }
+  // the CTA's sum as in block_gemm_kernel: warps 0 and 1 add the real and
+  // imaginary partial sums from shared memory
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = ax;
+  red[1][threadIdx.x] = ay;
   __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    double sx = lane < nw ? red[0][lane] : 0.0;
-    double sy = lane < nw ? red[1][lane] : 0.0;
-    for (int o = 4; o > 0; o >>= 1) {
-      sx += __shfl_down_sync(0xffffffffu, sx, o);
-      sy += __shfl_down_sync(0xffffffffu, sy, o);
-    }
-    if (lane == 0) sl.blk[(size_t)f * sl.nblk + j] = make_double2(sx, sy);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid < 2) {
+    double sv = 0.0;
+    for (int t = lane; t < blockDim.x; t += 32) sv += red[wid][t];
+    for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
+    if (lane == 0) reinterpret_cast<double*>(sl.blk + (size_t)f * sl.nblk + j)[wid] = sv;
   }
 }
 

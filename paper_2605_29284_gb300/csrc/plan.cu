@@ -107,8 +107,14 @@ void make_twiddles(int n, std::vector<double2>& t64, std::vector<float2>& t32) {
   }
 }
 
+// bumped by every device allocation or release of plan memory: a captured
+// host-group call is replayed only while no buffer it refers to has moved
+uint64_t g_alloc_epoch = 1;
+uint64_t g_plan_ids = 0;
+
 template <typename T>
 rk_status dalloc(T** p, size_t count) {
+  ++g_alloc_epoch;
   if (*p) { cudaFree(*p); *p = nullptr; }
   if (count == 0) return RK_OK;
   if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
@@ -120,6 +126,7 @@ rk_status dalloc(T** p, size_t count) {
 }
 
 rk_status dalloc_bytes(void** p, size_t bytes) {
+  ++g_alloc_epoch;
   if (*p) { cudaFree(*p); *p = nullptr; }
   if (bytes == 0) return RK_OK;
   if (cudaMalloc(p, bytes) != cudaSuccess) {
@@ -310,6 +317,9 @@ rk_status choose_block(rk_plan* p) {
 }
 
 void free_plan(rk_plan* p) {
+  ++g_alloc_epoch;
+  if (p->hg_exec) cudaGraphExecDestroy(p->hg_exec);
+  if (p->hg_stream) cudaStreamDestroy(p->hg_stream);
   void* bufs[] = {p->tw64x, p->tw64y, p->tw32x, p->tw32y, p->lam64, p->lam32, p->dlam64,
                   p->dlam32, p->kn_chol, p->kn_dlog, p->box, p->w64, p->w32, p->ssd, p->efac,
                   p->wdf, p->twdfx, p->twdfy,
@@ -883,6 +893,7 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
     return RK_ERR_INVALID_ARG;
 
   rk_plan* p = new (std::nothrow) rk_plan();
+  if (p) p->id = ++g_plan_ids;
   if (!p) return RK_ERR_OOM;
   p->nx = nx; p->ny = ny; p->L = L; p->M = 4 * L * L; p->precision = precision;
   p->x0 = extent[0]; p->x1 = extent[1]; p->y0 = extent[2]; p->y1 = extent[3];
@@ -903,7 +914,9 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
   do {
     if ((st = dalloc(&p->d_flag, 1)) != RK_OK) break;
     if ((st = dalloc(&p->d_sites_flag, 1)) != RK_OK) break;
-    if (cudaMallocHost((void**)&p->h_flag, sizeof(int)) != cudaSuccess) {
+    if (cudaMallocHost((void**)&p->h_flag, sizeof(int)) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&p->h_flag_dev, p->h_flag, 0) != cudaSuccess) {
+      if (p->h_flag) cudaFreeHost(p->h_flag);
       p->h_flag = nullptr;
       st = RK_ERR_OOM;
       break;
@@ -1288,6 +1301,74 @@ rk_status rk_predict_group(rk_plan* const* plans, int nplans, void* const* outs)
   return predict_group_impl<float>(plans, nplans, outs);
 }
 
+// The device-side address of page-locked host memory (the same address under
+// unified addressing), or null for memory the GPU cannot address directly.
+static void* mapped(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// The stream work of rk_predict_host_group once the buffers are sized: the
+// sites and coefficients in, the grouped site update, the grouped
+// prediction, the grids and the latches out.  Page-locked host buffers
+// (xy_map, c_map, out_map non-null) are read and written by the kernels
+// themselves over the host-device link (GB300's NVLink-C2C is coherent):
+// the weights kernels read the sites, one copy launch the coefficients, the
+// inverse row pass writes the grids and one launch the latches; other
+// buffers go through copies.
+static rk_status host_group_ops(rk_plan* const* plans, int nplans, const int* n,
+                                const double* const* xy_host, const int* B,
+                                const double* const* c_host, void* const* out_host,
+                                void* const* xy_map, void* const* c_map, void* const* out_map,
+                                int* const* flag_map) {
+  cudaStream_t s = plans[0]->stream;
+  const double* xy_dev[kMaxGroup];
+  void* out_dev[kMaxGroup];
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    if (xy_map[k]) {
+      xy_dev[k] = (const double*)xy_map[k];
+    } else {
+      RK_CU(cudaMemcpyAsync(p->h_xy, xy_host[k], (size_t)2 * n[k] * sizeof(double),
+                            cudaMemcpyHostToDevice, s));
+      xy_dev[k] = p->h_xy;
+    }
+    out_dev[k] = out_map[k] ? out_map[k] : p->h_out;
+  }
+  RK_TRY(rk_set_sites_group(plans, nplans, n, xy_dev));
+  Group<CopySlot> gc;
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    RK_TRY(ensure_coef(p, B[k]));
+    if (c_map[k])
+      gc.slot[gc.n++] = CopySlot{(const double*)c_map[k], p->c64, (long long)B[k] * n[k]};
+    else
+      RK_CU(cudaMemcpyAsync(p->c64, c_host[k], (size_t)B[k] * n[k] * sizeof(double),
+                            cudaMemcpyHostToDevice, s));
+    RK_TRY(finish_coef(p, B[k]));
+  }
+  if (gc.n > 0) RK_CU(launch_copy_group(gc, s));
+  RK_TRY(rk_predict_group(plans, nplans, out_dev));
+  Group<FlagSlot> gf;
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    const size_t esz = p->precision == RK_FP64 ? sizeof(double) : sizeof(float);
+    if (!out_map[k])
+      RK_CU(cudaMemcpyAsync(out_host[k], p->h_out, (size_t)B[k] * p->ny * p->nx * esz,
+                            cudaMemcpyDeviceToHost, s));
+    if (flag_map[k])
+      gf.slot[gf.n++] = FlagSlot{p->d_sites_flag, flag_map[k]};
+    else
+      RK_CU(cudaMemcpyAsync(p->h_flag, p->d_sites_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
+  if (gf.n > 0) RK_CU(launch_flag_group(gf, s));
+  return RK_OK;
+}
+
 rk_status rk_predict_host_group(rk_plan* const* plans, int nplans, const int* n,
                                 const double* const* xy_host, const int* B,
                                 const double* const* c_host, void* const* out_host) {
@@ -1303,8 +1384,6 @@ rk_status rk_predict_host_group(rk_plan* const* plans, int nplans, const int* n,
   }
   rk_plan* p0 = plans[0];
   cudaStream_t s = p0->stream;
-  const double* xy_dev[kMaxGroup];
-  void* out_dev[kMaxGroup];
   for (int k = 0; k < nplans; ++k) {
     rk_plan* p = plans[k];
     // capacities first (the only allocations, on growth)
@@ -1322,26 +1401,53 @@ rk_status rk_predict_host_group(rk_plan* const* plans, int nplans, const int* n,
       RK_TRY(dalloc_bytes(&p->h_out, out_bytes));
       p->h_out_cap = out_bytes;
     }
-    RK_CU(cudaMemcpyAsync(p->h_xy, xy_host[k], (size_t)2 * n[k] * sizeof(double),
-                          cudaMemcpyHostToDevice, s));
-    xy_dev[k] = p->h_xy;
-    out_dev[k] = p->h_out;
-  }
-  RK_TRY(rk_set_sites_group(plans, nplans, n, xy_dev));
-  for (int k = 0; k < nplans; ++k) {
-    rk_plan* p = plans[k];
     RK_TRY(ensure_coef(p, B[k]));
-    RK_CU(cudaMemcpyAsync(p->c64, c_host[k], (size_t)B[k] * n[k] * sizeof(double),
-                          cudaMemcpyHostToDevice, s));
-    RK_TRY(finish_coef(p, B[k]));
   }
-  RK_TRY(rk_predict_group(plans, nplans, out_dev));
+  // with page-locked host buffers the call's stream work is captured once and
+  // replayed: the key holds everything the captured work depends on (the
+  // allocation epoch covers every device buffer of every plan)
+  void* xy_map[kMaxGroup];
+  void* c_map[kMaxGroup];
+  void* out_map[kMaxGroup];
+  int* flag_map[kMaxGroup];
+  bool graphable = !g_prof_on;
   for (int k = 0; k < nplans; ++k) {
-    rk_plan* p = plans[k];
-    const size_t esz = p->precision == RK_FP64 ? sizeof(double) : sizeof(float);
-    RK_CU(cudaMemcpyAsync(out_host[k], p->h_out, (size_t)B[k] * p->ny * p->nx * esz,
-                          cudaMemcpyDeviceToHost, s));
-    RK_CU(cudaMemcpyAsync(p->h_flag, p->d_sites_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    xy_map[k] = mapped(xy_host[k]);
+    c_map[k] = mapped(c_host[k]);
+    out_map[k] = mapped(out_host[k]);
+    flag_map[k] = plans[k]->h_flag_dev;
+    graphable = graphable && xy_map[k] && c_map[k] && out_map[k];
+  }
+  uint64_t key[2 + 6 * kMaxGroup];
+  int len = 0;
+  key[len++] = g_alloc_epoch;
+  key[len++] = (uint64_t)nplans;
+  for (int k = 0; k < nplans; ++k) {
+    key[len++] = plans[k]->id;
+    key[len++] = ((uint64_t)(unsigned)n[k] << 32) | (unsigned)B[k];
+    key[len++] = (uint64_t)(uintptr_t)xy_host[k];
+    key[len++] = (uint64_t)(uintptr_t)c_host[k];
+    key[len++] = (uint64_t)(uintptr_t)out_host[k];
+    key[len++] = (uint64_t)(uintptr_t)plans[k];
+  }
+  const bool replay = graphable && p0->hg_exec && p0->hg_len == len &&
+                      memcmp(p0->hg_key, key, len * sizeof(uint64_t)) == 0;
+  if (replay) {
+    RK_CU(cudaGraphLaunch(p0->hg_exec, s));
+    // the host-side state the captured calls set
+    for (int k = 0; k < nplans; ++k) {
+      rk_plan* p = plans[k];
+      p->n = n[k];
+      p->xy_valid = true;
+      p->w64_stale = p->precision == RK_FP32;
+      p->have_chol = false;
+      p->have_adj = false;
+      p->B = B[k];
+      p->have_coef = true;
+    }
+  } else {
+    RK_TRY(host_group_ops(plans, nplans, n, xy_host, B, c_host, out_host, xy_map, c_map, out_map,
+                          flag_map));
   }
   RK_CU(cudaStreamSynchronize(s));   // the one synchronisation of the call
   bool outside = false;
@@ -1350,6 +1456,51 @@ rk_status rk_predict_host_group(rk_plan* const* plans, int nplans, const int* n,
       outside = true;
       RK_CU(cudaMemsetAsync(plans[k]->d_sites_flag, 0, sizeof(int), s));
     }
+  }
+  if (graphable && !replay) {
+    // capture the same work for the next call with this key, on a stream of
+    // the plan's own (the caller's may be the legacy default stream, which
+    // cannot be captured); the graph is launched on the caller's stream
+    if (p0->hg_exec) {
+      cudaGraphExecDestroy(p0->hg_exec);
+      p0->hg_exec = nullptr;
+    }
+    p0->hg_len = 0;
+    if (outside) RK_CU(cudaStreamSynchronize(s));
+    if (!p0->hg_stream &&
+        cudaStreamCreateWithFlags(&p0->hg_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      p0->hg_stream = nullptr;
+      cudaGetLastError();
+    }
+    if (p0->hg_stream &&
+        cudaStreamBeginCapture(p0->hg_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      p0->stream = p0->hg_stream;
+      const rk_status st = host_group_ops(plans, nplans, n, xy_host, B, c_host, out_host, xy_map,
+                                          c_map, out_map, flag_map);
+      p0->stream = s;
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(p0->hg_stream, &graph);
+      if (st == RK_OK && e == cudaSuccess && graph &&
+          cudaGraphInstantiate(&p0->hg_exec, graph, 0) == cudaSuccess) {
+        memcpy(p0->hg_key, key, len * sizeof(uint64_t));
+        p0->hg_len = len;
+      } else {
+        p0->hg_exec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();   // a capture that failed leaves no error behind
+    // the events recorded inside the capture mark points of the graph only:
+    // record them again outside it (the work they stood for is complete), so
+    // that later calls on these plans wait on ordinary events
+    for (int k = 0; k < nplans; ++k) {
+      rk_plan* p = plans[k];
+      cudaEventRecord(p->ev_sites, p->side);
+      cudaEventRecord(p->ev_fork, p->side);
+      cudaEventRecord(p->ev_join, p->side);
+      cudaEventRecord(p->ev_wfork, p->side);
+    }
+    cudaGetLastError();
   }
   return outside ? RK_ERR_OBS_OUTSIDE : RK_OK;
 }

@@ -184,3 +184,49 @@ def test_host_group_equals_device_group(rk):
     finally:
         for p in plans:
             p.close()
+
+
+def test_host_group_replays_with_page_locked_buffers(rk):
+    # with page-locked host buffers the second call with the same plans, sizes
+    # and pointers replays the first call's captured work: new contents of the
+    # same buffers must come through, an outside site must still be latched,
+    # and a change of size (a new key) must run and capture afresh
+    ext = (0.0, 1.6, 0.0, 1.0)
+    cells = [(0.5, 2), (2.5, 3)]
+    plans, coefs = _plans(rk, 200, ext, cells, "fp32", n=500, B=2)
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t, t.numpy()
+
+    try:
+        xy_t = [pinned(xy) for xy, _, _, _ in coefs]
+        c_t = [pinned(np.atleast_2d(c)) for _, c, _, _ in coefs]
+        o_t = [pinned(np.zeros((2, 200, 200), np.float32)) for _ in cells]
+        xys, cs, outs = [a for _, a in xy_t], [a for _, a in c_t], [a for _, a in o_t]
+        for rep in range(3):
+            for k in range(len(cells)):
+                cs[k][...] = np.atleast_2d(coefs[k][1]) * (1.0 + rep)
+            rk.predict_host_group(plans, xys, cs, outs)
+            for k, p in enumerate(plans):
+                p.set_sites(torch.from_numpy(xys[k].copy()).cuda())
+                p.set_coef(torch.from_numpy(cs[k].copy()).cuda())
+                ref = p.predict().double().cpu().numpy()
+                assert rel_err(outs[k].astype(np.float64), ref) <= 1e-6, (rep, k)
+            # the direct calls allocated nothing new: the next call replays
+        saved = xys[1][3].copy()
+        xys[1][3] = (-0.5, 0.5)
+        with pytest.raises(rk.RkError) as e:
+            rk.predict_host_group(plans, xys, cs, outs)
+        assert e.value.name == "RK_ERR_OBS_OUTSIDE"
+        xys[1][3] = saved
+        small = [x[:300] for x in xys]                       # new sizes: a new key
+        small_c = [np.ascontiguousarray(c[:, :300]) for c in cs]
+        res = rk.predict_host_group(plans, small, small_c)
+        for k, p in enumerate(plans):
+            p.set_sites(torch.from_numpy(np.ascontiguousarray(small[k])).cuda())
+            p.set_coef(torch.from_numpy(small_c[k]).cuda())
+            assert rel_err(res[k].astype(np.float64), p.predict().double().cpu().numpy()) <= 1e-6
+    finally:
+        for p in plans:
+            p.close()
