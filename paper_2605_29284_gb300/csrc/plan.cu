@@ -1412,7 +1412,11 @@ rk_status rk_predict_host_group(rk_plan* const* plans, int nplans, const int* n,
   int* flag_map[kMaxGroup];
   bool graphable = !g_prof_on;
   for (int k = 0; k < nplans; ++k) {
-    xy_map[k] = mapped(xy_host[k]);
+    // one query per distinct buffer (the plans of a sweep often share sites)
+    int same = -1;
+    for (int j = 0; j < k && same < 0; ++j)
+      if (xy_host[j] == xy_host[k]) same = j;
+    xy_map[k] = same >= 0 ? xy_map[same] : mapped(xy_host[k]);
     c_map[k] = mapped(c_host[k]);
     out_map[k] = mapped(out_host[k]);
     flag_map[k] = plans[k]->h_flag_dev;
