@@ -251,20 +251,18 @@ __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __res
   __syncthreads();
   const int r = (FWD ? k + nb : 0) + blockIdx.x * SU + threadIdx.x;
   if (r >= (FWD ? n : k)) return;
-  dfl acc[SF];
-#pragma unroll
-  for (int f = 0; f < SF; ++f) acc[f] = {0.f, 0.f};
+  dfacc acc[SF];
   const float2* col = adf + (size_t)k * n + r;
 #pragma unroll 8
   for (int c = 0; c < nb; ++c) {
     const float2 l2 = __ldg(col + (size_t)c * n);
     const dfl l = {l2.x, l2.y};
 #pragma unroll
-    for (int f = 0; f < SF; ++f) acc[f] = df_fma(l, {Xs[c][f].x, Xs[c][f].y}, acc[f]);
+    for (int f = 0; f < SF; ++f) dfacc_fma(acc[f], l, {Xs[c][f].x, Xs[c][f].y});
   }
 #pragma unroll
   for (int f = 0; f < SF; ++f)
-    if (f < nf) x[(size_t)(f0 + f) * n + r] -= df_double(acc[f]);
+    if (f < nf) x[(size_t)(f0 + f) * n + r] -= df_double(dfacc_value(acc[f]));
 }
 
 // RK_FP32 plans: the diagonal blocks of the double-float factor hold the
