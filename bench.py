@@ -275,19 +275,22 @@ class Arm:
         return max_over_ranks(total, self.dev), prof
 
     def e2e(self, steps, warmup):
-        """The same step through the host-buffer API (rk_predict_host_group, or
-        rk_predict_host per cell): sites and coefficients copied in from pinned
-        host memory, the grids copied back, inside the timed region."""
+        """The same step through the host-buffer API (a prepared
+        rk_predict_host_group call, or rk_predict_host per cell): sites and
+        coefficients in from pinned host memory, the grids back to it, inside
+        the timed region (the kernels read and write the pinned buffers over
+        NVLink-C2C)."""
         torch = self.torch
         xy = torch.from_numpy(self.xy_np).pin_memory().numpy()
         cs = [c.cpu().pin_memory().numpy() for _, c, _ in self.st]
         outs = [torch.empty(tuple(o.shape), dtype=o.dtype, pin_memory=True).numpy()
                 for _, _, o in self.st]
         plans = [p for p, _, _ in self.st]
+        call = self.rk.HostGroupCall(plans, [xy] * len(plans), cs, outs) if self.grouped else None
 
         def once():
-            if self.grouped:
-                self.rk.predict_host_group(plans, [xy] * len(plans), cs, outs)
+            if call is not None:
+                call.run()
             else:
                 for p, c, o in zip(plans, cs, outs):
                     p.predict_host(xy, c, o)

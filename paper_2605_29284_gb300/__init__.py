@@ -12,8 +12,8 @@ import torch
 from ._native import RK_FP32, RK_FP64, PlanInfo, RkError, check, lib, profile_enable, profile_read
 
 __all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "predict_group",
-           "predict_host_group", "profile_enable", "profile_read", "set_coef_group",
-           "set_sites_group"]
+           "predict_host_group", "HostGroupCall", "profile_enable", "profile_read",
+           "set_coef_group", "set_sites_group"]
 
 
 def _ptr(t):
@@ -233,14 +233,58 @@ def set_coef_group(plans, cs):
         p.B = int(c.shape[0])
 
 
+def _host_f64(a, two_d=False):
+    """a as a C-contiguous float64 numpy array (no copy when it already is one)."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+    return a[None] if two_d and a.ndim == 1 else a
+
+
+class HostGroupCall:
+    """A prepared rk_predict_host_group call for fixed plans and host arrays.
+
+    The argument arrays are marshalled once; run() issues the call on the
+    current stream (the arrays' contents may change between runs, their
+    shapes and addresses may not).  With page-locked arrays each run replays
+    the graph the library captured on the first one."""
+
+    def __init__(self, plans, xys, cs, outs=None):
+        self.plans = list(plans)
+        self.xys = [_host_f64(x) for x in xys]
+        self.cs = [_host_f64(c, two_d=True) for c in cs]
+        if outs is None:
+            outs = [np.empty((c.shape[0], p.ny, p.nx),
+                             dtype=np.float64 if p.precision == RK_FP64 else np.float32)
+                    for p, c in zip(self.plans, self.cs)]
+        self.outs = list(outs)
+        k = self.k = len(self.plans)
+        vp = ctypes.c_void_p
+        self._h = (vp * k)(*[p._h.value for p in self.plans])
+        self._n = (ctypes.c_int * k)(*[x.shape[0] for x in self.xys])
+        self._b = (ctypes.c_int * k)(*[c.shape[0] for c in self.cs])
+        self._x = (vp * k)(*[x.__array_interface__["data"][0] for x in self.xys])
+        self._c = (vp * k)(*[c.__array_interface__["data"][0] for c in self.cs])
+        self._o = (vp * k)(*[o.__array_interface__["data"][0] for o in self.outs])
+
+    def run(self):
+        check(lib.rk_set_stream(self.plans[0]._h, _stream()), "rk_set_stream")
+        check(lib.rk_predict_host_group(self._h, self.k, self._n, self._x, self._b, self._c,
+                                        self._o), "rk_predict_host_group")
+        for p, x, c in zip(self.plans, self.xys, self.cs):
+            p.n, p.B = x.shape[0], c.shape[0]
+        return self.outs
+
+
 def predict_host_group(plans, xys, cs, outs=None):
     """rk_predict_host_group: host sites and coefficients in, host grids out,
     for several plans with one synchronisation.  xys[k] (n_k x 2) and cs[k]
-    (B_k x n_k) are numpy arrays (pinned memory lets the copies overlap);
-    outs[k] (B_k x ny x nx, plan precision) are filled (allocated if None)."""
+    (B_k x n_k) are numpy arrays; outs[k] (B_k x ny x nx, plan precision) are
+    filled (allocated if None).  With page-locked arrays (e.g. torch's
+    pin_memory) the kernels read and write them directly and repeated calls
+    replay one captured graph."""
     plans = list(plans)
-    xys = [np.ascontiguousarray(x, dtype=np.float64) for x in xys]
-    cs = [np.ascontiguousarray(np.atleast_2d(c), dtype=np.float64) for c in cs]
+    xys = [_host_f64(x) for x in xys]
+    cs = [_host_f64(c, two_d=True) for c in cs]
     if outs is None:
         outs = [np.empty((c.shape[0], p.ny, p.nx),
                          dtype=np.float64 if p.precision == RK_FP64 else np.float32)
@@ -248,11 +292,11 @@ def predict_host_group(plans, xys, cs, outs=None):
     k = len(plans)
     vp = ctypes.c_void_p
     harr = (vp * k)(*[p._h.value for p in plans])
-    narr = (ctypes.c_int * k)(*[int(x.shape[0]) for x in xys])
-    barr = (ctypes.c_int * k)(*[int(c.shape[0]) for c in cs])
-    xarr = (vp * k)(*[x.ctypes.data for x in xys])
-    carr = (vp * k)(*[c.ctypes.data for c in cs])
-    oarr = (vp * k)(*[o.ctypes.data for o in outs])
+    narr = (ctypes.c_int * k)(*[x.shape[0] for x in xys])
+    barr = (ctypes.c_int * k)(*[c.shape[0] for c in cs])
+    xarr = (vp * k)(*[x.__array_interface__["data"][0] for x in xys])
+    carr = (vp * k)(*[c.__array_interface__["data"][0] for c in cs])
+    oarr = (vp * k)(*[o.__array_interface__["data"][0] for o in outs])
     check(lib.rk_set_stream(plans[0]._h, _stream()), "rk_set_stream")
     check(lib.rk_predict_host_group(harr, k, narr, xarr, barr, carr, oarr),
           "rk_predict_host_group")

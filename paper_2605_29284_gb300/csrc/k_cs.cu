@@ -15,20 +15,38 @@
 
 namespace rk {
 
-__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+// The ten round keys of Philox4x64-10 for key (seed, 0), formed once on the
+// host and passed by value: in the kernels they are parameter-space operands
+// of the XORs, not per-thread 64-bit additions (the generator's integer
+// instructions bound the noise passes).
+struct PhiloxKeys {
+  uint64_t k0[10], k1[10];
+};
+
+inline PhiloxKeys philox_keys(uint64_t seed) {
   const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+  PhiloxKeys K;
+  uint64_t k0 = seed, k1 = 0ull;
+  for (int r = 0; r < 10; ++r) {
+    K.k0[r] = k0;
+    K.k1[r] = k1;
+    k0 += W0;
+    k1 += W1;
+  }
+  return K;
+}
+
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], const PhiloxKeys& K) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
     const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
-    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    const uint64_t n0 = hi1 ^ c[1] ^ K.k0[r], n2 = hi0 ^ c[3] ^ K.k1[r];
     c[0] = n0;
     c[1] = lo1;
     c[2] = n2;
     c[3] = lo0;
-    k0 += W0;
-    k1 += W1;
   }
 }
 
@@ -67,9 +85,9 @@ __device__ __forceinline__ void box_muller(uint64_t wa, uint64_t wb, T& xi, T& e
 // (xi, eta) for element `index` of sub-stream `sub` in `stream`
 template <typename T>
 __device__ __forceinline__ void normal_pair(uint64_t index, uint64_t sub, uint64_t stream,
-                                            uint64_t seed, T& xi, T& eta) {
+                                            const PhiloxKeys& keys, T& xi, T& eta) {
   uint64_t c[4] = {index >> 1, sub, stream, 0ull};
-  philox4x64_10(c, seed, 0ull);
+  philox4x64_10(c, keys);
   box_muller<T>((index & 1) ? c[2] : c[0], (index & 1) ? c[3] : c[1], xi, eta);
 }
 
@@ -78,7 +96,7 @@ __device__ __forceinline__ void normal_pair(uint64_t index, uint64_t sub, uint64
 // y, rows [0, nkeep) written to tq[(p - pair0) * qx + kx][0..nkeep).
 template <typename T>
 __global__ void __launch_bounds__(256)
-ce_cols_kernel(const T* __restrict__ sqrtlam, int qx, int qy, unsigned long long seed, int pair0,
+ce_cols_kernel(const T* __restrict__ sqrtlam, int qx, int qy, const PhiloxKeys keys, int pair0,
                C<T>* __restrict__ tq, int ldq, int nkeep, FftPlan fpy,
                const C<T>* __restrict__ twy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -94,7 +112,7 @@ ce_cols_kernel(const T* __restrict__ sqrtlam, int qx, int qy, unsigned long long
   for (uint64_t kk = (kbase & ~1ull) + 2ull * threadIdx.x; kk < kbase + qy;
        kk += 2ull * blockDim.x) {
     uint64_t c[4] = {kk >> 1, (uint64_t)pair, 1ull, 0ull};
-    philox4x64_10(c, seed, 0ull);
+    philox4x64_10(c, keys);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const uint64_t k = kk + h;
@@ -159,7 +177,7 @@ template <typename T>
 __global__ void site_values_kernel(const T* __restrict__ fu, int p1x, long long fu_stride,
                                    int nreal, const int* __restrict__ box,
                                    const double* __restrict__ w64, const double* __restrict__ ssd,
-                                   int n, int L, double tau, unsigned long long seed, long long t0,
+                                   int n, int L, double tau, const PhiloxKeys keys, long long t0,
                                    int R, const double* __restrict__ z, double* __restrict__ rhs) {
   const int W = 2 * L, M = W * W;
   const long long total = (long long)n * nreal;
@@ -176,7 +194,7 @@ __global__ void site_values_kernel(const T* __restrict__ fu, int p1x, long long 
       mean += w64[(size_t)i * M + q] * (double)f[(size_t)(iy + bb) * p1x + ix + a];
     }
     double xi, eps;
-    normal_pair<double>((uint64_t)i, (uint64_t)tg, 2ull, seed, xi, eps);
+    normal_pair<double>((uint64_t)i, (uint64_t)tg, 2ull, keys, xi, eps);
     rhs[(size_t)j * n + i] = z[(size_t)b * n + i] - (mean + ssd[i] * xi + tau * eps);
   }
 }
@@ -192,7 +210,7 @@ struct CeVecs {
 
 template <typename T, int N>
 __global__ void __launch_bounds__(CeVecs<N>::value * Radix23<N>::THR)
-ce_cols_n(const T* __restrict__ sqrtlam, int qx, unsigned long long seed, int pair0,
+ce_cols_n(const T* __restrict__ sqrtlam, int qx, const PhiloxKeys keys, int pair0,
           C<T>* __restrict__ tq, int ldq, int nkeep, const C<T>* __restrict__ twy) {
   constexpr int V = CeVecs<N>::value, THR = Radix23<N>::THR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -207,7 +225,7 @@ ce_cols_n(const T* __restrict__ sqrtlam, int qx, unsigned long long seed, int pa
     const uint64_t kbase = (uint64_t)kx * N;
     for (uint64_t kk = (kbase & ~1ull) + 2ull * tid; kk < kbase + N; kk += 2ull * THR) {
       uint64_t c[4] = {kk >> 1, (uint64_t)pair, 1ull, 0ull};
-      philox4x64_10(c, seed, 0ull);
+      philox4x64_10(c, keys);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const uint64_t k = kk + h;
@@ -271,8 +289,8 @@ cudaError_t go_ce_cols(const T* sqrtlam, int qx, unsigned long long seed, int pa
   auto kern = ce_cols_n<T, N>;
   cudaError_t e = ensure_smem(kern, sm, smem_set);
   if (e != cudaSuccess) return e;
-  kern<<<dim3((qx + V - 1) / V, npairs), V * THR, sm, s>>>(sqrtlam, qx, seed, pair0, tq, ldq,
-                                                            nkeep, twy);
+  kern<<<dim3((qx + V - 1) / V, npairs), V * THR, sm, s>>>(sqrtlam, qx, philox_keys(seed), pair0,
+                                                            tq, ldq, nkeep, twy);
   return cudaGetLastError();
 }
 
@@ -308,7 +326,8 @@ cudaError_t launch_ce_cols(const T* sqrtlam, int qx, int qy, unsigned long long 
   static int smem_set = 0;
   cudaError_t e = ensure_smem(kern, sm, smem_set);
   if (e != cudaSuccess) return e;
-  kern<<<dim3(qx, npairs), 256, sm, s>>>(sqrtlam, qx, qy, seed, pair0, tq, ldq, nkeep, fpy, twy);
+  kern<<<dim3(qx, npairs), 256, sm, s>>>(sqrtlam, qx, qy, philox_keys(seed), pair0, tq, ldq, nkeep,
+                                         fpy, twy);
   return cudaGetLastError();
 }
 
@@ -345,7 +364,8 @@ cudaError_t launch_site_values(const T* fu, int p1x, long long fu_stride, int nr
   long long blocks = (total + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   site_values_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(fu, p1x, fu_stride, nreal, box, w64, ssd,
-                                                         n, L, tau, seed, t0, R, z, rhs);
+                                                         n, L, tau, philox_keys(seed), t0, R, z,
+                                                         rhs);
   return cudaGetLastError();
 }
 

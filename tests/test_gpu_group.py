@@ -214,6 +214,13 @@ def test_host_group_replays_with_page_locked_buffers(rk):
                 ref = p.predict().double().cpu().numpy()
                 assert rel_err(outs[k].astype(np.float64), ref) <= 1e-6, (rep, k)
             # the direct calls allocated nothing new: the next call replays
+        # the prepared call (arguments marshalled once) gives the same grids
+        call = rk.HostGroupCall(plans, xys, cs, outs)
+        ref = [o.copy() for o in rk.predict_host_group(plans, xys, cs)]
+        for _ in range(2):
+            got = call.run()
+            for a, b in zip(got, ref):      # the atomic scatter's order differs
+                assert rel_err(a.astype(np.float64), b.astype(np.float64)) <= 1e-6
         saved = xys[1][3].copy()
         xys[1][3] = (-0.5, 0.5)
         with pytest.raises(rk.RkError) as e:
