@@ -236,10 +236,16 @@ __global__ void __launch_bounds__(SU) solve_update_kernel(const double* __restri
 // chol_split) and double-float accumulation on the FP32 pipe: ~48-bit
 // products and sums instead of FP64, for RK_FP32 plans, whose outputs need
 // far less (the diagonal substitutions stay FP64).
+// knext >= 0: the CTA holding the next block's rows (the first row tile going
+// forward, the last going backward) then also takes that block's diagonal
+// step, x_next <- L^{-1} x_next (L^{-T} backward) with the inverted block of
+// chol_invert_diag_df, so the solve needs no separate launch for it.
 template <bool FWD>
 __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __restrict__ adf, int n,
-                                                             int k, double* x, int B) {
+                                                             int k, double* x, int B, int knext) {
   __shared__ float2 Xs[SB][SF];
+  __shared__ float2 Ys[SB][SF];             // the next block's updated rows (tail CTA)
+  __shared__ float2 Ps[SB][SF];             // half sums of its diagonal product
   const int nb = min(SB, n - k);
   const int f0 = blockIdx.y * SF;
   const int nf = min(SF, B - f0);
@@ -250,19 +256,67 @@ __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __res
   }
   __syncthreads();
   const int r = (FWD ? k + nb : 0) + blockIdx.x * SU + threadIdx.x;
-  if (r >= (FWD ? n : k)) return;
-  dfacc acc[SF];
-  const float2* col = adf + (size_t)k * n + r;
+  const bool live = r < (FWD ? n : k);
+  const bool tail = knext >= 0 && blockIdx.x == (FWD ? 0 : gridDim.x - 1);
+  const int nbn = knext >= 0 ? min(SB, n - knext) : 0;
+  const bool inblk = tail && r >= knext && r < knext + nbn;
+  if (live) {
+    dfacc acc[SF];
+    const float2* col = adf + (size_t)k * n + r;
 #pragma unroll 8
-  for (int c = 0; c < nb; ++c) {
-    const float2 l2 = __ldg(col + (size_t)c * n);
-    const dfl l = {l2.x, l2.y};
+    for (int c = 0; c < nb; ++c) {
+      const float2 l2 = __ldg(col + (size_t)c * n);
+      const dfl l = {l2.x, l2.y};
 #pragma unroll
-    for (int f = 0; f < SF; ++f) dfacc_fma(acc[f], l, {Xs[c][f].x, Xs[c][f].y});
+      for (int f = 0; f < SF; ++f) dfacc_fma(acc[f], l, {Xs[c][f].x, Xs[c][f].y});
+    }
+#pragma unroll
+    for (int f = 0; f < SF; ++f) {
+      if (f >= nf) continue;
+      const double u = x[(size_t)(f0 + f) * n + r] - df_double(dfacc_value(acc[f]));
+      if (inblk) {
+        const dfl v = df_make(u);
+        Ys[r - knext][f] = make_float2(v.hi, v.lo);
+      } else {
+        x[(size_t)(f0 + f) * n + r] = u;
+      }
+    }
   }
+  if (!tail) return;                        // uniform over the CTA
+  __syncthreads();
+  // x_next[row] = sum_c Tinv(row, c) y[c] (c <= row) forward, sum_c Tinv(c, row)
+  // y[c] (c >= row) backward: adf's diagonal block at column c, row `row`;
+  // threads 0-63 and 64-127 take the two halves of the c range
+  const int row = threadIdx.x % SB, half = threadIdx.x / SB;
+  dfacc acc[SF];
+  if (row < nbn) {
+    const int c0 = FWD ? 0 : row, c1 = FWD ? row + 1 : nbn;
+    const int mid = (c0 + c1) / 2;
+    const int ca = half ? mid : c0, cb = half ? c1 : mid;
+    const float2* blk = adf + (size_t)knext * n + knext + row;
+    for (int c = ca; c < cb; ++c) {
+      const float2 t2 = __ldg(blk + (size_t)c * n);
+      const dfl t = {t2.x, t2.y};
 #pragma unroll
-  for (int f = 0; f < SF; ++f)
-    if (f < nf) x[(size_t)(f0 + f) * n + r] -= df_double(dfacc_value(acc[f]));
+      for (int f = 0; f < SF; ++f) dfacc_fma(acc[f], t, {Ys[c][f].x, Ys[c][f].y});
+    }
+  }
+  if (half) {
+#pragma unroll
+    for (int f = 0; f < SF; ++f) {
+      const dfl v = dfacc_value(acc[f]);
+      Ps[row][f] = make_float2(v.hi, v.lo);
+    }
+  }
+  __syncthreads();
+  if (!half && row < nbn) {
+#pragma unroll
+    for (int f = 0; f < SF; ++f) {
+      if (f >= nf) continue;
+      const dfl v = df_add(dfacc_value(acc[f]), {Ps[row][f].x, Ps[row][f].y});
+      x[(size_t)(f0 + f) * n + knext + row] = df_double(v);
+    }
+  }
 }
 
 // RK_FP32 plans: the diagonal blocks of the double-float factor hold the
@@ -383,24 +437,26 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
   const int dgrid = (B + 3) / 4;              // four warps (right-hand sides) per CTA
   const int igrid = (B + kDiagRhs - 1) / kDiagRhs;
   const int fblocks = (B + SF - 1) / SF;
+  // double-float: the first block's diagonal step is a launch of its own,
+  // every later one runs in the tail CTA of the update before it
+  if (adf) solve_diag_inv_df_kernel<true><<<igrid, SB * kDiagRhs, 0, s>>>(adf, n, 0, x, B);
   for (int k = 0; k < n; k += SB) {
     const int nb = n - k < SB ? n - k : SB;
-    if (adf) solve_diag_inv_df_kernel<true><<<igrid, SB * kDiagRhs, 0, s>>>(adf, n, k, x, B);
-    else solve_diag_kernel<true><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
+    if (!adf) solve_diag_kernel<true><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     const int rest = n - k - nb;
     if (rest > 0) {
       const dim3 grid((rest + SU - 1) / SU, fblocks);
-      if (adf) solve_update_df_kernel<true><<<grid, SU, 0, s>>>(adf, n, k, x, B);
+      if (adf) solve_update_df_kernel<true><<<grid, SU, 0, s>>>(adf, n, k, x, B, k + nb);
       else solve_update_kernel<true><<<grid, SU, 0, s>>>(a, n, k, x, B);
     }
   }
   const int last = ((n - 1) / SB) * SB;
+  if (adf) solve_diag_inv_df_kernel<false><<<igrid, SB * kDiagRhs, 0, s>>>(adf, n, last, x, B);
   for (int k = last; k >= 0; k -= SB) {
-    if (adf) solve_diag_inv_df_kernel<false><<<igrid, SB * kDiagRhs, 0, s>>>(adf, n, k, x, B);
-    else solve_diag_kernel<false><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
+    if (!adf) solve_diag_kernel<false><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     if (k > 0) {
       const dim3 grid((k + SU - 1) / SU, fblocks);
-      if (adf) solve_update_df_kernel<false><<<grid, SU, 0, s>>>(adf, n, k, x, B);
+      if (adf) solve_update_df_kernel<false><<<grid, SU, 0, s>>>(adf, n, k, x, B, k - SB);
       else solve_update_kernel<false><<<grid, SU, 0, s>>>(a, n, k, x, B);
     }
   }
