@@ -260,6 +260,13 @@ __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __res
   const bool tail = knext >= 0 && blockIdx.x == (FWD ? 0 : gridDim.x - 1);
   const int nbn = knext >= 0 ? min(SB, n - knext) : 0;
   const bool inblk = tail && r >= knext && r < knext + nbn;
+  if (tail) {
+    // the next diagonal block is read after the update: start moving its
+    // 128-byte lines (16 float2 of a column) into L2 now
+    const int c = threadIdx.x % SB;
+    for (int j = threadIdx.x / SB; j * 16 < nbn && c < nbn; j += SU / SB)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(adf + (size_t)(knext + c) * n + knext + j * 16));
+  }
   if (live) {
     dfacc acc[SF];
     const float2* col = adf + (size_t)k * n + r;
@@ -294,6 +301,7 @@ __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __res
     const int mid = (c0 + c1) / 2;
     const int ca = half ? mid : c0, cb = half ? c1 : mid;
     const float2* blk = adf + (size_t)knext * n + knext + row;
+#pragma unroll 8
     for (int c = ca; c < cb; ++c) {
       const float2 t2 = __ldg(blk + (size_t)c * n);
       const dfl t = {t2.x, t2.y};
