@@ -737,7 +737,10 @@ block_factor_df_kernel(const __grid_constant__ Group<BlockFactorDfSlot> g) {
 
 BlockFactorDfSlot block_factor_df_slot(const rk_plan* p, int n) {
   const size_t per_site = sizeof(float4) * (size_t)(p->blk_kx + 1) * 2 * p->L;
-  int NS = kBfSites;
+  // L >= 3: 16 lanes per site, which halves the per-thread rounds of the
+  // longest sites; fewer sites per CTA for L <= 2 would only add CTAs that
+  // compete with the main stream's passes running beside this kernel
+  int NS = p->L >= 3 ? kBfSites / 2 : kBfSites;
   while (NS > 1 && NS * per_site > 96 * 1024) NS /= 2;
   return BlockFactorDfSlot{p->box, p->wdf, p->twdfx, p->twdfy, p->efac, n, p->L, p->px,
                            p->py, p->blk_kx, p->blk_ky, NS};
