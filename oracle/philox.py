@@ -7,17 +7,19 @@ ten rounds of two 64x64->128-bit multiplies with a Weyl-sequence key bump.
 Uniforms and normals (the definition shared with the CUDA library, which has
 its own independent implementation):
 
-* u(w) = ((w >> 11) + 1/2) * 2^-53, a uniform in (0, 1) from a 64-bit word.
-* Box-Muller: r = sqrt(-2 ln u1); (xi, eta) = (r cos 2 pi u2, r sin 2 pi u2).
+* each 64-bit word w gives two 32-bit halves, h = w >> 32 and l = w mod 2^32,
+  and u(x) = (x + 1/2) * 2^-32 is a uniform in (0, 1) from a half;
+* Box-Muller on one word: r = sqrt(-2 ln u(h)); (xi, eta) =
+  (r cos 2 pi u(l), r sin 2 pi u(l)).
 
-Counter layout (key = (seed, 0)):
+Counter layout (key = (seed, 0)); one generator call serves four
+consecutive indices, index j taking word j mod 4:
 
 * stream 1, the circulant-embedding noise of realisation pair p at torus
-  index k (column-major, k = kx * Qy + ky): counter (k >> 1, p, 1, 0); the
-  words (w0, w1) serve even k, (w2, w3) odd k, giving (xi_k, eta_k).
+  index k (column-major, k = kx * Qy + ky): counter (k >> 2, p, 1, 0), word
+  k mod 4, giving (xi_k, eta_k).
 * stream 2, the site noise of realisation t at site i: counter
-  (i >> 1, t, 2, 0), words (w0, w1) for even i, (w2, w3) for odd i, giving
-  (xi'_i, eps_i).
+  (i >> 2, t, 2, 0), word i mod 4, giving (xi'_i, eps_i).
 """
 import numpy as np
 
@@ -61,24 +63,23 @@ def philox4x64(c0, c1, c2, c3, k0, k1, rounds=10):
     return c0, c1, c2, c3
 
 
-def uniform(w):
-    """u(w) = ((w >> 11) + 1/2) 2^-53 in (0, 1), exact in FP64."""
-    return ((np.asarray(w, np.uint64) >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+def uniform(x):
+    """u(x) = (x + 1/2) 2^-32 in (0, 1) for a 32-bit half x, exact in FP64."""
+    return (np.asarray(x, np.uint64).astype(np.float64) + 0.5) * 2.0 ** -32
 
 
-def box_muller(w1, w2):
-    """Two independent N(0, 1) from two 64-bit words."""
-    r = np.sqrt(-2.0 * np.log(uniform(w1)))
-    t = 2.0 * np.pi * uniform(w2)
+def box_muller(w):
+    """Two independent N(0, 1) from the two halves of a 64-bit word."""
+    w = np.asarray(w, np.uint64)
+    r = np.sqrt(-2.0 * np.log(uniform(w >> _S32)))
+    t = 2.0 * np.pi * uniform(w & _LO32)
     return r * np.cos(t), r * np.sin(t)
 
 
 def normal_pairs(index, sub, stream, seed):
     """The normal pair assigned to element `index` of realisation `sub` in `stream`."""
     index = np.asarray(index, dtype=np.uint64)
-    w = philox4x64(index >> np.uint64(1), np.uint64(sub), np.uint64(stream), 0,
+    w = philox4x64(index >> np.uint64(2), np.uint64(sub), np.uint64(stream), 0,
                    np.uint64(seed), 0)
-    odd = (index & np.uint64(1)).astype(bool)
-    wa = np.where(odd, w[2], w[0])
-    wb = np.where(odd, w[3], w[1])
-    return box_muller(wa, wb)
+    j = (index & np.uint64(3)).astype(np.int64)
+    return box_muller(np.choose(j, w))

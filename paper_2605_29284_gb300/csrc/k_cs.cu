@@ -2,13 +2,14 @@
 // of the simulated data; Section 6: circulant embedding).
 //
 // Noise: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by
-// (seed, 0).  Uniform u(w) = ((w >> 11) + 1/2) 2^-53; Box-Muller
-// (r cos 2 pi u2, r sin 2 pi u2), r = sqrt(-2 ln u1).
-//   stream 1: circulant-embedding noise of realisation pair p at torus index
-//             k = kx * qy + ky: counter (k >> 1, p, 1, 0), words (0, 1) for even
-//             k, (2, 3) for odd k.
+// (seed, 0).  A 64-bit word w gives two 32-bit halves h = w >> 32 and
+// l = w mod 2^32, u(x) = (x + 1/2) 2^-32; Box-Muller on one word:
+// (r cos 2 pi u(l), r sin 2 pi u(l)), r = sqrt(-2 ln u(h)).  One generator
+// call serves four consecutive indices, index j taking word j mod 4:
+//   stream 1: circulant-embedding noise of realisation pair p at torus
+//             index k = kx * qy + ky: counter (k >> 2, p, 1, 0).
 //   stream 2: site noise of global realisation t at site i: counter
-//             (i >> 1, t, 2, 0), words (0, 1) for even i, (2, 3) for odd i.
+//             (i >> 2, t, 2, 0).
 #include "common.cuh"
 #include "fft.cuh"
 #include "fftn.cuh"
@@ -50,30 +51,28 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], const PhiloxKeys& K
   }
 }
 
-// The uniform ((w >> 11) + 1/2) 2^-53 in float, within one unit in the last
-// place.  With v = w >> 11 = hi 2^21 + lo (hi < 2^32, lo < 2^21):
-// lo 2^-53 + 2^-54 is exact in float, and a fused multiply-add adds hi 2^-32
-// (hi itself rounded to 24 bits when it is longer).  Only 32-bit integer
-// conversions: the 64-bit one runs on GB300's FP64 pipe.
-__device__ __forceinline__ float uniform_f32(uint64_t w) {
-  const uint64_t v = w >> 11;
-  const float lo = fmaf((float)(unsigned)(v & 0x1fffffu), 0x1.0p-53f, 0x1.0p-54f);
-  return fmaf((float)(unsigned)(v >> 21), 0x1.0p-32f, lo);
+// The uniform (x + 1/2) 2^-32 of a 32-bit half x, rounded once to float:
+// the low byte's part (lo + 1/2) 2^-32 is exact in float, and a fused
+// multiply-add adds the high 24 bits' part (x >> 8) 2^-24.
+__device__ __forceinline__ float uniform_f32(uint32_t x) {
+  const float lo = fmaf((float)(x & 0xffu), 0x1.0p-32f, 0x1.0p-33f);
+  return fmaf((float)(x >> 8), 0x1.0p-24f, lo);
 }
 
-// Box-Muller on the words (wa, wb)
+// Box-Muller on the two halves of the word w
 template <typename T>
-__device__ __forceinline__ void box_muller(uint64_t wa, uint64_t wb, T& xi, T& eta) {
+__device__ __forceinline__ void box_muller(uint64_t w, T& xi, T& eta) {
+  const uint32_t h = (uint32_t)(w >> 32), l = (uint32_t)w;
   if (sizeof(T) == sizeof(double)) {
-    const double u1 = ((double)(wa >> 11) + 0.5) * 0x1.0p-53;
-    const double u2 = ((double)(wb >> 11) + 0.5) * 0x1.0p-53;
+    const double u1 = ((double)h + 0.5) * 0x1.0p-32;
+    const double u2 = ((double)l + 0.5) * 0x1.0p-32;
     const double r = sqrt(-2.0 * log(u1));
     double s, co;
     sincospi(2.0 * u2, &s, &co);
     xi = (T)(r * co);
     eta = (T)(r * s);
   } else {
-    const float u1 = uniform_f32(wa), u2 = uniform_f32(wb);
+    const float u1 = uniform_f32(h), u2 = uniform_f32(l);
     const float r = sqrtf(-2.0f * logf(u1));
     float s, co;
     sincospif(2.0f * u2, &s, &co);
@@ -86,9 +85,10 @@ __device__ __forceinline__ void box_muller(uint64_t wa, uint64_t wb, T& xi, T& e
 template <typename T>
 __device__ __forceinline__ void normal_pair(uint64_t index, uint64_t sub, uint64_t stream,
                                             const PhiloxKeys& keys, T& xi, T& eta) {
-  uint64_t c[4] = {index >> 1, sub, stream, 0ull};
+  uint64_t c[4] = {index >> 2, sub, stream, 0ull};
   philox4x64_10(c, keys);
-  box_muller<T>((index & 1) ? c[2] : c[0], (index & 1) ? c[3] : c[1], xi, eta);
+  const int j = (int)(index & 3);
+  box_muller<T>(j == 0 ? c[0] : j == 1 ? c[1] : j == 2 ? c[2] : c[3], xi, eta);
 }
 
 // ------------------------------------------------------------ CE columns --
@@ -106,20 +106,20 @@ ce_cols_kernel(const T* __restrict__ sqrtlam, int qx, int qy, const PhiloxKeys k
   const int pair = pair0 + blockIdx.y;
   const int kxh = kx < qx - kx ? kx : qx - kx;
   const T* sl = sqrtlam + (size_t)kxh * qy;
-  // one Philox call serves the torus indices 2m and 2m + 1 (words 0-1 and
-  // 2-3): each thread takes such a pair of this column's indices
+  // one Philox call serves the torus indices 4m .. 4m + 3 (word h for
+  // 4m + h): each thread takes such a quadruple of this column's indices
   const uint64_t kbase = (uint64_t)kx * qy;
-  for (uint64_t kk = (kbase & ~1ull) + 2ull * threadIdx.x; kk < kbase + qy;
-       kk += 2ull * blockDim.x) {
-    uint64_t c[4] = {kk >> 1, (uint64_t)pair, 1ull, 0ull};
+  for (uint64_t kk = (kbase & ~3ull) + 4ull * threadIdx.x; kk < kbase + qy;
+       kk += 4ull * blockDim.x) {
+    uint64_t c[4] = {kk >> 2, (uint64_t)pair, 1ull, 0ull};
     philox4x64_10(c, keys);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 4; ++h) {
       const uint64_t k = kk + h;
       if (k < kbase || k >= kbase + qy) continue;
       const int ky = (int)(k - kbase);
       T xi, eta;
-      box_muller<T>(c[2 * h], c[2 * h + 1], xi, eta);
+      box_muller<T>(c[h], xi, eta);
       const T s = sl[ky];
       bufa[ky] = mk<T>(s * xi, s * eta);
     }
@@ -223,16 +223,16 @@ ce_cols_n(const T* __restrict__ sqrtlam, int qx, const PhiloxKeys keys, int pair
     const int kxh = kx < qx - kx ? kx : qx - kx;
     const T* sl = sqrtlam + (size_t)kxh * N;
     const uint64_t kbase = (uint64_t)kx * N;
-    for (uint64_t kk = (kbase & ~1ull) + 2ull * tid; kk < kbase + N; kk += 2ull * THR) {
-      uint64_t c[4] = {kk >> 1, (uint64_t)pair, 1ull, 0ull};
+    for (uint64_t kk = (kbase & ~3ull) + 4ull * tid; kk < kbase + N; kk += 4ull * THR) {
+      uint64_t c[4] = {kk >> 2, (uint64_t)pair, 1ull, 0ull};
       philox4x64_10(c, keys);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < 4; ++h) {
         const uint64_t k = kk + h;
         if (k < kbase || k >= kbase + N) continue;
         const int ky = (int)(k - kbase);
         T xi, eta;
-        box_muller<T>(c[2 * h], c[2 * h + 1], xi, eta);
+        box_muller<T>(c[h], xi, eta);
         const T sv = sl[ky];
         buf[ky] = mk<T>(sv * xi, sv * eta);
       }

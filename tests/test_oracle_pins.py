@@ -6,6 +6,7 @@ least one of them.  Grids are deliberately rectangular and anisotropic
 (nx != ny, hx != hy) so that a transposition cannot cancel out.
 """
 import json
+import math
 import os
 from fractions import Fraction
 
@@ -335,13 +336,24 @@ def test_philox_matches_library_implementation():
 
 
 def test_uniform_and_normals():
-    w = np.array([0, 2 ** 64 - 1], dtype=np.uint64)
-    u = philox.uniform(w)
-    assert u[0] == 0.5 * 2.0 ** -53 and u[1] == 1.0 - 0.5 * 2.0 ** -53
+    x = np.array([0, 2 ** 32 - 1], dtype=np.uint64)
+    u = philox.uniform(x)
+    assert u[0] == 0.5 * 2.0 ** -32 and u[1] == 1.0 - 0.5 * 2.0 ** -32
+    # one generator call serves indices 4m .. 4m + 3, each from its own word:
+    # the high half through the radius, the low half through the angle
+    w = [int(v) for v in philox.philox4x64(5, 3, 1, 0, 99, 0)]
+    xi, eta = philox.normal_pairs(np.arange(20, 24, dtype=np.uint64), 3, 1, 99)
+    for j in range(4):
+        r = math.sqrt(-2.0 * math.log(((w[j] >> 32) + 0.5) / 2 ** 32))
+        a = 2.0 * math.pi * (((w[j] & 0xFFFFFFFF) + 0.5) / 2 ** 32)
+        assert abs(xi[j] - r * math.cos(a)) <= 1e-15 * max(r, 1.0)
+        assert abs(eta[j] - r * math.sin(a)) <= 1e-15 * max(r, 1.0)
     xi, eta = philox.normal_pairs(np.arange(200000, dtype=np.uint64), 3, 1, 99)
     for s in (xi, eta):
         assert abs(s.mean()) < 0.01 and abs(s.var() - 1) < 0.015
     assert abs(np.mean(xi * eta)) < 0.01
+    # neighbouring indices (same call, different words) are uncorrelated
+    assert abs(np.mean(xi[0::2] * xi[1::2])) < 0.01
 
 
 # ---------------------------------------------------- conditional simulation ----
