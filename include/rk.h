@@ -291,7 +291,11 @@ rk_status rk_predict_host_group(rk_plan* const* plans, int nplans, const int* n,
  * non-negative), site values z_u = A_i f_u[N(i)] + s_i xi + tau eps with
  * s_i^2 = max(0, sigma2 - k_i^T A_i), coefficients c = M^{-1} (z - z_u), and
  * f_c = rapid prediction of c + f_u on the window.  Noise is Philox4x64-10
- * keyed by seed (counter layout in the library's documentation).
+ * keyed by (seed, 0): one call per four consecutive indices (counter
+ * (index >> 2, realisation or pair, stream, 0), index j taking word j mod 4),
+ * Box-Muller on a word's high and low 32-bit halves, u(x) = (x + 1/2) 2^-32.
+ * Stream 1 is the embedding's noise at torus index kx * qy + ky for the
+ * realisation pair, stream 2 the site noise at site i for the realisation.
  *   out_dev  device, B x R x ny x nx in plan precision.
  * Needs rk_solve_coef (else RK_ERR_STATE); RK_ERR_CE_NEGATIVE if no
  * embedding up to four-fold growth is non-negative.
