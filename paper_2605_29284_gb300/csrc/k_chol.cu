@@ -240,12 +240,20 @@ __global__ void __launch_bounds__(SU) solve_update_kernel(const double* __restri
 // forward, the last going backward) then also takes that block's diagonal
 // step, x_next <- L^{-1} x_next (L^{-T} backward) with the inverted block of
 // chol_invert_diag_df, so the solve needs no separate launch for it.
+// Two threads per row, each summing one half of the block's columns (the
+// halves meet in shared memory): launches below one wave, most of them in
+// the later blocks, take the time of one CTA's chain, which this halves.
+constexpr int kUpdParts = 2;
+constexpr int kTailParts = SU * kUpdParts / SB;   // column quarters of the tail product
+
 template <bool FWD>
-__global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __restrict__ adf, int n,
-                                                             int k, double* x, int B, int knext) {
+__global__ void __launch_bounds__(SU * kUpdParts)
+solve_update_df_kernel(const float2* __restrict__ adf, int n, int k, double* x, int B,
+                       int knext) {
   __shared__ float2 Xs[SB][SF];
   __shared__ float2 Ys[SB][SF];             // the next block's updated rows (tail CTA)
-  __shared__ float2 Ps[SB][SF];             // half sums of its diagonal product
+  __shared__ float2 Hs[SU][SF];             // second column half's sums per row
+  __shared__ float2 Ps[kTailParts - 1][SB][SF];   // partial sums of the tail product
   const int nb = min(SB, n - k);
   const int f0 = blockIdx.y * SF;
   const int nf = min(SF, B - f0);
@@ -255,7 +263,8 @@ __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __res
     Xs[c][f] = make_float2(v.hi, v.lo);
   }
   __syncthreads();
-  const int r = (FWD ? k + nb : 0) + blockIdx.x * SU + threadIdx.x;
+  const int tr = threadIdx.x % SU, part = threadIdx.x / SU;
+  const int r = (FWD ? k + nb : 0) + blockIdx.x * SU + tr;
   const bool live = r < (FWD ? n : k);
   const bool tail = knext >= 0 && blockIdx.x == (FWD ? 0 : gridDim.x - 1);
   const int nbn = knext >= 0 ? min(SB, n - knext) : 0;
@@ -264,26 +273,39 @@ __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __res
     // the next diagonal block is read after the update: start moving its
     // 128-byte lines (16 float2 of a column) into L2 now
     const int c = threadIdx.x % SB;
-    for (int j = threadIdx.x / SB; j * 16 < nbn && c < nbn; j += SU / SB)
+    for (int j = threadIdx.x / SB; j * 16 < nbn && c < nbn; j += blockDim.x / SB)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(adf + (size_t)(knext + c) * n + knext + j * 16));
   }
+  dfacc acc[SF];
   if (live) {
-    dfacc acc[SF];
+    const int mid = (nb + 1) / 2;
+    const int ca = part ? mid : 0, cb = part ? nb : mid;
     const float2* col = adf + (size_t)k * n + r;
 #pragma unroll 8
-    for (int c = 0; c < nb; ++c) {
+    for (int c = ca; c < cb; ++c) {
       const float2 l2 = __ldg(col + (size_t)c * n);
       const dfl l = {l2.x, l2.y};
 #pragma unroll
       for (int f = 0; f < SF; ++f) dfacc_fma(acc[f], l, {Xs[c][f].x, Xs[c][f].y});
     }
+  }
+  if (part) {
+#pragma unroll
+    for (int f = 0; f < SF; ++f) {
+      const dfl v = dfacc_value(acc[f]);
+      Hs[tr][f] = make_float2(v.hi, v.lo);
+    }
+  }
+  __syncthreads();
+  if (!part && live) {
 #pragma unroll
     for (int f = 0; f < SF; ++f) {
       if (f >= nf) continue;
-      const double u = x[(size_t)(f0 + f) * n + r] - df_double(dfacc_value(acc[f]));
+      const dfl v = df_add(dfacc_value(acc[f]), {Hs[tr][f].x, Hs[tr][f].y});
+      const double u = x[(size_t)(f0 + f) * n + r] - df_double(v);
       if (inblk) {
-        const dfl v = df_make(u);
-        Ys[r - knext][f] = make_float2(v.hi, v.lo);
+        const dfl w = df_make(u);
+        Ys[r - knext][f] = make_float2(w.hi, w.lo);
       } else {
         x[(size_t)(f0 + f) * n + r] = u;
       }
@@ -293,35 +315,36 @@ __global__ void __launch_bounds__(SU) solve_update_df_kernel(const float2* __res
   __syncthreads();
   // x_next[row] = sum_c Tinv(row, c) y[c] (c <= row) forward, sum_c Tinv(c, row)
   // y[c] (c >= row) backward: adf's diagonal block at column c, row `row`;
-  // threads 0-63 and 64-127 take the two halves of the c range
-  const int row = threadIdx.x % SB, half = threadIdx.x / SB;
-  dfacc acc[SF];
+  // the c range in kTailParts pieces, one per thread of the row
+  const int row = threadIdx.x % SB, q = threadIdx.x / SB;
+  dfacc tacc[SF];
   if (row < nbn) {
     const int c0 = FWD ? 0 : row, c1 = FWD ? row + 1 : nbn;
-    const int mid = (c0 + c1) / 2;
-    const int ca = half ? mid : c0, cb = half ? c1 : mid;
+    const int ca = c0 + (c1 - c0) * q / kTailParts, cb = c0 + (c1 - c0) * (q + 1) / kTailParts;
     const float2* blk = adf + (size_t)knext * n + knext + row;
 #pragma unroll 8
     for (int c = ca; c < cb; ++c) {
       const float2 t2 = __ldg(blk + (size_t)c * n);
       const dfl t = {t2.x, t2.y};
 #pragma unroll
-      for (int f = 0; f < SF; ++f) dfacc_fma(acc[f], t, {Ys[c][f].x, Ys[c][f].y});
+      for (int f = 0; f < SF; ++f) dfacc_fma(tacc[f], t, {Ys[c][f].x, Ys[c][f].y});
     }
   }
-  if (half) {
+  if (q > 0) {
 #pragma unroll
     for (int f = 0; f < SF; ++f) {
-      const dfl v = dfacc_value(acc[f]);
-      Ps[row][f] = make_float2(v.hi, v.lo);
+      const dfl v = dfacc_value(tacc[f]);
+      Ps[q - 1][row][f] = make_float2(v.hi, v.lo);
     }
   }
   __syncthreads();
-  if (!half && row < nbn) {
+  if (q == 0 && row < nbn) {
 #pragma unroll
     for (int f = 0; f < SF; ++f) {
       if (f >= nf) continue;
-      const dfl v = df_add(dfacc_value(acc[f]), {Ps[row][f].x, Ps[row][f].y});
+      dfl v = dfacc_value(tacc[f]);
+#pragma unroll
+      for (int j = 0; j < kTailParts - 1; ++j) v = df_add(v, {Ps[j][row][f].x, Ps[j][row][f].y});
       x[(size_t)(f0 + f) * n + knext + row] = df_double(v);
     }
   }
@@ -454,7 +477,7 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
     const int rest = n - k - nb;
     if (rest > 0) {
       const dim3 grid((rest + SU - 1) / SU, fblocks);
-      if (adf) solve_update_df_kernel<true><<<grid, SU, 0, s>>>(adf, n, k, x, B, k + nb);
+      if (adf) solve_update_df_kernel<true><<<grid, SU * kUpdParts, 0, s>>>(adf, n, k, x, B, k + nb);
       else solve_update_kernel<true><<<grid, SU, 0, s>>>(a, n, k, x, B);
     }
   }
@@ -464,7 +487,7 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
     if (!adf) solve_diag_kernel<false><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     if (k > 0) {
       const dim3 grid((k + SU - 1) / SU, fblocks);
-      if (adf) solve_update_df_kernel<false><<<grid, SU, 0, s>>>(adf, n, k, x, B, k - SB);
+      if (adf) solve_update_df_kernel<false><<<grid, SU * kUpdParts, 0, s>>>(adf, n, k, x, B, k - SB);
       else solve_update_kernel<false><<<grid, SU, 0, s>>>(a, n, k, x, B);
     }
   }
