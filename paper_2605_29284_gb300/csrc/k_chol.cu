@@ -240,16 +240,16 @@ __global__ void __launch_bounds__(SU) solve_update_kernel(const double* __restri
 // forward, the last going backward) then also takes that block's diagonal
 // step, x_next <- L^{-1} x_next (L^{-T} backward) with the inverted block of
 // chol_invert_diag_df, so the solve needs no separate launch for it.
-// Two threads per row, each summing one half of the block's columns (the
-// halves meet in shared memory): launches below one wave, most of them in
-// the later blocks, take the time of one CTA's chain, which this halves.
-constexpr int kUpdParts = 2;
-constexpr int kTailParts = SU * kUpdParts / SB;   // column quarters of the tail product
-
-template <bool FWD>
-__global__ void __launch_bounds__(SU * kUpdParts)
+// P = 2: two threads per row, each summing one half of the block's columns
+// (the halves meet in shared memory): a launch below one wave takes the
+// time of one CTA's chain, which this halves.  P = 1 for launches of more
+// than a wave, where the denser one-thread-per-row CTAs fit more per SM.
+template <bool FWD, int P>
+__global__ void __launch_bounds__(SU * P)
 solve_update_df_kernel(const float2* __restrict__ adf, int n, int k, double* x, int B,
                        int knext) {
+  constexpr int kUpdParts = P;
+  constexpr int kTailParts = SU * P / SB;   // column pieces of the tail product
   __shared__ float2 Xs[SB][SF];
   __shared__ float2 Ys[SB][SF];             // the next block's updated rows (tail CTA)
   __shared__ float2 Hs[SU][SF];             // second column half's sums per row
@@ -278,8 +278,7 @@ solve_update_df_kernel(const float2* __restrict__ adf, int n, int k, double* x, 
   }
   dfacc acc[SF];
   if (live) {
-    const int mid = (nb + 1) / 2;
-    const int ca = part ? mid : 0, cb = part ? nb : mid;
+    const int ca = nb * part / kUpdParts, cb = nb * (part + 1) / kUpdParts;
     const float2* col = adf + (size_t)k * n + r;
 #pragma unroll 8
     for (int c = ca; c < cb; ++c) {
@@ -289,19 +288,22 @@ solve_update_df_kernel(const float2* __restrict__ adf, int n, int k, double* x, 
       for (int f = 0; f < SF; ++f) dfacc_fma(acc[f], l, {Xs[c][f].x, Xs[c][f].y});
     }
   }
-  if (part) {
+  if (kUpdParts > 1) {
+    if (part) {
 #pragma unroll
-    for (int f = 0; f < SF; ++f) {
-      const dfl v = dfacc_value(acc[f]);
-      Hs[tr][f] = make_float2(v.hi, v.lo);
+      for (int f = 0; f < SF; ++f) {
+        const dfl v = dfacc_value(acc[f]);
+        Hs[tr][f] = make_float2(v.hi, v.lo);
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (!part && live) {
 #pragma unroll
     for (int f = 0; f < SF; ++f) {
       if (f >= nf) continue;
-      const dfl v = df_add(dfacc_value(acc[f]), {Hs[tr][f].x, Hs[tr][f].y});
+      dfl v = dfacc_value(acc[f]);
+      if (kUpdParts > 1) v = df_add(v, {Hs[tr][f].x, Hs[tr][f].y});
       const double u = x[(size_t)(f0 + f) * n + r] - df_double(v);
       if (inblk) {
         const dfl w = df_make(u);
@@ -468,6 +470,15 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
   const int dgrid = (B + 3) / 4;              // four warps (right-hand sides) per CTA
   const int igrid = (B + kDiagRhs - 1) / kDiagRhs;
   const int fblocks = (B + SF - 1) / SF;
+  // CTAs of the two-thread-per-row update that one wave holds (four per SM)
+  static unsigned one_wave = 0;
+  if (one_wave == 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cudaGetLastError();
+    one_wave = 4u * (unsigned)sms;
+  }
   // double-float: the first block's diagonal step is a launch of its own,
   // every later one runs in the tail CTA of the update before it
   if (adf) solve_diag_inv_df_kernel<true><<<igrid, SB * kDiagRhs, 0, s>>>(adf, n, 0, x, B);
@@ -477,7 +488,12 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
     const int rest = n - k - nb;
     if (rest > 0) {
       const dim3 grid((rest + SU - 1) / SU, fblocks);
-      if (adf) solve_update_df_kernel<true><<<grid, SU * kUpdParts, 0, s>>>(adf, n, k, x, B, k + nb);
+      if (adf) {
+        if (grid.x * grid.y <= one_wave)
+          solve_update_df_kernel<true, 2><<<grid, SU * 2, 0, s>>>(adf, n, k, x, B, k + nb);
+        else
+          solve_update_df_kernel<true, 1><<<grid, SU, 0, s>>>(adf, n, k, x, B, k + nb);
+      }
       else solve_update_kernel<true><<<grid, SU, 0, s>>>(a, n, k, x, B);
     }
   }
@@ -487,7 +503,12 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
     if (!adf) solve_diag_kernel<false><<<dgrid, 128, 0, s>>>(a, n, k, x, B);
     if (k > 0) {
       const dim3 grid((k + SU - 1) / SU, fblocks);
-      if (adf) solve_update_df_kernel<false><<<grid, SU * kUpdParts, 0, s>>>(adf, n, k, x, B, k - SB);
+      if (adf) {
+        if (grid.x * grid.y <= one_wave)
+          solve_update_df_kernel<false, 2><<<grid, SU * 2, 0, s>>>(adf, n, k, x, B, k - SB);
+        else
+          solve_update_df_kernel<false, 1><<<grid, SU, 0, s>>>(adf, n, k, x, B, k - SB);
+      }
       else solve_update_kernel<false><<<grid, SU, 0, s>>>(a, n, k, x, B);
     }
   }
