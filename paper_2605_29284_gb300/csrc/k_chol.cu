@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(SU) solve_update_kernel(const double* __restri
 // P = 2: two threads per row, each summing one half of the block's columns
 // (the halves meet in shared memory): a launch below one wave takes the
 // time of one CTA's chain, which this halves.  P = 1 for launches of more
-// than a wave, where the denser one-thread-per-row CTAs fit more per SM.
+// than two such waves, where the denser one-thread-per-row CTAs fit more
+// per SM.
 template <bool FWD, int P>
 __global__ void __launch_bounds__(SU * P)
 solve_update_df_kernel(const float2* __restrict__ adf, int n, int k, double* x, int B,
@@ -470,14 +471,15 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
   const int dgrid = (B + 3) / 4;              // four warps (right-hand sides) per CTA
   const int igrid = (B + kDiagRhs - 1) / kDiagRhs;
   const int fblocks = (B + SF - 1) / SF;
-  // CTAs of the two-thread-per-row update that one wave holds (four per SM)
-  static unsigned one_wave = 0;
-  if (one_wave == 0) {
+  // two waves of the two-thread-per-row update (four CTAs per SM): up to
+  // there its shorter chains win, beyond it the denser one-thread CTAs
+  static unsigned two_waves = 0;
+  if (two_waves == 0) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return cudaGetLastError();
-    one_wave = 4u * (unsigned)sms;
+    two_waves = 8u * (unsigned)sms;
   }
   // double-float: the first block's diagonal step is a launch of its own,
   // every later one runs in the tail CTA of the update before it
@@ -489,7 +491,7 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
     if (rest > 0) {
       const dim3 grid((rest + SU - 1) / SU, fblocks);
       if (adf) {
-        if (grid.x * grid.y <= one_wave)
+        if (grid.x * grid.y <= two_waves)
           solve_update_df_kernel<true, 2><<<grid, SU * 2, 0, s>>>(adf, n, k, x, B, k + nb);
         else
           solve_update_df_kernel<true, 1><<<grid, SU, 0, s>>>(adf, n, k, x, B, k + nb);
@@ -504,7 +506,7 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
     if (k > 0) {
       const dim3 grid((k + SU - 1) / SU, fblocks);
       if (adf) {
-        if (grid.x * grid.y <= one_wave)
+        if (grid.x * grid.y <= two_waves)
           solve_update_df_kernel<false, 2><<<grid, SU * 2, 0, s>>>(adf, n, k, x, B, k - SB);
         else
           solve_update_df_kernel<false, 1><<<grid, SU, 0, s>>>(adf, n, k, x, B, k - SB);
