@@ -354,22 +354,25 @@ __global__ void __launch_bounds__(256) matvec_dkxx_df_kernel(const float2* __res
       const int ee = rows ? e : e - kDF * kDT;
       const int f = ee / kDT, t = ee % kDT;
       if (f0 + f >= B || (!rows && diag)) continue;
-      dfl acc = {0.f, 0.f};
+      // unnormalised double-float sums: one addition per term on the
+      // accumulator's dependency chain instead of a full renormalisation
+      dfacc acc;
       if (rows) {
 #pragma unroll 4
         for (int b = 0; b < kDT; ++b) {
           const float2 k = Ks[t][b], x = cJ[f][b];
-          acc = df_fma({k.x, k.y}, {x.x, x.y}, acc);
+          dfacc_fma(acc, {k.x, k.y}, {x.x, x.y});
         }
       } else {
 #pragma unroll 4
         for (int a = 0; a < kDT; ++a) {
           const float2 k = Ks[a][t], x = cI[f][a];
-          acc = df_fma({k.x, k.y}, {x.x, x.y}, acc);
+          dfacc_fma(acc, {k.x, k.y}, {x.x, x.y});
         }
       }
+      const dfl v = dfacc_value(acc);
       part[(((size_t)tile * 2 + (rows ? 0 : 1)) * B + f0 + f) * kDT + t] =
-          make_float2(acc.hi, acc.lo);
+          make_float2(v.hi, v.lo);
     }
   }
 }
