@@ -673,7 +673,7 @@ __device__ __forceinline__ void block_factor_df_cta(const BlockFactorDfSlot& sl,
   // stage 1: t(kx, b) = sum_a A_i[a + W b] e^{-2 pi i kx (ix + a) / px}
   for (int p = lane; p < nk * W; p += lanes) {
     const int kx = p / W, b = p - kx * W;
-    dfl tr = {0.f, 0.f}, ti = {0.f, 0.f};
+    dfacc ar, ai;                           // unnormalised pair sums
     if (live) {
       int m = (kx * ix) % px;               // kx (ix + a) mod px, stepped by kx
 #pragma unroll
@@ -681,12 +681,13 @@ __device__ __forceinline__ void block_factor_df_cta(const BlockFactorDfSlot& sl,
         const float4 tw = twx[m];
         const float2 wv = wdf[(size_t)i * M + a + W * b];
         const dfl w = {wv.x, wv.y};
-        tr = df_fma(w, {tw.x, tw.y}, tr);
-        ti = df_fma(w, {tw.z, tw.w}, ti);
+        dfacc_fma(ar, w, {tw.x, tw.y});
+        dfacc_fma(ai, w, {tw.z, tw.w});
         m += kx;
         m = m >= px ? m - px : m;
       }
     }
+    const dfl tr = dfacc_value(ar), ti = dfacc_value(ai);
     tsm[(si * nk + kx) * W + b] = make_float4(tr.hi, tr.lo, ti.hi, ti.lo);
   }
   __syncthreads();
@@ -698,19 +699,21 @@ __device__ __forceinline__ void block_factor_df_cta(const BlockFactorDfSlot& sl,
   for (int q = lane; q < nk * nky; q += lanes) {
     const int kx = q / nky, ky = q - kx * nky;
     const float4* t = tsm + (si * nk + kx) * W;
-    dfl A = {0.f, 0.f}, Bs = {0.f, 0.f}, Cs = {0.f, 0.f}, D = {0.f, 0.f};
+    dfacc sa, sb, sc, sd;
     int m = (ky * iy) % py;                 // ky (iy + b) mod py, stepped by ky
 #pragma unroll
     for (int b = 0; b < W; ++b) {
       const float4 f = twy[m], tb = t[b];
       const dfl fr = {f.x, f.y}, fi = {f.z, f.w}, tr = {tb.x, tb.y}, ti = {tb.z, tb.w};
-      A = df_fma(tr, fr, A);
-      Bs = df_fma(ti, fi, Bs);
-      Cs = df_fma(tr, fi, Cs);
-      D = df_fma(ti, fr, D);
+      dfacc_fma(sa, tr, fr);
+      dfacc_fma(sb, ti, fi);
+      dfacc_fma(sc, tr, fi);
+      dfacc_fma(sd, ti, fr);
       m += ky;
       m = m >= py ? m - py : m;
     }
+    const dfl A = dfacc_value(sa), Bs = dfacc_value(sb), Cs = dfacc_value(sc),
+              D = dfacc_value(sd);
     double2* out = efac + (size_t)kx * bw * n + i;
     out[(size_t)(KY + ky) * n] = make_double2(df_double(df_add(A, df_neg(Bs))),
                                              df_double(df_add(Cs, D)));
