@@ -425,7 +425,7 @@ TRAFFIC = {
     # profiles/weights_paper350.md: the grouped double-float weights of the nine cells
     ("weights", "paper350"): {"bytes_per_launch": 128768 + 0,
                               "sources": ["k_sites.cu", "common.cuh", "dfloat.cuh"],
-                              "digest": "8f0bc7b0947edbd7"},
+                              "digest": "4905b3db313c491b"},
 }
 
 def _sources_digest(files):
