@@ -15,9 +15,11 @@
  *  - Every call is asynchronous on the plan's CUDA stream unless its comment
  *    says otherwise.  Pointers named *_dev are device pointers owned by the
  *    caller; *_host pointers are host memory owned by the caller.  The plan
- *    owns all of its scratch space; it is allocated by rk_plan_create,
- *    rk_set_sites and rk_set_coef/rk_solve_coef (never by rk_predict,
- *    rk_simulate or rk_predict_backward).
+ *    owns all of its scratch space.  It is allocated by rk_plan_create,
+ *    rk_set_sites and rk_set_coef/rk_solve_coef; rk_predict and
+ *    rk_predict_group never allocate; rk_simulate and rk_predict_backward
+ *    allocate their own scratch on their first call and again whenever the
+ *    number of fields (times realisations) grows beyond what they hold.
  *  - Statuses are returned, never raised: no entry point exits, traps or
  *    prints.  After any status other than RK_OK and RK_ERR_CUDA the plan is
  *    still usable; after RK_ERR_CUDA it must be destroyed.
@@ -245,8 +247,10 @@ rk_status rk_predict_group(rk_plan* const* plans, int nplans, void* const* outs)
  * before any stream capture.  Every call shares the one array and the array
  * keeps the last call's contents, so calls that overlap on the GPU (on
  * different streams or host threads) race and must be serialised by the
- * caller; the scatter writes every element of c* on every call, so nothing
- * carries over from one call to the next.
+ * caller.  Nothing carries over from one call to the next: with fewer than
+ * 4096 sites the scatter clears c* in the array before it accumulates into
+ * it, and with 4096 or more the tiled scatter writes every element of c*;
+ * every other buffer in the array is fully written before it is read.
  */
 rk_status rk_predict_static(rk_plan* plan, void* out_dev);
 

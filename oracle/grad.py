@@ -34,8 +34,68 @@ def _dist(a, b):
     return np.sqrt(dx * dx + dy * dy)
 
 
-def adjoint(xy, z, gbar, g, nu, rho, sigma2, tau2):
-    """(d/dz, d/dlog rho, d/dlog sigma^2) of sum(gbar * g_hat) per field."""
+class _DenseGrid:
+    """The grid products K_gg a, K_gg^T gbar and K'_gg a as dense matrices."""
+
+    def __init__(self, g, nu, rho, sigma2):
+        D = _dist(g.nodes(), g.padded_nodes())
+        self.K = matern.cov(D, nu, rho, sigma2)            # N x P1^2
+        self.dK = matern.cov_dlogrho(D, nu, rho, sigma2)
+
+    def fwd(self, a):
+        return a @ self.K.T
+
+    def adj(self, gb):
+        return gb @ self.K
+
+    def dfwd(self, a):
+        return a @ self.dK.T
+
+
+class _FftGrid:
+    """The same three products through the circulant embedding of steps 2, 6, 7
+    (torus of rapid.torus_size): the symmetric base makes K_gg^T gbar the same
+    circulant convolution, with gbar placed at the window offset L - 1 and the
+    result kept on the padded grid."""
+
+    def __init__(self, g, nu, rho, sigma2):
+        self.g = g
+        self.px, self.py = rapid.torus_size(g.nx, g.L), rapid.torus_size(g.ny, g.L)
+        kx, ky = np.arange(self.px), np.arange(self.py)
+        dx = np.minimum(kx, self.px - kx) * g.hx
+        dy = np.minimum(ky, self.py - ky) * g.hy
+        D = np.sqrt(dx[None, :] ** 2 + dy[:, None] ** 2)
+        self.lam = np.fft.fft2(matern.cov(D, nu, rho, sigma2))
+        self.dlam = np.fft.fft2(matern.cov_dlogrho(D, nu, rho, sigma2))
+
+    def _conv(self, x, lam, r0, nr, nc, o0, on_r, on_c):
+        out = []
+        for row in x:
+            C = np.zeros((self.py, self.px))
+            C[r0:r0 + nr, r0:r0 + nc] = row.reshape(nr, nc)
+            full = np.fft.ifft2(lam * np.fft.fft2(C)).real
+            out.append(full[o0:o0 + on_r, o0:o0 + on_c].ravel())
+        return np.array(out)
+
+    def fwd(self, a, lam=None):
+        g = self.g
+        return self._conv(a, self.lam if lam is None else lam, 0, g.p1y, g.p1x, g.L - 1,
+                          g.ny, g.nx)
+
+    def adj(self, gb):
+        g = self.g
+        return self._conv(gb, self.lam, g.L - 1, g.ny, g.nx, 0, g.p1y, g.p1x)
+
+    def dfwd(self, a):
+        return self.fwd(a, self.dlam)
+
+
+def adjoint(xy, z, gbar, g, nu, rho, sigma2, tau2, grid_products="dense"):
+    """(d/dz, d/dlog rho, d/dlog sigma^2) of sum(gbar * g_hat) per field.
+
+    grid_products: "dense" forms K_gg (tiny grids); "fft" evaluates the same
+    products through the circulant embedding (the torus of steps 2, 6, 7).
+    """
     xy = np.asarray(xy, np.float64)
     z = np.atleast_2d(np.asarray(z, np.float64))
     gbar = np.asarray(gbar, np.float64).reshape(z.shape[0], g.ny * g.nx)
@@ -44,14 +104,13 @@ def adjoint(xy, z, gbar, g, nu, rho, sigma2, tau2):
     _, _, W = rapid.weights(xy, g, nu, rho, sigma2)
     c = kriging.solve_chol(Lc, z.T).T                     # B x n
     cstar = rapid.scatter(ix, iy, W, c, g).reshape(z.shape[0], -1)
-    nodes, pnodes = g.nodes(), g.padded_nodes()
-    Dgp = _dist(nodes, pnodes)
-    Kgp = matern.cov(Dgp, nu, rho, sigma2)
-    dKgp = matern.cov_dlogrho(Dgp, nu, rho, sigma2)
-    ghat = cstar @ Kgp.T                                  # B x N
-    abar = gbar @ Kgp                                     # B x P1^2
-    A = rapid.dense_A(ix, iy, W, g)                       # n x P1^2
-    cbar = abar @ A.T                                     # B x n
+    gp = (_DenseGrid if grid_products == "dense" else _FftGrid)(g, nu, rho, sigma2)
+    ghat = gp.fwd(cstar)                                  # B x N
+    abar = gp.adj(gbar)                                   # B x P1^2
+    ab2 = abar.reshape(-1, g.p1y, g.p1x)
+    a_, b_ = rapid.local_offsets(g.L)
+    cbar = np.einsum("nq,bnq->bn", W,
+                     ab2[:, iy[:, None] + b_[None, :], ix[:, None] + a_[None, :]])
     zbar = kriging.solve_chol(Lc, cbar.T).T               # B x n
     Dxx = _dist(xy, xy)
     Kxx = matern.cov(Dxx, nu, rho, sigma2)
@@ -73,7 +132,7 @@ def adjoint(xy, z, gbar, g, nu, rho, sigma2, tau2):
         an = ab[iy[:, None] + b[None, :], ix[:, None] + a[None, :]]   # n x M
         un = linalg.cho_solve(cf, an.T).T                              # n x M
         wterm = np.sum(dk * un, axis=1) - np.sum((W @ dKN) * un, axis=1)
-        g_rho[f] = (gbar[f] @ (dKgp @ cstar[f]) + np.sum(c[f] * wterm)
+        g_rho[f] = (gbar[f] @ gp.dfwd(cstar[f:f + 1])[0] + np.sum(c[f] * wterm)
                     - zbar[f] @ (dKxx @ c[f]))
     return zbar, g_rho, g_s2
 

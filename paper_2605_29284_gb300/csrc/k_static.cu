@@ -49,7 +49,9 @@ static rk_status predict_static(rk_plan* p, T* out, unsigned char* base) {
   const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
   const C<T>* twy = f32 ? (const C<T>*)p->tw32y : (const C<T>*)p->tw64y;
-  // the tiled scatter writes every element of c*, so nothing needs clearing
+  // c* needs no clearing here: below kTileSortMin sites launch_scatter
+  // clears it before the atomic accumulation, and from kTileSortMin on the
+  // tiled scatter writes every element of it
   if (launch_scatter<T>(p, w, p->c64, B, cstar, s) != cudaSuccess ||
       launch_rows_fwd<T>(cstar, p->p1y, p->p1x, (long long)plane, p->p1x, tb, p->ldt,
                          (long long)p->H * p->ldt, B, p->fpx, twx, p->H, s) != cudaSuccess)

@@ -401,6 +401,41 @@ def test_conditional_simulation_matches_kriging_moments_on_nodes():
     assert abs(ratio - 1.0) < 0.08
 
 
+def test_site_values_off_node_have_field_moments():
+    # Reading of the local simulation step: for a site off the nodes,
+    # z_u,i = W_i . f[N(i)] + s_i xi' + tau eps with s_i^2 = sigma^2 - k_i^T W_i.
+    # If f is an exact GP draw, two moments follow from K_N W_i = k_i alone:
+    # Var z_u,i = k_i^T W_i + s_i^2 + tau^2 = sigma^2 + tau^2, and
+    # Cov(z_u,i, f_q) = (K_N W_i)_q = k(s_i, s_q) for every neighbour q.
+    # The fields here come from a dense Cholesky of the padded grid's
+    # covariance, not from the circulant embedding.
+    ext = (0.0, 1.0, 0.0, 0.9)
+    g = rapid.Grid(9, 8, ext, 2)
+    nu, rho, sigma2, tau2 = 0.5, 0.06, 1.3, 0.4
+    xy = synth.sites_uniform(10, ext, 41)
+    s = cs.site_sd(xy, g, nu, rho, sigma2)
+    assert np.mean(s ** 2) > 0.3 * sigma2     # the residual term carries real weight
+    pn = g.padded_nodes()
+    Lf = np.linalg.cholesky(matern.cross_cov(pn, pn, nu, rho, sigma2)
+                            + 1e-12 * np.eye(len(pn)))
+    R = 6000
+    F = (Lf @ synth.normals((len(pn), R), 42)).T            # R x (P1y P1x)
+    zu = np.stack([cs.site_values(F[t].reshape(g.p1y, g.p1x), xy, g, nu, rho, sigma2, tau2,
+                                  t, 43) for t in range(R)])
+    var = zu.var(axis=0)
+    se = (sigma2 + tau2) * np.sqrt(2.0 / R)
+    assert np.abs(var - (sigma2 + tau2)).max() < 5 * se
+    assert abs(var.mean() - (sigma2 + tau2)) < 4 * se / np.sqrt(3.0)
+    ix, iy, _, _ = rapid.box_assign(xy, g)
+    a, b = rapid.local_offsets(g.L)
+    q = (iy[:, None] + b[None, :]) * g.p1x + (ix[:, None] + a[None, :])   # n x M padded index
+    zc = zu - zu.mean(0)
+    Fc = F - F.mean(0)
+    emp = np.einsum("ti,tiq->iq", zc, Fc[:, q]) / R
+    ref = matern.cross_cov(xy, pn, nu, rho, sigma2)[np.arange(len(xy))[:, None], q]
+    assert np.abs(emp - ref).max() < 5 * np.sqrt((sigma2 + tau2) * sigma2 / R)
+
+
 # ------------------------------------------------------------- gradients ----
 
 def test_adjoint_matches_finite_differences():
@@ -420,6 +455,21 @@ def test_adjoint_matches_finite_differences():
         zp[:, i] += 1e-6
         dz = (grad.loss_linear(xy, zp, gbar, g, *th) - base) / 1e-6
         np.testing.assert_allclose(zbar[:, i], dz, rtol=1e-4, atol=1e-6)
+
+
+def test_adjoint_fft_route_equals_dense_route():
+    # the adjoint's three grid products through the circulant embedding equal
+    # the dense K_gg products (rectangular, anisotropic grid, L = 3)
+    ext = (0.0, 1.2, 0.0, 0.8)
+    g = rapid.Grid(17, 13, ext, 3)
+    xy = synth.sites_uniform(30, ext, 36)
+    z = synth.normals((2, 30), 37)
+    gbar = synth.normals((2, 13, 17), 38)
+    th = (2.5, 0.3, 1.1, 1e-2)
+    dense = grad.adjoint(xy, z, gbar, g, *th)
+    fft = grad.adjoint(xy, z, gbar, g, *th, grid_products="fft")
+    for a, b in zip(fft, dense):
+        assert np.abs(a - b).max() <= 1e-11 * np.abs(b).max()
 
 
 def test_adjoint_close_to_exact_kriging_gradient():

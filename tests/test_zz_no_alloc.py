@@ -32,16 +32,19 @@ def _static(rk, plan, out):
     return out
 
 
+# n = 1368 scatters with atomics into a cleared c*; n = 5000 (>= 4096) takes
+# the tiled scatter, which writes every element of c* without clearing it
+@pytest.mark.parametrize("n,B", [(1368, 2), (5000, 1)])
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("fp64", 1e-12)])
-def test_static_scratch_matches_rk_predict_on_consecutive_calls(rk, prec, tol):
+def test_static_scratch_matches_rk_predict_on_consecutive_calls(rk, prec, tol, n, B):
     ext = (0.0, 1.6, 0.0, 1.0)
-    nx, ny, n, L, B = 350, 350, 1368, 2, 2
+    nx, ny, L = 350, 350, 2
     xy = torch.from_numpy(synth.sites("rainfall_standin", n, ext, 20705)).cuda()
     with rk.Plan(nx, ny, ext, 1.5, 0.15, 1.0, 1e-3, L, precision=prec) as p:
         p.set_sites(xy)
         for call, seed in enumerate((1, 2)):
-            # different coefficients on each call: the second call must not
-            # see anything the first one left in the shared array
+            # very different coefficients on each call: the second call must
+            # not see anything the first one left in the shared array
             c = torch.from_numpy(synth.normals((B, n), seed) * (30.0 if call else 1.0)).cuda()
             p.set_coef(c)
             ref = p.predict().double()
@@ -50,6 +53,24 @@ def test_static_scratch_matches_rk_predict_on_consecutive_calls(rk, prec, tol):
             torch.cuda.synchronize()
             err = float((got - ref).abs().max() / ref.abs().max())
             assert err <= tol, (call, err)
+
+
+def test_static_calls_leave_free_device_memory_unchanged(rk):
+    ext = (0.0, 1.0, 0.0, 1.0)
+    n, B = 5000, 1
+    xy = torch.from_numpy(synth.sites("uniform", n, ext, 20805)).cuda()
+    c = torch.from_numpy(synth.normals((B, n), 3)).cuda()
+    with rk.Plan(256, 256, ext, 1.5, 0.1, 1.0, 1e-3, 2, precision="fp32") as p:
+        p.set_sites(xy)
+        p.set_coef(c)
+        out = torch.empty((B, 256, 256), dtype=p.dtype, device="cuda")
+        _static(rk, p, out)          # the first call looks the array's address up
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(5):
+            _static(rk, p, out)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_static_scratch_rejects_oversized_batches(rk):
