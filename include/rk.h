@@ -351,6 +351,37 @@ typedef struct {
 rk_status rk_profile_enable(int on);
 int rk_profile_read(rk_profile_entry* out, int max);
 
+/*
+ * FFT pass variants and their tuner (no counterpart in the paper: how the
+ * transforms of steps 6-7 are run).  Each of the three passes of a
+ * compile-time torus length n (rows of c* forward, columns forward-spectrum-
+ * inverse, rows inverse; pass 0, 1, 2) has variant 0, one transform per
+ * radix stage in shared memory, and variants 1.., register-resident
+ * transforms with E elements per thread (radix plan) and V transforms per
+ * CTA.  The first plan created with a torus length (per precision, per
+ * process) times every variant of each pass on a synthetic batch and keeps
+ * the fastest; RK_FFT_TUNE=0 in the environment keeps variant 1 instead.
+ * The choice is process-wide; the per-length twiddle tables are per device.
+ *
+ * rk_fft_variants     number of variants of a pass (1 for lengths with no
+ *                     specialisation, which run the generic kernels).
+ * rk_fft_get_choice   *cand = the variant in use, -1 before the first plan.
+ * rk_fft_set_choice   forces a variant (RK_ERR_INVALID_ARG out of range);
+ *                     uploads its tables to the current device.
+ * rk_fft_variant_info *e, *v of a variant (0, 0 for variant 0).
+ * rk_fft_tune         re-times every variant of the three passes on stream
+ *                     (NULL: legacy default) and keeps the fastest; when
+ *                     times_ms is not NULL it receives 24 doubles,
+ *                     times_ms[pass * 8 + variant] = mean milliseconds per
+ *                     launch (-1 where a variant could not launch).
+ *                     Allocates and frees its test buffers; synchronises.
+ */
+int rk_fft_variants(int n, int precision, int pass);
+rk_status rk_fft_get_choice(int n, int precision, int pass, int* cand);
+rk_status rk_fft_set_choice(int n, int precision, int pass, int cand);
+rk_status rk_fft_variant_info(int n, int precision, int pass, int cand, int* e, int* v);
+rk_status rk_fft_tune(int n, int precision, void* stream, double* times_ms);
+
 /* A static string naming the status. */
 const char* rk_status_string(rk_status s);
 

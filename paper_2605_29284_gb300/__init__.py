@@ -10,6 +10,8 @@ import numpy as np
 import torch
 
 from ._native import RK_FP32, RK_FP64, PlanInfo, RkError, check, lib, profile_enable, profile_read
+from ._native import (FFT_PASSES, fft_get_choice, fft_set_choice, fft_tune, fft_variant_info,
+                      fft_variants)
 
 __all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "predict_group",
            "predict_host_group", "HostGroupCall", "profile_enable", "profile_read",

@@ -73,6 +73,10 @@ _SIGS = {
     "rk_simulate": [_vp, _int, ctypes.c_ulonglong, _vp],
     "rk_predict_backward": [_vp, _vp, _vp, _vp, _vp],
     "rk_debug_copy": [_vp, _int, _vp, ctypes.c_size_t],
+    "rk_fft_get_choice": [_int, _int, _int, ctypes.POINTER(_int)],
+    "rk_fft_set_choice": [_int, _int, _int, _int],
+    "rk_fft_variant_info": [_int, _int, _int, _int, ctypes.POINTER(_int), ctypes.POINTER(_int)],
+    "rk_fft_tune": [_int, _int, _vp, ctypes.POINTER(_dbl)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -82,6 +86,8 @@ lib.rk_profile_enable.argtypes = [_int]
 lib.rk_profile_enable.restype = _int
 lib.rk_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), _int]
 lib.rk_profile_read.restype = _int
+lib.rk_fft_variants.argtypes = [_int, _int, _int]
+lib.rk_fft_variants.restype = _int
 lib.rk_status_string.argtypes = [_int]
 lib.rk_status_string.restype = ctypes.c_char_p
 
@@ -103,3 +109,41 @@ def profile_read():
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes, buf[i].flops,
                                    buf[i].pipe)
             for i in range(k)}
+
+
+FFT_PASSES = ("rows_fwd", "cols", "rows_inv")
+
+
+def fft_variants(n, precision, pass_):
+    """Number of FFT pass variants for torus length n (variant 0: the
+    one-transform-per-stage kernels; 1..: register-resident variants)."""
+    return lib.rk_fft_variants(int(n), int(precision), int(pass_))
+
+
+def fft_variant_info(n, precision, pass_, cand):
+    """(elements per thread, transforms per CTA) of a variant ((0, 0) for variant 0)."""
+    e, v = _int(), _int()
+    check(lib.rk_fft_variant_info(int(n), int(precision), int(pass_), int(cand), ctypes.byref(e),
+                                  ctypes.byref(v)), "rk_fft_variant_info")
+    return e.value, v.value
+
+
+def fft_get_choice(n, precision, pass_):
+    """The variant in use (-1 before the first plan with this length)."""
+    c = _int()
+    check(lib.rk_fft_get_choice(int(n), int(precision), int(pass_), ctypes.byref(c)),
+          "rk_fft_get_choice")
+    return c.value
+
+
+def fft_set_choice(n, precision, pass_, cand):
+    check(lib.rk_fft_set_choice(int(n), int(precision), int(pass_), int(cand)),
+          "rk_fft_set_choice")
+
+
+def fft_tune(n, precision, stream=None):
+    """Re-tunes the three passes of length n; returns {pass: [ms per variant]}."""
+    t = (_dbl * 24)()
+    check(lib.rk_fft_tune(int(n), int(precision), stream, t), "rk_fft_tune")
+    return {name: [t[p * 8 + c] for c in range(fft_variants(n, precision, p))]
+            for p, name in enumerate(FFT_PASSES)}

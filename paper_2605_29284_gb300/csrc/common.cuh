@@ -324,6 +324,22 @@ bool launch_rows_inv_group(const Group<RowsInvSlot<T>>& g, int N, const C<T>* tw
                            cudaStream_t s, cudaError_t* err);
 // true when a specialised pass exists for length N
 bool fftn_specialised(int N);
+// The register-resident variants of the specialised passes (k_fftr.cu):
+// candidate 0 of each pass is the k_fftn.cu kernel, 1.. the variants; the
+// choice per (N, precision, pass) is made by fft_setup (tuned on first use)
+// or rk_fft_set_choice.  The rfft_* launchers return false when candidate 0
+// is chosen (the caller then runs its own kernel).
+enum { FFT_PASS_ROWS_FWD = 0, FFT_PASS_COLS = 1, FFT_PASS_ROWS_INV = 2 };
+int fft_variants(int N, int precision, int pass);
+int fft_choice(int N, int precision, int pass);
+cudaError_t fft_prepare(int N, int precision);
+cudaError_t fft_setup(int N, int precision, cudaStream_t s);
+template <typename T>
+bool rfft_rows_fwd(const Group<RowsFwdSlot<T>>& g, int N, cudaStream_t s, cudaError_t* err);
+template <typename T>
+bool rfft_cols(Group<ColsSlot<T>>& g, int mode, int N, int H, cudaStream_t s, cudaError_t* err);
+template <typename T>
+bool rfft_rows_inv(const Group<RowsInvSlot<T>>& g, int N, cudaStream_t s, cudaError_t* err);
 // true when RK_FFT_GENERIC is set in the environment: use only the generic passes
 bool fft_generic_only();
 

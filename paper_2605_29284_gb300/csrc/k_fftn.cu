@@ -351,6 +351,7 @@ bool fftn_specialised(int N) {
 template <typename T>
 bool launch_rows_fwd_group(const Group<RowsFwdSlot<T>>& g, int N, const C<T>* tw, int H,
                            cudaStream_t s, cudaError_t* err) {
+  if (rfft_rows_fwd<T>(g, N, s, err)) return true;
   switch (N) {
 #define RK_CASE(NN) case NN: *err = go_rows_fwd<T, NN>(g, tw, H, s); return true;
     RK_SIZES(RK_CASE)
@@ -362,6 +363,7 @@ bool launch_rows_fwd_group(const Group<RowsFwdSlot<T>>& g, int N, const C<T>* tw
 template <typename T>
 bool launch_cols_group(Group<ColsSlot<T>>& g, int mode, int N, const C<T>* tw, int H,
                        cudaStream_t s, cudaError_t* err) {
+  if (rfft_cols<T>(g, mode, N, H, s, err)) return true;
   switch (N) {
 #define RK_CASE(NN) case NN: *err = go_cols<T, NN>(g, mode, H, tw, s); return true;
     RK_SIZES(RK_CASE)
@@ -373,6 +375,7 @@ bool launch_cols_group(Group<ColsSlot<T>>& g, int mode, int N, const C<T>* tw, i
 template <typename T>
 bool launch_rows_inv_group(const Group<RowsInvSlot<T>>& g, int N, const C<T>* tw, int H,
                            cudaStream_t s, cudaError_t* err) {
+  if (rfft_rows_inv<T>(g, N, s, err)) return true;
   switch (N) {
 #define RK_CASE(NN) case NN: *err = go_rows_inv<T, NN>(g, tw, H, s); return true;
     RK_SIZES(RK_CASE)

@@ -905,8 +905,10 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
   p->px = choose_torus(2 * (nx + L - 2) > p->p1x ? 2 * (nx + L - 2) : p->p1x);
   p->py = choose_torus(2 * (ny + L - 2) > p->p1y ? 2 * (ny + L - 2) : p->p1y);
   p->H = p->px / 2 + 1;
-  p->ldt = p->p1y;
-  p->ldu = p->p1y;   // the adjoint writes p1y rows
+  // transposed spectra: a multiple of 16 rows per column, so that the row
+  // passes' blocks of 2V rows start on 64-byte (FP32) boundaries
+  p->ldt = (p->p1y + 15) / 16 * 16;
+  p->ldu = p->ldt;   // the adjoint writes p1y rows
   p->stream = (cudaStream_t)stream;
   p->fpx = make_fft_plan(p->px);
   p->fpy = make_fft_plan(p->py);
@@ -944,6 +946,14 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
     if (precision == RK_FP32 && ((st = upload_twiddles_df(p->px, &p->twdfx)) != RK_OK ||
                                  (st = upload_twiddles_df(p->py, &p->twdfy)) != RK_OK))
       break;
+    // the FFT pass variants of these lengths (tuned on their first use in
+    // the process); the spectrum below already runs on them
+    if (!fft_generic_only() &&
+        (fft_setup(p->px, precision, p->stream) != cudaSuccess ||
+         (p->py != p->px && fft_setup(p->py, precision, p->stream) != cudaSuccess))) {
+      st = RK_ERR_CUDA;
+      break;
+    }
     if ((st = compute_spectrum(p, 0, &p->lam64, &p->lam32)) != RK_OK) break;
     if (precision == RK_FP32 && (st = choose_block(p)) != RK_OK) break;
     if ((st = dalloc(&p->kn_chol, (size_t)p->M * p->M)) != RK_OK) break;
