@@ -1,20 +1,26 @@
 """Benchmark of rapid Kriging prediction on GB300 (one JSON line on rank 0).
 
-Workload (default "paper350"): the paper-scale single prediction -- n = 1368
-clustered sites on [0,1.6] x [0,1], a 350 x 350 grid, range 0.15, sigma^2 = 1,
-tau^2 = 1e-3 -- swept over nu in {0.5, 1.5, 2.5} and L in {1, 2, 3}.  One
-step is the rapid prediction of all nine cells from (sites, coefficients)
-resident in HBM: box assignment and weights (steps 3-4), scatter c* = A^T c
-(step 5) and the FFT convolution and crop (steps 6-7).  Coefficients
-c = M^{-1} z come from the library's FP64 Cholesky at set-up, like the fitted
-model of the paper's timing.  The plans (K_N factor, circulant eigenvalues)
-are built once per covariance before timing.
+Workload (default "pred1024"): the 1024 x 1024 grid on [0,1]^2 with n = 20000
+uniform sites and 16 data fields, Matern nu = 5/2, range 0.08, sigma^2 = 1,
+tau^2 = 1e-3, L = 3 (M = 36; torus 2187^2).  One step is the rapid
+prediction of the 16 fields from (sites, coefficients) resident in HBM: box
+assignment and weights (steps 3-4), the exact low-frequency block, the
+scatter c* = A^T c (step 5) and the FFT convolution and crop (steps 6-7),
+replayed as a CUDA graph.  The coefficients c = M^{-1} z come from the
+library's FP64 Cholesky at set-up, like the fitted model of the paper's
+timing; z are seeded smooth fields at the sites (synth.smooth_field).
 
-"grad1024" runs the 1024 x 1024 grid (n = 20000, 16 fields, nu = 2.5,
-range 0.08, L = 3) forward prediction instead.
+"paper350" runs the paper-scale configuration instead (n = 1368 clustered
+sites, 350^2 grid on [0,1.6] x [0,1], range 0.15, tau^2 = 1e-3, nine cells
+nu in {1/2, 3/2, 5/2} x L in {1, 2, 3}); by default it is measured as a
+secondary, with conditional simulation (512^2, R = 256), the three-grid
+simulation call (128^2, 256^2, 512^2, R = 64 each) and the 1024^2 adjoint.
 
---impl reference times the FP64 CPU oracle (direct Eq. (9) sum) on a bounded
-sample of the same workload on the host cores.
+The oracle (FP64, numpy, host cores) runs only in the cpu_baseline leg: its
+rate on a bounded sample, and its values at seeded grid nodes, against which
+the GPU outputs saved by the GPU arm are compared (the "error" entries).
+
+--impl reference times the oracle on a bounded sample of the same workload.
 """
 import argparse
 import json
@@ -33,6 +39,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "grid-point predictions/s (N x realizations)"
+NODE_SAMPLE = 128          # seeded grid nodes per checked field
 
 
 def parse():
@@ -41,15 +48,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper350", choices=["paper350", "grad1024"])
+    ap.add_argument("--workload", default="pred1024", choices=["pred1024", "paper350"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU path")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the CPU oracle leg (rate and errors)")
     ap.add_argument("--no-secondary", action="store_true",
-                    help="skip the 1024^2, conditional-simulation and adjoint measurements")
+                    help="skip the secondary measurements")
     ap.add_argument("--backward-n", type=int, default=None,
                     help="sites for the adjoint measurement (default: the workload's 20000)")
-    ap.add_argument("--secondary-only", choices=["cs512", "grad1024_backward"], default=None,
+    ap.add_argument("--secondary-only", default=None,
+                    choices=["paper350", "cs512", "grad1024_backward"],
                     help="run one secondary measurement alone and print it (for profiling)")
     return ap.parse_args()
 
@@ -57,8 +66,9 @@ def parse():
 # ------------------------------------------------------------------ workloads --
 
 def workload_cells(name):
-    """[(cell name, plan kwargs, n, B)] and the sites of the workload."""
-    w = synth.WORKLOADS[name]
+    """The workload's sites and [(cell name, plan kwargs, fields)]."""
+    key = "grad1024" if name == "pred1024" else name
+    w = synth.WORKLOADS[key]
     seed = synth.seed_for(w["config"])
     xy = synth.sites(w["sites"], w["n"], w["extent"], seed)
     cells = []
@@ -69,10 +79,16 @@ def workload_cells(name):
                                                    nu=nu, rho=w["rho"], sigma2=w["sigma2"],
                                                    tau2=w["tau2"], L=L), w["B"]))
     else:
-        cells.append(("grad1024", dict(nx=w["nx"], ny=w["ny"], extent=w["extent"], nu=w["nu"],
-                                       rho=w["rho"], sigma2=w["sigma2"], tau2=w["tau2"],
-                                       L=w["L"]), w["B"]))
+        cells.append((name, dict(nx=w["nx"], ny=w["ny"], extent=w["extent"], nu=w["nu"],
+                                 rho=w["rho"], sigma2=w["sigma2"], tau2=w["tau2"],
+                                 L=w["L"]), w["B"]))
     return w, xy, cells
+
+
+def workload_data(name):
+    """The data fields z (B x n): seeded smooth fields at the sites."""
+    w, xy, cells = workload_cells(name)
+    return synth.smooth_field(xy, cells[0][2], synth.seed_for(w["config"], 1))
 
 
 def max_over_ranks(x, device):
@@ -90,9 +106,22 @@ def max_over_ranks(x, device):
 def workload_config(name, world=1):
     """The workload part of the JSON line's config (both arms)."""
     w, xy, cells = workload_cells(name)
-    return {"workload": name, "cells": [c[0] for c in cells],
-            "grid": f"{cells[0][1]['nx']}x{cells[0][1]['ny']}", "n": int(xy.shape[0]),
-            "fields_per_cell": cells[0][2], "parallelism": f"replicas x{world}"}
+    kw = cells[0][1]
+    cfg = {"workload": name, "grid": f"{kw['nx']}x{kw['ny']}", "n": int(xy.shape[0]),
+           "fields_per_cell": cells[0][2], "parallelism": f"replicas x{world}",
+           "data": "seeded smooth fields at the sites (synth.smooth_field); c = M^-1 z "
+                   "by the library's FP64 Cholesky at set-up"}
+    if name == "paper350":
+        cfg["cells"] = [c[0] for c in cells]
+        cfg["sites"] = "1368 clustered (60% jittered lattice, 40% in 5 Gaussian blobs)"
+    else:
+        cfg.update(nu=kw["nu"], range=kw["rho"], tau2=kw["tau2"], L=kw["L"])
+    return cfg
+
+
+def sample_nodes(nx, ny, seed=7, k=NODE_SAMPLE):
+    rs = np.random.default_rng(seed)
+    return rs.integers(0, nx, k), rs.integers(0, ny, k)
 
 
 # -------------------------------------------------------------------- clocks --
@@ -149,7 +178,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------- our arm --
+# ------------------------------------------------------------- roofline --
 
 def _load_peaks():
     try:
@@ -158,37 +187,111 @@ def _load_peaks():
         return {}
 
 
+# GB300's FP64 peak from its unit counts and clock: 152 SMs x 2070 MHz x
+# 4 FP64 operations per clock per SM (two fused multiply-adds) = 1.26 TFLOP/s,
+# NVIDIA's nominal 1.25 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+# double-float on the FP32 pipe: 152 SMs x 128 lanes x 2070 MHz FP32
+# instructions per second, 12 of them per double-float multiply-add of an
+# unnormalised pair sum (product, its error, two cross terms, TwoSum, one
+# add), 2 operations per multiply-add = 6.7 TFLOP/s of FP64-class work
+DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
+
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel (its
+# summary file under profiles/ gives the command), the workload it was taken
+# on and a digest of the sources it was built from; reported only while the
+# sources are unchanged
+TRAFFIC = {}
+
+
+def _sources_digest(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2605_29284_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, workload):
+    t = TRAFFIC.get((kernel, workload))
+    if not t:
+        return None
+    try:
+        return t["bytes_per_launch"] if _sources_digest(t["sources"]) == t["digest"] else None
+    except OSError:
+        return None
+
+
+def roofline(prof, steps, peaks, workload=None):
+    """The dominant kernel's roofline (by time): HBM-bound passes as algorithmic
+    bytes per second against the measured copy bandwidth, FP64 and
+    double-float passes as algorithmic FP64-class operations per second."""
+    hbm = peaks.get("hbm_gbs")
+    src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    dname, (dl, dms, dbytes, dflops, dpipe) = max(prof.items(), key=lambda kv: kv[1][1])
+    kernels = {}
+    for k, v in prof.items():
+        e = {"launches": v[0], "ms_per_step": v[1] / steps,
+             "GBps": v[2] / (v[1] / 1e3) / 1e9 if v[1] > 0 else None,
+             "bytes_per_launch": v[2] / v[0]}
+        if v[3] > 0:
+            key = "fp64_TFLOPs" if v[4] == 64 else "double_float_TFLOPs"
+            e[key] = v[3] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None
+        kernels[k] = e
+    traffic = _traffic(dname, workload)
+    if dflops > 0:
+        achieved = dflops / (dms / 1e3) / 1e12
+        if dpipe == 64:
+            peak, psrc = FP64_PEAK_TFLOPS, "nominal FP64 (152 SMs x 2070 MHz x 4)"
+        else:
+            peak, psrc = DF_PEAK_TFLOPS, ("double-float on the FP32 pipe (152 SMs x 128 lanes x "
+                                          "2070 MHz / 12 instructions x 2)")
+        roof = {"bound": "alu", "kernel": dname, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": psrc}
+    else:
+        achieved = dbytes / dl / (dms / dl / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                "peak_source": src + " copy bandwidth"}
+    return roof, kernels
+
+
+def transform_model_bytes(nx, ny, L, P):
+    """Algorithmic bytes per FP32 field of the FFT convolution (steps 6-7) in the
+    two-pass model: c* in, the row spectra out and in, the needed column results
+    out and in, the window out: 4 P1^2 + 8 P1 H + 8 m H + 8 m H + 4 m^2 for a
+    square grid (m = nx = ny, P1 = m + 2 (L - 1), H = P / 2 + 1)."""
+    p1y, p1x, H = ny + 2 * (L - 1), nx + 2 * (L - 1), P // 2 + 1
+    return 4.0 * p1y * p1x + 8.0 * p1y * H + 16.0 * ny * H + 4.0 * ny * nx
+
+
+# ------------------------------------------------------------------ the arm --
+
 class Arm:
     """One workload on one device: plans, resident inputs and a timed step."""
 
-    def __init__(self, workload, precision, dev, solve=True):
+    def __init__(self, workload, precision, dev):
         import torch
         import paper_2605_29284_gb300 as rk
         self.torch, self.rk, self.dev = torch, rk, dev
+        self.name = workload
         self.w, self.xy_np, self.cells = workload_cells(workload)
+        self.z_np = workload_data(workload)
         self.xy = torch.from_numpy(self.xy_np).to(dev)
-        n = self.xy_np.shape[0]
         self.st = []
         for name, kw, B in self.cells:
             p = rk.Plan(kw["nx"], kw["ny"], kw["extent"], kw["nu"], kw["rho"], kw["sigma2"],
                         kw["tau2"], kw["L"], precision=precision)
-            if solve:
-                # coefficients from the library's FP64 Cholesky (untimed set-up)
-                z = torch.from_numpy(synth.normals((B, n), synth.seed_for(self.w["config"], 1)))
-                p.set_obs(self.xy, z.to(dev))
-                c = p.debug_copy("coef").clone()
-            else:
-                # timing does not depend on the values: seeded coefficients of the
-                # size the solve produces (|c| ~ 1 / sqrt(tau^2))
-                c = torch.from_numpy(synth.normals((B, n), synth.seed_for(self.w["config"], 2))
-                                     / np.sqrt(kw["tau2"])).to(dev)
-                p.set_sites(self.xy)
-                p.set_coef(c)
+            # coefficients from the library's FP64 Cholesky (untimed set-up)
+            p.set_obs(self.xy, torch.from_numpy(self.z_np[:B]).to(dev))
+            c = p.debug_copy("coef").clone()
             out = torch.empty((B, kw["ny"], kw["nx"]), dtype=p.dtype, device=dev)
             self.st.append((p, c, out))
         self.points = sum(kw["nx"] * kw["ny"] * B for _, kw, B in self.cells)
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-        # one stream per cell: the cells are independent predictions
         self.streams = [torch.cuda.Stream(device=dev) for _ in self.st]
         tori = {(p.info()["px"], p.info()["py"]) for p, _, _ in self.st}
         self.grouped = len(tori) == 1 and len(self.st) <= 16
@@ -224,7 +327,7 @@ class Arm:
             cur.wait_event(e)
 
     def capture(self):
-        """Capture one step (all cells, their streams forked and joined) in a CUDA graph."""
+        """Capture one step in a CUDA graph."""
         torch = self.torch
         for _ in range(2):
             self._issue()
@@ -274,6 +377,17 @@ class Arm:
             torch.distributed.barrier()
         return max_over_ranks(total, self.dev), prof
 
+    def samples(self):
+        """The last step's outputs at seeded nodes of the first and last field
+        of every cell: {cell: [(field, jx, jy, values)]} (host arrays)."""
+        self.torch.cuda.synchronize()
+        res = {}
+        for (name, kw, B), (p, c, out) in zip(self.cells, self.st):
+            jx, jy = sample_nodes(kw["nx"], kw["ny"])
+            o = out.double().cpu().numpy()
+            res[name] = [(f, jx, jy, o[f][jy, jx]) for f in sorted({0, B - 1})]
+        return res
+
     def e2e(self, steps, warmup):
         """The same step through the host-buffer API (a prepared
         rk_predict_host_group call, or rk_predict_host per cell): sites and
@@ -310,28 +424,79 @@ class Arm:
         d2h = sum(B * kw["nx"] * kw["ny"] * esz for _, kw, B in self.cells)
         return self.points * steps / acc, h2d, d2h
 
+    def launches_per_step(self):
+        """Our kernels per step: per L one weights launch (grouped), the scatter
+        order for n >= 4096 (scan, fill), for FP32 plans the block factors, the
+        coefficient split and the block GEMM; the coefficient copy; a zeroing
+        pass when a cell scatters with atomics (n < 4096); scatter, rows_fwd,
+        cols, rows_inv."""
+        f32 = self.st[0][0].dtype == self.torch.float32
+        ncell = len(self.cells)
+        nsite = int(self.xy_np.shape[0])
+        order = 2 if nsite >= 4096 else 0
+        zero = 0 if nsite >= 4096 else 1
+        blk = 3 if f32 else 0
+        if self.grouped:
+            nL = len({kw["L"] for _, kw, _ in self.cells})
+            return nL + ncell * order + blk + 1 + zero + 4
+        return ncell * (1 + order + blk + 1 + zero + 4)
+
     def close(self):
         for p, _, _ in self.st:
             p.close()
 
 
+# ------------------------------------------------------------ secondaries --
+
+def measure_paper350(dev, steps, peaks, world):
+    """The paper-scale step (nine cells) in FP32 and FP64, with outputs sampled
+    for the oracle leg."""
+    a = Arm("paper350", "fp32", dev)
+    ms_p, prof = a.timed(steps, 2, world, profile=True)
+    a.capture()
+    ms, _ = a.timed(steps, 2, world)
+    roof, kernels = roofline(prof, steps, peaks, "paper350")
+    res = {"value": a.points * steps * world / (ms / 1e3), "unit": "grid-point predictions/s",
+           "ms_per_step": ms / steps, "roofline": roof, "kernels": kernels,
+           "config": workload_config("paper350", world)}
+    samples = {"fp32": a.samples()}
+    a.close()
+    a64 = Arm("paper350", "fp64", dev)
+    a64.capture()
+    ms64, _ = a64.timed(max(2, steps // 2), 2, world)
+    res["fp64_path"] = {"value": a64.points * max(2, steps // 2) * world / (ms64 / 1e3),
+                        "ms_per_step": ms64 / max(2, steps // 2)}
+    samples["fp64"] = a64.samples()
+    a64.close()
+    return res, samples
+
+
+def _cs_plan(rk, torch, dev, name, nx, R=None):
+    w = synth.WORKLOADS[name]
+    xy = synth.sites(w["sites"], w["n"], w["extent"], synth.seed_for(w["config"]))
+    z = synth.smooth_field(xy, 1, synth.seed_for(w["config"], 1))
+    p = rk.Plan(nx, nx, w["extent"], w["nu"], w["rho"], w["sigma2"], w["tau2"], w["L"])
+    p.set_obs(torch.from_numpy(xy).to(dev), torch.from_numpy(z).to(dev))
+    return p, w, xy, z
+
+
 def measure_cs(dev, steps, peaks, R=None):
-    """Conditional simulation, 512 x 512 grid, n = 5000 sites, R realisations per call."""
+    """Conditional simulation, 512 x 512 grid, n = 5000 sites, R realisations per
+    call; realisations 0 and 1 of seed 1 are sampled for the oracle leg."""
     import torch
     import paper_2605_29284_gb300 as rk
     w = synth.WORKLOADS["cs512"]
     R = R or w["R"]
-    xy = torch.from_numpy(synth.sites(w["sites"], w["n"], w["extent"],
-                                      synth.seed_for(w["config"]))).to(dev)
-    z = torch.from_numpy(synth.normals((1, w["n"]), synth.seed_for(w["config"], 1))).to(dev)
-    p = rk.Plan(w["nx"], w["ny"], w["extent"], w["nu"], w["rho"], w["sigma2"], w["tau2"], w["L"])
     t0 = time.perf_counter()
-    p.set_obs(xy, z)                     # FP64 Cholesky of K_xx + tau^2 I (set-up)
+    p, _, _, _ = _cs_plan(rk, torch, dev, "cs512", w["nx"])
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     out = torch.empty((1, R, w["ny"], w["nx"]), dtype=torch.float32, device=dev)
     p.simulate(R, 1, out)
     torch.cuda.synchronize()
+    jx, jy = sample_nodes(w["nx"], w["ny"])
+    o = out[0, :2].double().cpu().numpy()
+    sample = [(t, jx, jy, o[t][jy, jx]) for t in range(2)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     total = 0.0
     rk.profile_read()
@@ -356,21 +521,25 @@ def measure_cs(dev, steps, peaks, R=None):
             "ms_per_call": sec * 1e3, "setup_cholesky_s": setup_s, "kernels": kernels,
             "roofline": roof,
             "config": {"grid": "512x512", "n": w["n"], "R": R, "nu": w["nu"], "range": w["rho"],
-                       "L": w["L"], "tau2": w["tau2"], "ce_torus": [info["qx"], info["qy"]]}}
+                       "L": w["L"], "tau2": w["tau2"], "ce_torus": [info["qx"], info["qy"]]}}, \
+        sample
 
 
 def measure_backward(dev, steps, peaks, n=None):
-    """Forward and adjoint on the 1024 x 1024 grid, 16 fields, nu = 5/2, L = 3."""
+    """Forward and adjoint on the 1024 x 1024 grid, 16 fields, nu = 5/2, L = 3,
+    and the FP32 theta-gradients against central differences of the FP64 map
+    (4-point stencil, step 0.03 in log range and log sigma^2; fields 0, 15)."""
     import torch
     import paper_2605_29284_gb300 as rk
     w = synth.WORKLOADS["grad1024"]
     n = n or w["n"]
-    xy = torch.from_numpy(synth.sites(w["sites"], n, w["extent"],
-                                      synth.seed_for(w["config"]))).to(dev)
-    z = torch.from_numpy(synth.normals((w["B"], n), synth.seed_for(w["config"], 1))).to(dev)
+    xy_np = synth.sites(w["sites"], n, w["extent"], synth.seed_for(w["config"]))
+    xy = torch.from_numpy(xy_np).to(dev)
+    z = torch.from_numpy(synth.smooth_field(xy_np, w["B"], synth.seed_for(w["config"], 1))).to(dev)
     gbar = torch.from_numpy(synth.normals((w["B"], w["ny"], w["nx"]),
                                           synth.seed_for(w["config"], 2))).float().to(dev)
-    p = rk.Plan(w["nx"], w["ny"], w["extent"], w["nu"], w["rho"], w["sigma2"], w["tau2"], w["L"])
+    args = (w["nx"], w["ny"], w["extent"], w["nu"], w["rho"], w["sigma2"], w["tau2"], w["L"])
+    p = rk.Plan(*args)
     t0 = time.perf_counter()
     p.set_obs(xy, z)
     torch.cuda.synchronize()
@@ -391,196 +560,76 @@ def measure_backward(dev, steps, peaks, n=None):
         c.synchronize()
         fwd += a.elapsed_time(b)
         bwd += b.elapsed_time(c)
+    _, g_rho, g_s2 = (t.cpu().numpy() if t is not None else None for t in p.backward(gbar))
     p.close()
+    # central differences of sum(gbar * g_hat) in FP64 plans
+    fields = [0, w["B"] - 1]
+    gb64 = gbar.double()[fields]
+    z2 = z[fields].contiguous()
+
+    def loss(rho, s2):
+        a2 = list(args)
+        a2[4], a2[5] = rho, s2
+        with rk.Plan(*a2, precision="fp64") as q:
+            q.set_obs(xy, z2)
+            return (q.predict() * gb64).sum(dim=(1, 2)).cpu().numpy()
+    # a 4-point stencil at h = 0.03 (error O(h^4)): the weights of each
+    # re-created plan carry the rounding of the neighbourhood solve (cond K_N
+    # ~ 1e12 at nu = 5/2, L = 3), which swamps quotients of steps near 1e-4
+    h = 0.03
+    r0, s0 = w["rho"], w["sigma2"]
+
+    def d4(f):
+        return (8.0 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12.0 * h)
+    fd_rho = d4(lambda t: loss(r0 * np.exp(t), s0))
+    fd_s2 = d4(lambda t: loss(r0, s0 * np.exp(t)))
+    err = max(float(np.abs(g_rho[fields] - fd_rho).max() / np.abs(fd_rho).max()),
+              float(np.abs(g_s2[fields] - fd_s2).max() / np.abs(fd_s2).max()))
+    with rk.Plan(*args, precision="fp64") as q:
+        q.set_obs(xy, z2)
+        _, r64, s64 = (t.cpu().numpy() for t in q.backward(gb64))
+    detail = {"fd_rho": fd_rho.tolist(), "fd_s2": fd_s2.tolist(),
+              "fp32_rho": g_rho[fields].tolist(), "fp32_s2": g_s2[fields].tolist(),
+              "fp64_rho": r64.tolist(), "fp64_s2": s64.tolist()}
     return {"forward_ms": fwd / steps, "backward_ms": bwd / steps,
             "value": w["B"] * w["nx"] * w["ny"] / ((fwd + bwd) / steps / 1e3),
             "unit": "grid-point predictions/s (forward + adjoint)", "setup_cholesky_s": setup_s,
+            "gradient_error_vs_fd": {"value": err, "fields": fields, "step": h,
+                                     "stencil": "4-point", "detail": detail,
+                                     "what": "max over log range and log sigma^2 of |FP32 "
+                                             "adjoint - central difference of the FP64 map| / "
+                                             "max |difference|"},
             "config": {"grid": "1024x1024", "n": n, "fields": w["B"], "nu": w["nu"],
                        "range": w["rho"], "L": w["L"], "tau2": w["tau2"]}}
 
 
-# GB300's FP64 peak from its unit counts and clock: 152 SMs x 2070 MHz x
-# 4 FP64 operations per clock per SM (two fused multiply-adds) = 1.26 TFLOP/s,
-# NVIDIA's nominal 1.25 TFLOP/s
-FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
-# double-float on the FP32 pipe: 152 SMs x 128 lanes x 2070 MHz FP32
-# instructions per second, 15 of them per double-float multiply-add (the
-# library's df_fma: product, its error, two cross terms, TwoSum, FastTwoSum),
-# 2 operations per multiply-add = 5.4 TFLOP/s of FP64-precision-equivalent work
-DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 15 * 2 / 1e12
-
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel, the
-# workload it was taken on and a digest of the sources it was built from; the
-# bench reports it only while those sources are unchanged (profiles/ has the
-# captures and commands)
-TRAFFIC = {
-    # profiles/cols_grad1024.md: ncu --set full, one launch (16 fields, P = 2187)
-    ("cols", "grad1024"): {"bytes_per_launch": 163075584 + 99437824,
-                           "sources": ["k_fftn.cu", "fftn.cuh", "fft.cuh"],
-                           "digest": "52d5115a63d8320e"},
-    # profiles/cols_paper350.md: the grouped column pass of the nine cells
-    ("cols", "paper350"): {"bytes_per_launch": 18881536 + 512,
-                           "sources": ["k_fftn.cu", "fftn.cuh", "fft.cuh"],
-                           "digest": "52d5115a63d8320e"},
-    # profiles/weights_paper350.md: the grouped double-float weights of the nine cells
-    ("weights", "paper350"): {"bytes_per_launch": 128768 + 0,
-                              "sources": ["k_sites.cu", "common.cuh", "dfloat.cuh"],
-                              "digest": "4905b3db313c491b"},
-}
-
-def _sources_digest(files):
-    import hashlib
-    h = hashlib.sha256()
-    for f in files:
-        with open(os.path.join(ROOT, "paper_2605_29284_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
-def _traffic(kernel, workload):
-    t = TRAFFIC.get((kernel, workload))
-    if not t:
-        return None
-    try:
-        return t["bytes_per_launch"] if _sources_digest(t["sources"]) == t["digest"] else None
-    except OSError:
-        return None
-
-
-def roofline(prof, steps, peaks, workload=None):
-    """The dominant kernel's roofline (by time): HBM-bound passes as algorithmic
-    bytes per second against the measured copy bandwidth, FP64-bound passes as
-    algorithmic FP64 operations per second against the FP64 peak."""
-    hbm = peaks.get("hbm_gbs")
-    src = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
-    dname, (dl, dms, dbytes, dflops, dpipe) = max(prof.items(), key=lambda kv: kv[1][1])
-    kernels = {}
-    for k, v in prof.items():
-        e = {"launches": v[0], "ms_per_step": v[1] / steps,
-             "GBps": v[2] / (v[1] / 1e3) / 1e9 if v[1] > 0 else None,
-             "bytes_per_launch": v[2] / v[0]}
-        if v[3] > 0:
-            key = "fp64_TFLOPs" if v[4] == 64 else "double_float_TFLOPs"
-            e[key] = v[3] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None
-        kernels[k] = e
-    traffic = _traffic(dname, workload)
-    if dflops > 0:
-        achieved = dflops / (dms / 1e3) / 1e12
-        if dpipe == 64:
-            peak, src = FP64_PEAK_TFLOPS, "nominal FP64 (152 SMs x 2070 MHz x 4)"
-        else:
-            peak, src = DF_PEAK_TFLOPS, ("double-float on the FP32 pipe (152 SMs x 128 lanes x "
-                                         "2070 MHz / 15 instructions x 2)")
-        roof = {"bound": "alu", "kernel": dname, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": src}
-    else:
-        achieved = dbytes / (dms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic, "peak_source": src}
-    return roof, kernels
-
-
-def run_ours(args, rank, world):
-    import torch
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    peaks = _load_peaks()
-    main = Arm(args.workload, args.precision, dev, solve=args.workload != "grad1024")
-    sampler = ClockSampler(dev.index)
-    sampler.start()
-    # timed region 1: the step issued from the host with per-kernel CUDA events
-    # (the roofline's kernel durations); timed region 2: the same step replayed
-    # from a CUDA graph (the headline value)
-    prof_ms, prof = main.timed(args.steps, args.warmup, world, profile=True)
-    main.capture()
-    total_ms, _ = main.timed(args.steps, args.warmup, world)
-    clocks = sampler.stop()
-    value = main.points * args.steps * world / (total_ms / 1e3)
-    value_nograph = main.points * args.steps * world / (prof_ms / 1e3)
-    roof, kernels = roofline(prof, args.steps, peaks, args.workload)
-    main.graph = None
-    e2e_value, h2d, d2h = main.e2e(max(3, args.steps // 2), 2)
-    fp64 = None
-    if not args.no_fp64 and args.precision == "fp32":
-        a64 = Arm(args.workload, "fp64", dev, solve=args.workload != "grad1024")
-        k64 = max(2, args.steps // 5)
-        a64.capture()
-        ms64, _ = a64.timed(k64, 2, world)
-        v64 = a64.points * k64 * world / (ms64 / 1e3)
-        fp64 = {"value": v64, "unit": "grid-point predictions/s", "ms_per_step": ms64 / k64,
-                "speedup_fp32_over_fp64": value / v64}
-        a64.close()
-    secondary = {}
-    if args.workload == "paper350" and not args.no_secondary:
-        # the 1024 x 1024 grid the roofline target is quoted on: 16 fields, n = 20000
-        a = Arm("grad1024", args.precision, dev, solve=False)
-        k = max(3, args.steps // 2)
-        ms, pr = a.timed(k, 2, world, profile=True)
-        r2, k2 = roofline(pr, k, peaks, "grad1024")
-        secondary["grad1024_forward"] = {
-            "value": a.points * k * world / (ms / 1e3), "unit": "grid-point predictions/s",
-            "ms_per_step": ms / k, "roofline": r2, "kernels": k2,
-            "config": {"grid": "1024x1024", "n": 20000, "fields": 16, "nu": 2.5,
-                       "range": 0.08, "L": 3, "coefficients": "seeded, sized like the solve"}}
-        a.close()
-        secondary["cs512_simulate"] = measure_cs(dev, max(2, args.steps // 5), peaks)
-        secondary["grad1024_backward"] = measure_backward(dev, max(2, args.steps // 5), peaks,
-                                                          n=args.backward_n)
-    # our kernels per step.  Sites: weights, the scatter order for n >= 4096
-    # (scan, fill), FP32 block factors; prediction: FP32 block GEMM, a zeroing
-    # pass when a cell scatters with atomics (n < 4096), scatter, rows_fwd,
-    # cols, rows_inv.  Grouped: one weights launch per L and one launch for
-    # each other pass over all cells.
-    f32 = args.precision == "fp32"
-    ncell = len(main.cells)
-    nsite = int(main.xy_np.shape[0])
-    order = 2 if nsite >= 4096 else 0
-    zero = 0 if nsite >= 4096 else 1
-    if main.grouped:
-        nL = len({kw["L"] for _, kw, _ in main.cells})
-        per_step = nL + ncell * order + (2 if f32 else 0) + zero + 4
-    else:
-        per_step = ncell * (1 + order + (2 if f32 else 0) + 4)
-    res = {
-        "metric": METRIC, "value": value, "unit": "grid-point predictions/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-        "data": "synthetic (seeded sites and data; see synth)",
-        "config": {**workload_config(args.workload, world),
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "issue": ("the cells' site updates grouped (rk_set_sites_group: one "
-                             "weights launch per L), their predictions grouped "
-                             "(rk_predict_group: one launch per pass), step replayed from a "
-                             "CUDA graph") if main.grouped else
-                            "one stream per cell, step replayed from a CUDA graph",
-                   "value_without_graph": value_nograph},
-        "roofline": roof,
-        "kernels": kernels,
-        "e2e": {"value": e2e_value, "unit": "grid-point predictions/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": per_step * args.steps,
-        "clocks": clocks,
-        "fp64_path": fp64,
-        "secondary": secondary,
-    }
-    main.close()
-    return res
-
-
 # ------------------------------------------------------------ CPU oracle --
 
-def cpu_oracle_rate(workload, budget_s=15.0, steps=1):
-    """Oracle (direct Eq. (9) sum) predictions/s on a seeded sample of grid nodes."""
-    from oracle import kriging, rapid
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def oracle_setup(workload):
+    """The oracle's coefficients c = M^{-1} z for every cell (dense FP64
+    Cholesky of K_xx + tau^2 I), timed as set-up."""
+    from oracle import kriging
     w, xy, cells = workload_cells(workload)
-    n = xy.shape[0]
+    z = workload_data(workload)
+    t0 = time.perf_counter()
+    coef = {}
+    for name, kw, B in cells:
+        coef[name] = kriging.coef(xy, z[:B].T, kw["nu"], kw["rho"], kw["sigma2"], kw["tau2"]).T
+    return xy, cells, coef, time.perf_counter() - t0
+
+
+def oracle_rate(workload, setup, budget_s=15.0, steps=1):
+    """Oracle predictions/s: weights, scatter and direct Eq. (9) sums at batches
+    of 256 seeded grid nodes of the middle cell, for about budget_s."""
+    from oracle import rapid
+    xy, cells, coef, setup_s = setup
     name, kw, B = cells[len(cells) // 2]
     g = rapid.Grid(kw["nx"], kw["ny"], kw["extent"], kw["L"])
-    z = synth.normals((B, n), synth.seed_for(w["config"], 1))
-    c = kriging.coef(xy, z.T, kw["nu"], kw["rho"], kw["sigma2"], kw["tau2"]).T
+    c = coef[name][:1]
     rs = np.random.default_rng(7)
     nodes = 256
     total_pts, total_t = 0, 0.0
@@ -591,17 +640,161 @@ def cpu_oracle_rate(workload, budget_s=15.0, steps=1):
             jy = rs.integers(0, g.ny, nodes)
             ix, iy, W = rapid.weights(xy, g, kw["nu"], kw["rho"], kw["sigma2"])
             cs = rapid.scatter(ix, iy, W, c, g)
-            rapid.bttb_predict(cs, g, kw["nu"], kw["rho"], kw["sigma2"], jx=jx, jy=jy)
-            total_pts += nodes * B
+            rapid.bttb_predict(cs, g, kw["nu"], kw["rho"], kw["sigma2"], jx=jx, jy=jy, chunk=32)
+            total_pts += nodes
             if time.perf_counter() - t0 > budget_s / steps:
                 break
         total_t += time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": total_pts / total_t, "unit": "grid-point predictions/s", "cores": cores,
-            "kind": "oracle",
-            "sample": f"cell {name}: weights, scatter and direct Eq. (9) sums at batches of "
-                      f"{nodes} seeded random grid nodes for ~{budget_s:.0f} s (numpy FP64, "
-                      "BLAS threads = host cores)"}
+    return {"value": total_pts / total_t, "unit": "grid-point predictions/s", "cores": _cores(),
+            "kind": "oracle", "setup_s": setup_s,
+            "sample": f"{workload} cell {name}, one field: weights, scatter and direct Eq. (9) "
+                      f"sums at batches of {nodes} seeded grid nodes for ~{budget_s:.0f} s "
+                      "(numpy FP64, BLAS threads = host cores); the set-up (the dense Cholesky "
+                      "of K_xx + tau^2 I for every cell and field) is timed apart"}
+
+
+def oracle_errors(setup, samples):
+    """max |GPU - oracle| / max |oracle| over the sampled nodes of every cell,
+    per precision; the oracle sums Eq. (9) directly with its own weights and
+    coefficients."""
+    from oracle import rapid
+    xy, cells, coef, _ = setup
+    res = {}
+    for prec, by_cell in samples.items():
+        worst = 0.0
+        per = {}
+        for name, kw, B in cells:
+            g = rapid.Grid(kw["nx"], kw["ny"], kw["extent"], kw["L"])
+            ix, iy, W = rapid.weights(xy, g, kw["nu"], kw["rho"], kw["sigma2"])
+            e = 0.0
+            for f, jx, jy, vals in by_cell[name]:
+                cs = rapid.scatter(ix, iy, W, coef[name][f], g)
+                ref = rapid.bttb_predict(cs, g, kw["nu"], kw["rho"], kw["sigma2"], jx=jx,
+                                         jy=jy, chunk=32)[0]
+                e = max(e, float(np.abs(vals - ref).max() / np.abs(ref).max()))
+            per[name] = e
+            worst = max(worst, e)
+        res[prec] = worst
+        if len(per) > 1:
+            res[prec + "_per_cell"] = per
+    res["nodes_per_field"] = NODE_SAMPLE
+    res["what"] = ("max |GPU - oracle| / max |oracle| at seeded grid nodes of the first and "
+                   "last field, oracle = direct Eq. (9) sums with its own weights and "
+                   "Cholesky coefficients (FP64 CPU)")
+    return res
+
+
+def oracle_cs_error(sample):
+    """Realisations 0 and 1 of the 512^2 simulation (seed 1) against the oracle's
+    own conditional simulation (same Philox streams), at the sampled nodes."""
+    from oracle import cs, rapid
+    w = synth.WORKLOADS["cs512"]
+    xy = synth.sites(w["sites"], w["n"], w["extent"], synth.seed_for(w["config"]))
+    z = synth.smooth_field(xy, 1, synth.seed_for(w["config"], 1))
+    g = rapid.Grid(w["nx"], w["ny"], w["extent"], w["L"])
+    ref = cs.simulate(xy, z, g, w["nu"], w["rho"], w["sigma2"], w["tau2"], 2, 1)[0]
+    e = 0.0
+    for t, jx, jy, vals in sample:
+        r = ref[t][jy, jx]
+        e = max(e, float(np.abs(vals - r).max() / np.abs(r).max()))
+    return {"fp32": e, "what": "realisations 0, 1 at seeded nodes against the oracle's "
+                               "simulation with the same counter-based noise"}
+
+
+def cpu_leg(workload, samples, secondary_samples, budget_s=15.0):
+    """Everything that runs the oracle: its rate (cpu_baseline) and the errors
+    of the GPU outputs sampled by the GPU arm."""
+    setup = oracle_setup(workload)
+    cb = oracle_rate(workload, setup, budget_s)
+    errors = {workload: oracle_errors(setup, samples)} if samples else {}
+    if "paper350" in secondary_samples:
+        errors["paper350"] = oracle_errors(oracle_setup("paper350"),
+                                           secondary_samples["paper350"])
+    if "cs512" in secondary_samples:
+        errors["cs512"] = oracle_cs_error(secondary_samples["cs512"])
+    return cb, errors
+
+
+# --------------------------------------------------------------- our arm --
+
+def run_ours(args, rank, world):
+    import torch
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    peaks = _load_peaks()
+    main = Arm(args.workload, args.precision, dev)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    # timed region 1: the step issued from the host with per-kernel CUDA events
+    # (the roofline's kernel durations); timed region 2: the same step replayed
+    # from a CUDA graph (the headline value)
+    prof_ms, prof = main.timed(args.steps, args.warmup, world, profile=True)
+    main.capture()
+    total_ms, _ = main.timed(args.steps, args.warmup, world)
+    clocks = sampler.stop()
+    samples = {args.precision: main.samples()}
+    value = main.points * args.steps * world / (total_ms / 1e3)
+    value_nograph = main.points * args.steps * world / (prof_ms / 1e3)
+    roof, kernels = roofline(prof, args.steps, peaks, args.workload)
+    ms_step = total_ms / args.steps
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    _, _, cells = workload_cells(args.workload)
+    model = 0.0
+    for (_, kw, B), (p, _, _) in zip(cells, main.st):
+        model += B * transform_model_bytes(kw["nx"], kw["ny"], kw["L"], p.info()["px"])
+    step_roof = {"model_bytes_per_step": model, "achieved_GBps": model / (ms_step / 1e3) / 1e9,
+                 "peak_GBps": hbm, "frac": model / (ms_step / 1e3) / 1e9 / hbm,
+                 "what": "the FFT convolution's algorithmic bytes (4 P1^2 + 8 P1 H + 16 m H + "
+                         "4 m^2 per FP32 field) over the whole step's time, weights and "
+                         "scatter included"}
+    main.graph = None
+    e2e_value, h2d, d2h = main.e2e(max(3, args.steps // 2), 2)
+    launches = main.launches_per_step()
+    main.close()
+    fp64 = None
+    if not args.no_fp64 and args.precision == "fp32":
+        a64 = Arm(args.workload, "fp64", dev)
+        k64 = max(2, args.steps // 5)
+        a64.capture()
+        ms64, _ = a64.timed(k64, 2, world)
+        v64 = a64.points * k64 * world / (ms64 / 1e3)
+        fp64 = {"value": v64, "unit": "grid-point predictions/s", "ms_per_step": ms64 / k64,
+                "speedup_fp32_over_fp64": value / v64}
+        samples["fp64"] = a64.samples()
+        a64.close()
+    secondary, sec_samples = {}, {}
+    if not args.no_secondary:
+        k = max(3, args.steps // 2)
+        if args.workload != "paper350":
+            secondary["paper350"], sec_samples["paper350"] = measure_paper350(dev, k, peaks,
+                                                                              world)
+        secondary["cs512_simulate"], sec_samples["cs512"] = measure_cs(dev, max(2, args.steps // 5),
+                                                                       peaks)
+        secondary["grad1024_backward"] = measure_backward(dev, max(2, args.steps // 5), peaks,
+                                                          n=args.backward_n)
+    res = {
+        "metric": METRIC, "value": value, "unit": "grid-point predictions/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded sites and smooth data fields)",
+        "config": {**workload_config(args.workload, world),
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "issue": ("the cells' site updates grouped (rk_set_sites_group), their "
+                             "predictions grouped (rk_predict_group: one launch per pass), "
+                             "the step replayed from a CUDA graph"),
+                   "value_without_graph": value_nograph},
+        "roofline": roof,
+        "step_roofline": step_roof,
+        "kernels": kernels,
+        "e2e": {"value": e2e_value, "unit": "grid-point predictions/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+        "fp64_path": fp64,
+        "secondary": secondary,
+    }
+    return res, samples, sec_samples
 
 
 def main():
@@ -611,8 +804,9 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        cb = cpu_oracle_rate(args.workload, budget_s=max(10.0, 2.0 * args.steps),
-                             steps=args.steps)
+        setup = oracle_setup(args.workload)
+        cb = oracle_rate(args.workload, setup, budget_s=max(10.0, 2.0 * args.steps),
+                         steps=args.steps)
         cfg = workload_config(args.workload, 1)
         w, _, cells = workload_cells(args.workload)
         points = sum(kw["nx"] * kw["ny"] * B for _, kw, B in cells)
@@ -620,7 +814,7 @@ def main():
                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": points / cb["value"] * 1e3,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic (seeded sites and data; see synth)",
+               "data": "synthetic (seeded sites and smooth data fields)",
                "config": {**cfg, "issue": "the FP64 CPU oracle on the host cores (sampled)"},
                "cpu_baseline": cb,
                "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
@@ -635,16 +829,18 @@ def main():
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
         torch.cuda.set_device(dev)
         peaks = _load_peaks()
-        if args.secondary_only == "cs512":
-            out = measure_cs(dev, args.steps, peaks)
+        if args.secondary_only == "paper350":
+            out = measure_paper350(dev, args.steps, peaks, 1)[0]
+        elif args.secondary_only == "cs512":
+            out = measure_cs(dev, args.steps, peaks)[0]
         else:
             out = measure_backward(dev, args.steps, peaks, n=args.backward_n)
         if rank == 0:
             print(json.dumps({"secondary": args.secondary_only, **out}))
         return 0
-    res = run_ours(args, rank, world)
-    if rank == 0 and not args.no_cpu:
-        res["cpu_baseline"] = cpu_oracle_rate(args.workload)
+    res, samples, sec_samples = run_ours(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        res["cpu_baseline"], res["error"] = cpu_leg(args.workload, samples, sec_samples)
     if rank == 0:
         print(json.dumps(res))
     if world > 1:

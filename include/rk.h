@@ -32,9 +32,10 @@
  *  - Precision RK_FP64: every step in double.  RK_FP32: scatter and FFT
  *    butterflies in float; the weights, the Cholesky factors and the circulant
  *    eigenvalues in double; the lowest spatial frequencies of F(c*) (where the
- *    Matern spectrum exceeds 1e-2 of its peak) are computed exactly in double
- *    from the sites' weights and replace the float values before the
- *    spectrum is applied.
+ *    Matern spectrum exceeds 1e-2 of its peak) are computed from the sites'
+ *    weights in double-float arithmetic (pairs of floats, about 48
+ *    significant bits) and replace the float values before the spectrum is
+ *    applied.
  */
 #ifndef RK_H
 #define RK_H
@@ -233,8 +234,9 @@ rk_status rk_predict_group(rk_plan* const* plans, int nplans, void* const* outs)
  * already fully reserved by another allocator, or a latency-critical loop
  * that cannot afford cudaMalloc's implicit device synchronisation.  This
  * entry point computes exactly what rk_predict computes, but keeps the
- * per-call scratch (c*, the two transposed half spectra and the
- * low-frequency block) in one file-scope device array of 32 MiB (33554432
+ * per-call scratch (c*, the two transposed half spectra, the low-frequency
+ * block and the coefficients as float pairs) in one file-scope device array
+ * of 32 MiB (33554432
  * bytes) that the library holds on every GPU that loads it, until the
  * process exits.  It calls no cudaMalloc, cudaFree or other allocating
  * routine.

@@ -122,7 +122,10 @@ struct rk_plan {
   double* ssd = nullptr;       // n: sqrt(max(0, sigma2 - k_i^T W_i)) (CS)
   float2* wdf = nullptr;       // RK_FP32: n x M, the weights as double-float pairs
   bool w64_stale = false;      // w64 not yet formed from wdf (ensure_w64)
-  double2* efac = nullptr;     // RK_FP32: n x nblk Fourier factors of A_i on the block
+  float4* efac = nullptr;      // RK_FP32: nblk x n Fourier factors of A_i on the block,
+                               // double-float pairs (re.hi, re.lo, im.hi, im.lo)
+  float2* cdf = nullptr;       // RK_FP32: B x n coefficients as float pairs (block GEMM)
+  size_t cdf_cap = 0;
   float4* twdfx = nullptr;     // RK_FP32: the px and py twiddles as double-float pairs
   float4* twdfy = nullptr;     //   (re.hi, re.lo, im.hi, im.lo)
   // sites ordered by the 32 x 32 tile of the padded grid holding their box
@@ -292,17 +295,18 @@ BlockFactorSlot block_factor_slot(const int* box, const double* w64, int n, cons
 cudaError_t launch_block_factors_group(Group<BlockFactorSlot>& g, cudaStream_t s);
 // the forward block of RK_FP32 plans, in double-float
 struct BlockFactorDfSlot {
-  const int* box; const float2* wdf; const float4* twx; const float4* twy; double2* efac;
+  const int* box; const float2* wdf; const float4* twx; const float4* twy; float4* efac;
   int n, L, px, py, KX, KY, NS;
 };
 BlockFactorDfSlot block_factor_df_slot(const rk_plan* p, int n);
 cudaError_t launch_block_factors_df_group(Group<BlockFactorDfSlot>& g, cudaStream_t s);
 cudaError_t launch_block_factors_df(const rk_plan* p, int n, cudaStream_t s);
-struct BlockGemmSlot {
-  const double* c; const double2* efac; double2* blk;
+// the forward block of RK_FP32 plans in double-float (c split into cdf first)
+struct BlockGemmDfSlot {
+  const double* c; float2* cdf; const float4* efac; double2* blk;
   int n, B, nblk;
 };
-cudaError_t launch_block_gemm_group(const Group<BlockGemmSlot>& g, cudaStream_t s);
+cudaError_t launch_block_gemm_df_group(Group<BlockGemmDfSlot>& g, cudaStream_t s);
 template <typename T>
 struct ScatterSlot {
   const int* box; const T* w; const double* c; T* cstar;

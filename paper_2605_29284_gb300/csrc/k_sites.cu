@@ -642,8 +642,8 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
 
 // The forward block of RK_FP32 plans in double-float on the FP32 pipe: the
 // same two stages as block_factor_kernel, from the weights' float pairs and
-// double-float twiddles (re.hi, re.lo, im.hi, im.lo); E_i is stored in double
-// for the FP64 block GEMM.  The block only has to be far more accurate than
+// double-float twiddles (re.hi, re.lo, im.hi, im.lo); E_i is stored as the
+// same float pairs for the double-float block GEMM.  The block only has to be far more accurate than
 // the single-precision transforms it corrects; double-float (about 2^-47 per
 // operation) is, and runs at 64x the FP64 rate.
 // Threads: NS sites per CTA (a power of two, the fastest index, so the
@@ -660,7 +660,7 @@ __device__ __forceinline__ void block_factor_df_cta(const BlockFactorDfSlot& sl,
   constexpr int M = W * W;
   const int* __restrict__ box = sl.box;
   const float2* __restrict__ wdf = sl.wdf;
-  double2* __restrict__ efac = sl.efac;
+  float4* __restrict__ efac = sl.efac;
   const int n = sl.n, px = sl.px, py = sl.py, KY = sl.KY;
   const int nk = sl.KX + 1, nky = KY + 1, bw = 2 * KY + 1;
   const int NS = sl.NS, lanes = kBfThreads / NS;
@@ -714,12 +714,9 @@ __device__ __forceinline__ void block_factor_df_cta(const BlockFactorDfSlot& sl,
     }
     const dfl A = dfacc_value(sa), Bs = dfacc_value(sb), Cs = dfacc_value(sc),
               D = dfacc_value(sd);
-    double2* out = efac + (size_t)kx * bw * n + i;
-    out[(size_t)(KY + ky) * n] = make_double2(df_double(df_add(A, df_neg(Bs))),
-                                             df_double(df_add(Cs, D)));
-    if (ky > 0)
-      out[(size_t)(KY - ky) * n] = make_double2(df_double(df_add(A, Bs)),
-                                               df_double(df_add(D, df_neg(Cs))));
+    float4* out = efac + (size_t)kx * bw * n + i;
+    out[(size_t)(KY + ky) * n] = cdf_pack(df_add(A, df_neg(Bs)), df_add(Cs, D));
+    if (ky > 0) out[(size_t)(KY - ky) * n] = cdf_pack(df_add(A, Bs), df_add(D, df_neg(Cs)));
   }
 }
 
@@ -817,47 +814,6 @@ __global__ void block_gemm_kernel(const double* __restrict__ c, int B, int n,
   }
 }
 
-// The block GEMMs of several plans in one launch (rk_predict_group): grid.y
-// runs over every plan's fields, grid.x over the largest block.
-__global__ void block_gemm_group_kernel(const __grid_constant__ Group<BlockGemmSlot> g) {
-  int ks = 0;
-  while (ks + 1 < g.n && (int)blockIdx.y >= g.start[ks + 1]) ++ks;
-  const BlockGemmSlot& sl = g.slot[ks];
-  const int j = blockIdx.x;
-  if (j >= sl.nblk) return;
-  const int f = blockIdx.y - g.start[ks], n = sl.n;
-  const double2* e = sl.efac + (size_t)j * n;
-  const double* c = sl.c + (size_t)f * n;
-  double ax = 0.0, ay = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double2 ev = e[i];
-    const double cv = c[i];
-    ax = fma(cv, ev.x, ax);
-    ay = fma(cv, ev.y, ay);
-  }
-  // the CTA's sum as in block_gemm_kernel: warps 0 and 1 add the real and
-  // imaginary partial sums from shared memory
-  __shared__ double red[2][256];
-  red[0][threadIdx.x] = ax;
-  red[1][threadIdx.x] = ay;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (wid < 2) {
-    double sv = 0.0;
-    for (int t = lane; t < blockDim.x; t += 32) sv += red[wid][t];
-    for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
-    if (lane == 0) reinterpret_cast<double*>(sl.blk + (size_t)f * sl.nblk + j)[wid] = sv;
-  }
-}
-
-cudaError_t launch_block_gemm_group(const Group<BlockGemmSlot>& g, cudaStream_t s) {
-  int most = 0;
-  for (int k = 0; k < g.n; ++k) most = g.slot[k].nblk > most ? g.slot[k].nblk : most;
-  if (g.n == 0 || most == 0 || g.start[g.n] == 0) return cudaSuccess;
-  block_gemm_group_kernel<<<dim3(most, g.start[g.n]), 256, 0, s>>>(g);
-  return cudaGetLastError();
-}
-
 // blk[f][j] = sum_i c[f][i] E_i(j), double: one CTA per (j, group of F
 // fields), F = 1, 2 or 4 by the batch, so small batches spend no FP64 issue
 // slots on empty accumulators.
@@ -869,6 +825,120 @@ cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac
   if (F == 4) block_gemm_kernel<4><<<grid, 256, 0, s>>>(c, B, n, efac, nblk, blk);
   else if (F == 2) block_gemm_kernel<2><<<grid, 256, 0, s>>>(c, B, n, efac, nblk, blk);
   else block_gemm_kernel<1><<<grid, 256, 0, s>>>(c, B, n, efac, nblk, blk);
+  return cudaGetLastError();
+}
+
+// The forward block of RK_FP32 plans in double-float: blk[f][j] =
+// sum_i c[f][i] E_i(j) with E_i as float pairs (re.hi, re.lo, im.hi, im.lo)
+// and c split into float pairs first (split_coef_group_kernel: the FP64
+// conversions once per coefficient, not once per product).  A CTA takes two
+// block entries, F fields and one range of the sites (grid.z: about 16 sites
+// per thread, so that enough CTAs hide the loads' latency); its threads run
+// over the range with unnormalised pair sums, the CTA's partial sums meet in
+// shared memory by double-float additions, and each range's sum is added to
+// the block in double (FP64 atomics; the block was zeroed by the split).  Each term costs
+// about 12 FP32 instructions against two FMAs on the FP64 pipe, which runs
+// at 1/64 of the FP32 rate.
+__global__ void split_coef_group_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
+  const BlockGemmDfSlot& sl = g.slot[blockIdx.y];
+  const size_t count = (size_t)sl.B * sl.n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const double d = sl.c[t];
+    const float h = (float)d;
+    sl.cdf[t] = make_float2(h, (float)(d - (double)h));
+  }
+  // the block's sums start at zero (the GEMM's site ranges add into them)
+  const size_t nb = (size_t)sl.B * sl.nblk;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nb;
+       t += (size_t)gridDim.x * blockDim.x)
+    sl.blk[t] = make_double2(0.0, 0.0);
+}
+
+constexpr int kBgJ = 2;
+
+template <int F>
+__global__ void __launch_bounds__(256)
+block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
+  int ks = 0;
+  while (ks + 1 < g.n && (int)blockIdx.y >= g.start[ks + 1]) ++ks;
+  const BlockGemmDfSlot& sl = g.slot[ks];
+  const int j0 = blockIdx.x * kBgJ;
+  if (j0 >= sl.nblk) return;                     // uniform over the CTA
+  const int f0 = (blockIdx.y - g.start[ks]) * F, n = sl.n, nblk = sl.nblk;
+  const int nf = min(F, sl.B - f0), nj = min(kBgJ, nblk - j0);
+  const int chunk = (n + gridDim.z - 1) / gridDim.z;
+  const int i0 = blockIdx.z * chunk, i1 = min(n, i0 + chunk);
+  if (i0 >= i1) return;                          // uniform over the CTA
+  dfacc acc[F][kBgJ][2];
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    float4 e[kBgJ];
+#pragma unroll
+    for (int jj = 0; jj < kBgJ; ++jj)
+      e[jj] = jj < nj ? sl.efac[(size_t)(j0 + jj) * n + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      if (f < nf) {
+        const float2 cv = sl.cdf[(size_t)(f0 + f) * n + i];
+        const dfl c = {cv.x, cv.y};
+#pragma unroll
+        for (int jj = 0; jj < kBgJ; ++jj) {
+          dfacc_fma(acc[f][jj][0], c, {e[jj].x, e[jj].y});
+          dfacc_fma(acc[f][jj][1], c, {e[jj].z, e[jj].w});
+        }
+      }
+    }
+  }
+  // the CTA's sum: pairs normalised, added across each warp by shuffles,
+  // then across the warps in shared memory
+  constexpr int NV = F * kBgJ * 2;
+  __shared__ float2 red[8][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int jj = 0; jj < kBgJ; ++jj)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        dfl v = dfacc_value(acc[f][jj][c]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const dfl w = {__shfl_down_sync(0xffffffffu, v.hi, o),
+                         __shfl_down_sync(0xffffffffu, v.lo, o)};
+          v = df_add(v, w);
+        }
+        if (lane == 0) red[wid][(f * kBgJ + jj) * 2 + c] = make_float2(v.hi, v.lo);
+      }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (threadIdx.x < NV) {
+    dfl v = {red[0][threadIdx.x].x, red[0][threadIdx.x].y};
+    for (int w = 1; w < nw; ++w) v = df_add(v, {red[w][threadIdx.x].x, red[w][threadIdx.x].y});
+    const int c = threadIdx.x & 1, jj = (threadIdx.x >> 1) % kBgJ, f = threadIdx.x / (2 * kBgJ);
+    if (f < nf && jj < nj)
+      atomicAdd(reinterpret_cast<double*>(sl.blk + (size_t)(f0 + f) * nblk + j0 + jj) + c,
+                df_double(v));
+  }
+}
+
+cudaError_t launch_block_gemm_df_group(Group<BlockGemmDfSlot>& g, cudaStream_t s) {
+  int most = 0, maxb = 0;
+  for (int k = 0; k < g.n; ++k) {
+    if (g.slot[k].nblk <= 0) g.slot[k].B = 0;
+    most = g.slot[k].nblk > most ? g.slot[k].nblk : most;
+    maxb = g.slot[k].B > maxb ? g.slot[k].B : maxb;
+  }
+  if (g.n == 0 || most == 0 || maxb == 0) return cudaSuccess;
+  split_coef_group_kernel<<<dim3(64, g.n), 256, 0, s>>>(g);
+  const int F = maxb >= 4 ? 4 : 1;
+  g.start[0] = 0;
+  for (int k = 0; k < g.n; ++k) g.start[k + 1] = g.start[k] + (g.slot[k].B + F - 1) / F;
+  int nmax = 0;
+  for (int k = 0; k < g.n; ++k) nmax = g.slot[k].n > nmax ? g.slot[k].n : nmax;
+  const int ranges = nmax / (256 * 16) < 1 ? 1 : (nmax / (256 * 16) > 64 ? 64 : nmax / (256 * 16));
+  const dim3 grid((most + kBgJ - 1) / kBgJ, g.start[g.n], ranges);
+  if (F == 4) block_gemm_df_kernel<4><<<grid, 256, 0, s>>>(g);
+  else block_gemm_df_kernel<1><<<grid, 256, 0, s>>>(g);
   return cudaGetLastError();
 }
 
@@ -946,28 +1016,76 @@ cudaError_t launch_tile_sites(const int* box, int n, rk_plan* p, bool counted, c
 // fields per CTA: the accumulators of FB fields share one pass over the sites
 constexpr int kScF = 4;
 
-template <typename T>
-__device__ __forceinline__ void scatter_tile(const ScatterSlot<T>& sl, int tile, int f0,
-                                             T (*acc)[kTile * kTile]) {
-  const int W = 2 * sl.L, M = W * W;
+// One tile of the scatter for neighbourhood order LL (W = 2 LL, M = W^2 at
+// compile time).  The candidate sites of the four source tiles are taken 256
+// at a time; those whose W x W footprint meets this tile go into a shared
+// list with their tile-local corner and their coefficients, converted to T
+// once per site and field; then one thread per (listed site, footprint
+// entry) adds the entry's products into the tile's accumulators.
+template <typename T, int LL>
+__device__ __forceinline__ void scatter_tile_l(const ScatterSlot<T>& sl, int tile, int f0,
+                                               T (*acc)[kTile * kTile], int* lst, T (*lc)[256],
+                                               int* nsel) {
+  constexpr int W = 2 * LL, M = W * W;
   const int nf = min(kScF, sl.B - f0);
   for (int e = threadIdx.x; e < kScF * kTile * kTile; e += blockDim.x) (&acc[0][0])[e] = T(0);
-  __syncthreads();
   const int tx = tile % sl.ntx, ty = tile / sl.ntx;
   const int x0 = tx * kTile, y0 = ty * kTile;
-  for (int d = 0; d < 4; ++d) {
+  // source tiles (tx, ty), (tx - 1, ty), (tx, ty - 1), (tx - 1, ty - 1):
+  // their first site in the order and their site counts
+  auto src = [&](int d, int* st, int* ct) {
     const int hx = tx - (d & 1), hy = ty - (d >> 1);
-    if (hx < 0 || hy < 0) continue;
-    const int h = hy * sl.ntx + hx;
-    const int s0 = sl.tstart[h], cnt = sl.tstart[h + 1] - s0;
-    for (int e = threadIdx.x; e < cnt * M; e += blockDim.x) {
-      const int i = sl.order[s0 + e / M], q = e % M;
-      const int px = sl.box[2 * i] + q % W - x0, py = sl.box[2 * i + 1] + q / W - y0;
-      if ((unsigned)px >= (unsigned)kTile || (unsigned)py >= (unsigned)kTile) continue;
-      const T wv = sl.w[(size_t)i * M + q];
-      for (int f = 0; f < nf; ++f)
-        atomicAdd(&acc[f][py * kTile + px], wv * (T)sl.c[(size_t)(f0 + f) * sl.n + i]);
+    const bool ok = hx >= 0 && hy >= 0;
+    const int h = ok ? hy * sl.ntx + hx : 0;
+    *st = ok ? sl.tstart[h] : 0;
+    *ct = ok ? sl.tstart[h + 1] - *st : 0;
+  };
+  int hs0, hc0, hs1, hc1, hs2, hc2, hs3, hc3;
+  src(0, &hs0, &hc0);
+  src(1, &hs1, &hc1);
+  src(2, &hs2, &hc2);
+  src(3, &hs3, &hc3);
+  const int tot = hc0 + hc1 + hc2 + hc3;
+  for (int base = 0; base < tot; base += 256) {
+    if (threadIdx.x == 0) *nsel = 0;
+    __syncthreads();
+    const int cand = base + threadIdx.x;
+    if (cand < tot) {
+      int off = cand, st = hs0;
+      if (off >= hc0) {
+        off -= hc0;
+        st = hs1;
+        if (off >= hc1) {
+          off -= hc1;
+          st = hs2;
+          if (off >= hc2) {
+            off -= hc2;
+            st = hs3;
+          }
+        }
+      }
+      const int i = sl.order[st + off];
+      const int cx = sl.box[2 * i] - x0, cy = sl.box[2 * i + 1] - y0;
+      // the footprint [cx, cx + W) x [cy, cy + W) meets [0, 32)^2
+      if (cx > -W && cx < kTile && cy > -W && cy < kTile) {
+        const int slot = atomicAdd(nsel, 1);
+        lst[slot] = i;
+        lst[256 + slot] = cx;
+        lst[512 + slot] = cy;
+        for (int f = 0; f < nf; ++f) lc[f][slot] = (T)sl.c[(size_t)(f0 + f) * sl.n + i];
+      }
     }
+    __syncthreads();
+    const int ns = *nsel;
+    for (int e = threadIdx.x; e < ns * M; e += blockDim.x) {
+      const int sidx = e / M, q = e - sidx * M;
+      const int px = lst[256 + sidx] + q % W, py = lst[512 + sidx] + q / W;
+      if ((unsigned)px >= (unsigned)kTile || (unsigned)py >= (unsigned)kTile) continue;
+      const T wv = sl.w[(size_t)lst[sidx] * M + q];
+      T* a = &acc[0][py * kTile + px];
+      for (int f = 0; f < nf; ++f) atomicAdd(a + f * kTile * kTile, wv * lc[f][sidx]);
+    }
+    __syncthreads();
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nf * kTile * kTile; e += blockDim.x) {
@@ -975,6 +1093,20 @@ __device__ __forceinline__ void scatter_tile(const ScatterSlot<T>& sl, int tile,
     const int gx = x0 + r % kTile, gy = y0 + r / kTile;
     if (gx < sl.p1x && gy < sl.p1y)
       sl.cstar[((size_t)(f0 + f) * sl.p1y + gy) * sl.p1x + gx] = acc[f][r];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void scatter_tile(const ScatterSlot<T>& sl, int tile, int f0,
+                                             T (*acc)[kTile * kTile]) {
+  __shared__ int lst[3 * 256];
+  __shared__ T lc[kScF][256];
+  __shared__ int nsel;
+  switch (sl.L) {
+    case 1: scatter_tile_l<T, 1>(sl, tile, f0, acc, lst, lc, &nsel); break;
+    case 2: scatter_tile_l<T, 2>(sl, tile, f0, acc, lst, lc, &nsel); break;
+    case 3: scatter_tile_l<T, 3>(sl, tile, f0, acc, lst, lc, &nsel); break;
+    default: scatter_tile_l<T, 4>(sl, tile, f0, acc, lst, lc, &nsel); break;
   }
 }
 

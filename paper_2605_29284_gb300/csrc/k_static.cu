@@ -44,7 +44,9 @@ static rk_status predict_static(rk_plan* p, T* out, unsigned char* base) {
   T* cstar = (T*)base;
   C<T>* tb = (C<T>*)(base + cstar_b);
   C<T>* ub = (C<T>*)(base + cstar_b + t_b);
+  const size_t blk_b = align256((size_t)B * p->nblk * sizeof(double2));
   double2* blk = (double2*)(base + cstar_b + t_b + u_b);
+  float2* cdf = (float2*)(base + cstar_b + t_b + u_b + blk_b);   // B x n coefficient pairs
   const T* w = f32 ? (const T*)p->w32 : (const T*)p->w64;
   const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
@@ -58,9 +60,14 @@ static rk_status predict_static(rk_plan* p, T* out, unsigned char* base) {
     return RK_ERR_CUDA;
   const bool use_blk = f32 && p->nblk > 0;
   // the block factors of the last site update were computed on the side stream
-  if (use_blk && (cudaStreamWaitEvent(s, p->ev_sites, 0) != cudaSuccess ||
-                  launch_block_gemm(p->c64, B, p->n, p->efac, p->nblk, blk, s) != cudaSuccess))
-    return RK_ERR_CUDA;
+  if (use_blk) {
+    Group<BlockGemmDfSlot> g;
+    g.n = 1;
+    g.slot[0] = BlockGemmDfSlot{p->c64, cdf, p->efac, blk, p->n, B, p->nblk};
+    if (cudaStreamWaitEvent(s, p->ev_sites, 0) != cudaSuccess ||
+        launch_block_gemm_df_group(g, s) != cudaSuccess)
+      return RK_ERR_CUDA;
+  }
   if (launch_cols<T>(tb, p->ldt, (long long)p->H * p->ldt, p->p1y, ub, p->ldu,
                      (long long)p->H * p->ldu, p->L - 1, p->ny, lam, COLS_CONV,
                      use_blk ? blk : nullptr, p->blk_kx, p->blk_ky, p->nblk, B, p->H, p->fpy,
@@ -84,7 +91,8 @@ extern "C" rk_status rk_predict_static(rk_plan* p, void* out) {
   size_t need = align256((size_t)p->B * plane * es) +
                 align256((size_t)p->B * p->H * p->ldt * 2 * es) +
                 align256((size_t)p->B * p->H * p->ldu * 2 * es);
-  if (p->precision == RK_FP32 && p->nblk > 0) need += align256((size_t)p->B * p->nblk * 16);
+  if (p->precision == RK_FP32 && p->nblk > 0)
+    need += align256((size_t)p->B * p->nblk * 16) + align256((size_t)p->B * p->n * 8);
   if (need > kStaticScratchBytes) return RK_ERR_INVALID_ARG;
   void* base = nullptr;
   rk_status st = static_scratch(&base);

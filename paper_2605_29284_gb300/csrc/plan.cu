@@ -329,7 +329,7 @@ void free_plan(rk_plan* p) {
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
                   p->efac_g, p->gblk, p->bw_dk, p->tile_start,
                   p->tile_count, p->tile_cursor, p->site_order,
-                  p->mchol_df, p->kn_df};
+                  p->mchol_df, p->kn_df, p->cdf};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_flag) cudaFreeHost(p->h_flag);
@@ -361,6 +361,10 @@ rk_status ensure_field_scratch(rk_plan* p, int B) {
   if (p->precision == RK_FP32 && p->nblk > 0 && p->blk_cap < (size_t)B * p->nblk) {
     RK_TRY(dalloc(&p->blk, (size_t)B * p->nblk));
     p->blk_cap = (size_t)B * p->nblk;
+  }
+  if (p->precision == RK_FP32 && p->nblk > 0 && p->cdf_cap < (size_t)B * p->n) {
+    RK_TRY(dalloc(&p->cdf, (size_t)B * p->n));
+    p->cdf_cap = (size_t)B * p->n;
   }
   return RK_OK;
 }
@@ -395,8 +399,9 @@ rk_status ensure_w64(rk_plan* p) {
 // the weights in use, and the B x nblk buffer for sum_i c_i E_i(k).
 struct BlockUse {
   int kx, ky, nblk;
-  const double2* efac;
+  const double2* efac;     // the gradient blocks: FP64 factors
   double2* blk;
+  const float4* efac_df;   // the forward block: double-float factors (efac unused)
 };
 
 // Steps 5-7 for nf fields with coefficients c64 (double; the FP32 scatter
@@ -414,7 +419,7 @@ rk_status predict_fields(rk_plan* p, const double* c64, int nf, T* out,
   const bool f32 = sizeof(T) == sizeof(float);
   const T* w = w_override ? w_override : f32 ? (const T*)p->w32 : (const T*)p->w64;
   const T* lam = lam_override ? lam_override : f32 ? (const T*)p->lam32 : (const T*)p->lam64;
-  const BlockUse fwd = {p->blk_kx, p->blk_ky, p->nblk, p->efac, p->blk};
+  const BlockUse fwd = {p->blk_kx, p->blk_ky, p->nblk, nullptr, p->blk, p->efac};
   const BlockUse& bk = bu ? *bu : fwd;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
   const C<T>* twy = f32 ? (const C<T>*)p->tw32y : (const C<T>*)p->tw64y;
@@ -432,9 +437,17 @@ rk_status predict_fields(rk_plan* p, const double* c64, int nf, T* out,
     cudaStream_t s_main = s;
     {
       cudaStream_t s = p->side;
-      RK_PROF64("block_gemm", (double)bk.nblk * p->n * 16.0 + B * (p->n * 8.0 + bk.nblk * 16.0),
-                4.0 * B * p->n * bk.nblk);
-      RK_CU(launch_block_gemm(c64, B, p->n, bk.efac, bk.nblk, bk.blk, s));
+      const double bg_bytes = (double)bk.nblk * p->n * 16.0 + B * (p->n * 8.0 + bk.nblk * 16.0);
+      if (bk.efac_df) {
+        RK_PROFDF("block_gemm", bg_bytes, 4.0 * B * p->n * bk.nblk);
+        Group<BlockGemmDfSlot> g;
+        g.n = 1;
+        g.slot[0] = BlockGemmDfSlot{c64, p->cdf, bk.efac_df, bk.blk, p->n, B, bk.nblk};
+        RK_CU(launch_block_gemm_df_group(g, s));
+      } else {
+        RK_PROF64("block_gemm", bg_bytes, 4.0 * B * p->n * bk.nblk);
+        RK_CU(launch_block_gemm(c64, B, p->n, bk.efac, bk.nblk, bk.blk, s));
+      }
     }
     RK_CU(cudaEventRecord(p->ev_join, p->side));
     (void)s_main;
@@ -481,7 +494,7 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
   Group<RowsFwdSlot<T>> gf;
   Group<ColsSlot<T>> gc;
   Group<RowsInvSlot<T>> gi;
-  Group<BlockGemmSlot> gb;
+  Group<BlockGemmDfSlot> gb;
   gs.n = gf.n = gc.n = gi.n = gb.n = np;
   for (int k = 0; k < np; ++k) {
     rk_plan* p = plans[k];
@@ -500,8 +513,8 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
     gi.slot[k] = RowsInvSlot<T>{(const C<T>*)p->ubuf, (T*)outs[k], nullptr,
                                 (long long)p->H * p->ldu, (long long)p->ny * p->nx, 0, p->ldu,
                                 p->ny, p->nx, p->L - 1, p->nx, 0, 0, 0, B};
-    gb.slot[k] = BlockGemmSlot{p->c64, p->efac, p->blk, p->n, B, blk ? p->nblk : 0};
-    gb.start[k + 1] = gb.start[k] + B;
+    gb.slot[k] = BlockGemmDfSlot{p->c64, p->cdf, p->efac, p->blk, p->n, blk ? B : 0,
+                                 blk ? p->nblk : 0};
     gf.start[k + 1] = gf.start[k] + B;
     gi.start[k + 1] = gi.start[k] + B;
     const double es = sizeof(T), cs = 2.0 * es, nM = (double)p->n * p->M;
@@ -525,8 +538,8 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
     cudaStream_t s_main = s;
     {
       cudaStream_t s = p0->side;
-      RK_PROF64("block_gemm", bg_b, bg_f);
-      RK_CU(launch_block_gemm_group(gb, s));
+      RK_PROFDF("block_gemm", bg_b, bg_f);
+      RK_CU(launch_block_gemm_df_group(gb, s));
     }
     RK_CU(cudaEventRecord(p0->ev_join, p0->side));
     (void)s_main;

@@ -19,7 +19,15 @@ n = 1368 station subset of Section 5):
 * cs512     -- conditional simulation, R = 256, n = 5000 uniform sites,
                512 x 512 grid, nu = 1.5, range 0.1, tau^2 = 1e-3, L = 2.
 * grad1024  -- 1024 x 1024 grid, n = 20000 uniform sites, 16 fields,
-               nu = 2.5, range 0.08, tau^2 = 1e-3, L = 3.
+               nu = 2.5, range 0.08, tau^2 = 1e-3, L = 3 (the benchmark's
+               forward step "pred1024" and the differentiation workload).
+* cs_mixed  -- conditional simulation of three grids in one call:
+               128^2, 256^2, 512^2 on [0,1]^2, R = 64 each, n = 5000 uniform
+               sites, nu = 1.5, range 0.1, tau^2 = 1e-3, L = 2.
+
+Data for the large workloads are smooth_field values: a GP draw at n = 20000
+sites needs the 20000^2 Cholesky factor of the method's own covariance, which
+this module does not compute.
 """
 import numpy as np
 
@@ -40,6 +48,9 @@ WORKLOADS = {
                   sites="uniform"),
     "grad1024": dict(config=4, n=20000, nx=1024, ny=1024, extent=(0.0, 1.0, 0.0, 1.0),
                      nu=2.5, rho=0.08, sigma2=1.0, tau2=1e-3, L=3, B=16,
+                     sites="uniform"),
+    "cs_mixed": dict(config=3, n=5000, grids=(128, 256, 512), extent=(0.0, 1.0, 0.0, 1.0),
+                     nu=1.5, rho=0.1, sigma2=1.0, tau2=1e-3, L=2, B=1, R=64,
                      sites="uniform"),
 }
 
@@ -112,3 +123,20 @@ def sites(kind, n, extent, seed):
 def normals(shape, seed):
     """Standard-normal array (e.g. the xi of a GP draw z = chol(M) xi)."""
     return rng(seed).standard_normal(shape)
+
+
+def smooth_field(xy, B, seed, terms=12, max_freq=3.0, noise=0.03):
+    """B smooth random fields at the points xy (n x 2) plus white noise:
+    f_b(s) = sum_k a_bk cos(2 pi u_bk . s + p_bk) / sqrt(terms) + noise * eps,
+    with seeded a ~ N(0, 1), frequencies u uniform in the disc of radius
+    max_freq and phases uniform.  Returns a B x n array."""
+    g = rng(seed)
+    xy = np.asarray(xy, dtype=np.float64)
+    r = max_freq * np.sqrt(g.random((B, terms)))
+    t = 2.0 * np.pi * g.random((B, terms))
+    u = np.stack([r * np.cos(t), r * np.sin(t)], axis=-1)            # B x terms x 2
+    a = g.standard_normal((B, terms))
+    ph = 2.0 * np.pi * g.random((B, terms))
+    arg = 2.0 * np.pi * np.einsum("btk,nk->btn", u, xy) + ph[:, :, None]
+    f = np.einsum("bt,btn->bn", a, np.cos(arg)) / np.sqrt(terms)
+    return f + noise * g.standard_normal((B, xy.shape[0]))
