@@ -27,8 +27,9 @@
  *    hx = (x1 - x0) / (nx - 1), hy likewise; outputs are row-major
  *    [field][iy][ix] (ix fastest).
  *  - Covariance (Eq. Matern1, Section 3): k(s, s') = sigma2 * phi(|s - s'| /
- *    range), phi(d) = d^nu K_nu(d) / (2^(nu - 1) Gamma(nu)).  nu must be 0.5,
- *    1.5 or 2.5 (closed forms; other nu return RK_ERR_INVALID_ARG).
+ *    range), phi(d) = d^nu K_nu(d) / (2^(nu - 1) Gamma(nu)).  nu = 0.5, 1.5,
+ *    2.5 use the closed forms; any other 0.2 <= nu <= 8 a table of K_nu
+ *    built once per nu (see rk_matern_eval).
  *  - Precision RK_FP64: every step in double.  RK_FP32: scatter and FFT
  *    butterflies in float; the weights, the Cholesky factors and the circulant
  *    eigenvalues in double; the lowest spatial frequencies of F(c*) (where the
@@ -85,7 +86,8 @@ typedef struct {
  *   out        receives the plan; *out is NULL on failure.
  *   nx, ny     grid nodes per dimension, >= 2.
  *   extent     {x0, x1, y0, y1}, host pointer, x0 < x1, y0 < y1.
- *   nu         Matern smoothness: 0.5, 1.5 or 2.5.
+ *   nu         Matern smoothness, 0.2 <= nu <= 8 (0.5, 1.5, 2.5: closed forms;
+ *              others tabulated, see rk_matern_eval).
  *   range      Matern range (> 0); sigma2 > 0; tau2 >= 0 (nugget).
  *   L          neighbourhood order >= 1, M = (2L)^2 <= 64.
  *   precision  RK_FP32 or RK_FP64.
@@ -352,6 +354,72 @@ typedef struct {
 } rk_profile_entry;
 rk_status rk_profile_enable(int on);
 int rk_profile_read(rk_profile_entry* out, int max);
+
+/*
+ * rk_solve_gls -- universal Kriging, Eqs. (2)-(3) of Section 2: with site
+ * covariates X, the generalised least squares estimate
+ * beta = (X^T M^-1 X)^-1 X^T M^-1 z and the coefficients
+ * c = M^-1 (z - X beta) of the spatial part (the plan's coefficients, as
+ * rk_solve_coef sets them); the plan keeps z - X beta as its data (the
+ * conditional simulation conditions on it).  M^-1 X and M^-1 z take one pass
+ * of the plan's FP64 Cholesky solves (double-float updates for RK_FP32).
+ *   B       fields, >= 1; z_dev device, B x n doubles.
+ *   q       covariates, 1 <= q <= 16 and q < n; X_dev device, n x q doubles
+ *           (row i: the covariates of site i).
+ *   beta_dev  device, B x q doubles: the estimates.
+ * Allocates its scratch ((q + B) n + q (q + B) doubles) on first use and when
+ * it grows.  RK_ERR_NOT_PD when M or X^T M^-1 X is not positive definite.
+ * Synchronises with the stream.
+ */
+rk_status rk_solve_gls(rk_plan* plan, int B, const double* z_dev, int q, const double* X_dev,
+                       double* beta_dev);
+
+/*
+ * rk_add_trend -- Eq. (5): f = X_g beta + g_hat, the fixed effects added in
+ * place to a predicted grid.
+ *   Xg_dev    device, q x ny x nx doubles (covariate a at every node).
+ *   beta_dev  device, B x q doubles (e.g. from rk_solve_gls).
+ *   out_dev   device, B x ny x nx in plan precision (rk_predict's output).
+ */
+rk_status rk_add_trend(rk_plan* plan, int B, int q, const double* Xg_dev, const double* beta_dev,
+                       void* out_dev);
+
+/*
+ * rk_interp -- prediction at irregular locations from a predicted grid, the
+ * extension proposed in Section 6 (Conclusion & Discussion): predict onto a
+ * fine regular mesh with the rapid method, then interpolate off the mesh by
+ * a local polynomial rule.  The rule here is tensor-product Lagrange
+ * interpolation with K points per axis (K = 2: bilinear; 4: cubic; 6:
+ * quintic): for a target with grid coordinate gx = (x - x0) / hx the stencil
+ * is the K nodes from clamp(floor(gx) - K/2 + 1, 0, nx - K), likewise in y;
+ * weights and sums in double.
+ *   grid_dev  device, B x ny x nx in plan precision (e.g. rk_predict's output).
+ *   B         fields, >= 1.
+ *   np        targets, >= 0; xy_dev device, np x 2 doubles (x, y).
+ *   K         2, 4 or 6 (at most nx and ny).
+ *   out_dev   device, B x np in plan precision.
+ * Returns RK_ERR_OBS_OUTSIDE when a target lies outside the extent (its
+ * outputs are NaN, the others are valid); RK_ERR_INVALID_ARG for bad sizes.
+ * Synchronises with the stream (to read the outside-extent flag).
+ */
+rk_status rk_interp(rk_plan* plan, const void* grid_dev, int B, int np, const double* xy_dev,
+                    int K, void* out_dev);
+
+/*
+ * rk_matern_eval -- the library's Matern correlation for a smoothness without
+ * a closed form, evaluated on the host (no GPU).  Plans with nu other than
+ * 1/2, 3/2, 5/2 (0.2 <= nu <= 8, at most 8 distinct values per process) use
+ * phi(t) = 2^(1-nu) / Gamma(nu) t^nu K_nu(t) (Eq. Matern1) and its log-range
+ * derivative -t phi'(t) = 2^(1-nu) / Gamma(nu) t^(nu+1) K_(nu-1)(t) from a
+ * table built once per nu: K_nu by the trapezoidal rule on its integral
+ * representation in long double, then Chebyshev series of degree 20 on
+ * segments [2^-(k+1), 2^-k] (k < 60) and [1 + j, 2 + j] up to the tail where
+ * both fall below 1e-20 (zero beyond; for 0 < t < 2^-60 the value at 2^-60).
+ * The device kernels evaluate the same table.
+ *   which  0: phi(t); 1: -t phi'(t).   t, out: host arrays of n doubles.
+ * RK_ERR_INVALID_ARG for nu outside [0.2, 8] or bad arguments.
+ */
+rk_status rk_matern_eval(double nu, int which, int n, const double* t, double* out);
 
 /*
  * FFT pass variants and their tuner (no counterpart in the paper: how the

@@ -167,6 +167,41 @@ class Plan:
                    _ptr(gr) if gr is not None else nul, _ptr(gs) if gs is not None else nul)
         return gz, gr, gs
 
+    def solve_gls(self, z, X):
+        """Universal Kriging (rk_solve_gls): beta (B x q) by generalised least
+        squares for site covariates X (n x q); sets the coefficients."""
+        z = _dev_f64(z)
+        if z.dim() == 1:
+            z = z[None]
+        X = _dev_f64(X)
+        if X.dim() == 1:
+            X = X[:, None]
+        beta = torch.empty((z.shape[0], X.shape[1]), dtype=torch.float64, device="cuda")
+        self._call("rk_solve_gls", int(z.shape[0]), _ptr(z), int(X.shape[1]), _ptr(X),
+                   _ptr(beta))
+        self.B = z.shape[0]
+        return beta
+
+    def add_trend(self, out, Xg, beta):
+        """out += X_g beta on the grid (rk_add_trend); Xg: q x ny x nx."""
+        Xg = _dev_f64(Xg)
+        beta = _dev_f64(beta)
+        self._call("rk_add_trend", int(beta.shape[0]), int(beta.shape[1]), _ptr(Xg), _ptr(beta),
+                   _ptr(out))
+        return out
+
+    def interp(self, grid, xy, K=4, out=None):
+        """Values at the targets xy (np x 2) from a predicted grid (B x ny x nx),
+        by local Lagrange interpolation with K points per axis (rk_interp)."""
+        grid = torch.as_tensor(grid).to(device="cuda", dtype=self.dtype).contiguous()
+        B = grid.shape[0] if grid.dim() == 3 else 1
+        xy = _dev_f64(xy)
+        npts = xy.shape[0]
+        if out is None:
+            out = torch.empty((B, npts), dtype=self.dtype, device="cuda")
+        self._call("rk_interp", _ptr(grid), int(B), int(npts), _ptr(xy), int(K), _ptr(out))
+        return out
+
     def debug_copy(self, what):
         """Internal buffers for tests: 'box', 'weights', 'lambda', 'cstar', 'coef'."""
         info = self.info()

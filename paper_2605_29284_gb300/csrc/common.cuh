@@ -33,27 +33,6 @@ template <typename T> __device__ __forceinline__ C<T> cmul_mi(C<T> a, int dir) {
   return dir > 0 ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
 }
 
-// ------------------------------------------------------------------ Matern --
-// phi(d) of Eq. (Matern1) for the half-integer smoothness values, which have
-// elementary closed forms: nu = 1/2: e^-d; 3/2: (1 + d) e^-d;
-// 5/2: (1 + d + d^2 / 3) e^-d.  nu_code: 0 -> 1/2, 1 -> 3/2, 2 -> 5/2.
-template <typename T>
-__device__ __forceinline__ T matern_phi(T d, int nu_code) {
-  T e = exp(-d);
-  if (nu_code == 0) return e;
-  if (nu_code == 1) return (T(1) + d) * e;
-  return (T(1) + d + d * d * T(1.0 / 3.0)) * e;   // a multiply: FP64 division is a long sequence
-}
-// -t phi'(t): derivative of phi(d / rho) with respect to log rho.
-// nu = 1/2: t e^-t; 3/2: t^2 e^-t; 5/2: (t^2 / 3)(1 + t) e^-t.
-template <typename T>
-__device__ __forceinline__ T matern_dlogrho(T t, int nu_code) {
-  T e = exp(-t);
-  if (nu_code == 0) return t * e;
-  if (nu_code == 1) return t * t * e;
-  return (t * t * T(1.0 / 3.0)) * (T(1) + t) * e;
-}
-
 // Raises a kernel's dynamic shared-memory limit when a launch needs more than
 // any earlier launch (the attribute persists, so this is done once per size).
 template <typename K>
@@ -88,6 +67,11 @@ struct DevBuf {
 
 // at most this many plans in one grouped call
 constexpr int kMaxGroup = 16;
+
+// smoothness range of the tabulated (general) Matern correlation
+constexpr double kMaternNuMin = 0.2, kMaternNuMax = 8.0;
+// table id of a general nu (k_matern.cu), uploaded to the current device
+rk_status matern_general(double nu, int* id);
 
 }  // namespace rk
 
@@ -138,6 +122,8 @@ struct rk_plan {
   int* site_order = nullptr;
   // coefficients
   int B = 0, B_cap = 0, n_cap_coef = 0;
+  double* gls_buf = nullptr;   // universal Kriging scratch: (q + B) x n + q (q + B)
+  size_t gls_cap = 0;
   double* c64 = nullptr;       // B x n
   double* z64 = nullptr;       // B x n data (after rk_solve_coef)
   bool have_coef = false, have_chol = false;
@@ -380,6 +366,16 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
                        const float2* adf = nullptr);
 cudaError_t chol_split(const double* a, int n, float2* adf, cudaStream_t s);
 cudaError_t chol_invert_diag_df(const double* a, int n, float2* adf, cudaStream_t s);
+// universal Kriging (k_gls.cu)
+cudaError_t launch_gls_transpose(const double* X, int n, int q, double* rhs, cudaStream_t s);
+cudaError_t launch_gls_beta(const double* X, const double* sol, int n, int q, int B, double* G,
+                            double* beta, int* flag, cudaStream_t s);
+cudaError_t launch_gls_coef(const double* sol, const double* z, const double* X,
+                            const double* beta, int n, int q, int B, double* c, double* zr,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_trend(const double* Xg, const double* beta, size_t N, int q, int B, T* out,
+                         cudaStream_t s);
 // doubles split into float pairs (hi, lo)
 cudaError_t launch_split_pairs(const double* src, size_t count, float2* dst, cudaStream_t s);
 

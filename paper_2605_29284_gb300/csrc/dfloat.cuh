@@ -146,28 +146,4 @@ __device__ __forceinline__ float4 cdf_pack(dfl re, dfl im) {
   return make_float4(re.hi, re.lo, im.hi, im.lo);
 }
 
-// The Matern closed forms of phi (nu = 1/2, 3/2, 5/2; see matern_phi) and of
-// -t phi'(t) (see matern_dlogrho) in double-float, for d, t >= 0.
-__device__ __forceinline__ dfl matern_phi_df(dfl d, int nu_code) {
-  const dfl e = df_exp_neg(d);
-  const dfl one = {1.f, 0.f};
-  if (nu_code == 0) return e;
-  if (nu_code == 1) return df_mul(df_add(one, d), e);
-  constexpr double kThird = 1.0 / 3.0;
-  constexpr float kThirdHi = (float)kThird;
-  const dfl third = {kThirdHi, (float)(kThird - (double)kThirdHi)};
-  return df_mul(df_fma(d, df_fma(d, third, one), one), e);   // 1 + d + d^2 / 3
-}
-
-__device__ __forceinline__ dfl matern_dlogrho_df(dfl t, int nu_code) {
-  const dfl e = df_exp_neg(t);
-  if (nu_code == 0) return df_mul(t, e);
-  const dfl t2e = df_mul(df_mul(t, t), e);
-  if (nu_code == 1) return t2e;
-  constexpr double kThird = 1.0 / 3.0;
-  constexpr float kThirdHi = (float)kThird;
-  const dfl third = {kThirdHi, (float)(kThird - (double)kThirdHi)};
-  return df_mul(df_mul(t2e, third), df_add({1.f, 0.f}, t));   // (t^2 / 3)(1 + t) e^-t
-}
-
 }  // namespace rk

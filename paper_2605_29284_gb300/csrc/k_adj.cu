@@ -7,6 +7,7 @@
 // where ' is d / dlog rho and A' has rows W_i' = K_N^{-1} (k_i' - K_N' W_i).
 #include "common.cuh"
 #include "dfloat.cuh"
+#include "matern.cuh"
 
 namespace rk {
 

@@ -5,6 +5,7 @@
 // lower triangle is used.  Right-looking blocked algorithm with 32 x 32 tiles.
 #include "common.cuh"
 #include "dfloat.cuh"
+#include "matern.cuh"
 
 namespace rk {
 

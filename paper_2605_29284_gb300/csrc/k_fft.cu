@@ -15,6 +15,7 @@
 // and rounded once.
 #include "common.cuh"
 #include "fft.cuh"
+#include "matern.cuh"
 
 #include <stdlib.h>
 

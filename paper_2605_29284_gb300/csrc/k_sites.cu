@@ -4,6 +4,7 @@
 
 #include "common.cuh"
 #include "dfloat.cuh"
+#include "matern.cuh"
 
 namespace rk {
 

@@ -311,7 +311,9 @@ rk_status lambda_host(rk_plan* p, std::vector<double>& lam) {
 rk_status choose_block(rk_plan* p) {
   std::vector<double> lam;
   RK_TRY(lambda_host(p, lam));
-  block_for_eta(lam, p->H, p->py, p->nu_code == 0 ? kBlockEtaExp : kBlockEta, &p->blk_kx,
+  // the coarser threshold for spectra decaying no faster than the exponential
+  // kernel's (nu <= 1/2); nu = 1 already decays like |k|^-4
+  block_for_eta(lam, p->H, p->py, p->nu <= 0.5 + 1e-12 ? kBlockEtaExp : kBlockEta, &p->blk_kx,
                 &p->blk_ky, &p->nblk);
   return RK_OK;
 }
@@ -329,7 +331,7 @@ void free_plan(rk_plan* p) {
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
                   p->efac_g, p->gblk, p->bw_dk, p->tile_start,
                   p->tile_count, p->tile_cursor, p->site_order,
-                  p->mchol_df, p->kn_df, p->cdf};
+                  p->mchol_df, p->kn_df, p->cdf, p->gls_buf};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_flag) cudaFreeHost(p->h_flag);
@@ -899,7 +901,15 @@ rk_status rk_plan_create(rk_plan** out, int nx, int ny, const double extent[4], 
   if (fabs(nu - 0.5) < 1e-12) nu_code = 0;
   else if (fabs(nu - 1.5) < 1e-12) nu_code = 1;
   else if (fabs(nu - 2.5) < 1e-12) nu_code = 2;
-  else return RK_ERR_INVALID_ARG;
+  else if (nu >= kMaternNuMin && nu <= kMaternNuMax) {
+    // other smoothness: the tabulated K_nu form (matern.cuh)
+    int id = 0;
+    const rk_status ms = matern_general(nu, &id);
+    if (ms != RK_OK) return ms;
+    nu_code = 3 + id;
+  } else {
+    return RK_ERR_INVALID_ARG;
+  }
   if ((long long)nx * ny > (1LL << 28)) return RK_ERR_INVALID_ARG;
   // the 1-D transforms hold two complex double rows per CTA in shared memory
   if (smooth23(2 * (nx + L - 2)) > kMaxTorus || smooth23(2 * (ny + L - 2)) > kMaxTorus)
@@ -1244,11 +1254,9 @@ rk_status rk_set_coef_group(rk_plan* const* plans, int nplans, const int* B,
   return RK_OK;
 }
 
-rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
-  if (!p || B < 1 || !z) return RK_ERR_INVALID_ARG;
-  if (p->n == 0 || !p->xy_valid) return RK_ERR_STATE;
+// The Cholesky factor of M = K_xx + tau^2 I (Eq. 3), formed once per site set.
+static rk_status ensure_factor(rk_plan* p) {
   const int n = p->n;
-  RK_TRY(ensure_coef(p, B));
   if (!p->have_chol) {
     if (p->mchol_cap < (size_t)n * n) {
       RK_TRY(dalloc(&p->mchol, (size_t)n * n));
@@ -1271,6 +1279,15 @@ rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
     if (flag) return RK_ERR_NOT_PD;
     p->have_chol = true;
   }
+  return RK_OK;
+}
+
+rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
+  if (!p || B < 1 || !z) return RK_ERR_INVALID_ARG;
+  if (p->n == 0 || !p->xy_valid) return RK_ERR_STATE;
+  const int n = p->n;
+  RK_TRY(ensure_coef(p, B));
+  RK_TRY(ensure_factor(p));
   RK_CU(cudaMemcpyAsync(p->z64, z, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice,
                         p->stream));
   RK_CU(cudaMemcpyAsync(p->c64, z, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1279,6 +1296,49 @@ rk_status rk_solve_coef(rk_plan* p, int B, const double* z) {
                    p->precision == RK_FP32 ? p->mchol_df : nullptr));
   RK_TRY(finish_coef(p, B));
   RK_CU(cudaStreamSynchronize(p->stream));
+  return RK_OK;
+}
+
+// Universal Kriging (Eqs. 2-5): beta by generalised least squares, then the
+// coefficients of the detrended data; the plan keeps z - X beta as its data.
+rk_status rk_solve_gls(rk_plan* p, int B, const double* z, int q, const double* X,
+                       double* beta) {
+  if (!p || B < 1 || !z || !X || !beta || q < 1 || q > 16) return RK_ERR_INVALID_ARG;
+  if (p->n == 0 || !p->xy_valid) return RK_ERR_STATE;
+  const int n = p->n;
+  if (q >= n) return RK_ERR_INVALID_ARG;
+  RK_TRY(ensure_coef(p, B));
+  RK_TRY(ensure_factor(p));
+  const size_t need = (size_t)(q + B) * n + (size_t)q * (q + B);
+  if (p->gls_cap < need) {
+    RK_TRY(dalloc(&p->gls_buf, need));
+    p->gls_cap = need;
+  }
+  double* sol = p->gls_buf;                        // [X^T | z] then M^-1 [X^T | z]
+  double* G = p->gls_buf + (size_t)(q + B) * n;    // q x (q + B) normal equations
+  cudaStream_t s = p->stream;
+  RK_CU(launch_gls_transpose(X, n, q, sol, s));
+  RK_CU(cudaMemcpyAsync(sol + (size_t)q * n, z, (size_t)B * n * sizeof(double),
+                        cudaMemcpyDeviceToDevice, s));
+  RK_CU(chol_solve(p->mchol, n, sol, q + B, s, p->precision == RK_FP32 ? p->mchol_df : nullptr));
+  RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s));
+  RK_CU(launch_gls_beta(X, sol, n, q, B, G, beta, p->d_flag, s));
+  RK_CU(launch_gls_coef(sol, z, X, beta, n, q, B, p->c64, p->z64, s));
+  int flag = 0;
+  RK_TRY(read_flag(p, &flag));
+  if (flag) return RK_ERR_NOT_PD;
+  return finish_coef(p, B);
+}
+
+// f = X_g beta + g_hat (Eq. 5): the trend added to a predicted grid in place.
+rk_status rk_add_trend(rk_plan* p, int B, int q, const double* Xg, const double* beta,
+                       void* out) {
+  if (!p || B < 1 || q < 1 || q > 16 || !Xg || !beta || !out) return RK_ERR_INVALID_ARG;
+  const size_t N = (size_t)p->nx * p->ny;
+  if (p->precision == RK_FP64)
+    RK_CU(launch_trend<double>(Xg, beta, N, q, B, (double*)out, p->stream));
+  else
+    RK_CU(launch_trend<float>(Xg, beta, N, q, B, (float*)out, p->stream));
   return RK_OK;
 }
 

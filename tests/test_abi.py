@@ -43,7 +43,8 @@ def test_invalid_arguments_rejected_before_any_gpu_work(repo_root):
     f.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
                   ctypes.POINTER(ctypes.c_double)] + [ctypes.c_double] * 4 + [ctypes.c_int] * 2 + [ctypes.c_void_p]
     assert f(ctypes.byref(h), 1, 10, ext, 1.5, 0.1, 1.0, 0.0, 2, 0, None) == 1   # nx < 2
-    assert f(ctypes.byref(h), 10, 10, ext, 1.0, 0.1, 1.0, 0.0, 2, 0, None) == 1  # nu = 1
+    assert f(ctypes.byref(h), 10, 10, ext, 0.1, 0.1, 1.0, 0.0, 2, 0, None) == 1  # nu < 0.2
+    assert f(ctypes.byref(h), 10, 10, ext, 9.0, 0.1, 1.0, 0.0, 2, 0, None) == 1  # nu > 8
     assert f(ctypes.byref(h), 10, 10, ext, 1.5, -0.1, 1.0, 0.0, 2, 0, None) == 1  # range < 0
     assert f(ctypes.byref(h), 10, 10, ext, 1.5, 0.1, 1.0, 0.0, 5, 0, None) == 1   # L > 4
     assert not h.value

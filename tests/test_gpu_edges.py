@@ -28,7 +28,8 @@ def rk():
     (10, 10, (0.0, 1.0, 0.0, 1.0), 1.5, 0.2, 1.0, 1e-3, 0),    # L = 0
     (10, 10, (0.0, 1.0, 0.0, 1.0), 1.5, 0.2, 1.0, 1e-3, 5),    # L > 4
     (10, 10, (1.0, 0.0, 0.0, 1.0), 1.5, 0.2, 1.0, 1e-3, 2),    # empty extent
-    (10, 10, (0.0, 1.0, 0.0, 1.0), 1.0, 0.2, 1.0, 1e-3, 2),    # nu without a closed form
+    (10, 10, (0.0, 1.0, 0.0, 1.0), 0.1, 0.2, 1.0, 1e-3, 2),    # nu below the tabulated range
+    (10, 10, (0.0, 1.0, 0.0, 1.0), 9.0, 0.2, 1.0, 1e-3, 2),    # nu above it
     (10, 10, (0.0, 1.0, 0.0, 1.0), 1.5, -0.2, 1.0, 1e-3, 2),   # range <= 0
     (10, 10, (0.0, 1.0, 0.0, 1.0), 1.5, 0.2, 0.0, 1e-3, 2),    # sigma^2 <= 0
     (10, 10, (0.0, 1.0, 0.0, 1.0), 1.5, 0.2, 1.0, -1e-3, 2),   # tau^2 < 0

@@ -15,7 +15,7 @@ import pytest
 from scipy import special
 
 import synth
-from oracle import cs, grad, kriging, matern, philox, rapid
+from oracle import cs, grad, kriging, matern, offgrid, philox, rapid
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -487,3 +487,69 @@ def test_adjoint_close_to_exact_kriging_gradient():
         e = grad.exact_adjoint(xy, z, gbar, g, *th)
         errs.append(max(np.abs(x - y).max() / np.abs(y).max() for x, y in zip(a, e)))
     assert errs[1] < 2e-4 and errs[1] < 0.2 * errs[0]
+
+
+# --------------------------------------------------- off-grid interpolation ----
+
+@pytest.mark.parametrize("K", [2, 4, 6])
+def test_offgrid_reproduces_tensor_polynomials_exactly(K):
+    # Lagrange interpolation with K points per axis is exact for every
+    # polynomial of degree < K in x times degree < K in y (here on an
+    # anisotropic grid, targets anywhere including the borders)
+    ext = (-0.3, 1.2, 0.1, 0.9)
+    nx, ny = 17, 11
+    rs = np.random.default_rng(K)
+    C = rs.standard_normal((K, K))
+    gx = np.linspace(ext[0], ext[1], nx)
+    gy = np.linspace(ext[2], ext[3], ny)
+
+    def f(x, y):
+        return sum(C[i, j] * x ** i * y ** j for i in range(K) for j in range(K))
+    grid = f(gx[None, :], gy[:, None])
+    pts = np.column_stack([rs.uniform(ext[0], ext[1], 300), rs.uniform(ext[2], ext[3], 300)])
+    pts = np.vstack([pts, [[ext[0], ext[2]], [ext[1], ext[3]], [ext[1], ext[2]]]])
+    got = offgrid.interpolate(grid, pts, ext, K)[0]
+    assert np.abs(got - f(pts[:, 0], pts[:, 1])).max() < 1e-11 * np.abs(grid).max()
+    # a polynomial of degree K in x is not reproduced (the rule is not exact beyond)
+    bad = offgrid.interpolate(gx[None, :] ** K + 0 * gy[:, None], pts, ext, K)[0]
+    assert np.abs(bad - pts[:, 0] ** K).max() > 1e-6
+
+
+def test_offgrid_bilinear_and_node_values():
+    ext = (0.0, 2.0, 0.0, 1.0)
+    rs = np.random.default_rng(3)
+    grid = rs.standard_normal((2, 5, 9))
+    # at the nodes: the node values, for every K
+    nodes = np.array([[2 * i / 8, j / 4] for j in range(5) for i in range(9)])
+    for K in (2, 4):
+        got = offgrid.interpolate(grid, nodes, ext, K)
+        np.testing.assert_allclose(got, grid.reshape(2, -1), atol=1e-14)
+    # K = 2 is the textbook bilinear formula inside each box
+    x, y = 0.61, 0.37
+    gx, gy = x / 0.25, y / 0.25
+    i, j = int(gx), int(gy)
+    u, v = gx - i, gy - j
+    ref = ((1 - u) * (1 - v) * grid[:, j, i] + u * (1 - v) * grid[:, j, i + 1]
+           + (1 - u) * v * grid[:, j + 1, i] + u * v * grid[:, j + 1, i + 1])
+    np.testing.assert_allclose(offgrid.interpolate(grid, [[x, y]], ext, 2)[:, 0], ref,
+                               rtol=1e-14)
+
+
+def test_offgrid_error_order_on_smooth_fields():
+    # halving the spacing divides the interpolation error of a smooth field by
+    # about 2^K (the local Taylor remainder is O(h^K))
+    ext = (0.0, 1.0, 0.0, 1.0)
+    rs = np.random.default_rng(9)
+    pts = rs.uniform(0.1, 0.9, (400, 2))
+
+    def f(x, y):
+        return np.sin(3.1 * x + 0.4) * np.cos(2.3 * y - 0.2)
+    for K in (2, 4, 6):
+        errs = []
+        for m in (21, 41):
+            g = np.linspace(0, 1, m)
+            grid = f(g[None, :], g[:, None])
+            errs.append(np.abs(offgrid.interpolate(grid, pts, ext, K)[0]
+                               - f(pts[:, 0], pts[:, 1])).max())
+        order = np.log2(errs[0] / errs[1])
+        assert abs(order - K) < 0.6, (K, order)
