@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--backward-n", type=int, default=None,
                     help="sites for the adjoint measurement (default: the workload's 20000)")
     ap.add_argument("--secondary-only", default=None,
-                    choices=["paper350", "cs512", "grad1024_backward"],
+                    choices=["paper350", "cs512", "cs_mixed", "table2", "grad1024_backward"],
                     help="run one secondary measurement alone and print it (for profiling)")
     return ap.parse_args()
 
@@ -525,6 +525,75 @@ def measure_cs(dev, steps, peaks, R=None):
         sample
 
 
+def measure_cs_mixed(dev, steps, peaks):
+    """One rk_simulate_group call: the 128^2, 256^2 and 512^2 grids of one data
+    set (n = 5000 sites, nu = 3/2, range 0.1, L = 2), R = 64 realisations
+    each; realisations 0 and 1 of every grid are sampled for the oracle leg."""
+    import torch
+    import paper_2605_29284_gb300 as rk
+    w = synth.WORKLOADS["cs_mixed"]
+    R = w["R"]
+    xy = synth.sites(w["sites"], w["n"], w["extent"], synth.seed_for(w["config"]))
+    z = synth.smooth_field(xy, 1, synth.seed_for(w["config"], 1))
+    plans = []
+    for m in w["grids"]:
+        p = rk.Plan(m, m, w["extent"], w["nu"], w["rho"], w["sigma2"], w["tau2"], w["L"])
+        p.set_obs(torch.from_numpy(xy).to(dev), torch.from_numpy(z).to(dev))
+        plans.append(p)
+    outs = rk.simulate_group(plans, R, 1)
+    torch.cuda.synchronize()
+    sample = {}
+    for m, o in zip(w["grids"], outs):
+        jx, jy = sample_nodes(m, m)
+        oo = o[0, :2].double().cpu().numpy()
+        sample[m] = [(t, jx, jy, oo[t][jy, jx]) for t in range(2)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    total = 0.0
+    for i in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        rk.simulate_group(plans, R, 100 + i, outs)
+        b.record()
+        b.synchronize()
+        total += a.elapsed_time(b)
+    qs = [p.info()["qx"] for p in plans]
+    for p in plans:
+        p.close()
+    sec = total / steps / 1e3
+    nreal = R * len(w["grids"])
+    points = R * sum(m * m for m in w["grids"])
+    return {"realisations_per_s": nreal / sec, "value": points / sec,
+            "unit": "grid-point predictions/s", "ms_per_call": sec * 1e3,
+            "config": {"grids": list(w["grids"]), "R_each": R, "n": w["n"], "nu": w["nu"],
+                       "range": w["rho"], "L": w["L"], "tau2": w["tau2"], "ce_tori": qs,
+                       "issue": "one rk_simulate_group call: one shared triangular solve "
+                                "for the three grids' 192 right-hand sides"}}, sample
+
+
+def measure_table2(dev):
+    """Lambda(Omega, s*) of Section 3.2 on the GPU over Table 2's grids
+    (range 0.25, L = 2, m in 20 .. 200, mesh h / 2) and the fitted orders."""
+    import torch
+    import paper_2605_29284_gb300 as rk
+    ms = [20, 40, 60, 80, 100, 140, 200]
+    res, t0 = {}, time.perf_counter()
+    for nu in (0.5, 1.0, 1.5, 2.5):
+        lam = []
+        for m in ms:
+            with rk.Plan(m, m, (0.0, 1.0, 0.0, 1.0), nu, 0.25, 1.0, 1e-3, 2,
+                         precision="fp64") as p:
+                lam.append(p.kernel_error(2))
+        use = [i for i, m in enumerate(ms) if nu != 2.5 or m <= 140]
+        slope = -np.polyfit(np.log10([ms[i] for i in use]), np.log10([lam[i] for i in use]),
+                            1)[0]
+        res[str(nu)] = {"lambda": lam, "order": float(slope)}
+    torch.cuda.synchronize()
+    return {"grids": ms, "by_nu": res, "seconds": time.perf_counter() - t0,
+            "paper_orders": {"0.5": 1.00, "1.0": 1.99, "1.5": 2.00, "2.5 (<= 140^2)": 2.99}}
+
+
 def measure_backward(dev, steps, peaks, n=None):
     """Forward and adjoint on the 1024 x 1024 grid, 16 fields, nu = 5/2, L = 3,
     and the FP32 theta-gradients against central differences of the FP64 map
@@ -701,6 +770,24 @@ def oracle_cs_error(sample):
                                "simulation with the same counter-based noise"}
 
 
+def oracle_cs_mixed_error(sample):
+    """Realisations 0 and 1 of each grid of the group call against the oracle's
+    simulation of that grid alone (same seed, same noise)."""
+    from oracle import cs, rapid
+    w = synth.WORKLOADS["cs_mixed"]
+    xy = synth.sites(w["sites"], w["n"], w["extent"], synth.seed_for(w["config"]))
+    z = synth.smooth_field(xy, 1, synth.seed_for(w["config"], 1))
+    e = 0.0
+    for m, rows in sample.items():
+        g = rapid.Grid(m, m, w["extent"], w["L"])
+        ref = cs.simulate(xy, z, g, w["nu"], w["rho"], w["sigma2"], w["tau2"], 2, 1)[0]
+        for t, jx, jy, vals in rows:
+            r = ref[t][jy, jx]
+            e = max(e, float(np.abs(vals - r).max() / np.abs(r).max()))
+    return {"fp32": e, "what": "realisations 0, 1 of every grid at seeded nodes against "
+                               "the oracle's simulation of that grid"}
+
+
 def cpu_leg(workload, samples, secondary_samples, budget_s=15.0):
     """Everything that runs the oracle: its rate (cpu_baseline) and the errors
     of the GPU outputs sampled by the GPU arm."""
@@ -712,6 +799,8 @@ def cpu_leg(workload, samples, secondary_samples, budget_s=15.0):
                                            secondary_samples["paper350"])
     if "cs512" in secondary_samples:
         errors["cs512"] = oracle_cs_error(secondary_samples["cs512"])
+    if "cs_mixed" in secondary_samples:
+        errors["cs_mixed"] = oracle_cs_mixed_error(secondary_samples["cs_mixed"])
     return cb, errors
 
 
@@ -770,8 +859,11 @@ def run_ours(args, rank, world):
                                                                               world)
         secondary["cs512_simulate"], sec_samples["cs512"] = measure_cs(dev, max(2, args.steps // 5),
                                                                        peaks)
+        secondary["cs_mixed_simulate"], sec_samples["cs_mixed"] = measure_cs_mixed(
+            dev, max(2, args.steps // 5), peaks)
         secondary["grad1024_backward"] = measure_backward(dev, max(2, args.steps // 5), peaks,
                                                           n=args.backward_n)
+        secondary["table2_kernel_error"] = measure_table2(dev)
     res = {
         "metric": METRIC, "value": value, "unit": "grid-point predictions/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -833,6 +925,10 @@ def main():
             out = measure_paper350(dev, args.steps, peaks, 1)[0]
         elif args.secondary_only == "cs512":
             out = measure_cs(dev, args.steps, peaks)[0]
+        elif args.secondary_only == "cs_mixed":
+            out = measure_cs_mixed(dev, args.steps, peaks)[0]
+        elif args.secondary_only == "table2":
+            out = measure_table2(dev)
         else:
             out = measure_backward(dev, args.steps, peaks, n=args.backward_n)
         if rank == 0:

@@ -385,6 +385,40 @@ rk_status rk_add_trend(rk_plan* plan, int B, int q, const double* Xg_dev, const 
                        void* out_dev);
 
 /*
+ * rk_simulate_group -- rk_simulate for several plans in one call: R
+ * realisations of every data field of every plan (plan k's output as
+ * rk_simulate's, B_k x R x ny_k x nx_k), the noise of each plan exactly as
+ * rk_simulate draws it (same seed: the same realisations).  Plans that share
+ * their sites, covariance and precision (e.g. one data set predicted at
+ * several grid resolutions) share M = K_xx + tau^2 I, and all their
+ * right-hand sides go through one pass of the triangular solves with the
+ * first plan's factor (the dominant cost of a simulation); up to 2048
+ * realisations in total, otherwise plan after plan.  Runs on the first plan's
+ * stream; allocates scratch as rk_simulate does and, for the shared solve,
+ * (sum of B_k R) x n doubles in the first plan.
+ *   nplans  1 .. 16 distinct plans;  outs  device pointers, one per plan.
+ * RK_ERR_STATE / RK_ERR_CE_NEGATIVE as rk_simulate; synchronises once to
+ * compare the plans' sites.
+ */
+rk_status rk_simulate_group(rk_plan* const* plans, int nplans, int R, unsigned long long seed,
+                            void* const* outs);
+
+/*
+ * rk_kernel_error -- Lambda(Omega, s*) of Section 3.2: the largest error of
+ * the local kernel approximation, sup over s in Omega of
+ * |k_approx(s, s*) - k(s, s*)|, k_approx(s, s*) = sum_q W_q k(s, s_q) over the
+ * 2L x 2L neighbours of s* with K_N W = k(s*) (Eq. weights; Cholesky in
+ * double), for s* at the centre of the central box (node indices
+ * ((nx - 2) / 2, (ny - 2) / 2)).  Omega is the plan's extent; the supremum is
+ * taken on the mesh of spacing (hx / sub, hy / sub) covering it (its nodes
+ * include the grid's).  Uses the plan's covariance (sigma2 scales Lambda).
+ *   sub   1 .. 64 mesh points per grid spacing;  out  host, one double.
+ * Needs nx, ny >= 2L.  RK_ERR_NOT_PD when K_N's factorisation fails.
+ * Allocates 65 doubles on first use; synchronises with the stream.
+ */
+rk_status rk_kernel_error(rk_plan* plan, int sub, double* out);
+
+/*
  * rk_interp -- prediction at irregular locations from a predicted grid, the
  * extension proposed in Section 6 (Conclusion & Discussion): predict onto a
  * fine regular mesh with the rapid method, then interpolate off the mesh by

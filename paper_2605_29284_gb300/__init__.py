@@ -190,6 +190,12 @@ class Plan:
                    _ptr(out))
         return out
 
+    def kernel_error(self, sub=2):
+        """Lambda(Omega, s*) of Section 3.2 for this grid and covariance (rk_kernel_error)."""
+        v = ctypes.c_double()
+        self._call("rk_kernel_error", int(sub), ctypes.byref(v))
+        return v.value
+
     def interp(self, grid, xy, K=4, out=None):
         """Values at the targets xy (np x 2) from a predicted grid (B x ny x nx),
         by local Lagrange interpolation with K points per axis (rk_interp)."""
@@ -233,6 +239,21 @@ def predict_group(plans, outs=None):
     oarr = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
     check(lib.rk_set_stream(plans[0]._h, _stream()), "rk_set_stream")
     check(lib.rk_predict_group(harr, n, oarr), "rk_predict_group")
+    return outs
+
+
+def simulate_group(plans, R, seed, outs=None):
+    """rk_simulate_group: R conditional realisations per field of every plan in
+    one call (one shared solve for plans with the same sites and covariance);
+    outs[k] is plans[k]'s B x R x ny x nx output.  Issued on the current stream."""
+    plans = list(plans)
+    if outs is None:
+        outs = [torch.empty((p.B, R, p.ny, p.nx), dtype=p.dtype, device="cuda") for p in plans]
+    n = len(plans)
+    harr = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+    oarr = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+    check(lib.rk_set_stream(plans[0]._h, _stream()), "rk_set_stream")
+    check(lib.rk_simulate_group(harr, n, int(R), int(seed), oarr), "rk_simulate_group")
     return outs
 
 

@@ -75,6 +75,9 @@ _SIGS = {
     "rk_debug_copy": [_vp, _int, _vp, ctypes.c_size_t],
     "rk_interp": [_vp, _vp, _int, _int, _vp, _int, _vp],
     "rk_solve_gls": [_vp, _int, _vp, _int, _vp, _vp],
+    "rk_kernel_error": [_vp, _int, ctypes.POINTER(_dbl)],
+    "rk_simulate_group": [ctypes.POINTER(_vp), _int, _int, ctypes.c_ulonglong,
+                          ctypes.POINTER(_vp)],
     "rk_add_trend": [_vp, _int, _int, _vp, _vp, _vp],
     "rk_fft_get_choice": [_int, _int, _int, ctypes.POINTER(_int)],
     "rk_fft_set_choice": [_int, _int, _int, _int],

@@ -122,6 +122,7 @@ struct rk_plan {
   int* site_order = nullptr;
   // coefficients
   int B = 0, B_cap = 0, n_cap_coef = 0;
+  double* kerr_buf = nullptr;  // Lambda(Omega, s*): W and the result (65 doubles)
   double* gls_buf = nullptr;   // universal Kriging scratch: (q + B) x n + q (q + B)
   size_t gls_cap = 0;
   double* c64 = nullptr;       // B x n
@@ -156,6 +157,7 @@ struct rk_plan {
   float2* tw32qx = nullptr; float2* tw32qy = nullptr;
   double* ce_sqrt64 = nullptr; float* ce_sqrt32 = nullptr;   // sqrt(lambda_Q / (qx qy)), qy x qx
   void* cs_buf = nullptr; size_t cs_bytes = 0;
+  double* grp_rhs = nullptr; size_t grp_rhs_cap = 0;   // rk_simulate_group's shared solve
   // adjoint state (built on the first rk_predict_backward)
   double* wd64 = nullptr; float* wd32 = nullptr;   // W' = dW / dlog rho, n x M
   // the gradient path's exact block (a smaller eta than the forward block:
@@ -366,6 +368,8 @@ cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
                        const float2* adf = nullptr);
 cudaError_t chol_split(const double* a, int n, float2* adf, cudaStream_t s);
 cudaError_t chol_invert_diag_df(const double* a, int n, float2* adf, cudaStream_t s);
+// Lambda(Omega, s*) (k_kerr.cu): scratch holds 64 doubles of W, then the result
+cudaError_t launch_kernel_error(const rk_plan* p, int sub, double* scratch, cudaStream_t s);
 // universal Kriging (k_gls.cu)
 cudaError_t launch_gls_transpose(const double* X, int n, int q, double* rhs, cudaStream_t s);
 cudaError_t launch_gls_beta(const double* X, const double* sol, int n, int q, int B, double* G,

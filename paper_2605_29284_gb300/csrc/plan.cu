@@ -331,7 +331,7 @@ void free_plan(rk_plan* p) {
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
                   p->efac_g, p->gblk, p->bw_dk, p->tile_start,
                   p->tile_count, p->tile_cursor, p->site_order,
-                  p->mchol_df, p->kn_df, p->cdf, p->gls_buf};
+                  p->mchol_df, p->kn_df, p->cdf, p->gls_buf, p->kerr_buf, p->grp_rhs};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_flag) cudaFreeHost(p->h_flag);
@@ -629,6 +629,109 @@ rk_status ensure_ce(rk_plan* p) {
 constexpr int kCsChunk = 64;     // fields per CE / prediction pass
 constexpr int kCsSolve = 512;    // right-hand sides per FP64 solve
 
+// Per-plan buffers of conditional simulation for S realisations at a time:
+// the unconditional fields on the padded grid (S x P1^2), the CE column
+// spectra of one chunk, and (own_rhs) the S x n right-hand sides.
+template <typename T>
+struct CsBufs {
+  T* fu;
+  C<T>* tq;
+  double* rhs;
+};
+
+template <typename T>
+rk_status cs_buffers(rk_plan* p, int S, bool own_rhs, CsBufs<T>* b) {
+  const int G = S < kCsChunk ? S : kCsChunk;
+  const size_t plane = (size_t)p->p1y * p->p1x;
+  const int maxpairs = G / 2 + 1;
+  const size_t fu_b = (size_t)S * plane * sizeof(T);
+  const size_t tq_b = (size_t)maxpairs * p->qx * p->p1y * 2 * sizeof(T);
+  const size_t rhs_b = own_rhs ? (size_t)S * p->n * sizeof(double) : 0;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t need = al(fu_b) + al(tq_b) + al(rhs_b);
+  if (p->cs_bytes < need) {
+    RK_TRY(dalloc_bytes(&p->cs_buf, need));
+    p->cs_bytes = need;
+  }
+  RK_TRY(ensure_field_scratch(p, G));
+  char* base = (char*)p->cs_buf;
+  b->fu = (T*)base;
+  b->tq = (C<T>*)(base + al(fu_b));
+  b->rhs = own_rhs ? (double*)(base + al(fu_b) + al(tq_b)) : nullptr;
+  return RK_OK;
+}
+
+// Steps a8-a10 for realisations [s0, s0 + sn) of plan p (global index
+// b R + t): unconditional fields into fu, z - z_u into rhs (sn x n).
+template <typename T>
+rk_status cs_draws(rk_plan* p, int R, unsigned long long seed, long long s0, int sn,
+                   const CsBufs<T>& b, double* rhs, cudaStream_t s) {
+  const int n = p->n;
+  const int G = sn < kCsChunk ? sn : kCsChunk;
+  const size_t plane = (size_t)p->p1y * p->p1x;
+  const int ldq = p->p1y;
+  const bool f32 = sizeof(T) == sizeof(float);
+  const T* sl = f32 ? (const T*)p->ce_sqrt32 : (const T*)p->ce_sqrt64;
+  const C<T>* twqx = f32 ? (const C<T>*)p->tw32qx : (const C<T>*)p->tw64qx;
+  const C<T>* twqy = f32 ? (const C<T>*)p->tw32qy : (const C<T>*)p->tw64qy;
+  for (long long g0 = s0; g0 < s0 + sn; g0 += G) {
+    const int g = (int)(s0 + sn - g0 < G ? s0 + sn - g0 : G);
+    const int pair0 = (int)(g0 / 2);
+    const int npairs = (int)((g0 + g - 1) / 2 - g0 / 2 + 1);
+    T* fug = b.fu + (size_t)(g0 - s0) * plane;
+    {
+      RK_PROF("ce_cols", (double)npairs * p->qx * (p->qy / 2 + 1) * sizeof(T) +
+                             (double)npairs * p->qx * p->p1y * 2 * sizeof(T));
+      RK_CU(launch_ce_cols<T>(sl, p->qx, p->qy, seed, pair0, npairs, b.tq, ldq, p->p1y, p->fqy,
+                              twqy, s));
+    }
+    {
+      RK_PROF("ce_rows", (double)npairs * p->qx * p->p1y * 2 * sizeof(T) +
+                             (double)g * plane * sizeof(T));
+      RK_CU(launch_ce_rows<T>(b.tq, p->qx, ldq, p->p1y, fug, p->p1x, g0, g, pair0, npairs,
+                              p->fqx, twqx, s));
+    }
+    {
+      RK_PROF("site_values", (double)g * n * (p->M * sizeof(T) + 16.0) + (double)n * p->M * 8);
+      RK_CU(launch_site_values<T>(fug, p->p1x, (long long)plane, g, p->box, p->w64, p->ssd, n,
+                                  p->L, sqrt(p->tau2), seed, g0, R, p->z64,
+                                  rhs + (size_t)(g0 - s0) * n, s));
+    }
+  }
+  return RK_OK;
+}
+
+// Step a11: c = M^-1 rhs for sn right-hand sides with plan p's factor.
+template <typename T>
+rk_status cs_solve(rk_plan* p, double* rhs, int sn, cudaStream_t s) {
+  const int n = p->n;
+  const float2* sdf = sizeof(T) == sizeof(float) ? p->mchol_df : nullptr;
+  if (sdf) {   // double-float updates on the FP32 pipe
+    RK_PROFDF("chol_solve", (double)sn * n * 16.0 + (double)n * (double)n * 8.0,
+              2.0 * n * (double)n * sn);
+    RK_CU(chol_solve(p->mchol, n, rhs, sn, s, sdf));
+  } else {
+    RK_PROF64("chol_solve", (double)sn * n * 16.0 + (double)n * (double)n * 8.0,
+              2.0 * n * (double)n * sn);
+    RK_CU(chol_solve(p->mchol, n, rhs, sn, s));
+  }
+  return RK_OK;
+}
+
+// Step a12: the rapid predictions of the coefficients with f_u added.
+template <typename T>
+rk_status cs_predict(rk_plan* p, long long s0, int sn, const double* rhs, const CsBufs<T>& b,
+                     T* out) {
+  const int G = sn < kCsChunk ? sn : kCsChunk;
+  const size_t plane = (size_t)p->p1y * p->p1x;
+  for (long long g0 = s0; g0 < s0 + sn; g0 += G) {
+    const int g = (int)(s0 + sn - g0 < G ? s0 + sn - g0 : G);
+    RK_TRY(predict_fields<T>(p, rhs + (size_t)(g0 - s0) * p->n, g,
+                             out + (size_t)g0 * p->ny * p->nx, b.fu + (size_t)(g0 - s0) * plane));
+  }
+  return RK_OK;
+}
+
 // Conditional simulation (Section 2, the linearity form): for each group of
 // up to kCsSolve realisations, (1) unconditional fields on the padded grid
 // and their values at the sites, kCsChunk at a time, (2) one FP64 solve of
@@ -639,73 +742,72 @@ template <typename T>
 rk_status simulate_impl(rk_plan* p, int R, unsigned long long seed, T* out) {
   RK_TRY(ensure_w64(p));
   cudaStream_t s = p->stream;
-  const float2* sdf = sizeof(T) == sizeof(float) ? p->mchol_df : nullptr;
-  const int n = p->n;
   const long long total = (long long)p->B * R;
-  const int G = total < kCsChunk ? (int)total : kCsChunk;
   const int S = total < kCsSolve ? (int)total : kCsSolve;
-  const size_t plane = (size_t)p->p1y * p->p1x;
-  const int ldq = p->p1y;
-  const int maxpairs = G / 2 + 1;
-  const size_t fu_b = (size_t)S * plane * sizeof(T);
-  const size_t tq_b = (size_t)maxpairs * p->qx * ldq * 2 * sizeof(T);
-  const size_t rhs_b = (size_t)S * n * sizeof(double);
-  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t need = al(fu_b) + al(tq_b) + al(rhs_b);
-  if (p->cs_bytes < need) {
-    RK_TRY(dalloc_bytes(&p->cs_buf, need));
-    p->cs_bytes = need;
-  }
-  RK_TRY(ensure_field_scratch(p, G));
-  char* base = (char*)p->cs_buf;
-  T* fu = (T*)base;
-  C<T>* tq = (C<T>*)(base + al(fu_b));
-  double* rhs = (double*)(base + al(fu_b) + al(tq_b));
-  const bool f32 = sizeof(T) == sizeof(float);
-  const T* sl = f32 ? (const T*)p->ce_sqrt32 : (const T*)p->ce_sqrt64;
-  const C<T>* twqx = f32 ? (const C<T>*)p->tw32qx : (const C<T>*)p->tw64qx;
-  const C<T>* twqy = f32 ? (const C<T>*)p->tw32qy : (const C<T>*)p->tw64qy;
+  CsBufs<T> b;
+  RK_TRY(cs_buffers<T>(p, S, true, &b));
   for (long long s0 = 0; s0 < total; s0 += S) {
     const int sn = (int)(total - s0 < S ? total - s0 : S);
-    for (long long g0 = s0; g0 < s0 + sn; g0 += G) {
-      const int g = (int)(s0 + sn - g0 < G ? s0 + sn - g0 : G);
-      const int pair0 = (int)(g0 / 2);
-      const int npairs = (int)((g0 + g - 1) / 2 - g0 / 2 + 1);
-      T* fug = fu + (size_t)(g0 - s0) * plane;
-      {
-        RK_PROF("ce_cols", (double)npairs * p->qx * (p->qy / 2 + 1) * sizeof(T) +
-                               (double)npairs * p->qx * p->p1y * 2 * sizeof(T));
-        RK_CU(launch_ce_cols<T>(sl, p->qx, p->qy, seed, pair0, npairs, tq, ldq, p->p1y, p->fqy,
-                                twqy, s));
-      }
-      {
-        RK_PROF("ce_rows", (double)npairs * p->qx * p->p1y * 2 * sizeof(T) +
-                               (double)g * plane * sizeof(T));
-        RK_CU(launch_ce_rows<T>(tq, p->qx, ldq, p->p1y, fug, p->p1x, g0, g, pair0, npairs,
-                                p->fqx, twqx, s));
-      }
-      {
-        RK_PROF("site_values", (double)g * n * (p->M * sizeof(T) + 16.0) + (double)n * p->M * 8);
-        RK_CU(launch_site_values<T>(fug, p->p1x, (long long)plane, g, p->box, p->w64, p->ssd, n,
-                                    p->L, sqrt(p->tau2), seed, g0, R, p->z64,
-                                    rhs + (size_t)(g0 - s0) * n, s));
-      }
+    RK_TRY(cs_draws<T>(p, R, seed, s0, sn, b, b.rhs, s));
+    RK_TRY(cs_solve<T>(p, b.rhs, sn, s));
+    RK_TRY(cs_predict<T>(p, s0, sn, b.rhs, b, out));
+  }
+  return RK_OK;
+}
+
+// Conditional simulation of several plans in one call (e.g. one field at
+// several grid resolutions).  Plans that share sites, covariance and
+// precision share M = K_xx + tau^2 I: their right-hand sides are solved
+// together in one pass over the first plan's factor (the solve dominates a
+// simulation, and its cost is one read of the factor per pass).  The draws
+// and the predictions stay per plan (their transforms are compiled per
+// torus length), on the first plan's stream.
+template <typename T>
+rk_status simulate_group_impl(rk_plan* const* plans, int np, int R, unsigned long long seed,
+                              void* const* outs, bool shared) {
+  rk_plan* p0 = plans[0];
+  cudaStream_t s = p0->stream;
+  long long tot = 0;
+  for (int k = 0; k < np; ++k) {
+    RK_TRY(ensure_w64(plans[k]));
+    tot += (long long)plans[k]->B * R;
+  }
+  if (!shared || tot > 4 * kCsSolve) {
+    for (int k = 0; k < np; ++k) {
+      cudaStream_t keep = plans[k]->stream;
+      plans[k]->stream = s;
+      const rk_status st = simulate_impl<T>(plans[k], R, seed, (T*)outs[k]);
+      plans[k]->stream = keep;
+      RK_TRY(st);
     }
-    if (sdf) {   // double-float updates on the FP32 pipe
-      RK_PROFDF("chol_solve", (double)sn * n * 16.0 + (double)n * (double)n * 8.0,
-                2.0 * n * (double)n * sn);
-      RK_CU(chol_solve(p->mchol, n, rhs, sn, s, sdf));
-    } else {
-      RK_PROF64("chol_solve", (double)sn * n * 16.0 + (double)n * (double)n * 8.0,
-                2.0 * n * (double)n * sn);
-      RK_CU(chol_solve(p->mchol, n, rhs, sn, s));
-    }
-    for (long long g0 = s0; g0 < s0 + sn; g0 += G) {
-      const int g = (int)(s0 + sn - g0 < G ? s0 + sn - g0 : G);
-      const double* rg = rhs + (size_t)(g0 - s0) * n;
-      RK_TRY(predict_fields<T>(p, rg, g, out + (size_t)g0 * p->ny * p->nx,
-                               fu + (size_t)(g0 - s0) * plane));
-    }
+    return RK_OK;
+  }
+  const int n = p0->n;
+  if (p0->grp_rhs_cap < (size_t)tot * n) {
+    RK_TRY(dalloc(&p0->grp_rhs, (size_t)tot * n));
+    p0->grp_rhs_cap = (size_t)tot * n;
+  }
+  std::vector<CsBufs<T>> bufs(np);
+  long long off = 0;
+  for (int k = 0; k < np; ++k) {
+    rk_plan* p = plans[k];
+    const int sk = p->B * R;
+    RK_TRY(cs_buffers<T>(p, sk, false, &bufs[k]));
+    RK_TRY(cs_draws<T>(p, R, seed, 0, sk, bufs[k], p0->grp_rhs + (size_t)off * n, s));
+    off += sk;
+  }
+  RK_TRY(cs_solve<T>(p0, p0->grp_rhs, (int)tot, s));
+  off = 0;
+  for (int k = 0; k < np; ++k) {
+    rk_plan* p = plans[k];
+    const int sk = p->B * R;
+    cudaStream_t keep = p->stream;
+    p->stream = s;
+    const rk_status st = cs_predict<T>(p, 0, sk, p0->grp_rhs + (size_t)off * n, bufs[k],
+                                       (T*)outs[k]);
+    p->stream = keep;
+    RK_TRY(st);
+    off += sk;
   }
   return RK_OK;
 }
@@ -1330,6 +1432,20 @@ rk_status rk_solve_gls(rk_plan* p, int B, const double* z, int q, const double* 
   return finish_coef(p, B);
 }
 
+// Lambda(Omega, s*) of Section 3.2 for the plan's grid and covariance.
+rk_status rk_kernel_error(rk_plan* p, int sub, double* out) {
+  if (!p || !out || sub < 1 || sub > 64 || p->nx < 2 * p->L || p->ny < 2 * p->L)
+    return RK_ERR_INVALID_ARG;
+  if (!p->kerr_buf) RK_TRY(dalloc(&p->kerr_buf, 65));
+  RK_CU(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
+  RK_CU(launch_kernel_error(p, sub, p->kerr_buf, p->stream));
+  int flag = 0;
+  RK_TRY(read_flag(p, &flag));
+  if (flag) return RK_ERR_NOT_PD;
+  RK_CU(cudaMemcpy(out, p->kerr_buf + 64, sizeof(double), cudaMemcpyDeviceToHost));
+  return RK_OK;
+}
+
 // f = X_g beta + g_hat (Eq. 5): the trend added to a predicted grid in place.
 rk_status rk_add_trend(rk_plan* p, int B, int q, const double* Xg, const double* beta,
                        void* out) {
@@ -1635,6 +1751,42 @@ rk_status rk_simulate(rk_plan* p, int R, unsigned long long seed, void* out) {
   RK_TRY(ensure_ce(p));
   if (p->precision == RK_FP64) return simulate_impl<double>(p, R, seed, (double*)out);
   return simulate_impl<float>(p, R, seed, (float*)out);
+}
+
+rk_status rk_simulate_group(rk_plan* const* plans, int nplans, int R, unsigned long long seed,
+                            void* const* outs) {
+  if (!plans || !outs || nplans < 1 || nplans > kMaxGroup || R < 1) return RK_ERR_INVALID_ARG;
+  rk_plan* p0 = plans[0];
+  for (int k = 0; k < nplans; ++k) {
+    rk_plan* p = plans[k];
+    if (!p || !outs[k]) return RK_ERR_INVALID_ARG;
+    for (int j = 0; j < k; ++j)
+      if (plans[j] == p) return RK_ERR_INVALID_ARG;
+    if (p->precision != p0->precision) return RK_ERR_INVALID_ARG;
+    if (p->n == 0 || !p->have_chol || !p->have_coef) return RK_ERR_STATE;
+    RK_TRY(ensure_ce(p));
+  }
+  // one factor serves every plan with the same sites and covariance
+  bool shared = true;
+  for (int k = 1; k < nplans && shared; ++k) {
+    rk_plan* p = plans[k];
+    shared = p->n == p0->n && p->nu == p0->nu && p->rho == p0->rho &&
+             p->sigma2 == p0->sigma2 && p->tau2 == p0->tau2 && p->xy_valid && p0->xy_valid;
+  }
+  if (shared && nplans > 1) {
+    std::vector<double> a((size_t)2 * p0->n), b((size_t)2 * p0->n);
+    RK_CU(cudaStreamSynchronize(p0->stream));
+    RK_CU(cudaMemcpy(a.data(), p0->xy, a.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int k = 1; k < nplans && shared; ++k) {
+      RK_CU(cudaStreamSynchronize(plans[k]->stream));
+      RK_CU(cudaMemcpy(b.data(), plans[k]->xy, b.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost));
+      shared = memcmp(a.data(), b.data(), a.size() * sizeof(double)) == 0;
+    }
+  }
+  if (p0->precision == RK_FP64)
+    return simulate_group_impl<double>(plans, nplans, R, seed, outs, shared);
+  return simulate_group_impl<float>(plans, nplans, R, seed, outs, shared);
 }
 
 rk_status rk_predict_backward(rk_plan* p, const void* gbar, double* gz, double* grho,

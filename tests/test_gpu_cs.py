@@ -89,3 +89,47 @@ def test_realisations_on_a_compile_time_torus(rk):
         out = p.simulate(R, seed).double().cpu().numpy()
         assert (p.info()["qx"], p.info()["qy"]) == (qx, qy)
     assert rel_err(out, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_group_of_grids_matches_oracle(rk, prec, tol):
+    # one data set simulated at three grid resolutions in one call (the
+    # shared-factor path), each grid's realisations element by element against
+    # the oracle's own simulation with the same noise
+    ext = (0.0, 1.0, 0.0, 1.0)
+    n, R, th, tau2, L, seed = 60, 4, (1.5, 0.2, 1.0), 1e-2, 2, 4242
+    xy = synth.sites_uniform(n, ext, 71)
+    z = synth.normals((1, n), 72)
+    sizes = (24, 33, 48)
+    plans = [rk.Plan(m, m, ext, *th, tau2, L, precision=prec) for m in sizes]
+    try:
+        for p in plans:
+            p.set_obs(torch.from_numpy(xy).cuda(), torch.from_numpy(z).cuda())
+        outs = rk.simulate_group(plans, R, seed)
+        alone = plans[1].simulate(R, seed).double().cpu().numpy()
+        for m, o in zip(sizes, outs):
+            ref = cs.simulate(xy, z, rapid.Grid(m, m, ext, L), *th, tau2, R, seed)
+            assert rel_err(o.double().cpu().numpy(), ref) <= tol, m
+        # the shared solve gives what one plan's own simulation gives
+        assert rel_err(outs[1].double().cpu().numpy(), alone) <= tol
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_group_with_different_sites_solves_per_plan(rk):
+    ext = (0.0, 1.0, 0.0, 1.0)
+    th, tau2, L, seed = (1.5, 0.2, 1.0), 1e-2, 2, 99
+    a = rk.Plan(30, 30, ext, *th, tau2, L, precision="fp64")
+    b = rk.Plan(40, 40, ext, *th, tau2, L, precision="fp64")
+    try:
+        xa, xb = synth.sites_uniform(40, ext, 73), synth.sites_uniform(40, ext, 74)
+        z = synth.normals((1, 40), 75)
+        a.set_obs(torch.from_numpy(xa).cuda(), torch.from_numpy(z).cuda())
+        b.set_obs(torch.from_numpy(xb).cuda(), torch.from_numpy(z).cuda())
+        oa, ob = rk.simulate_group([a, b], 3, seed)
+        ref = cs.simulate(xb, z, rapid.Grid(40, 40, ext, L), *th, tau2, 3, seed)
+        assert rel_err(ob.double().cpu().numpy(), ref) <= 1e-10
+    finally:
+        a.close()
+        b.close()
