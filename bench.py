@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--backward-n", type=int, default=None,
                     help="sites for the adjoint measurement (default: the workload's 20000)")
     ap.add_argument("--secondary-only", default=None,
-                    choices=["paper350", "cs512", "cs_mixed", "table2", "grad1024_backward"],
+                    choices=["paper350", "cs512", "cs_mixed", "table2", "factorial",
+                             "grad1024_backward"],
                     help="run one secondary measurement alone and print it (for profiling)")
     return ap.parse_args()
 
@@ -572,6 +573,68 @@ def measure_cs_mixed(dev, steps, peaks):
                                 "for the three grids' 192 right-hand sides"}}, sample
 
 
+def _range_for_correlation(rk, nu, dist, corr=0.7):
+    """range rho with phi(dist / rho) = corr, phi from the library's table
+    (host evaluation, rk_matern_eval) by bisection in t = dist / rho."""
+    lo, hi = 1e-6, 50.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if rk.matern_eval(nu, 0, [mid])[0] > corr else (lo, mid)
+    return dist / (0.5 * (lo + hi))
+
+
+def measure_factorial(dev, sets=5):
+    """The factorial study of Section 3.1 on the GPU: mean absolute error of the
+    rapid prediction against exact Kriging at five grid nodes (centre, quarter
+    point, corner, two edge points) over `sets` seeded uniform site sets per
+    cell, data drawn from the model (rk_draw_obs), sigma^2 = 1, on [0,1]^2.
+    Levels: n 200/500/1500; range with correlation 0.7 at 0.2/0.4/0.8; nu
+    0.5/1/1.5; tau^2 0.01/0.1/0.5; L 2/4 (the paper's L = 8, M = 256, is past
+    this library's M <= 64); grids 100^2/350^2/500^2.  Reports the mean of
+    log10(mean abs error) per level of each factor, and the worst cell."""
+    import itertools
+    import torch
+    import paper_2605_29284_gb300 as rk
+    levels = {"n": (200, 500, 1500), "dist": (0.2, 0.4, 0.8), "nu": (0.5, 1.0, 1.5),
+              "tau2": (0.01, 0.1, 0.5), "L": (2, 4), "grid": (100, 350, 500)}
+    ext = (0.0, 1.0, 0.0, 1.0)
+    t0 = time.perf_counter()
+    cells = []
+    for nu, dist, tau2, L, m in itertools.product(levels["nu"], levels["dist"], levels["tau2"],
+                                                  levels["L"], levels["grid"]):
+        rho = _range_for_correlation(rk, nu, dist)
+        nodes = [(m // 2, m // 2), (m // 4, m // 4), (0, 0), (0, m // 2), (m // 2, m - 1)]
+        pts = torch.tensor([[i / (m - 1), j / (m - 1)] for i, j in nodes], dtype=torch.float64,
+                           device=dev)
+        jx = torch.tensor([i for i, _ in nodes], device=dev)
+        jy = torch.tensor([j for _, j in nodes], device=dev)
+        with rk.Plan(m, m, ext, nu, rho, 1.0, tau2, L, precision="fp64") as p:
+            for n in levels["n"]:
+                errs = []
+                for k in range(sets):
+                    seed = synth.seed_for(2, 1000 + 10 * k) + n
+                    xy = torch.from_numpy(synth.sites_uniform(n, ext, seed)).to(dev)
+                    p.set_sites(xy)
+                    z = p.draw_obs(torch.from_numpy(synth.normals((1, n), seed + 1)).to(dev))
+                    p.solve_coef(z)
+                    exact = p.exact_predict(pts)[0]
+                    rapid = p.predict()[0][jy, jx]
+                    errs.append((rapid - exact).abs())
+                e = torch.stack(errs).mean().item()
+                cells.append({"nu": nu, "dist": dist, "tau2": tau2, "L": L, "grid": m, "n": n,
+                              "range": rho, "mean_abs_error": e})
+    torch.cuda.synchronize()
+    effects = {}
+    for f, lv in levels.items():
+        effects[f] = {str(v): float(np.mean([np.log10(c["mean_abs_error"]) for c in cells
+                                             if c[f] == v])) for v in lv}
+    worst = max(cells, key=lambda c: c["mean_abs_error"])
+    return {"cells": len(cells), "sets_per_cell": sets, "seconds": time.perf_counter() - t0,
+            "mean_log10_error_by_level": effects, "worst_cell": worst,
+            "paper": "worst case nu = 0.5, tau^2 = 0.01, L = 2: mean log10 error below -2; "
+                     "error falls with nu, L, grid size and tau^2 (Table 1 / A2)"}
+
+
 def measure_table2(dev):
     """Lambda(Omega, s*) of Section 3.2 on the GPU over Table 2's grids
     (range 0.25, L = 2, m in 20 .. 200, mesh h / 2) and the fitted orders."""
@@ -864,6 +927,7 @@ def run_ours(args, rank, world):
         secondary["grad1024_backward"] = measure_backward(dev, max(2, args.steps // 5), peaks,
                                                           n=args.backward_n)
         secondary["table2_kernel_error"] = measure_table2(dev)
+        secondary["factorial"] = measure_factorial(dev)
     res = {
         "metric": METRIC, "value": value, "unit": "grid-point predictions/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -929,6 +993,8 @@ def main():
             out = measure_cs_mixed(dev, args.steps, peaks)[0]
         elif args.secondary_only == "table2":
             out = measure_table2(dev)
+        elif args.secondary_only == "factorial":
+            out = measure_factorial(dev)
         else:
             out = measure_backward(dev, args.steps, peaks, n=args.backward_n)
         if rank == 0:

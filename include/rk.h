@@ -404,6 +404,26 @@ rk_status rk_simulate_group(rk_plan* const* plans, int nplans, int R, unsigned l
                             void* const* outs);
 
 /*
+ * rk_exact_predict -- exact Kriging, Eq. (4) of Section 2, at np points:
+ * g_hat(s_p) = sum_i k(s_p, s_i) c_i with the plan's sites and coefficients
+ * (c = M^-1 z from rk_solve_coef), summed in double over all n sites.  For
+ * checking the rapid predictor against exact Kriging (the paper's factorial
+ * study, Section 3.1) at a few points; O(np n).
+ *   pts_dev  device, np x 2 doubles;  out_dev  device, B x np doubles.
+ * RK_ERR_STATE before sites (not weights) and coefficients; B <= 16.
+ */
+rk_status rk_exact_predict(rk_plan* plan, int np, const double* pts_dev, double* out_dev);
+
+/*
+ * rk_draw_obs -- observations drawn from the model at the plan's sites:
+ * z = L_M xi with L_M the lower Cholesky factor of M = K_xx + tau^2 I (formed
+ * here when the sites have none yet), so that z ~ N(0, M) for standard
+ * normal xi: the simulated data of Section 3.1's study.
+ *   xi_dev, z_dev  device, B x n doubles.
+ */
+rk_status rk_draw_obs(rk_plan* plan, int B, const double* xi_dev, double* z_dev);
+
+/*
  * rk_kernel_error -- Lambda(Omega, s*) of Section 3.2: the largest error of
  * the local kernel approximation, sup over s in Omega of
  * |k_approx(s, s*) - k(s, s*)|, k_approx(s, s*) = sum_q W_q k(s, s_q) over the

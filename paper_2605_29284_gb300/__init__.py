@@ -11,7 +11,7 @@ import torch
 
 from ._native import RK_FP32, RK_FP64, PlanInfo, RkError, check, lib, profile_enable, profile_read
 from ._native import (FFT_PASSES, fft_get_choice, fft_set_choice, fft_tune, fft_variant_info,
-                      fft_variants)
+                      fft_variants, matern_eval)
 
 __all__ = ["Plan", "RkError", "RK_FP32", "RK_FP64", "lib", "predict_group",
            "predict_host_group", "HostGroupCall", "profile_enable", "profile_read",
@@ -189,6 +189,22 @@ class Plan:
         self._call("rk_add_trend", int(beta.shape[0]), int(beta.shape[1]), _ptr(Xg), _ptr(beta),
                    _ptr(out))
         return out
+
+    def exact_predict(self, pts):
+        """Exact Kriging (Eq. 4) at the points pts (np x 2): B x np (rk_exact_predict)."""
+        pts = _dev_f64(pts)
+        out = torch.empty((self.B, pts.shape[0]), dtype=torch.float64, device="cuda")
+        self._call("rk_exact_predict", int(pts.shape[0]), _ptr(pts), _ptr(out))
+        return out
+
+    def draw_obs(self, xi):
+        """Observations z = L_M xi drawn from the model at the sites (rk_draw_obs)."""
+        xi = _dev_f64(xi)
+        if xi.dim() == 1:
+            xi = xi[None]
+        z = torch.empty_like(xi)
+        self._call("rk_draw_obs", int(xi.shape[0]), _ptr(xi), _ptr(z))
+        return z
 
     def kernel_error(self, sub=2):
         """Lambda(Omega, s*) of Section 3.2 for this grid and covariance (rk_kernel_error)."""

@@ -76,6 +76,9 @@ _SIGS = {
     "rk_interp": [_vp, _vp, _int, _int, _vp, _int, _vp],
     "rk_solve_gls": [_vp, _int, _vp, _int, _vp, _vp],
     "rk_kernel_error": [_vp, _int, ctypes.POINTER(_dbl)],
+    "rk_exact_predict": [_vp, _int, _vp, _vp],
+    "rk_matern_eval": [_dbl, _int, _int, _vp, _vp],
+    "rk_draw_obs": [_vp, _int, _vp, _vp],
     "rk_simulate_group": [ctypes.POINTER(_vp), _int, _int, ctypes.c_ulonglong,
                           ctypes.POINTER(_vp)],
     "rk_add_trend": [_vp, _int, _int, _vp, _vp, _vp],
@@ -153,3 +156,14 @@ def fft_tune(n, precision, stream=None):
     check(lib.rk_fft_tune(int(n), int(precision), stream, t), "rk_fft_tune")
     return {name: [t[p * 8 + c] for c in range(fft_variants(n, precision, p))]
             for p, name in enumerate(FFT_PASSES)}
+
+
+def matern_eval(nu, which, t):
+    """The library's Matern phi (which = 0) or -t phi'(t) (which = 1) at the
+    host points t, from its general-nu table (rk_matern_eval)."""
+    import numpy as np
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    out = np.empty_like(t)
+    check(lib.rk_matern_eval(float(nu), int(which), int(t.size), t.ctypes.data, out.ctypes.data),
+          "rk_matern_eval")
+    return out

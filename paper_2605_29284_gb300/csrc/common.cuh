@@ -370,6 +370,11 @@ cudaError_t chol_split(const double* a, int n, float2* adf, cudaStream_t s);
 cudaError_t chol_invert_diag_df(const double* a, int n, float2* adf, cudaStream_t s);
 // Lambda(Omega, s*) (k_kerr.cu): scratch holds 64 doubles of W, then the result
 cudaError_t launch_kernel_error(const rk_plan* p, int sub, double* scratch, cudaStream_t s);
+// exact Kriging at points, observation draws (k_exact.cu)
+cudaError_t launch_exact_predict(const rk_plan* p, int B, const double* pts, int np, double* out,
+                                 cudaStream_t s);
+cudaError_t launch_draw_obs(const rk_plan* p, const double* xi, int B, double* z,
+                            cudaStream_t s);
 // universal Kriging (k_gls.cu)
 cudaError_t launch_gls_transpose(const double* X, int n, int q, double* rhs, cudaStream_t s);
 cudaError_t launch_gls_beta(const double* X, const double* sol, int n, int q, int B, double* G,

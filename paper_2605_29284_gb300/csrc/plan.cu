@@ -1446,6 +1446,25 @@ rk_status rk_kernel_error(rk_plan* p, int sub, double* out) {
   return RK_OK;
 }
 
+// Eq. (4) at given points with the plan's sites and coefficients.
+rk_status rk_exact_predict(rk_plan* p, int np, const double* pts, double* out) {
+  if (!p || np < 0 || (np > 0 && (!pts || !out))) return RK_ERR_INVALID_ARG;
+  if (p->n == 0 || !p->xy_valid || !p->have_coef) return RK_ERR_STATE;
+  if (p->B > 16) return RK_ERR_INVALID_ARG;
+  if (np == 0) return RK_OK;
+  RK_CU(launch_exact_predict(p, p->B, pts, np, out, p->stream));
+  return RK_OK;
+}
+
+// Observations drawn from the model at the plan's sites: z = L_M xi.
+rk_status rk_draw_obs(rk_plan* p, int B, const double* xi, double* z) {
+  if (!p || B < 1 || !xi || !z) return RK_ERR_INVALID_ARG;
+  if (p->n == 0 || !p->xy_valid) return RK_ERR_STATE;
+  RK_TRY(ensure_factor(p));
+  RK_CU(launch_draw_obs(p, xi, B, z, p->stream));
+  return RK_OK;
+}
+
 // f = X_g beta + g_hat (Eq. 5): the trend added to a predicted grid in place.
 rk_status rk_add_trend(rk_plan* p, int B, int q, const double* Xg, const double* beta,
                        void* out) {
