@@ -485,6 +485,10 @@ rk_status rk_matern_eval(double nu, int which, int n, const double* t, double* o
  * CTA.  The first plan created with a torus length (per precision, per
  * process) times every variant of each pass on a synthetic batch and keeps
  * the fastest; RK_FFT_TUNE=0 in the environment keeps variant 1 instead.
+ * With RK_FFT_CACHE=path the choices are read from that text file (lines
+ * "n precision pass variant") when it has them for the length, and a process
+ * that tunes appends its choices there (so that, e.g., a profiled run takes
+ * the choices of the plain run before it).
  * The choice is process-wide; the per-length twiddle tables are per device.
  *
  * rk_fft_variants     number of variants of a pass (1 for lengths with no

@@ -231,6 +231,14 @@ struct RPlan {
     return o;
   }
   static constexpr int tw_size() { return tw_off(S); }
+  // offset of stage s's full twiddles w_N^(r k TWS), r = 1 .. R-1, laid out
+  // [r - 1][k], after the digit twiddles of every stage
+  static constexpr int twf_off(int s) {
+    int o = tw_size();
+    for (int i = 1; i < s; ++i) o += (radix(i) - 1) * span(i);
+    return o;
+  }
+  static constexpr int table_size() { return twf_off(S); }
   static constexpr bool valid() { return S > 0 && N % E == 0; }
   // shared-memory layout: element e at e + (e >> PSH) (a pad slot every 2^PSH
   // elements breaks the power-of-two strides of radix-2^k stores), and an odd
@@ -246,7 +254,8 @@ struct RPlan {
 
 // the per-plan table of stage twiddles: for stage s >= 1 with radix R and
 // span NS, entries w_N^(k TWS rp_dmul(R, d)) at tw_off(s) + d NS + k (k < NS,
-// d < rp_ndig(R)), TWS = N / (NS R); filled on the host in extended precision
+// d < rp_ndig(R)), TWS = N / (NS R), and every twiddle w_N^(r k TWS) at
+// twf_off(s) + (r - 1) NS + k; filled on the host in extended precision
 template <int N, int E>
 inline void rplan_twiddles(double* re, double* im) {
   using P = RPlan<N, E>;
@@ -259,6 +268,14 @@ inline void rplan_twiddles(double* re, double* im) {
         const long long e = ((long long)k * tws * rp_dmul(R, d)) % N;
         const long double ang = 2.0L * pi * (long double)e / (long double)N;
         const int o = P::tw_off(s) + d * NS + k;
+        re[o] = (double)cosl(ang);
+        im[o] = (double)-sinl(ang);
+      }
+    for (int r = 1; r < R; ++r)
+      for (int k = 0; k < NS; ++k) {
+        const long long e = ((long long)r * k * tws) % N;
+        const long double ang = 2.0L * pi * (long double)e / (long double)N;
+        const int o = P::twf_off(s) + (r - 1) * NS + k;
         re[o] = (double)cosl(ang);
         im[o] = (double)-sinl(ang);
       }
@@ -298,17 +315,18 @@ __device__ __forceinline__ void apply_digit_twiddles(const C<T>* g, C<T>* a) {
 }
 
 // One transform on register array v (stage-0 inputs x[t + THR r] in v[r]),
-// DIR = +1 forward, -1 unnormalised inverse.  buf: NPAD elements of shared
+// DIR = +1 forward, -1 unnormalised inverse; TWM = 0: stage twiddles from
+// their digit values, 1: every stage twiddle loaded from the table.  buf: NPAD elements of shared
 // memory for this transform (barriers are CTA-wide: every thread of the CTA
 // calls this the same number of times).  On return v[q] holds
 // X[t + THR out_m(q)].
-template <typename T, int N, int E, int DIR, int s = 0>
+template <typename T, int N, int E, int DIR, int TWM = 0, int s = 0>
 __device__ __forceinline__ void rfft(C<T> (&v)[E], C<T>* buf, const C<T>* __restrict__ stw,
                                      int t) {
   using P = RPlan<N, E>;
   if constexpr (s == 0) {
     RegDft<T, E, DIR>::run(v);
-    if constexpr (P::S > 1) rfft<T, N, E, DIR, 1>(v, buf, stw, t);
+    if constexpr (P::S > 1) rfft<T, N, E, DIR, TWM, 1>(v, buf, stw, t);
   } else {
     // exchange: store stage s-1's outputs in autosort order, load stage s's inputs
     constexpr int Rp = P::radix(s - 1), NSp = P::span(s - 1), ITp = E / Rp;
@@ -334,13 +352,22 @@ __device__ __forceinline__ void rfft(C<T> (&v)[E], C<T>* buf, const C<T>* __rest
     for (int i = 0; i < IT; ++i) {
       const int j = t + P::THR * i;
       const int k = j % NS;
-      C<T> g[p];
+      if constexpr (TWM == 0) {
+        C<T> g[p];
 #pragma unroll
-      for (int d = 0; d < p; ++d) g[d] = stw[P::tw_off(s) + d * NS + k];
-      apply_digit_twiddles<T, R, DIR>(g, v + i * R);
+        for (int d = 0; d < p; ++d) g[d] = stw[P::tw_off(s) + d * NS + k];
+        apply_digit_twiddles<T, R, DIR>(g, v + i * R);
+      } else {
+        // every twiddle from the table (loads instead of products)
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const C<T> w = __ldg(stw + P::twf_off(s) + (r - 1) * NS + k);
+          v[i * R + r] = DIR > 0 ? cmul<T>(v[i * R + r], w) : cmulc<T>(v[i * R + r], w);
+        }
+      }
       RegDft<T, R, DIR>::run(v + i * R);
     }
-    if constexpr (s + 1 < P::S) rfft<T, N, E, DIR, s + 1>(v, buf, stw, t);
+    if constexpr (s + 1 < P::S) rfft<T, N, E, DIR, TWM, s + 1>(v, buf, stw, t);
   }
 }
 

@@ -15,6 +15,7 @@
 //             Hermitian-paired sequence, inverse transform, the window written
 //             (plus an addend in conditional simulation).
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -44,7 +45,7 @@ __device__ __forceinline__ int rslot_of(const G& g, int u) {
 }
 
 // ---------------------------------------------------------------- rows_fwd --
-template <typename T, int N, int E, int V, int MB>
+template <typename T, int N, int E, int V, int MB, int TW>
 __global__ void __launch_bounds__(V * RPlan<N, E>::THR, MB > 0 ? MB : rminb(V * RPlan<N, E>::THR))
 rrows_fwd(const __grid_constant__ Group<RowsFwdSlot<T>> g, const C<T>* __restrict__ stw) {
   using P = RPlan<N, E>;
@@ -70,7 +71,7 @@ rrows_fwd(const __grid_constant__ Group<RowsFwdSlot<T>> g, const C<T>* __restric
     x[r] = mk<T>(xa, xb);
   }
   C<T>* buf = sm + v * NP;
-  rfft<T, N, E, +1>(x, buf, stw, t);
+  rfft<T, N, E, +1, TW>(x, buf, stw, t);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < E; ++q) buf[P::pad(t + THR * P::out_m(q))] = x[q];
@@ -108,7 +109,7 @@ __device__ __forceinline__ void rcp_async(E* dst, const E* src) {
 // Each CTA takes V columns of the fields fg0, fg0 + ng, ... of its slot: the
 // next field's columns stream into a staging buffer (cp.async) while the
 // current ones are transformed in registers and the exchange buffer.
-template <typename T, int N, int E, int V, int MB>
+template <typename T, int N, int E, int V, int MB, int TW>
 __global__ void __launch_bounds__(V * RPlan<N, E>::THR, MB > 0 ? MB : rminb(V * RPlan<N, E>::THR))
 rcols(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
       const C<T>* __restrict__ stw) {
@@ -150,7 +151,7 @@ rcols(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
     }
     __syncthreads();                             // the staging buffer is free
     if (f + ng < B) issue(f + ng);
-    rfft<T, N, E, +1>(x, buf, stw, t);
+    rfft<T, N, E, +1, TW>(x, buf, stw, t);
     C<T>* dst = sl.uout + (size_t)f * sl.ufs + (size_t)kk * sl.ldu;
     if (mode != COLS_FWD_ONLY) {
       double2* bsl = use_blk ? blk + (size_t)f * sl.nblk + (size_t)k * bw : nullptr;
@@ -175,7 +176,7 @@ rcols(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
         }
       }
       rfft_reorder<T, N, E>(x);
-      rfft<T, N, E, -1>(x, buf, stw, t);
+      rfft<T, N, E, -1, TW>(x, buf, stw, t);
     }
     if (kvalid) {
 #pragma unroll
@@ -189,7 +190,7 @@ rcols(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
 }
 
 // ---------------------------------------------------------------- rows_inv --
-template <typename T, int N, int E, int V, int MB>
+template <typename T, int N, int E, int V, int MB, int TW>
 __global__ void __launch_bounds__(V * RPlan<N, E>::THR, MB > 0 ? MB : rminb(V * RPlan<N, E>::THR))
 rrows_inv(const __grid_constant__ Group<RowsInvSlot<T>> g, const C<T>* __restrict__ stw) {
   using P = RPlan<N, E>;
@@ -227,7 +228,7 @@ rrows_inv(const __grid_constant__ Group<RowsInvSlot<T>> g, const C<T>* __restric
     x[r] = mk<T>(X.x - Y.y, X.y + Y.x);          // X + iY
   }
   // rfft's first exchange starts with a barrier, so sm may be reused
-  rfft<T, N, E, -1>(x, sm + v * NP, stw, t);
+  rfft<T, N, E, -1, TW>(x, sm + v * NP, stw, t);
   const int ra = r0 + 2 * v, rb = ra + 1;
   T* out = sl.out + (size_t)f * sl.ofs;
   const T* add = sl.add ? sl.add + (size_t)f * sl.afs : nullptr;
@@ -251,39 +252,41 @@ rrows_inv(const __grid_constant__ Group<RowsInvSlot<T>> g, const C<T>* __restric
 }
 
 // -------------------------------------------------------------- variants --
-// Candidate (E, V, MB) per pass: E elements per thread, V transforms per
+// Candidate (E, V, MB, TW) per pass: E elements per thread, V transforms per
 // CTA, MB CTAs per SM asked of the compiler (a register cap; 0: at most 128
-// registers).  Candidate 0 of every pass is the k_fftn.cu kernel, candidates
-// 1.. are these.
+// registers), TW the stage twiddles (0: from digit values, 1: all loaded).
+// Candidate 0 of every pass is the k_fftn.cu kernel, candidates 1.. are these.
 template <typename T, int N> struct RCands {
   static constexpr int nrow = 0, ncol = 0;
-  static constexpr int row[1][3] = {{1, 1, 0}};
-  static constexpr int col[1][3] = {{1, 1, 0}};
+  static constexpr int row[1][4] = {{1, 1, 0, 0}};
+  static constexpr int col[1][4] = {{1, 1, 0, 0}};
 };
 #define RK_CANDS(TT, NN, NR, ROWS, NC, COLS)                 \
   template <> struct RCands<TT, NN> {                        \
     static constexpr int nrow = NR, ncol = NC;               \
-    static constexpr int row[NR][3] = ROWS;                  \
-    static constexpr int col[NC][3] = COLS;                  \
+    static constexpr int row[NR][4] = ROWS;                  \
+    static constexpr int col[NC][4] = COLS;                  \
   };
 #define RK_L(...) {__VA_ARGS__}
-RK_CANDS(float, 2187, 5, RK_L({27, 2, 0}, {9, 2, 3}, {9, 2, 4}, {9, 4, 2}, {9, 1, 6}),
-         6, RK_L({27, 2, 0}, {9, 1, 3}, {9, 1, 4}, {9, 1, 5}, {9, 2, 2}, {9, 2, 3}))
-RK_CANDS(float, 2048, 5, RK_L({16, 2, 0}, {16, 4, 0}, {8, 2, 3}, {8, 2, 4}, {8, 4, 2}),
-         5, RK_L({16, 2, 0}, {16, 1, 4}, {8, 1, 3}, {8, 1, 4}, {8, 2, 2}))
-RK_CANDS(float, 729, 3, RK_L({27, 4, 0}, {27, 8, 0}, {9, 4, 0}),
-         4, RK_L({27, 4, 0}, {27, 2, 0}, {9, 3, 0}, {9, 3, 3}))
-RK_CANDS(float, 1024, 3, RK_L({16, 4, 0}, {16, 8, 0}, {8, 4, 0}),
-         4, RK_L({16, 4, 0}, {16, 2, 0}, {16, 2, 4}, {8, 2, 0}))
-RK_CANDS(float, 128, 2, RK_L({16, 16, 0}, {8, 16, 0}), 2, RK_L({16, 32, 0}, {8, 16, 0}))
-RK_CANDS(float, 768, 2, RK_L({24, 2, 0}, {24, 4, 0}), 2, RK_L({24, 2, 0}, {24, 4, 0}))
-RK_CANDS(float, 1152, 2, RK_L({24, 2, 0}, {24, 4, 0}), 2, RK_L({24, 2, 0}, {24, 1, 0}))
-RK_CANDS(float, 2304, 2, RK_L({24, 2, 0}, {24, 4, 0}), 2, RK_L({24, 1, 0}, {24, 2, 0}))
-RK_CANDS(double, 2187, 1, RK_L({9, 2, 0}), 1, RK_L({9, 1, 0}))
-RK_CANDS(double, 2048, 1, RK_L({8, 2, 0}), 1, RK_L({8, 1, 0}))
-RK_CANDS(double, 729, 1, RK_L({9, 4, 0}), 1, RK_L({9, 3, 0}))
-RK_CANDS(double, 1024, 1, RK_L({8, 4, 0}), 1, RK_L({8, 2, 0}))
-RK_CANDS(double, 128, 1, RK_L({8, 16, 0}), 1, RK_L({8, 16, 0}))
+RK_CANDS(float, 2187, 4, RK_L({9, 2, 3, 0}, {9, 2, 4, 0}, {9, 1, 6, 0}, {27, 2, 2, 1}),
+         4, RK_L({9, 1, 3, 0}, {9, 1, 4, 0}, {9, 1, 4, 1}, {27, 1, 2, 0}))
+RK_CANDS(float, 2048, 5,
+         RK_L({16, 2, 0, 0}, {8, 2, 3, 0}, {8, 2, 4, 0}, {8, 4, 2, 0}, {16, 2, 0, 1}),
+         4, RK_L({16, 2, 0, 0}, {16, 1, 4, 0}, {8, 1, 4, 0}, {16, 2, 0, 1}))
+RK_CANDS(float, 729, 4, RK_L({27, 4, 0, 0}, {27, 8, 0, 0}, {9, 4, 0, 0}, {9, 4, 0, 1}),
+         5, RK_L({27, 4, 0, 0}, {27, 2, 0, 0}, {9, 3, 0, 0}, {9, 3, 3, 0}, {9, 3, 3, 1}))
+RK_CANDS(float, 1024, 4, RK_L({16, 4, 0, 0}, {16, 8, 0, 0}, {8, 4, 0, 0}, {8, 4, 0, 1}),
+         5, RK_L({16, 4, 0, 0}, {16, 2, 0, 0}, {16, 2, 4, 0}, {8, 2, 0, 0}, {16, 2, 4, 1}))
+RK_CANDS(float, 128, 2, RK_L({16, 16, 0, 0}, {8, 16, 0, 0}), 2,
+         RK_L({16, 32, 0, 0}, {8, 16, 0, 0}))
+RK_CANDS(float, 768, 2, RK_L({24, 2, 0, 0}, {24, 4, 0, 0}), 2, RK_L({24, 2, 0, 0}, {24, 4, 0, 0}))
+RK_CANDS(float, 1152, 2, RK_L({24, 2, 0, 0}, {24, 4, 0, 0}), 2, RK_L({24, 2, 0, 0}, {24, 1, 0, 0}))
+RK_CANDS(float, 2304, 2, RK_L({24, 2, 0, 0}, {24, 4, 0, 0}), 2, RK_L({24, 1, 0, 0}, {24, 2, 0, 0}))
+RK_CANDS(double, 2187, 1, RK_L({9, 2, 0, 0}), 1, RK_L({9, 1, 0, 0}))
+RK_CANDS(double, 2048, 1, RK_L({8, 2, 0, 0}), 1, RK_L({8, 1, 0, 0}))
+RK_CANDS(double, 729, 1, RK_L({9, 4, 0, 0}), 1, RK_L({9, 3, 0, 0}))
+RK_CANDS(double, 1024, 1, RK_L({8, 4, 0, 0}), 1, RK_L({8, 2, 0, 0}))
+RK_CANDS(double, 128, 1, RK_L({8, 16, 0, 0}), 1, RK_L({8, 16, 0, 0}))
 #undef RK_CANDS
 #undef RK_L
 
@@ -307,7 +310,7 @@ struct RTable {
     if (e != cudaSuccess) return e;
     if (d < 0 || d >= kMaxDev) return cudaErrorInvalidDevice;
     if (!dev[d]) {
-      constexpr int n = RPlan<N, E>::tw_size() > 0 ? RPlan<N, E>::tw_size() : 1;
+      constexpr int n = RPlan<N, E>::table_size() > 0 ? RPlan<N, E>::table_size() : 1;
       std::vector<double> re(n, 1.0), im(n, 0.0);
       rplan_twiddles<N, E>(re.data(), im.data());
       std::vector<C<T>> h(n);
@@ -339,16 +342,16 @@ static cudaError_t rsmem(K kern, size_t bytes) {
   static int current = 0;
   return ensure_smem(kern, bytes, current);
 }
-template <typename T, int N, int E, int V, int MB, int PASS> struct RTag {};
+template <typename T, int N, int E, int V, int MB, int PASS> struct RTag {};  // MB: 2 MB + TW
 
-template <typename T, int N, int E, int V, int MB>
+template <typename T, int N, int E, int V, int MB, int TW>
 static cudaError_t go_rrows_fwd(const Group<RowsFwdSlot<T>>& g, cudaStream_t s) {
   using P = RPlan<N, E>;
   const C<T>* stw = RTable<T, N, E>::get();
   if (!stw) return cudaErrorNotReady;
   const size_t sm = sizeof(C<T>) * V * P::NPAD;
-  auto kern = rrows_fwd<T, N, E, V, MB>;
-  cudaError_t e = rsmem<RTag<T, N, E, V, MB, 0>>(kern, sm);
+  auto kern = rrows_fwd<T, N, E, V, MB, TW>;
+  cudaError_t e = rsmem<RTag<T, N, E, V, MB * 2 + TW, 0>>(kern, sm);
   if (e != cudaSuccess) return e;
   int rows = 0;
   for (int k = 0; k < g.n; ++k) rows = g.slot[k].nrows > rows ? g.slot[k].nrows : rows;
@@ -358,14 +361,14 @@ static cudaError_t go_rrows_fwd(const Group<RowsFwdSlot<T>>& g, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-template <typename T, int N, int E, int V, int MB>
+template <typename T, int N, int E, int V, int MB, int TW>
 static cudaError_t go_rcols(Group<ColsSlot<T>>& g, int mode, int H, cudaStream_t s) {
   using P = RPlan<N, E>;
   const C<T>* stw = RTable<T, N, E>::get();
   if (!stw) return cudaErrorNotReady;
   const size_t sm = sizeof(C<T>) * 2 * V * P::NPAD;
-  auto kern = rcols<T, N, E, V, MB>;
-  cudaError_t e = rsmem<RTag<T, N, E, V, MB, 1>>(kern, sm);
+  auto kern = rcols<T, N, E, V, MB, TW>;
+  cudaError_t e = rsmem<RTag<T, N, E, V, MB * 2 + TW, 1>>(kern, sm);
   if (e != cudaSuccess) return e;
   // field groups per slot: enough CTAs for about four waves of the resident
   // CTAs, the rest of each slot's fields looped inside a CTA (prefetched)
@@ -400,15 +403,15 @@ static cudaError_t go_rcols(Group<ColsSlot<T>>& g, int mode, int H, cudaStream_t
   return cudaGetLastError();
 }
 
-template <typename T, int N, int E, int V, int MB>
+template <typename T, int N, int E, int V, int MB, int TW>
 static cudaError_t go_rrows_inv(const Group<RowsInvSlot<T>>& g, cudaStream_t s) {
   using P = RPlan<N, E>;
   const C<T>* stw = RTable<T, N, E>::get();
   if (!stw) return cudaErrorNotReady;
   constexpr size_t a = (size_t)V * P::NPAD, b = (size_t)(N / 2 + 1) * (2 * V + 1);
   const size_t sm = sizeof(C<T>) * (a > b ? a : b);
-  auto kern = rrows_inv<T, N, E, V, MB>;
-  cudaError_t e = rsmem<RTag<T, N, E, V, MB, 2>>(kern, sm);
+  auto kern = rrows_inv<T, N, E, V, MB, TW>;
+  cudaError_t e = rsmem<RTag<T, N, E, V, MB * 2 + TW, 2>>(kern, sm);
   if (e != cudaSuccess) return e;
   int rows = 0;
   for (int k = 0; k < g.n; ++k) rows = g.slot[k].nrows > rows ? g.slot[k].nrows : rows;
@@ -430,7 +433,7 @@ static bool run_rows_fwd(int c, const Group<RowsFwdSlot<T>>& g, cudaStream_t s,
     constexpr int i = decltype(ic)::value;
     if (i + 1 == c) {
       if (RTable<T, N, Cs::row[i][0]>::get()) {
-        *err = go_rrows_fwd<T, N, Cs::row[i][0], Cs::row[i][1], Cs::row[i][2]>(g, s);
+        *err = go_rrows_fwd<T, N, Cs::row[i][0], Cs::row[i][1], Cs::row[i][2], Cs::row[i][3]>(g, s);
         done = true;
       }
     }
@@ -446,7 +449,7 @@ static bool run_cols(int c, Group<ColsSlot<T>>& g, int mode, int H, cudaStream_t
     constexpr int i = decltype(ic)::value;
     if (i + 1 == c) {
       if (RTable<T, N, Cs::col[i][0]>::get()) {
-        *err = go_rcols<T, N, Cs::col[i][0], Cs::col[i][1], Cs::col[i][2]>(g, mode, H, s);
+        *err = go_rcols<T, N, Cs::col[i][0], Cs::col[i][1], Cs::col[i][2], Cs::col[i][3]>(g, mode, H, s);
         done = true;
       }
     }
@@ -462,7 +465,7 @@ static bool run_rows_inv(int c, const Group<RowsInvSlot<T>>& g, cudaStream_t s,
     constexpr int i = decltype(ic)::value;
     if (i + 1 == c) {
       if (RTable<T, N, Cs::row[i][0]>::get()) {
-        *err = go_rrows_inv<T, N, Cs::row[i][0], Cs::row[i][1], Cs::row[i][2]>(g, s);
+        *err = go_rrows_inv<T, N, Cs::row[i][0], Cs::row[i][1], Cs::row[i][2], Cs::row[i][3]>(g, s);
         done = true;
       }
     }
@@ -694,8 +697,39 @@ static cudaError_t tune_t(int N, cudaStream_t s, double* times) {
   return e;
 }
 
-// Makes the choice for (N, precision) on first use: the tuned one, or, with
-// RK_FFT_TUNE=0 in the environment, the first register variant of each pass.
+// The tuning cache named by RK_FFT_CACHE: lines "N precision pass variant".
+// A process that finds its (N, precision) there takes those choices without
+// timing anything (a profiler's replays, for one, would distort the timings);
+// one that tunes appends its choices.
+static bool cache_load(int N, int precision) {
+  const char* path = getenv("RK_FFT_CACHE");
+  if (!path || !*path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  int n, pr, pass, c, found = 0;
+  while (fscanf(f, "%d %d %d %d", &n, &pr, &pass, &c) == 4)
+    if (n == N && pr == precision && pass >= 0 && pass < 3 && c >= 0 &&
+        c < fft_variants(N, precision, pass)) {
+      choice_set(N, precision, pass, c);
+      found |= 1 << pass;
+    }
+  fclose(f);
+  return found == 7;
+}
+
+static void cache_store(int N, int precision) {
+  const char* path = getenv("RK_FFT_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  for (int pass = 0; pass < 3; ++pass)
+    fprintf(f, "%d %d %d %d\n", N, precision, pass, choice_get(N, precision, pass));
+  fclose(f);
+}
+
+// Makes the choice for (N, precision) on first use: from the RK_FFT_CACHE
+// file when it has one, else tuned; with RK_FFT_TUNE=0 in the environment the
+// first register variant of each pass.
 cudaError_t fft_setup(int N, int precision, cudaStream_t s) {
   cudaError_t e = fft_prepare(N, precision);
   if (e != cudaSuccess) return e;
@@ -706,7 +740,10 @@ cudaError_t fft_setup(int N, int precision, cudaStream_t s) {
       choice_set(N, precision, pass, fft_variants(N, precision, pass) > 1 ? 1 : 0);
     return cudaSuccess;
   }
-  return precision == RK_FP64 ? tune_t<double>(N, s, nullptr) : tune_t<float>(N, s, nullptr);
+  if (cache_load(N, precision)) return cudaSuccess;
+  e = precision == RK_FP64 ? tune_t<double>(N, s, nullptr) : tune_t<float>(N, s, nullptr);
+  if (e == cudaSuccess) cache_store(N, precision);
+  return e;
 }
 
 }  // namespace rk
