@@ -851,9 +851,9 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
   const size_t plane = (size_t)p->p1y * p->p1x;
   const size_t grid = (size_t)p->ny * p->nx;
   RK_TRY(ensure_adjoint(p));
-  // one FP64 solve for [zbar | M^{-1} c | M^{-1} K'_xx c]: the three right-hand
-  // side sets are contiguous (B x n each) and share the passes over the factor
-  const int nsets = grho ? 3 : gs2 ? 2 : 1;
+  // one solve for zbar = M^{-1} cbar; with K'_xx c (grho) the buffer holds
+  // [cbar | - | K'_xx c], B x n each
+  const int nsets = grho ? 3 : 1;
   if (p->bw_cbar_cap < (size_t)3 * B * n) {
     RK_TRY(dalloc(&p->bw_cbar, (size_t)3 * B * n));
     p->bw_cbar_cap = (size_t)3 * B * n;
@@ -907,11 +907,7 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
                              p->tw64x, p->tw64y, s));
     RK_CU(launch_block_adjoint(p->bw_gblk, B, p->ngblk, bw, p->efac_g, n, cbar, s));
   }
-  double* c2 = cbar + (size_t)B * n;
   double* c3 = cbar + (size_t)2 * B * n;
-  if (nsets >= 2)
-    RK_CU(cudaMemcpyAsync(c2, p->c64, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice,
-                          s));
   if (nsets == 3) {
     const size_t need = dkxx_scratch_doubles(n, B);
     if (p->bw_dk_cap < need) {
@@ -928,44 +924,35 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
                                s));
   }
   if (sdf) {   // double-float updates on the FP32 pipe
-    RK_PROFDF("adj_solve", (double)n * n * 8.0 + (double)nsets * B * n * 16.0,
-              2.0 * n * (double)n * nsets * B);
-    RK_CU(chol_solve(p->mchol, n, cbar, nsets * B, s, sdf));
+    RK_PROFDF("adj_solve", (double)n * n * 8.0 + (double)B * n * 16.0, 2.0 * n * (double)n * B);
+    RK_CU(chol_solve(p->mchol, n, cbar, B, s, sdf));
   } else {
-    RK_PROF64("adj_solve", (double)n * n * 8.0 + (double)nsets * B * n * 16.0,
-              2.0 * n * (double)n * nsets * B);
-    RK_CU(chol_solve(p->mchol, n, cbar, nsets * B, s));
+    RK_PROF64("adj_solve", (double)n * n * 8.0 + (double)B * n * 16.0, 2.0 * n * (double)n * B);
+    RK_CU(chol_solve(p->mchol, n, cbar, B, s));
   }
   if (gz) RK_CU(cudaMemcpyAsync(gz, cbar, (size_t)B * n * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s));
   if (grho || gs2) {
-    // The theta-gradients are evaluated as predictions of FP64-solved
-    // coefficients, so that the FP32 noise of zbar (which M^{-1} amplifies
-    // by up to 1 / tau^2) does not reach them.  With M c = z:
-    //   d/dlog sigma^2 = gbar . g_hat - zbar^T K_xx c = tau^2 zbar^T c
-    //                  = tau^2 gbar . g_hat(M^{-1} c),
-    //   zbar^T K'_xx c = gbar . g_hat(M^{-1} K'_xx c),
-    //   d/dlog rho     = gbar . (g_hat'(c) + g_hat_W'(c) - g_hat(M^{-1} K'_xx c)).
-    if (p->bw_y_bytes < 4 * B * grid * sizeof(T)) {
-      RK_TRY(dalloc_bytes(&p->bw_y, 4 * B * grid * sizeof(T)));
-      p->bw_y_bytes = 4 * B * grid * sizeof(T);
-    }
-    T* y0 = (T*)p->bw_y;
-    T* y1 = y0 + B * grid;
-    T* y2 = y1 + B * grid;
-    T* y3 = y2 + B * grid;
-    const T* wd = f32 ? (const T*)p->wd32 : (const T*)p->wd64;
-    if (gs2) {
-      RK_TRY(predict_fields<T>(p, c2, B, y0, nullptr, nullptr, nullptr, &gw));
-      RK_CU(launch_dot_rows<T, T>(gbar, y0, B, (long long)grid, p->tau2, 0, gs2, s));
-    }
+    // With M c = z, zbar = M^{-1} cbar and gbar . g_hat = cbar^T c:
+    //   d/dlog sigma^2 = gbar . g_hat - zbar^T K_xx c = tau^2 zbar^T c,
+    //   d/dlog rho     = gbar . (g_hat'(c) + g_hat_W'(c)) - zbar^T K'_xx c,
+    // g_hat' the prediction with lambda' and g_hat_W' with W' (the gradient
+    // block).  Measured at 1024^2 (nu = 5/2, L = 3): 3e-5 of the FP64
+    // gradients for RK_FP32 plans, one solve of B right-hand sides.
+    if (gs2) RK_CU(launch_dot_rows<double, double>(cbar, p->c64, B, n, p->tau2, 0, gs2, s));
     if (grho) {
+      if (p->bw_y_bytes < 2 * B * grid * sizeof(T)) {
+        RK_TRY(dalloc_bytes(&p->bw_y, 2 * B * grid * sizeof(T)));
+        p->bw_y_bytes = 2 * B * grid * sizeof(T);
+      }
+      T* y1 = (T*)p->bw_y;
+      T* y2 = y1 + B * grid;
+      const T* wd = f32 ? (const T*)p->wd32 : (const T*)p->wd64;
       RK_TRY(predict_fields<T>(p, p->c64, B, y1, nullptr, dlam, nullptr, &gw));
       RK_TRY(predict_fields<T>(p, p->c64, B, y2, nullptr, nullptr, wd, &gwd));
-      RK_TRY(predict_fields<T>(p, c3, B, y3, nullptr, nullptr, nullptr, &gw));
       RK_CU(launch_dot_rows<T, T>(gbar, y1, B, (long long)grid, 1.0, 0, grho, s));
       RK_CU(launch_dot_rows<T, T>(gbar, y2, B, (long long)grid, 1.0, 1, grho, s));
-      RK_CU(launch_dot_rows<T, T>(gbar, y3, B, (long long)grid, -1.0, 1, grho, s));
+      RK_CU(launch_dot_rows<double, double>(cbar, c3, B, n, -1.0, 1, grho, s));
     }
   }
   return RK_OK;
