@@ -236,9 +236,8 @@ rk_status rk_predict_group(rk_plan* const* plans, int nplans, void* const* outs)
  * already fully reserved by another allocator, or a latency-critical loop
  * that cannot afford cudaMalloc's implicit device synchronisation.  This
  * entry point computes exactly what rk_predict computes, but keeps the
- * per-call scratch (c*, the two transposed half spectra, the low-frequency
- * block and the coefficients as float pairs) in one file-scope device array
- * of 32 MiB (33554432
+ * per-call scratch (c*, the two transposed half spectra and the
+ * low-frequency block) in one file-scope device array of 32 MiB (33554432
  * bytes) that the library holds on every GPU that loads it, until the
  * process exits.  It calls no cudaMalloc, cudaFree or other allocating
  * routine.

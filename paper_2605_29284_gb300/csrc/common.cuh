@@ -108,8 +108,6 @@ struct rk_plan {
   bool w64_stale = false;      // w64 not yet formed from wdf (ensure_w64)
   float4* efac = nullptr;      // RK_FP32: nblk x n Fourier factors of A_i on the block,
                                // double-float pairs (re.hi, re.lo, im.hi, im.lo)
-  float2* cdf = nullptr;       // RK_FP32: B x n coefficients as float pairs (block GEMM)
-  size_t cdf_cap = 0;
   float4* twdfx = nullptr;     // RK_FP32: the px and py twiddles as double-float pairs
   float4* twdfy = nullptr;     //   (re.hi, re.lo, im.hi, im.lo)
   // sites ordered by the 32 x 32 tile of the padded grid holding their box
@@ -289,9 +287,9 @@ struct BlockFactorDfSlot {
 BlockFactorDfSlot block_factor_df_slot(const rk_plan* p, int n);
 cudaError_t launch_block_factors_df_group(Group<BlockFactorDfSlot>& g, cudaStream_t s);
 cudaError_t launch_block_factors_df(const rk_plan* p, int n, cudaStream_t s);
-// the forward block of RK_FP32 plans in double-float (c split into cdf first)
+// the forward block of RK_FP32 plans in double-float
 struct BlockGemmDfSlot {
-  const double* c; float2* cdf; const float4* efac; double2* blk;
+  const double* c; const float4* efac; double2* blk;
   int n, B, nblk;
 };
 cudaError_t launch_block_gemm_df_group(Group<BlockGemmDfSlot>& g, cudaStream_t s);

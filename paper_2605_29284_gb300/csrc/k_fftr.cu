@@ -205,10 +205,21 @@ rrows_inv(const __grid_constant__ Group<RowsInvSlot<T>> g, const C<T>* __restric
   const int r0 = blockIdx.x * per_k;
   if (r0 >= nrows) return;                       // uniform over the CTA
   const C<T>* src = sl.uin + (size_t)f * sl.ufs;
-  for (int idx = threadIdx.x; idx < HN * per_k; idx += V * THR) {
+  // all of a thread's loads issued before any is used (one memory latency)
+  constexpr int NL = (HN * per_k + V * THR - 1) / (V * THR);
+  C<T> ld[NL];
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    const int idx = threadIdx.x + j * V * THR;
     const int k = idx / per_k, rr = idx - k * per_k;
     const int row = r0 + rr;
-    sm[k * SLD + rr] = row < nrows ? src[(size_t)k * ldu + row] : mk<T>(T(0), T(0));
+    ld[j] = idx < HN * per_k && row < nrows ? src[(size_t)k * ldu + row] : mk<T>(T(0), T(0));
+  }
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    const int idx = threadIdx.x + j * V * THR;
+    const int k = idx / per_k, rr = idx - k * per_k;
+    if (idx < HN * per_k) sm[k * SLD + rr] = ld[j];
   }
   __syncthreads();
   const int v = threadIdx.x / THR, t = threadIdx.x - v * THR;

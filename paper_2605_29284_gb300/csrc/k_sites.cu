@@ -643,124 +643,139 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
 
 // The forward block of RK_FP32 plans in double-float on the FP32 pipe: the
 // same two stages as block_factor_kernel, from the weights' float pairs and
-// double-float twiddles (re.hi, re.lo, im.hi, im.lo); E_i is stored as the
-// same float pairs for the double-float block GEMM.  The block only has to be far more accurate than
-// the single-precision transforms it corrects; double-float (about 2^-47 per
-// operation) is, and runs at 64x the FP64 rate.
-// Threads: NS sites per CTA (a power of two, the fastest index, so the
-// factors' writes coalesce) times 128 / NS lanes over a site's (kx, b) and
-// (kx, ky) pairs; W = 2L is a compile-time constant, so the pair indices
-// split cheaply.  NS = 16 unless the row sums (NS (KX + 1) W float4) would
-// pass 96 KB of shared memory.
-constexpr int kBfThreads = 128;
-constexpr int kBfSites = 16;
+// double-float twiddles (re.hi, re.lo, im.hi, im.lo); E_i is stored site-major
+// (efac[i nblk + j]) as the same float pairs, for the double-float block GEMM.
+// The block only has to be far more accurate than the single-precision
+// transforms it corrects; double-float (about 2^-47 per operation) is, and
+// runs at 64x the FP64 rate.
+// One warp per site.  It first gathers the site's (KX + 1) W x-twiddles
+// e^{-2 pi i kx (ix + a) / px} and (KY + 1) W y-twiddles e^{-2 pi i ky (iy + b)
+// / py}, and its W^2 weights, into its own shared memory, so that the two
+// stages read each of them from there instead of gathering it again for
+// every term: stage 1 over (kx, b, re | im), stage 2 over (kx, ky >= 0).
+constexpr int kBfWarps = 8;
+
+struct BfLayout {                 // one warp's shared memory, in float4
+  int x, y, t, w, total;
+};
+__host__ __device__ inline BfLayout bf_layout(int KX, int KY, int W) {
+  BfLayout l;
+  l.x = 0;
+  l.y = (KX + 1) * W;
+  l.t = l.y + (KY + 1) * W;
+  l.w = l.t + (KX + 1) * W;
+  l.total = l.w + (W * W + 1) / 2;
+  return l;
+}
 
 template <int W>
-__device__ __forceinline__ void block_factor_df_cta(const BlockFactorDfSlot& sl, int cta,
-                                                    float4* tsm) {
+__device__ __forceinline__ void block_factor_df_warp(const BlockFactorDfSlot& sl, int i,
+                                                     float4* sm) {
   constexpr int M = W * W;
-  const int* __restrict__ box = sl.box;
-  const float2* __restrict__ wdf = sl.wdf;
-  float4* __restrict__ efac = sl.efac;
-  const int n = sl.n, px = sl.px, py = sl.py, KY = sl.KY;
-  const int nk = sl.KX + 1, nky = KY + 1, bw = 2 * KY + 1;
-  const int NS = sl.NS, lanes = kBfThreads / NS;
-  const float4* __restrict__ twx = sl.twx;
-  const float4* __restrict__ twy = sl.twy;
-  const int si = threadIdx.x & (NS - 1), lane = threadIdx.x / NS;
-  const int i = cta * NS + si;
-  const bool live = i < n;
-  const int ix = live ? box[2 * i] : 0, iy = live ? box[2 * i + 1] : 0;
-  // stage 1: t(kx, b) = sum_a A_i[a + W b] e^{-2 pi i kx (ix + a) / px}
-  for (int p = lane; p < nk * W; p += lanes) {
-    const int kx = p / W, b = p - kx * W;
-    dfacc ar, ai;                           // unnormalised pair sums
-    if (live) {
-      int m = (kx * ix) % px;               // kx (ix + a) mod px, stepped by kx
-#pragma unroll
-      for (int a = 0; a < W; ++a) {
-        const float4 tw = twx[m];
-        const float2 wv = wdf[(size_t)i * M + a + W * b];
-        const dfl w = {wv.x, wv.y};
-        dfacc_fma(ar, w, {tw.x, tw.y});
-        dfacc_fma(ai, w, {tw.z, tw.w});
-        m += kx;
-        m = m >= px ? m - px : m;
-      }
-    }
-    const dfl tr = dfacc_value(ar), ti = dfacc_value(ai);
-    tsm[(si * nk + kx) * W + b] = make_float4(tr.hi, tr.lo, ti.hi, ti.lo);
+  const int lane = threadIdx.x & 31;
+  const int nk = sl.KX + 1, nky = sl.KY + 1, KY = sl.KY, bw = 2 * KY + 1, nblk = nk * bw;
+  const int px = sl.px, py = sl.py;
+  const BfLayout lo = bf_layout(sl.KX, KY, W);
+  float4* X = sm + lo.x;
+  float4* Y = sm + lo.y;
+  float2* T = reinterpret_cast<float2*>(sm + lo.t);     // t(kx, b) as (re pair, im pair)
+  float2* Wt = reinterpret_cast<float2*>(sm + lo.w);
+  const int ix = sl.box[2 * i], iy = sl.box[2 * i + 1];
+  for (int q = lane; q < M; q += 32) Wt[q] = sl.wdf[(size_t)i * M + q];
+  for (int q = lane; q < nk * W; q += 32) {
+    const int kx = q / W, a = q - kx * W;
+    X[q] = sl.twx[(kx * (ix + a)) % px];
   }
-  __syncthreads();
-  if (!live) return;
+  for (int q = lane; q < nky * W; q += 32) {
+    const int ky = q / W, b = q - ky * W;
+    Y[q] = sl.twy[(ky * (iy + b)) % py];
+  }
+  __syncwarp();
+  // stage 1: t(kx, b) = sum_a A_i[a + W b] e^{-2 pi i kx (ix + a) / px}
+  for (int q = lane; q < 2 * nk * W; q += 32) {
+    const int p = q >> 1, im = q & 1, kx = p / W, b = p - kx * W;
+    dfacc acc;
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      const float4 tw = X[kx * W + a];
+      const float2 wv = Wt[a + W * b];
+      dfacc_fma(acc, {wv.x, wv.y}, im ? dfl{tw.z, tw.w} : dfl{tw.x, tw.y});
+    }
+    const dfl v = dfacc_value(acc);
+    T[2 * p + im] = make_float2(v.hi, v.lo);
+  }
+  __syncwarp();
   // stage 2, ky and -ky together: with t = tr + i ti and f = e^{-2 pi i ky
   // (iy + b) / py}, e^{+2 pi i ...} = conj(f), so from A = sum tr fr,
   // B = sum ti fi, C = sum tr fi, D = sum ti fr:  E(ky) = (A - B) + i (C + D)
   // and E(-ky) = (A + B) + i (D - C): four real products per term for both
-  for (int q = lane; q < nk * nky; q += lanes) {
+  float4* out = sl.efac + (size_t)i * nblk;
+  for (int q = lane; q < nk * nky; q += 32) {
     const int kx = q / nky, ky = q - kx * nky;
-    const float4* t = tsm + (si * nk + kx) * W;
     dfacc sa, sb, sc, sd;
-    int m = (ky * iy) % py;                 // ky (iy + b) mod py, stepped by ky
 #pragma unroll
     for (int b = 0; b < W; ++b) {
-      const float4 f = twy[m], tb = t[b];
-      const dfl fr = {f.x, f.y}, fi = {f.z, f.w}, tr = {tb.x, tb.y}, ti = {tb.z, tb.w};
+      const float4 f = Y[ky * W + b];
+      const float2 r = T[2 * (kx * W + b)], m = T[2 * (kx * W + b) + 1];
+      const dfl fr = {f.x, f.y}, fi = {f.z, f.w}, tr = {r.x, r.y}, ti = {m.x, m.y};
       dfacc_fma(sa, tr, fr);
       dfacc_fma(sb, ti, fi);
       dfacc_fma(sc, tr, fi);
       dfacc_fma(sd, ti, fr);
-      m += ky;
-      m = m >= py ? m - py : m;
     }
     const dfl A = dfacc_value(sa), Bs = dfacc_value(sb), Cs = dfacc_value(sc),
               D = dfacc_value(sd);
-    float4* out = efac + (size_t)kx * bw * n + i;
-    out[(size_t)(KY + ky) * n] = cdf_pack(df_add(A, df_neg(Bs)), df_add(Cs, D));
-    if (ky > 0) out[(size_t)(KY - ky) * n] = cdf_pack(df_add(A, Bs), df_add(D, df_neg(Cs)));
+    out[kx * bw + KY + ky] = cdf_pack(df_add(A, df_neg(Bs)), df_add(Cs, D));
+    if (ky > 0) out[kx * bw + KY - ky] = cdf_pack(df_add(A, Bs), df_add(D, df_neg(Cs)));
   }
 }
 
-__global__ void __launch_bounds__(kBfThreads)
-block_factor_df_kernel(const __grid_constant__ Group<BlockFactorDfSlot> g) {
-  extern __shared__ float4 tsm4[];        // [kBfSites][KX + 1][2L]
+__global__ void __launch_bounds__(32 * kBfWarps)
+block_factor_df_kernel(const __grid_constant__ Group<BlockFactorDfSlot> g, int per_warp) {
+  extern __shared__ float4 bf_sm[];
   int ks = 0;
   while (ks + 1 < g.n && (int)blockIdx.x >= g.start[ks + 1]) ++ks;
   const BlockFactorDfSlot& sl = g.slot[ks];
-  const int cta = blockIdx.x - g.start[ks];
+  const int warp = threadIdx.x >> 5;
+  const int i = (blockIdx.x - g.start[ks]) * sl.NS + warp;
+  if (warp >= sl.NS || i >= sl.n) return;        // uniform over the warp
+  float4* sm = bf_sm + (size_t)warp * per_warp;
   switch (sl.L) {
-    case 1: block_factor_df_cta<2>(sl, cta, tsm4); break;
-    case 2: block_factor_df_cta<4>(sl, cta, tsm4); break;
-    case 3: block_factor_df_cta<6>(sl, cta, tsm4); break;
-    default: block_factor_df_cta<8>(sl, cta, tsm4); break;
+    case 1: block_factor_df_warp<2>(sl, i, sm); break;
+    case 2: block_factor_df_warp<4>(sl, i, sm); break;
+    case 3: block_factor_df_warp<6>(sl, i, sm); break;
+    default: block_factor_df_warp<8>(sl, i, sm); break;
   }
 }
 
+// NS (sites, i.e. warps, per CTA) is set at launch
 BlockFactorDfSlot block_factor_df_slot(const rk_plan* p, int n) {
-  const size_t per_site = sizeof(float4) * (size_t)(p->blk_kx + 1) * 2 * p->L;
-  // L >= 3: 16 lanes per site, which halves the per-thread rounds of the
-  // longest sites; fewer sites per CTA for L <= 2 would only add CTAs that
-  // compete with the main stream's passes running beside this kernel
-  int NS = p->L >= 3 ? kBfSites / 2 : kBfSites;
-  while (NS > 1 && NS * per_site > 96 * 1024) NS /= 2;
   return BlockFactorDfSlot{p->box, p->wdf, p->twdfx, p->twdfy, p->efac, n, p->L, p->px,
-                           p->py, p->blk_kx, p->blk_ky, NS};
+                           p->py, p->blk_kx, p->blk_ky, kBfWarps};
 }
 
 cudaError_t launch_block_factors_df_group(Group<BlockFactorDfSlot>& g, cudaStream_t s) {
-  size_t sm = 0;
+  // one warp area per site, sized for the largest slot; the CTA's warps
+  // (sites) shrink to keep the areas within 96 KB, for every slot alike
+  int per_warp = 0;
+  for (int k = 0; k < g.n; ++k) {
+    const int b = bf_layout(g.slot[k].KX, g.slot[k].KY, 2 * g.slot[k].L).total;
+    per_warp = b > per_warp ? b : per_warp;
+  }
+  int warps = kBfWarps;
+  while (warps > 1 && (size_t)warps * per_warp * sizeof(float4) > 96 * 1024) --warps;
   g.start[0] = 0;
   for (int k = 0; k < g.n; ++k) {
-    const BlockFactorDfSlot& sl = g.slot[k];
-    const size_t b = sizeof(float4) * (size_t)(sl.KX + 1) * 2 * sl.L * sl.NS;
-    sm = b > sm ? b : sm;
-    g.start[k + 1] = g.start[k] + (sl.n + sl.NS - 1) / sl.NS;
+    g.slot[k].NS = warps;
+    g.start[k + 1] = g.start[k] + (g.slot[k].n + warps - 1) / warps;
   }
   if (g.n == 0 || g.start[g.n] == 0) return cudaSuccess;
+  const size_t sm = sizeof(float4) * (size_t)per_warp * warps;
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
   static int smem_set = 0;
   cudaError_t e = ensure_smem(block_factor_df_kernel, sm, smem_set);
   if (e != cudaSuccess) return e;
-  block_factor_df_kernel<<<g.start[g.n], kBfThreads, sm, s>>>(g);
+  block_factor_df_kernel<<<g.start[g.n], 32 * warps, sm, s>>>(g, per_warp);
   return cudaGetLastError();
 }
 
@@ -830,116 +845,150 @@ cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac
 }
 
 // The forward block of RK_FP32 plans in double-float: blk[f][j] =
-// sum_i c[f][i] E_i(j) with E_i as float pairs (re.hi, re.lo, im.hi, im.lo)
-// and c split into float pairs first (split_coef_group_kernel: the FP64
-// conversions once per coefficient, not once per product).  A CTA takes two
-// block entries, F fields and one range of the sites (grid.z: about 16 sites
-// per thread, so that enough CTAs hide the loads' latency); its threads run
-// over the range with unnormalised pair sums, the CTA's partial sums meet in
-// shared memory by double-float additions, and each range's sum is added to
-// the block in double (FP64 atomics; the block was zeroed by the split).  Each term costs
-// about 12 FP32 instructions against two FMAs on the FP64 pipe, which runs
-// at 1/64 of the FP32 rate.
-__global__ void split_coef_group_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
+// sum_i c[f][i] E_i(j), E_i as float pairs (re.hi, re.lo, im.hi, im.lo) and
+// c converted to float pairs as it is staged.  A CTA takes 16 fields (the
+// fast thread index), 16 kBgJ block entries (entry jq + 16 r for thread row
+// jq) and one range of the sites (grid.x); every thread owns its 2 kBgJ
+// (field, entry) sums for the whole range, so E and c are read from global
+// memory once per CTA: chunks of kBgS sites stream into shared memory by
+// cp.async (E) and register loads (c, converted on the way), double
+// buffered.  Each term costs 12 FP32 instructions (the exact hi * hi product
+// and a two-sum into an unnormalised pair) against two FMAs on the FP64 pipe,
+// which runs at 1/64 of the FP32 rate.  The ranges' sums are added to the
+// block in double (FP64 atomics, into a block zeroed first).
+constexpr int kBgS = 32;     // sites per staged chunk
+constexpr int kBgJ = 2;      // entries per thread
+constexpr int kBgE = 16 * kBgJ;
+constexpr int kBgCtas = 2 * 152;
+
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+               "r"(ok ? 16 : 0)
+               : "memory");
+}
+
+__global__ void zero_blk_group_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
   const BlockGemmDfSlot& sl = g.slot[blockIdx.y];
-  const size_t count = (size_t)sl.B * sl.n;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const double d = sl.c[t];
-    const float h = (float)d;
-    sl.cdf[t] = make_float2(h, (float)(d - (double)h));
-  }
-  // the block's sums start at zero (the GEMM's site ranges add into them)
   const size_t nb = (size_t)sl.B * sl.nblk;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nb;
        t += (size_t)gridDim.x * blockDim.x)
     sl.blk[t] = make_double2(0.0, 0.0);
 }
 
-constexpr int kBgJ = 2;
-
-template <int F>
 __global__ void __launch_bounds__(256)
 block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
+  __shared__ __align__(16) float4 es[2][kBgS][kBgE];
+  __shared__ __align__(16) float2 cs[2][kBgS][16];
   int ks = 0;
   while (ks + 1 < g.n && (int)blockIdx.y >= g.start[ks + 1]) ++ks;
   const BlockGemmDfSlot& sl = g.slot[ks];
-  const int j0 = blockIdx.x * kBgJ;
-  if (j0 >= sl.nblk) return;                     // uniform over the CTA
-  const int f0 = (blockIdx.y - g.start[ks]) * F, n = sl.n, nblk = sl.nblk;
-  const int nf = min(F, sl.B - f0), nj = min(kBgJ, nblk - j0);
-  const int chunk = (n + gridDim.z - 1) / gridDim.z;
-  const int i0 = blockIdx.z * chunk, i1 = min(n, i0 + chunk);
-  if (i0 >= i1) return;                          // uniform over the CTA
-  dfacc acc[F][kBgJ][2];
-  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    float4 e[kBgJ];
+  const int n = sl.n, B = sl.B, nblk = sl.nblk;
+  const int ntj = (nblk + kBgE - 1) / kBgE;
+  const int tile = blockIdx.y - g.start[ks];
+  const int fb = (tile / ntj) * 16, jb = (tile % ntj) * kBgE;
+  const int chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  if (i0 >= i1) return;                                   // uniform over the CTA
+  const int nch = (i1 - i0 + kBgS - 1) / kBgS;
+  const int t = threadIdx.x, fq = t & 15, jq = t >> 4;
+  const float4* __restrict__ efac = sl.efac;
+  const double* __restrict__ c = sl.c;
+  // staging maps (consecutive threads on consecutive addresses): E copy
+  // q -> (site q / kBgE, entry q % kBgE) from the site-major factors, c load
+  // q -> (field q / kBgS, site q % kBgS)
+  auto stage_e = [&](int k, int buf) {
+    const int ib = i0 + k * kBgS;
 #pragma unroll
-    for (int jj = 0; jj < kBgJ; ++jj)
-      e[jj] = jj < nj ? sl.efac[(size_t)(j0 + jj) * n + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < kBgS * kBgE / 256; ++r) {
+      const int q = t + 256 * r, s = q / kBgE, jj = q - s * kBgE;
+      const int i = ib + s, j = jb + jj;
+      const bool ok = i < i1 && j < nblk;
+      cp_async16_zfill(&es[buf][s][jj], ok ? efac + (size_t)i * nblk + j : efac, ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  double cv[kBgS * 16 / 256];
+  auto load_c = [&](int k) {
+    const int ib = i0 + k * kBgS;
 #pragma unroll
-    for (int f = 0; f < F; ++f) {
-      if (f < nf) {
-        const float2 cv = sl.cdf[(size_t)(f0 + f) * n + i];
-        const dfl c = {cv.x, cv.y};
+    for (int r = 0; r < kBgS * 16 / 256; ++r) {
+      const int q = t + 256 * r, f = q / kBgS, s = q - f * kBgS;
+      const int i = ib + s;
+      cv[r] = (i < i1 && fb + f < B) ? c[(size_t)(fb + f) * n + i] : 0.0;
+    }
+  };
+  auto store_c = [&](int buf) {
 #pragma unroll
-        for (int jj = 0; jj < kBgJ; ++jj) {
-          dfacc_fma(acc[f][jj][0], c, {e[jj].x, e[jj].y});
-          dfacc_fma(acc[f][jj][1], c, {e[jj].z, e[jj].w});
-        }
+    for (int r = 0; r < kBgS * 16 / 256; ++r) {
+      const int q = t + 256 * r, f = q / kBgS, s = q - f * kBgS;
+      const float h = (float)cv[r];
+      cs[buf][s][f] = make_float2(h, (float)(cv[r] - (double)h));
+    }
+  };
+  dfacc acc[kBgJ][2];
+  stage_e(0, 0);
+  load_c(0);
+  store_c(0);
+  for (int k = 0; k < nch; ++k) {
+    const int buf = k & 1;
+    const bool more = k + 1 < nch;
+    if (more) {
+      stage_e(k + 1, buf ^ 1);
+      load_c(k + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();                                      // chunk k in shared memory
+#pragma unroll 4
+    for (int s = 0; s < kBgS; ++s) {
+      const float2 cw = cs[buf][s][fq];
+      const dfl cc = {cw.x, cw.y};
+#pragma unroll
+      for (int r = 0; r < kBgJ; ++r) {
+        const float4 e = es[buf][s][jq + 16 * r];
+        dfacc_fma(acc[r][0], cc, {e.x, e.y});
+        dfacc_fma(acc[r][1], cc, {e.z, e.w});
       }
     }
+    if (more) store_c(buf ^ 1);
+    __syncthreads();                                      // buffer buf free again
   }
-  // the CTA's sum: pairs normalised, added across each warp by shuffles,
-  // then across the warps in shared memory
-  constexpr int NV = F * kBgJ * 2;
-  __shared__ float2 red[8][NV];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int f = fb + fq;
+  if (f >= B) return;
 #pragma unroll
-  for (int f = 0; f < F; ++f)
-#pragma unroll
-    for (int jj = 0; jj < kBgJ; ++jj)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        dfl v = dfacc_value(acc[f][jj][c]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const dfl w = {__shfl_down_sync(0xffffffffu, v.hi, o),
-                         __shfl_down_sync(0xffffffffu, v.lo, o)};
-          v = df_add(v, w);
-        }
-        if (lane == 0) red[wid][(f * kBgJ + jj) * 2 + c] = make_float2(v.hi, v.lo);
-      }
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-  if (threadIdx.x < NV) {
-    dfl v = {red[0][threadIdx.x].x, red[0][threadIdx.x].y};
-    for (int w = 1; w < nw; ++w) v = df_add(v, {red[w][threadIdx.x].x, red[w][threadIdx.x].y});
-    const int c = threadIdx.x & 1, jj = (threadIdx.x >> 1) % kBgJ, f = threadIdx.x / (2 * kBgJ);
-    if (f < nf && jj < nj)
-      atomicAdd(reinterpret_cast<double*>(sl.blk + (size_t)(f0 + f) * nblk + j0 + jj) + c,
-                df_double(v));
+  for (int r = 0; r < kBgJ; ++r) {
+    const int j = jb + jq + 16 * r;
+    if (j < nblk) {
+      double* dst = reinterpret_cast<double*>(sl.blk + (size_t)f * nblk + j);
+      atomicAdd(dst, df_double(dfacc_value(acc[r][0])));
+      atomicAdd(dst + 1, df_double(dfacc_value(acc[r][1])));
+    }
   }
 }
 
 cudaError_t launch_block_gemm_df_group(Group<BlockGemmDfSlot>& g, cudaStream_t s) {
-  int most = 0, maxb = 0;
-  for (int k = 0; k < g.n; ++k) {
-    if (g.slot[k].nblk <= 0) g.slot[k].B = 0;
-    most = g.slot[k].nblk > most ? g.slot[k].nblk : most;
-    maxb = g.slot[k].B > maxb ? g.slot[k].B : maxb;
-  }
-  if (g.n == 0 || most == 0 || maxb == 0) return cudaSuccess;
-  split_coef_group_kernel<<<dim3(64, g.n), 256, 0, s>>>(g);
-  const int F = maxb >= 4 ? 4 : 1;
+  int nmax = 0, nbmax = 0, maxb = 0;
   g.start[0] = 0;
-  for (int k = 0; k < g.n; ++k) g.start[k + 1] = g.start[k] + (g.slot[k].B + F - 1) / F;
-  int nmax = 0;
-  for (int k = 0; k < g.n; ++k) nmax = g.slot[k].n > nmax ? g.slot[k].n : nmax;
-  const int ranges = nmax / (256 * 16) < 1 ? 1 : (nmax / (256 * 16) > 64 ? 64 : nmax / (256 * 16));
-  const dim3 grid((most + kBgJ - 1) / kBgJ, g.start[g.n], ranges);
-  if (F == 4) block_gemm_df_kernel<4><<<grid, 256, 0, s>>>(g);
-  else block_gemm_df_kernel<1><<<grid, 256, 0, s>>>(g);
+  for (int k = 0; k < g.n; ++k) {
+    BlockGemmDfSlot& sl = g.slot[k];
+    if (sl.nblk <= 0 || sl.n <= 0) sl.B = 0;
+    const int tiles = sl.B > 0 ? ((sl.B + 15) / 16) * ((sl.nblk + kBgE - 1) / kBgE) : 0;
+    g.start[k + 1] = g.start[k] + tiles;
+    nmax = sl.n > nmax ? sl.n : nmax;
+    nbmax = sl.B * sl.nblk > nbmax ? sl.B * sl.nblk : nbmax;
+    maxb = sl.B > maxb ? sl.B : maxb;
+  }
+  if (g.n == 0 || maxb == 0 || g.start[g.n] == 0) return cudaSuccess;
+  const int zb = (nbmax + 255) / 256;
+  zero_blk_group_kernel<<<dim3(zb > 64 ? 64 : zb, g.n), 256, 0, s>>>(g);
+  // site ranges: about kBgCtas CTAs in all, at least two chunks per range
+  int ranges = (kBgCtas + g.start[g.n] - 1) / g.start[g.n];
+  const int most = (nmax + 2 * kBgS - 1) / (2 * kBgS);
+  ranges = ranges > most ? most : ranges;
+  ranges = ranges < 1 ? 1 : ranges;
+  block_gemm_df_kernel<<<dim3(ranges, g.start[g.n]), 256, 0, s>>>(g);
   return cudaGetLastError();
 }
 

@@ -44,9 +44,7 @@ static rk_status predict_static(rk_plan* p, T* out, unsigned char* base) {
   T* cstar = (T*)base;
   C<T>* tb = (C<T>*)(base + cstar_b);
   C<T>* ub = (C<T>*)(base + cstar_b + t_b);
-  const size_t blk_b = align256((size_t)B * p->nblk * sizeof(double2));
   double2* blk = (double2*)(base + cstar_b + t_b + u_b);
-  float2* cdf = (float2*)(base + cstar_b + t_b + u_b + blk_b);   // B x n coefficient pairs
   const T* w = f32 ? (const T*)p->w32 : (const T*)p->w64;
   const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
@@ -63,7 +61,7 @@ static rk_status predict_static(rk_plan* p, T* out, unsigned char* base) {
   if (use_blk) {
     Group<BlockGemmDfSlot> g;
     g.n = 1;
-    g.slot[0] = BlockGemmDfSlot{p->c64, cdf, p->efac, blk, p->n, B, p->nblk};
+    g.slot[0] = BlockGemmDfSlot{p->c64, p->efac, blk, p->n, B, p->nblk};
     if (cudaStreamWaitEvent(s, p->ev_sites, 0) != cudaSuccess ||
         launch_block_gemm_df_group(g, s) != cudaSuccess)
       return RK_ERR_CUDA;
@@ -92,7 +90,7 @@ extern "C" rk_status rk_predict_static(rk_plan* p, void* out) {
                 align256((size_t)p->B * p->H * p->ldt * 2 * es) +
                 align256((size_t)p->B * p->H * p->ldu * 2 * es);
   if (p->precision == RK_FP32 && p->nblk > 0)
-    need += align256((size_t)p->B * p->nblk * 16) + align256((size_t)p->B * p->n * 8);
+    need += align256((size_t)p->B * p->nblk * 16);
   if (need > kStaticScratchBytes) return RK_ERR_INVALID_ARG;
   void* base = nullptr;
   rk_status st = static_scratch(&base);

@@ -24,6 +24,7 @@ constexpr double kBlockEta = 1e-2;
 constexpr double kBlockEtaExp = 1e-1;
 constexpr double kBlockEtaGrad = 1e-4;
 constexpr int kBlockMax = 1024;
+constexpr int kBlockSideMax = 127;   // KX and KY at most (the factor kernel's shared memory)
 // largest torus length per dimension (shared-memory limit of the FFT passes)
 constexpr int kMaxTorus = 3456;
 
@@ -273,7 +274,8 @@ rk_status compute_spectrum(rk_plan* p, int deriv, double** lam64, float** lam32)
 
 // The exact low-frequency block: the smallest rectangle kx <= KX, |ky| <= KY
 // holding every lambda > eta max(lambda), eta doubled from eta0 until the
-// rectangle has at most kBlockMax entries (none if that never happens).
+// rectangle has at most kBlockMax entries and sides KX, KY of at most
+// kBlockSideMax (none if that never happens).
 void block_for_eta(const std::vector<double>& lam, int H, int py, double eta0, int* kx_out,
                    int* ky_out, int* nblk_out) {
   double lmax = 0.0;
@@ -290,7 +292,7 @@ void block_for_eta(const std::vector<double>& lam, int H, int py, double eta0, i
         }
     if (ky_max >= (py - 1) / 2) ky_max = (py - 1) / 2;
     const int nblk = (kx_max + 1) * (2 * ky_max + 1);
-    if (kx_max >= 0 && nblk <= kBlockMax) {
+    if (kx_max >= 0 && nblk <= kBlockMax && kx_max <= kBlockSideMax && ky_max <= kBlockSideMax) {
       *kx_out = kx_max;
       *ky_out = ky_max;
       *nblk_out = nblk;
@@ -331,7 +333,7 @@ void free_plan(rk_plan* p) {
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
                   p->efac_g, p->gblk, p->bw_dk, p->tile_start,
                   p->tile_count, p->tile_cursor, p->site_order,
-                  p->mchol_df, p->kn_df, p->cdf, p->gls_buf, p->kerr_buf, p->grp_rhs};
+                  p->mchol_df, p->kn_df, p->gls_buf, p->kerr_buf, p->grp_rhs};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_flag) cudaFreeHost(p->h_flag);
@@ -363,10 +365,6 @@ rk_status ensure_field_scratch(rk_plan* p, int B) {
   if (p->precision == RK_FP32 && p->nblk > 0 && p->blk_cap < (size_t)B * p->nblk) {
     RK_TRY(dalloc(&p->blk, (size_t)B * p->nblk));
     p->blk_cap = (size_t)B * p->nblk;
-  }
-  if (p->precision == RK_FP32 && p->nblk > 0 && p->cdf_cap < (size_t)B * p->n) {
-    RK_TRY(dalloc(&p->cdf, (size_t)B * p->n));
-    p->cdf_cap = (size_t)B * p->n;
   }
   return RK_OK;
 }
@@ -444,7 +442,7 @@ rk_status predict_fields(rk_plan* p, const double* c64, int nf, T* out,
         RK_PROFDF("block_gemm", bg_bytes, 4.0 * B * p->n * bk.nblk);
         Group<BlockGemmDfSlot> g;
         g.n = 1;
-        g.slot[0] = BlockGemmDfSlot{c64, p->cdf, bk.efac_df, bk.blk, p->n, B, bk.nblk};
+        g.slot[0] = BlockGemmDfSlot{c64, bk.efac_df, bk.blk, p->n, B, bk.nblk};
         RK_CU(launch_block_gemm_df_group(g, s));
       } else {
         RK_PROF64("block_gemm", bg_bytes, 4.0 * B * p->n * bk.nblk);
@@ -515,7 +513,7 @@ rk_status predict_group_impl(rk_plan* const* plans, int np, void* const* outs) {
     gi.slot[k] = RowsInvSlot<T>{(const C<T>*)p->ubuf, (T*)outs[k], nullptr,
                                 (long long)p->H * p->ldu, (long long)p->ny * p->nx, 0, p->ldu,
                                 p->ny, p->nx, p->L - 1, p->nx, 0, 0, 0, B};
-    gb.slot[k] = BlockGemmDfSlot{p->c64, p->cdf, p->efac, p->blk, p->n, blk ? B : 0,
+    gb.slot[k] = BlockGemmDfSlot{p->c64, p->efac, p->blk, p->n, blk ? B : 0,
                                  blk ? p->nblk : 0};
     gf.start[k + 1] = gf.start[k] + B;
     gi.start[k + 1] = gi.start[k] + B;
