@@ -128,7 +128,6 @@ rcols(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
   const int nrin = sl.nrin, orow0 = sl.orow0, nrout = sl.nrout;
   C<T>* buf = sm + v * NP;                       // exchange buffer
   C<T>* stage = sm + (V + v) * NP;               // the next field's column
-  const T* __restrict__ lcol = sl.lam + (size_t)kk * N;
   double2* blk = sl.blk;
   const int bky = sl.blk_ky, bw = 2 * bky + 1;
   const bool use_blk = blk != nullptr && kvalid && k <= sl.blk_kx;
@@ -140,6 +139,17 @@ rcols(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
   if (fg0 < B) issue(fg0);
+  // the column's spectrum, the same for every field: read once into shared
+  // memory (visible after the loop's first barrier)
+  T* lsm = reinterpret_cast<T*>(sm + 2 * V * NP) + v * N;
+  if (mode != COLS_FWD_ONLY) {
+    const T* __restrict__ lcol = sl.lam + (size_t)kk * N;
+    T lv[E];                                     // N = THR E: all loads, then the stores
+#pragma unroll
+    for (int r = 0; r < E; ++r) lv[r] = kvalid ? lcol[t + THR * r] : T(0);
+#pragma unroll
+    for (int r = 0; r < E; ++r) lsm[t + THR * r] = lv[r];
+  }
   for (int f = fg0; f < B; f += ng) {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
@@ -158,7 +168,7 @@ rcols(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const int e = t + THR * P::out_m(q);
-        const T lv = kvalid ? lcol[e] : T(0);
+        const T lv = lsm[e];
         const int ky = e <= bky ? e : (e >= N - bky ? e - N : N);
         const bool inb = use_blk && ky != N;
         if (mode == COLS_CONV) {
@@ -377,7 +387,7 @@ static cudaError_t go_rcols(Group<ColsSlot<T>>& g, int mode, int H, cudaStream_t
   using P = RPlan<N, E>;
   const C<T>* stw = RTable<T, N, E>::get();
   if (!stw) return cudaErrorNotReady;
-  const size_t sm = sizeof(C<T>) * 2 * V * P::NPAD;
+  const size_t sm = sizeof(C<T>) * 2 * V * P::NPAD + sizeof(T) * V * N;
   auto kern = rcols<T, N, E, V, MB, TW>;
   cudaError_t e = rsmem<RTag<T, N, E, V, MB * 2 + TW, 1>>(kern, sm);
   if (e != cudaSuccess) return e;
