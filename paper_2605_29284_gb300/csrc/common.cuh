@@ -32,6 +32,52 @@ template <typename T> __device__ __forceinline__ C<T> cconj(C<T> a) { return mk<
 template <typename T> __device__ __forceinline__ C<T> cmul_mi(C<T> a, int dir) {
   return dir > 0 ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
 }
+// a s + c for a real s
+template <typename T> __device__ __forceinline__ C<T> cfma_r(C<T> a, T s, C<T> c) {
+  return mk<T>(fma(a.x, s, c.x), fma(a.y, s, c.y));
+}
+
+// FP32 complex additions, subtractions and real scalings as packed f32x2
+// instructions (sm_100 family, PTX ISA 8.6): both components in one
+// instruction, each rounded exactly as the scalar operation would be.
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define RK_F32X2_OP(NAME, OPC)                                                        \
+  __device__ __forceinline__ float2 NAME(float2 a, float2 b) {                        \
+    float2 r;                                                                         \
+    asm("{ .reg .b64 ra, rb, rd;\n\t"                                                  \
+        "mov.b64 ra, {%2, %3};\n\t"                                                    \
+        "mov.b64 rb, {%4, %5};\n\t" OPC                                                \
+        " rd, ra, rb;\n\t"                                                             \
+        "mov.b64 {%0, %1}, rd; }"                                                      \
+        : "=f"(r.x), "=f"(r.y)                                                        \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                    \
+    return r;                                                                         \
+  }
+RK_F32X2_OP(f2_add, "add.rn.f32x2")
+RK_F32X2_OP(f2_sub, "sub.rn.f32x2")
+RK_F32X2_OP(f2_mul, "mul.rn.f32x2")
+#undef RK_F32X2_OP
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{ .reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+      "mov.b64 {%0, %1}, rd; }"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+template <> __device__ __forceinline__ float2 cadd<float>(float2 a, float2 b) { return f2_add(a, b); }
+template <> __device__ __forceinline__ float2 csub<float>(float2 a, float2 b) { return f2_sub(a, b); }
+template <> __device__ __forceinline__ float2 cscale<float>(float2 a, float s) {
+  return f2_mul(a, make_float2(s, s));
+}
+template <> __device__ __forceinline__ float2 cfma_r<float>(float2 a, float s, float2 c) {
+  return f2_fma(a, make_float2(s, s), c);
+}
+#endif
 
 // Raises a kernel's dynamic shared-memory limit when a launch needs more than
 // any earlier launch (the attribute persists, so this is done once per size).

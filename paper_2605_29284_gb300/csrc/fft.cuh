@@ -13,25 +13,34 @@ __device__ __forceinline__ void dft2(C<T>* a) {
   a[1] = csub<T>(t, a[1]);
 }
 
+// The rotations by -i dir are folded into the last additions as real
+// operations on swapped components; the other additions are whole complex
+// operations (packed for FP32).
 template <typename T>
 __device__ __forceinline__ void dft3(C<T>* a, int dir) {
   const T s3 = T(0.86602540378443864676372317075294);
-  C<T> t1 = cadd<T>(a[1], a[2]);
-  C<T> t2 = mk<T>(a[0].x - T(0.5) * t1.x, a[0].y - T(0.5) * t1.y);
-  C<T> t3 = cscale<T>(cmul_mi<T>(csub<T>(a[1], a[2]), dir), s3);
+  const C<T> t1 = cadd<T>(a[1], a[2]);
+  const C<T> d = csub<T>(a[1], a[2]);
+  const C<T> t2 = cfma_r<T>(t1, T(-0.5), a[0]);   // a0 - t1 / 2
+  const T sd = T(dir) * s3;                       // t3 = s3 (-i dir) d = sd (d.y, -d.x)
   a[0] = cadd<T>(a[0], t1);
-  a[1] = cadd<T>(t2, t3);
-  a[2] = csub<T>(t2, t3);
+  a[1] = mk<T>(fma(sd, d.y, t2.x), fma(-sd, d.x, t2.y));
+  a[2] = mk<T>(fma(-sd, d.y, t2.x), fma(sd, d.x, t2.y));
 }
 
 template <typename T>
 __device__ __forceinline__ void dft4v(C<T>& b0, C<T>& b1, C<T>& b2, C<T>& b3, int dir) {
-  C<T> t0 = cadd<T>(b0, b2), t1 = csub<T>(b0, b2);
-  C<T> t2 = cadd<T>(b1, b3), t3 = cmul_mi<T>(csub<T>(b1, b3), dir);
+  const C<T> t0 = cadd<T>(b0, b2), t1 = csub<T>(b0, b2);
+  const C<T> t2 = cadd<T>(b1, b3), d = csub<T>(b1, b3);   // t3 = -i dir d = dir (d.y, -d.x)
   b0 = cadd<T>(t0, t2);
   b2 = csub<T>(t0, t2);
-  b1 = cadd<T>(t1, t3);
-  b3 = csub<T>(t1, t3);
+  if (dir > 0) {
+    b1 = mk<T>(t1.x + d.y, t1.y - d.x);
+    b3 = mk<T>(t1.x - d.y, t1.y + d.x);
+  } else {
+    b1 = mk<T>(t1.x - d.y, t1.y + d.x);
+    b3 = mk<T>(t1.x + d.y, t1.y - d.x);
+  }
 }
 
 template <typename T>
