@@ -245,7 +245,10 @@ struct RPlan {
   // per-transform stride so that transforms side by side do not collide
   static constexpr int ilog2(int v) { int l = 0; while ((1 << (l + 1)) <= v) ++l; return l; }
   static constexpr int PSH = (N % 2 == 0) ? ((E & (E - 1)) == 0 ? ilog2(E) : 3) : 30;
-  static constexpr int pad(int e) { return e + (e >> PSH); }
+  static constexpr int pad(int e) {
+    if constexpr (PSH >= 30) return e;          // odd N: no pad slots
+    else return e + (e >> PSH);
+  }
   static constexpr int NPAD = ((N - 1) + ((N - 1) >> PSH) + 1) | 1;
   // element held by register q (q = i R + r) after the last stage
   static constexpr int RL = radix(S - 1), ITL = E / RL;

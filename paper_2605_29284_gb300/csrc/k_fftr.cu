@@ -165,23 +165,28 @@ rcols(const __grid_constant__ Group<ColsSlot<T>> g, int mode, int H,
     C<T>* dst = sl.uout + (size_t)f * sl.ufs + (size_t)kk * sl.ldu;
     if (mode != COLS_FWD_ONLY) {
       double2* bsl = use_blk ? blk + (size_t)f * sl.nblk + (size_t)k * bw : nullptr;
+      if (!use_blk) {                            // uniform over the transform
 #pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const int e = t + THR * P::out_m(q);
-        const T lv = lsm[e];
-        const int ky = e <= bky ? e : (e >= N - bky ? e - N : N);
-        const bool inb = use_blk && ky != N;
-        if (mode == COLS_CONV) {
-          if (inb) {
-            const double2 bv = bsl[ky + bky];
-            x[q] = mk<T>((T)bv.x, (T)bv.y);
-          }
-          x[q] = cscale<T>(x[q], lv);
-        } else {                                 // COLS_ADJ
-          x[q] = cscale<T>(x[q], lv);
-          if (inb) {
-            bsl[ky + bky] = make_double2((double)x[q].x, (double)x[q].y);
-            x[q] = mk<T>(T(0), T(0));
+        for (int q = 0; q < E; ++q) x[q] = cscale<T>(x[q], lsm[t + THR * P::out_m(q)]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int e = t + THR * P::out_m(q);
+          const T lv = lsm[e];
+          const int ky = e <= bky ? e : (e >= N - bky ? e - N : N);
+          const bool inb = ky != N;
+          if (mode == COLS_CONV) {
+            if (inb) {
+              const double2 bv = bsl[ky + bky];
+              x[q] = mk<T>((T)bv.x, (T)bv.y);
+            }
+            x[q] = cscale<T>(x[q], lv);
+          } else {                                 // COLS_ADJ
+            x[q] = cscale<T>(x[q], lv);
+            if (inb) {
+              bsl[ky + bky] = make_double2((double)x[q].x, (double)x[q].y);
+              x[q] = mk<T>(T(0), T(0));
+            }
           }
         }
       }
