@@ -846,16 +846,19 @@ cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac
 
 // The forward block of RK_FP32 plans in double-float: blk[f][j] =
 // sum_i c[f][i] E_i(j), E_i as float pairs (re.hi, re.lo, im.hi, im.lo) and
-// c converted to float pairs as it is staged.  A CTA takes 16 fields (the
-// fast thread index), 16 kBgJ block entries (entry jq + 16 r for thread row
-// jq) and one range of the sites (grid.x); every thread owns its 2 kBgJ
-// (field, entry) sums for the whole range, so E and c are read from global
-// memory once per CTA: chunks of kBgS sites stream into shared memory by
-// cp.async (E) and register loads (c, converted on the way), double
-// buffered.  Each term costs 12 FP32 instructions (the exact hi * hi product
-// and a two-sum into an unnormalised pair) against two FMAs on the FP64 pipe,
-// which runs at 1/64 of the FP32 rate.  The ranges' sums are added to the
-// block in double (FP64 atomics, into a block zeroed first).
+// c converted to float pairs as it is staged.  A CTA takes FB fields (FB a
+// power of two covering the batch, at most 16; the fast thread index),
+// kBgE = 16 kBgJ block entries (entry jq + 16 r for thread row jq) and one
+// range of the sites (grid.x); its 256 / (16 FB) = SP thread groups split
+// each staged chunk's sites, so small batches keep every thread busy.  Every
+// thread owns its 2 kBgJ (field, entry) sums for the whole range, so E and c
+// are read from global memory once per CTA: chunks of kBgS sites stream
+// into shared memory by cp.async (E) and register loads (c, converted on the
+// way), double buffered.  Each term costs 12 FP32 instructions (the exact
+// hi * hi product and a two-sum into an unnormalised pair) against two FMAs
+// on the FP64 pipe, which runs at 1/64 of the FP32 rate.  The SP groups'
+// sums meet in shared memory, and the ranges' sums are added to the block
+// in double (FP64 atomics, into a block zeroed first).
 constexpr int kBgS = 32;     // sites per staged chunk
 constexpr int kBgJ = 2;      // entries per thread
 constexpr int kBgE = 16 * kBgJ;
@@ -876,22 +879,26 @@ __global__ void zero_blk_group_kernel(const __grid_constant__ Group<BlockGemmDfS
     sl.blk[t] = make_double2(0.0, 0.0);
 }
 
+template <int FB>
 __global__ void __launch_bounds__(256)
 block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
+  constexpr int SP = 256 / (16 * FB);            // site groups
+  constexpr int NC = kBgS * FB;                  // coefficients per chunk
+  constexpr int CR = (NC + 255) / 256;           // ... per thread
   __shared__ __align__(16) float4 es[2][kBgS][kBgE];
-  __shared__ __align__(16) float2 cs[2][kBgS][16];
+  __shared__ __align__(16) float2 cs[2][kBgS][FB];
   int ks = 0;
   while (ks + 1 < g.n && (int)blockIdx.y >= g.start[ks + 1]) ++ks;
   const BlockGemmDfSlot& sl = g.slot[ks];
   const int n = sl.n, B = sl.B, nblk = sl.nblk;
   const int ntj = (nblk + kBgE - 1) / kBgE;
   const int tile = blockIdx.y - g.start[ks];
-  const int fb = (tile / ntj) * 16, jb = (tile % ntj) * kBgE;
+  const int fb = (tile / ntj) * FB, jb = (tile % ntj) * kBgE;
   const int chunk = (n + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
   if (i0 >= i1) return;                                   // uniform over the CTA
   const int nch = (i1 - i0 + kBgS - 1) / kBgS;
-  const int t = threadIdx.x, fq = t & 15, jq = t >> 4;
+  const int t = threadIdx.x, fq = t % FB, jq = (t / FB) % 16, sp = t / (16 * FB);
   const float4* __restrict__ efac = sl.efac;
   const double* __restrict__ c = sl.c;
   // staging maps (consecutive threads on consecutive addresses): E copy
@@ -908,22 +915,22 @@ block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  double cv[kBgS * 16 / 256];
+  double cv[CR];
   auto load_c = [&](int k) {
     const int ib = i0 + k * kBgS;
 #pragma unroll
-    for (int r = 0; r < kBgS * 16 / 256; ++r) {
+    for (int r = 0; r < CR; ++r) {
       const int q = t + 256 * r, f = q / kBgS, s = q - f * kBgS;
       const int i = ib + s;
-      cv[r] = (i < i1 && fb + f < B) ? c[(size_t)(fb + f) * n + i] : 0.0;
+      cv[r] = (q < NC && i < i1 && fb + f < B) ? c[(size_t)(fb + f) * n + i] : 0.0;
     }
   };
   auto store_c = [&](int buf) {
 #pragma unroll
-    for (int r = 0; r < kBgS * 16 / 256; ++r) {
+    for (int r = 0; r < CR; ++r) {
       const int q = t + 256 * r, f = q / kBgS, s = q - f * kBgS;
       const float h = (float)cv[r];
-      cs[buf][s][f] = make_float2(h, (float)(cv[r] - (double)h));
+      if (q < NC) cs[buf][s][f] = make_float2(h, (float)(cv[r] - (double)h));
     }
   };
   dfacc acc[kBgJ][2];
@@ -942,7 +949,7 @@ block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
     }
     __syncthreads();                                      // chunk k in shared memory
 #pragma unroll 4
-    for (int s = 0; s < kBgS; ++s) {
+    for (int s = sp; s < kBgS; s += SP) {
       const float2 cw = cs[buf][s][fq];
       const dfl cc = {cw.x, cw.y};
 #pragma unroll
@@ -955,6 +962,32 @@ block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
     if (more) store_c(buf ^ 1);
     __syncthreads();                                      // buffer buf free again
   }
+  // the SP groups' sums meet in shared memory (the E buffers are free now)
+  dfl v[kBgJ][2];
+#pragma unroll
+  for (int r = 0; r < kBgJ; ++r) {
+    v[r][0] = dfacc_value(acc[r][0]);
+    v[r][1] = dfacc_value(acc[r][1]);
+  }
+  if constexpr (SP > 1) {
+    float4* red = &es[0][0][0];                           // [SP - 1][16 FB][kBgJ]
+    if (sp > 0) {
+#pragma unroll
+      for (int r = 0; r < kBgJ; ++r)
+        red[((sp - 1) * 16 * FB + (t % (16 * FB))) * kBgJ + r] =
+            make_float4(v[r][0].hi, v[r][0].lo, v[r][1].hi, v[r][1].lo);
+    }
+    __syncthreads();
+    if (sp > 0) return;
+#pragma unroll
+    for (int q = 1; q < SP; ++q)
+#pragma unroll
+      for (int r = 0; r < kBgJ; ++r) {
+        const float4 w = red[((q - 1) * 16 * FB + t) * kBgJ + r];
+        v[r][0] = df_add(v[r][0], {w.x, w.y});
+        v[r][1] = df_add(v[r][1], {w.z, w.w});
+      }
+  }
   const int f = fb + fq;
   if (f >= B) return;
 #pragma unroll
@@ -962,25 +995,30 @@ block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
     const int j = jb + jq + 16 * r;
     if (j < nblk) {
       double* dst = reinterpret_cast<double*>(sl.blk + (size_t)f * nblk + j);
-      atomicAdd(dst, df_double(dfacc_value(acc[r][0])));
-      atomicAdd(dst + 1, df_double(dfacc_value(acc[r][1])));
+      atomicAdd(dst, df_double(v[r][0]));
+      atomicAdd(dst + 1, df_double(v[r][1]));
     }
   }
 }
 
 cudaError_t launch_block_gemm_df_group(Group<BlockGemmDfSlot>& g, cudaStream_t s) {
   int nmax = 0, nbmax = 0, maxb = 0;
-  g.start[0] = 0;
   for (int k = 0; k < g.n; ++k) {
     BlockGemmDfSlot& sl = g.slot[k];
     if (sl.nblk <= 0 || sl.n <= 0) sl.B = 0;
-    const int tiles = sl.B > 0 ? ((sl.B + 15) / 16) * ((sl.nblk + kBgE - 1) / kBgE) : 0;
-    g.start[k + 1] = g.start[k] + tiles;
     nmax = sl.n > nmax ? sl.n : nmax;
     nbmax = sl.B * sl.nblk > nbmax ? sl.B * sl.nblk : nbmax;
     maxb = sl.B > maxb ? sl.B : maxb;
   }
-  if (g.n == 0 || maxb == 0 || g.start[g.n] == 0) return cudaSuccess;
+  if (g.n == 0 || maxb == 0) return cudaSuccess;
+  int FB = 1;
+  while (FB < maxb && FB < 16) FB *= 2;
+  g.start[0] = 0;
+  for (int k = 0; k < g.n; ++k) {
+    const BlockGemmDfSlot& sl = g.slot[k];
+    const int tiles = sl.B > 0 ? ((sl.B + FB - 1) / FB) * ((sl.nblk + kBgE - 1) / kBgE) : 0;
+    g.start[k + 1] = g.start[k] + tiles;
+  }
   const int zb = (nbmax + 255) / 256;
   zero_blk_group_kernel<<<dim3(zb > 64 ? 64 : zb, g.n), 256, 0, s>>>(g);
   // site ranges: about kBgCtas CTAs in all, at least two chunks per range
@@ -988,7 +1026,14 @@ cudaError_t launch_block_gemm_df_group(Group<BlockGemmDfSlot>& g, cudaStream_t s
   const int most = (nmax + 2 * kBgS - 1) / (2 * kBgS);
   ranges = ranges > most ? most : ranges;
   ranges = ranges < 1 ? 1 : ranges;
-  block_gemm_df_kernel<<<dim3(ranges, g.start[g.n]), 256, 0, s>>>(g);
+  const dim3 grid(ranges, g.start[g.n]);
+  switch (FB) {
+    case 1: block_gemm_df_kernel<1><<<grid, 256, 0, s>>>(g); break;
+    case 2: block_gemm_df_kernel<2><<<grid, 256, 0, s>>>(g); break;
+    case 4: block_gemm_df_kernel<4><<<grid, 256, 0, s>>>(g); break;
+    case 8: block_gemm_df_kernel<8><<<grid, 256, 0, s>>>(g); break;
+    default: block_gemm_df_kernel<16><<<grid, 256, 0, s>>>(g); break;
+  }
   return cudaGetLastError();
 }
 
