@@ -466,9 +466,210 @@ cudaError_t launch_split_pairs(const double* src, size_t count, float2* dst, cud
   return cudaGetLastError();
 }
 
+// ------------------------------------- many right-hand sides, tiled --
+// RK_FP32 plans with B >= kTileRhs right-hand sides (conditional simulation:
+// one per realisation) solve with x held as double-float pairs in place:
+// each double of x becomes its (hi, lo) float pair in the same 8 bytes first
+// and is formed back at the end, so no FP64 instruction runs in the block
+// steps.  A block step is the diagonal product x_k <- L_kk^{-1} x_k (L_kk^{-T}
+// backward) with the inverted diagonal block (solve_diag_pairs_kernel), then
+// the trailing update tiled like a GEMM (solve_update_tile_kernel): a CTA
+// takes 16 RT rows by kTileRhs right-hand sides, stages the block's columns of
+// L for its rows and the block's x for its right-hand sides in shared memory
+// once, and each thread keeps RT x 4 double-float sums; a factor element is
+// read from L2 once per kTileRhs right-hand sides instead of once per SF.
+constexpr int kTileRhs = 64;
+constexpr int kXsLd = kTileRhs + 2;    // padded row of the staged x block (float2)
+
+__device__ __forceinline__ unsigned long long pair_bits(dfl v) {
+  return ((unsigned long long)__float_as_uint(v.lo) << 32) | __float_as_uint(v.hi);
+}
+
+__global__ void x_to_pairs_kernel(double* x, size_t count) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[t];
+    reinterpret_cast<unsigned long long*>(x)[t] = pair_bits(df_make(v));
+  }
+}
+
+__global__ void x_from_pairs_kernel(double* x, size_t count) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = reinterpret_cast<const unsigned long long*>(x)[t];
+    const dfl v = {__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32))};
+    x[t] = df_double(v);
+  }
+}
+
+// x_k <- T x_k for the block at k (T = L_kk^{-1} forward, L_kk^{-T}
+// backward, from adf's inverted diagonal block), x as float pairs: kPairRhs
+// right-hand sides per CTA, thread (row r, right-hand side) summing its up to
+// 64 terms into two unnormalised pair sums; the block and the right-hand
+// sides are staged with all of a thread's loads issued first.
+constexpr int kPairRhs = 8;
+
+template <bool FWD>
+__global__ void __launch_bounds__(SB * kPairRhs)
+solve_diag_pairs_kernel(const float2* __restrict__ adf, int n, int k, float2* xp, int B) {
+  __shared__ float2 Ts[SB * SB];            // Ts[c * SB + r] = adf[(k + c) n + k + r]
+  __shared__ float2 xs[kPairRhs][SB];
+  constexpr int NT = SB * SB / (SB * kPairRhs);
+  const int nb = min(SB, n - k);
+  {
+    float2 v[NT];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      const int q = threadIdx.x + u * SB * kPairRhs, c = q / SB, r = q % SB;
+      v[u] = (r < nb && c < nb) ? adf[(size_t)(k + c) * n + k + r] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u) Ts[threadIdx.x + u * SB * kPairRhs] = v[u];
+  }
+  const int r = threadIdx.x % SB, fl = threadIdx.x / SB;
+  const int f = blockIdx.x * kPairRhs + fl;
+  const bool live = f < B;
+  float2* xf = xp + (size_t)(live ? f : 0) * n + k;
+  xs[fl][r] = live && r < nb ? xf[r] : make_float2(0.f, 0.f);
+  __syncthreads();
+  if (!live || r >= nb) return;
+  dfacc acc0, acc1;
+  const int c0 = FWD ? 0 : r, c1 = FWD ? r + 1 : nb;     // L^{-1}: c <= r; L^{-T}: c >= r
+  int c = c0;
+#pragma unroll 4
+  for (; c + 1 < c1; c += 2) {
+    const float2 l0 = Ts[c * SB + r], l1 = Ts[(c + 1) * SB + r];
+    const float2 x0 = xs[fl][c], x1 = xs[fl][c + 1];
+    dfacc_fma(acc0, {l0.x, l0.y}, {x0.x, x0.y});
+    dfacc_fma(acc1, {l1.x, l1.y}, {x1.x, x1.y});
+  }
+  if (c < c1) {
+    const float2 l0 = Ts[c * SB + r];
+    const float2 x0 = xs[fl][c];
+    dfacc_fma(acc0, {l0.x, l0.y}, {x0.x, x0.y});
+  }
+  const dfl v = df_add(dfacc_value(acc0), dfacc_value(acc1));
+  xf[r] = make_float2(v.hi, v.lo);
+}
+
+// rows below the block (forward) or above it (backward) lose L(r, k + c)
+// x_{k + c} (forward) or L(k + c, r) x_{k + c} (backward); both read
+// adf[(k + c) n + r] (the mirrored factor)
+template <bool FWD, int RT>
+__global__ void __launch_bounds__(256)
+solve_update_tile_kernel(const float2* __restrict__ adf, int n, int k, float2* __restrict__ xp,
+                         int B) {
+  constexpr int RB = 16 * RT;
+  extern __shared__ __align__(16) float2 tile_sm[];
+  float2* Xs = tile_sm;                    // [SB][kXsLd]: Xs[c][f]
+  float2* Ls = tile_sm + SB * kXsLd;       // [SB][RB]: Ls[c][rr]
+  const int nb = min(SB, n - k);
+  const int rbase = FWD ? k + nb : 0, rend = FWD ? n : k;
+  const int r0 = rbase + blockIdx.x * RB;
+  const int f0 = blockIdx.y * kTileRhs;
+  const int t = threadIdx.x;
+  // every load of a staging round issued before its stores (one latency)
+  constexpr int NX = SB * kTileRhs / 256, NL = SB * RB / 256;
+  {
+    float2 v[NX];
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {                     // along each field's row of x
+      const int q = t + 256 * u, f = q / SB, c = q - f * SB;
+      v[u] = (c < nb && f0 + f < B) ? xp[(size_t)(f0 + f) * n + k + c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+      const int q = t + 256 * u, f = q / SB, c = q - f * SB;
+      Xs[c * kXsLd + f] = v[u];
+    }
+  }
+  {
+    float2 v[NL];
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {                     // along each column of L
+      const int q = t + 256 * u, c = q / RB, rr = q - c * RB;
+      const int r = r0 + rr;
+      v[u] = (c < nb && r < rend) ? adf[(size_t)(k + c) * n + r] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+      const int q = t + 256 * u, c = q / RB, rr = q - c * RB;
+      Ls[c * RB + rr] = v[u];
+    }
+  }
+  __syncthreads();
+  const int tx = t & 15, ty = t >> 4;       // rows r0 + tx + 16 i, fields f0 + 4 ty + j
+  dfacc acc[RT][4];
+#pragma unroll 4
+  for (int c = 0; c < nb; ++c) {
+    const float4 xa = *reinterpret_cast<const float4*>(Xs + c * kXsLd + 4 * ty);
+    const float4 xb = *reinterpret_cast<const float4*>(Xs + c * kXsLd + 4 * ty + 2);
+    const dfl xv[4] = {{xa.x, xa.y}, {xa.z, xa.w}, {xb.x, xb.y}, {xb.z, xb.w}};
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+      const float2 l2 = Ls[c * RB + tx + 16 * i];
+      const dfl l = {l2.x, l2.y};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dfacc_fma(acc[i][j], l, xv[j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RT; ++i) {
+    const int r = r0 + tx + 16 * i;
+    if (r >= rend) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int f = f0 + 4 * ty + j;
+      if (f >= B) continue;
+      float2* p = xp + (size_t)f * n + r;
+      const float2 o = *p;
+      const dfl u = df_add({o.x, o.y}, df_neg(dfacc_value(acc[i][j])));
+      *p = make_float2(u.hi, u.lo);
+    }
+  }
+}
+
+template <int RT>
+static cudaError_t chol_solve_tiled_rt(const float2* adf, int n, double* x, int B, cudaStream_t s) {
+  constexpr int RB = 16 * RT;
+  const size_t sm = sizeof(float2) * ((size_t)SB * kXsLd + (size_t)SB * RB);
+  static int smem_f = 0, smem_b = 0;
+  cudaError_t e = ensure_smem(solve_update_tile_kernel<true, RT>, sm, smem_f);
+  if (e == cudaSuccess) e = ensure_smem(solve_update_tile_kernel<false, RT>, sm, smem_b);
+  if (e != cudaSuccess) return e;
+  const size_t count = (size_t)B * n;
+  const unsigned cb = (unsigned)((count + 255) / 256 > 4096 ? 4096 : (count + 255) / 256);
+  float2* xp = reinterpret_cast<float2*>(x);
+  const int igrid = (B + kPairRhs - 1) / kPairRhs, fgrid = (B + kTileRhs - 1) / kTileRhs;
+  x_to_pairs_kernel<<<cb, 256, 0, s>>>(x, count);
+  for (int k = 0; k < n; k += SB) {
+    const int nb = n - k < SB ? n - k : SB;
+    solve_diag_pairs_kernel<true><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
+    const int rest = n - k - nb;
+    if (rest > 0)
+      solve_update_tile_kernel<true, RT>
+          <<<dim3((rest + RB - 1) / RB, fgrid), 256, sm, s>>>(adf, n, k, xp, B);
+  }
+  for (int k = ((n - 1) / SB) * SB; k >= 0; k -= SB) {
+    solve_diag_pairs_kernel<false><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
+    if (k > 0)
+      solve_update_tile_kernel<false, RT>
+          <<<dim3((k + RB - 1) / RB, fgrid), 256, sm, s>>>(adf, n, k, xp, B);
+  }
+  x_from_pairs_kernel<<<cb, 256, 0, s>>>(x, count);
+  return cudaGetLastError();
+}
+
+// RT = 2 (32 rows by 64 right-hand sides per CTA): at n = 5000, 256
+// right-hand sides, 5.5 ms per solve against 6.2 ms with RT = 4
+static cudaError_t chol_solve_tiled(const float2* adf, int n, double* x, int B, cudaStream_t s) {
+  return chol_solve_tiled_rt<2>(adf, n, x, B, s);
+}
+
 cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
                        const float2* adf) {
   if (n <= 0 || B <= 0) return cudaSuccess;
+  if (adf && B >= kTileRhs) return chol_solve_tiled(adf, n, x, B, s);
   const int dgrid = (B + 3) / 4;              // four warps (right-hand sides) per CTA
   const int igrid = (B + kDiagRhs - 1) / kDiagRhs;
   const int fblocks = (B + SF - 1) / SF;
