@@ -433,6 +433,8 @@ cudaError_t launch_trend(const double* Xg, const double* beta, size_t N, int q, 
 cudaError_t launch_split_pairs(const double* src, size_t count, float2* dst, cudaStream_t s);
 
 // conditional simulation
+// uploads the stage twiddles of the register CE passes for these lengths
+cudaError_t ce_tables_setup(int qx, int qy);
 template <typename T>
 cudaError_t launch_ce_cols(const T* sqrtlam, int qx, int qy, unsigned long long seed, int pair0,
                            int npairs, C<T>* tq, int ldq, int nkeep, const FftPlan& fpy,

@@ -13,6 +13,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "fftn.cuh"
+#include "fftr.cuh"
 
 namespace rk {
 
@@ -278,6 +279,191 @@ ce_rows_n(const C<T>* __restrict__ tq, int ldq, int nrows, T* __restrict__ fu, i
   }
 }
 
+// ------------------------------------- CE passes, register transforms --
+// The same two passes with the register-resident transform of fftr.cuh
+// (THR = N / E threads per transform, E elements each; V transforms per CTA)
+// for the embedding lengths of the conditional-simulation workloads.  The
+// column pass draws a column's noise into its exchange buffer (four
+// consecutive elements per generator call, as above), takes its registers
+// from there and transforms; the row pass stages V rows of the column
+// spectra (rows fastest, odd stride) with all of a thread's loads issued
+// first, then transforms in registers.
+template <int N> struct CeR;   // (E, V, CTAs per SM asked of the compiler) per length
+template <> struct CeR<1944> { static constexpr int E = 18, V = 2, MB = 4; };
+template <> struct CeR<864> { static constexpr int E = 12, V = 4, MB = 3; };
+template <> struct CeR<384> { static constexpr int E = 12, V = 8, MB = 3; };
+#define RK_CER_SIZES(X) X(1944) X(864) X(384)
+
+template <typename T, int N>
+__global__ void __launch_bounds__(CeR<N>::V * RPlan<N, CeR<N>::E>::THR, CeR<N>::MB)
+ce_cols_r(const T* __restrict__ sqrtlam, int qx, const PhiloxKeys keys, int pair0,
+          C<T>* __restrict__ tq, int ldq, int nkeep, const C<T>* __restrict__ stw) {
+  constexpr int E = CeR<N>::E, V = CeR<N>::V;
+  using P = RPlan<N, E>;
+  constexpr int THR = P::THR, NP = P::NPAD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int v = threadIdx.x / THR, t = threadIdx.x - v * THR;
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw) + v * NP;
+  const int kx = blockIdx.x * V + v;
+  const int pair = pair0 + blockIdx.y;
+  const bool valid = kx < qx;
+  if (valid) {
+    const int kxh = kx < qx - kx ? kx : qx - kx;
+    const T* sl = sqrtlam + (size_t)kxh * N;
+    const uint64_t kbase = (uint64_t)kx * N;
+    // a fixed count of generator calls per thread, unrolled in pairs so
+    // that two independent multiply chains interleave
+    constexpr int NI = (N + 3 + 4 * THR - 1) / (4 * THR);
+#pragma unroll 2
+    for (int it = 0; it < NI; ++it) {
+      const uint64_t kk = (kbase & ~3ull) + 4ull * (t + (uint64_t)THR * it);
+      if (kk >= kbase + N) continue;
+      uint64_t c[4] = {kk >> 2, (uint64_t)pair, 1ull, 0ull};
+      philox4x64_10(c, keys);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const uint64_t k = kk + h;
+        if (k < kbase || k >= kbase + N) continue;
+        const int ky = (int)(k - kbase);
+        T xi, eta;
+        box_muller<T>(c[h], xi, eta);
+        const T sv = sl[ky];
+        buf[P::pad(ky)] = mk<T>(sv * xi, sv * eta);
+      }
+    }
+  }
+  __syncthreads();
+  C<T> x[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) x[r] = valid ? buf[P::pad(t + THR * r)] : mk<T>(T(0), T(0));
+  // rfft's first exchange starts with a barrier, so buf may be reused
+  rfft<T, N, E, +1, 0>(x, buf, stw, t);
+  if (valid) {
+    C<T>* dst = tq + ((size_t)blockIdx.y * qx + kx) * ldq;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int e = t + THR * P::out_m(q);
+      if (e < nkeep) dst[e] = x[q];
+    }
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(CeR<N>::V * RPlan<N, CeR<N>::E>::THR)
+ce_rows_r(const C<T>* __restrict__ tq, int ldq, int nrows, T* __restrict__ fu, int p1x,
+          long long t0, int treal, int pair0, const C<T>* __restrict__ stw) {
+  constexpr int E = CeR<N>::E, V = CeR<N>::V;
+  using P = RPlan<N, E>;
+  constexpr int THR = P::THR, NP = P::NPAD, SLD = V + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+  const int r0 = blockIdx.x * V;
+  const int pl = blockIdx.y;
+  const C<T>* src = tq + (size_t)pl * N * ldq;
+  // rows r0 .. r0 + V - 1: element (kx, row) at kx ldq + row, staged at
+  // kx SLD + (row - r0); all of a thread's loads issued before its stores
+  constexpr int NL = (N * V + V * THR - 1) / (V * THR);
+  {
+    C<T> ld[NL];
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+      const int idx = threadIdx.x + u * V * THR;
+      const int kx = idx / V, vv = idx - kx * V;
+      ld[u] = idx < N * V && r0 + vv < nrows ? src[(size_t)kx * ldq + r0 + vv]
+                                             : mk<T>(T(0), T(0));
+    }
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+      const int idx = threadIdx.x + u * V * THR;
+      const int kx = idx / V, vv = idx - kx * V;
+      if (idx < N * V) sm[kx * SLD + vv] = ld[u];
+    }
+  }
+  __syncthreads();
+  const int v = threadIdx.x / THR, t = threadIdx.x - v * THR;
+  C<T> x[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) x[r] = sm[(t + THR * r) * SLD + v];
+  rfft<T, N, E, +1, 0>(x, sm + v * NP, stw, t);   // its first exchange starts with a barrier
+  const int row = r0 + v;
+  if (row >= nrows) return;
+  const long long pair = pair0 + pl;
+#pragma unroll
+  for (int part = 0; part < 2; ++part) {
+    const long long j = 2 * pair + part - t0;
+    if (j < 0 || j >= treal) continue;
+    T* out = fu + ((size_t)j * nrows + row) * p1x;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int px = t + THR * P::out_m(q);
+      if (px < p1x) out[px] = part ? x[q].y : x[q].x;
+    }
+  }
+}
+
+template <typename T, int N>
+static size_t ce_cols_r_smem() {
+  return sizeof(C<T>) * CeR<N>::V * RPlan<N, CeR<N>::E>::NPAD;
+}
+template <typename T, int N>
+static size_t ce_rows_r_smem() {
+  const size_t a = (size_t)CeR<N>::V * RPlan<N, CeR<N>::E>::NPAD;
+  const size_t b = (size_t)N * (CeR<N>::V + 1);
+  return sizeof(C<T>) * (a > b ? a : b);
+}
+
+template <typename T, int N>
+static cudaError_t go_ce_cols_r(const T* sqrtlam, int qx, unsigned long long seed, int pair0,
+                                int npairs, C<T>* tq, int ldq, int nkeep, cudaStream_t s) {
+  constexpr int E = CeR<N>::E, V = CeR<N>::V, THR = RPlan<N, E>::THR;
+  const C<T>* stw = RTable<T, N, E>::get();
+  if (!stw) return cudaErrorNotReady;
+  const size_t sm = ce_cols_r_smem<T, N>();
+  static int smem_set = 0;
+  auto kern = ce_cols_r<T, N>;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((qx + V - 1) / V, npairs), V * THR, sm, s>>>(sqrtlam, qx, philox_keys(seed), pair0,
+                                                            tq, ldq, nkeep, stw);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t go_ce_rows_r(const C<T>* tq, int ldq, int nrows, T* fu, int p1x,
+                                long long t0, int treal, int pair0, int npairs, cudaStream_t s) {
+  constexpr int E = CeR<N>::E, V = CeR<N>::V, THR = RPlan<N, E>::THR;
+  const C<T>* stw = RTable<T, N, E>::get();
+  if (!stw) return cudaErrorNotReady;
+  const size_t sm = ce_rows_r_smem<T, N>();
+  static int smem_set = 0;
+  auto kern = ce_rows_r<T, N>;
+  cudaError_t e = ensure_smem(kern, sm, smem_set);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((nrows + V - 1) / V, npairs), V * THR, sm, s>>>(tq, ldq, nrows, fu, p1x, t0, treal,
+                                                               pair0, stw);
+  return cudaGetLastError();
+}
+
+// The register passes' stage twiddles for an embedding of qx x qy (FP32),
+// uploaded to the current device when a length has such a pass
+cudaError_t ce_tables_setup(int qx, int qy) {
+  cudaError_t e = cudaSuccess;
+  for (int q : {qx, qy}) {
+    switch (q) {
+#define RK_CASE(NN)                                                  \
+  case NN: {                                                         \
+    const C<float>* p = nullptr;                                     \
+    if (e == cudaSuccess) e = RTable<float, NN, CeR<NN>::E>::ensure(&p); \
+    break;                                                           \
+  }
+      RK_CER_SIZES(RK_CASE)
+#undef RK_CASE
+      default: break;
+    }
+  }
+  return e;
+}
+
 #define RK_CE_SIZES(X) X(1152) X(1296) X(1536) X(1728) X(1944) X(2304)
 
 template <typename T, int N>
@@ -313,6 +499,18 @@ cudaError_t launch_ce_cols(const T* sqrtlam, int qx, int qy, unsigned long long 
                            int npairs, C<T>* tq, int ldq, int nkeep, const FftPlan& fpy,
                            const C<T>* twy, cudaStream_t s) {
   if (sizeof(T) == sizeof(float) && !fft_generic_only()) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+      switch (qy) {
+#define RK_CASE(NN)                                                                          \
+  case NN:                                                                                   \
+    if (RTable<T, NN, CeR<NN>::E>::get())                                                   \
+      return go_ce_cols_r<T, NN>(sqrtlam, qx, seed, pair0, npairs, tq, ldq, nkeep, s);     \
+    break;
+        RK_CER_SIZES(RK_CASE)
+#undef RK_CASE
+        default: break;
+      }
+    }
     switch (qy) {
 #define RK_CASE(NN) \
   case NN: return go_ce_cols<T, NN>(sqrtlam, qx, seed, pair0, npairs, tq, ldq, nkeep, twy, s);
@@ -336,6 +534,18 @@ cudaError_t launch_ce_rows(const C<T>* tq, int qx, int ldq, int nrows, T* fu, in
                            long long t0, int treal, int pair0, int npairs, const FftPlan& fpx,
                            const C<T>* twx, cudaStream_t s) {
   if (sizeof(T) == sizeof(float) && !fft_generic_only()) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+      switch (qx) {
+#define RK_CASE(NN)                                                                          \
+  case NN:                                                                                   \
+    if (RTable<T, NN, CeR<NN>::E>::get())                                                   \
+      return go_ce_rows_r<T, NN>(tq, ldq, nrows, fu, p1x, t0, treal, pair0, npairs, s);    \
+    break;
+        RK_CER_SIZES(RK_CASE)
+#undef RK_CASE
+        default: break;
+      }
+    }
     switch (qx) {
 #define RK_CASE(NN)                                                                         \
   case NN:                                                                                  \

@@ -325,41 +325,6 @@ void hfor(F&& f) {
   hfor_impl(std::make_integer_sequence<int, N>{}, f);
 }
 
-// per-device stage-twiddle tables of every (T, N, E) in use
-constexpr int kMaxDev = 64;
-template <typename T, int N, int E>
-struct RTable {
-  static C<T>* dev[kMaxDev];
-  static cudaError_t ensure(const C<T>** out) {
-    int d = 0;
-    cudaError_t e = cudaGetDevice(&d);
-    if (e != cudaSuccess) return e;
-    if (d < 0 || d >= kMaxDev) return cudaErrorInvalidDevice;
-    if (!dev[d]) {
-      constexpr int n = RPlan<N, E>::table_size() > 0 ? RPlan<N, E>::table_size() : 1;
-      std::vector<double> re(n, 1.0), im(n, 0.0);
-      rplan_twiddles<N, E>(re.data(), im.data());
-      std::vector<C<T>> h(n);
-      for (int i = 0; i < n; ++i) h[i] = mk<T>((T)re[i], (T)im[i]);
-      C<T>* p = nullptr;
-      e = cudaMalloc((void**)&p, sizeof(C<T>) * n);
-      if (e != cudaSuccess) return e;
-      e = cudaMemcpy(p, h.data(), sizeof(C<T>) * n, cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) { cudaFree(p); return e; }
-      dev[d] = p;
-    }
-    *out = dev[d];
-    return cudaSuccess;
-  }
-  static const C<T>* get() {
-    int d = 0;
-    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDev) return nullptr;
-    return dev[d];
-  }
-};
-template <typename T, int N, int E>
-C<T>* RTable<T, N, E>::dev[kMaxDev] = {nullptr};
-
 // raises a kernel's dynamic shared-memory limit once: Tag is the kernel's
 // own launcher, so every instantiation keeps its own record (all variants of
 // a pass share one function type)

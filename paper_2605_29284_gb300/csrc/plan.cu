@@ -615,6 +615,7 @@ rk_status ensure_ce(rk_plan* p) {
       RK_CU(cudaMemcpy(p->ce_sqrt32, s32.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
       p->qx = qx; p->qy = qy; p->fqx = fx; p->fqy = fy;
       p->tw64qx = t64x; p->tw64qy = t64y; p->tw32qx = t32x; p->tw32qy = t32y;
+      RK_CU(ce_tables_setup(qx, qy));
       return RK_OK;
     }
     cudaFree(t64x); cudaFree(t64y); cudaFree(t32x); cudaFree(t32y);
