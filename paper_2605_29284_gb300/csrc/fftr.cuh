@@ -250,7 +250,27 @@ struct RPlan {
     if constexpr (PSH >= 30) return e;          // odd N: no pad slots
     else return e + (e >> PSH);
   }
-  static constexpr int NPAD = ((N - 1) + ((N - 1) >> PSH) + 1) | 1;
+  // Odd N: the exchange before stage s (1 < span(s - 1) < 16) leaves a gap
+  // of XD(s) elements after every span(s): the autosort stores write blocks
+  // of span(s - 1) consecutive elements span(s) apart, and the gap shifts
+  // each block onto the 8-byte banks the next lanes would otherwise share
+  // (XD = span(s - 1) - span(s) mod 16).  The stage's loads, j + (N / R) r,
+  // cross such gaps at a fixed count per r.
+  static constexpr int XD(int s) {
+    if (PSH < 30 || s < 1 || s >= S) return 0;
+    const int nsp = span(s - 1);
+    if (nsp <= 1 || nsp >= 16) return 0;
+    return ((nsp - span(s)) % 16 + 16) % 16;
+  }
+  static constexpr int npad() {
+    int m = (N - 1) + ((N - 1) >> PSH) + 1;
+    for (int s = 1; s < S; ++s) {
+      const int e = (N - 1) + XD(s) * ((N - 1) / span(s)) + 1;
+      m = e > m ? e : m;
+    }
+    return m | 1;
+  }
+  static constexpr int NPAD = npad();
   // element held by register q (q = i R + r) after the last stage
   static constexpr int RL = radix(S - 1), ITL = E / RL;
   static constexpr int out_m(int q) { return q / RL + ITL * (q % RL); }
@@ -372,21 +392,35 @@ __device__ __forceinline__ void rfft(C<T> (&v)[E], C<T>* buf, const C<T>* __rest
     constexpr int Rp = P::radix(s - 1), NSp = P::span(s - 1), ITp = E / Rp;
     constexpr int R = P::radix(s), NS = P::span(s), IT = E / R, NB = N / R;
     constexpr int p = rp_ndig(R);
+    constexpr int xd = P::XD(s), SP = P::span(s);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < ITp; ++i) {
       const int j = t + P::THR * i;
       const int k = j % NSp;
-      const int base = (j - k) * Rp + k;
+      if constexpr (xd == 0) {
+        const int base = (j - k) * Rp + k;
 #pragma unroll
-      for (int r = 0; r < Rp; ++r) buf[P::pad(base + NSp * r)] = v[i * Rp + r];
+        for (int r = 0; r < Rp; ++r) buf[P::pad(base + NSp * r)] = v[i * Rp + r];
+      } else {
+        const int base = (j - k) * Rp + k + xd * (j / NSp);   // element base, block j / NSp
+#pragma unroll
+        for (int r = 0; r < Rp; ++r) buf[base + NSp * r] = v[i * Rp + r];
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
       const int j = t + P::THR * i;
+      if constexpr (xd == 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i * R + r] = buf[P::pad(j + NB * r)];
+        for (int r = 0; r < R; ++r) v[i * R + r] = buf[P::pad(j + NB * r)];
+      } else {
+        static_assert(NB % SP == 0, "stage loads step whole blocks");
+        const int base = j + xd * (j / SP);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i * R + r] = buf[base + (NB + xd * (NB / SP)) * r];
+      }
     }
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
