@@ -37,9 +37,9 @@ template <typename T> __device__ __forceinline__ C<T> cfma_r(C<T> a, T s, C<T> c
   return mk<T>(fma(a.x, s, c.x), fma(a.y, s, c.y));
 }
 
-// FP32 complex additions, subtractions and real scalings as packed f32x2
-// instructions (sm_100 family, PTX ISA 8.6): both components in one
-// instruction, each rounded exactly as the scalar operation would be.
+// Packed FP32 pairs (f2_*): the sm_100 family's add/sub/mul/fma.rn.f32x2
+// (PTX ISA 8.6), both components in one instruction, each rounded exactly as
+// the scalar operation would be; plain float operations in the host pass.
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
 #define RK_F32X2_OP(NAME, OPC)                                                        \
   __device__ __forceinline__ float2 NAME(float2 a, float2 b) {                        \
@@ -69,6 +69,14 @@ __device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
       : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
   return r;
 }
+#else
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+#endif
 template <> __device__ __forceinline__ float2 cadd<float>(float2 a, float2 b) { return f2_add(a, b); }
 template <> __device__ __forceinline__ float2 csub<float>(float2 a, float2 b) { return f2_sub(a, b); }
 template <> __device__ __forceinline__ float2 cscale<float>(float2 a, float s) {
@@ -77,7 +85,6 @@ template <> __device__ __forceinline__ float2 cscale<float>(float2 a, float s) {
 template <> __device__ __forceinline__ float2 cfma_r<float>(float2 a, float s, float2 c) {
   return f2_fma(a, make_float2(s, s), c);
 }
-#endif
 
 // Raises a kernel's dynamic shared-memory limit when a launch needs more than
 // any earlier launch (the attribute persists, so this is done once per size).

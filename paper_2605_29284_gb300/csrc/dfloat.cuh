@@ -9,6 +9,8 @@
 
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace rk {
 
 struct dfl {
@@ -141,9 +143,38 @@ __device__ __forceinline__ dfl df_exp_neg(dfl d) {
   return {e.hi * sc, e.lo * sc};
 }
 
+// Two unnormalised pair sums side by side, each component in one half of
+// float2 registers, for the packed FP32 instructions: the operations of
+// dfacc_fma on both components at once (12 instructions for the two).
+// c_k += a_k b_k for k = 0, 1 with a = ahi + alo, b = bhi + blo componentwise
+// and nahi = -ahi (formed once where a is reused): np = -fl(a b) exactly, the
+// product error a b - fl(a b) = fma(ahi, bhi, np), the two-sum of c.s and
+// -np, and the cross terms and errors into c.e.
+struct dfacc2 {
+  float2 s = {0.f, 0.f}, e = {0.f, 0.f};
+};
+__device__ __forceinline__ void dfacc2_fma(dfacc2& c, float2 ahi, float2 nahi, float2 alo,
+                                           float2 bhi, float2 blo) {
+  const float2 np = f2_mul(nahi, bhi);
+  float2 pe = f2_fma(ahi, bhi, np);
+  pe = f2_fma(alo, bhi, f2_fma(ahi, blo, pe));
+  const float2 s = f2_sub(c.s, np);                  // c.s + p
+  const float2 bb = f2_sub(s, c.s);
+  const float2 t = f2_sub(f2_sub(c.s, f2_sub(s, bb)), f2_add(np, bb));   // two-sum error
+  c.s = s;
+  c.e = f2_add(c.e, f2_add(t, pe));
+}
+__device__ __forceinline__ dfl dfacc2_x(const dfacc2& c) { return fast_two_sum(c.s.x, c.e.x); }
+__device__ __forceinline__ dfl dfacc2_y(const dfacc2& c) { return fast_two_sum(c.s.y, c.e.y); }
+
 // complex double-float: (re.hi, re.lo, im.hi, im.lo) in a float4
 __device__ __forceinline__ float4 cdf_pack(dfl re, dfl im) {
   return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+// the same as packed pairs: (re.hi, im.hi, re.lo, im.lo), the hi and lo
+// halves of a complex value each one float2 for the packed instructions
+__device__ __forceinline__ float4 cdf_pack_pairs(dfl re, dfl im) {
+  return make_float4(re.hi, im.hi, re.lo, im.lo);
 }
 
 }  // namespace rk

@@ -198,8 +198,22 @@ __device__ __forceinline__ void weights_cta_df(const WeightsSlot& sl, int cta, f
   const float2* __restrict__ kdf = sl.kn_df;
   const int n = sl.n, nx = sl.nx, ny = sl.ny, ntx = sl.ntx, nu_code = sl.nu_code;
   const double x0 = sl.x0, x1 = sl.x1, y0 = sl.y0, y1 = sl.y1, hx = sl.hx, hy = sl.hy;
-  for (int t = threadIdx.x; t < M * M; t += blockDim.x) Ls[t] = kdf[t];
-  for (int t = threadIdx.x; t < M; t += blockDim.x) Linv[t] = kdf[M * M + t];
+  {
+    // the factor (M^2 + M float pairs): all of a thread's loads issued first
+    constexpr int NLD = (M * M + M + kWeightsDfThreads - 1) / kWeightsDfThreads;
+    float2 v[NLD];
+#pragma unroll
+    for (int u = 0; u < NLD; ++u) {
+      const int t = threadIdx.x + u * kWeightsDfThreads;
+      v[u] = t < M * M + M ? kdf[t] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < NLD; ++u) {
+      const int t = threadIdx.x + u * kWeightsDfThreads;
+      if (t < M * M) Ls[t] = v[u];
+      else if (t < M * M + M) Linv[t - M * M] = v[u];
+    }
+  }
   // the boxes and offsets in double, one lane per site of the CTA in the
   // first warp: the FP64 pipe takes a warp instruction whatever its active
   // lanes, so the other warps issue none
@@ -644,7 +658,8 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
 // The forward block of RK_FP32 plans in double-float on the FP32 pipe: the
 // same two stages as block_factor_kernel, from the weights' float pairs and
 // double-float twiddles (re.hi, re.lo, im.hi, im.lo); E_i is stored site-major
-// (efac[i nblk + j]) as the same float pairs, for the double-float block GEMM.
+// (efac[i nblk + j]) as packed pairs (re.hi, im.hi, re.lo, im.lo), for the
+// double-float block GEMM.
 // The block only has to be far more accurate than the single-precision
 // transforms it corrects; double-float (about 2^-47 per operation) is, and
 // runs at 64x the FP64 rate.
@@ -725,8 +740,8 @@ __device__ __forceinline__ void block_factor_df_warp(const BlockFactorDfSlot& sl
     }
     const dfl A = dfacc_value(sa), Bs = dfacc_value(sb), Cs = dfacc_value(sc),
               D = dfacc_value(sd);
-    out[kx * bw + KY + ky] = cdf_pack(df_add(A, df_neg(Bs)), df_add(Cs, D));
-    if (ky > 0) out[kx * bw + KY - ky] = cdf_pack(df_add(A, Bs), df_add(D, df_neg(Cs)));
+    out[kx * bw + KY + ky] = cdf_pack_pairs(df_add(A, df_neg(Bs)), df_add(Cs, D));
+    if (ky > 0) out[kx * bw + KY - ky] = cdf_pack_pairs(df_add(A, Bs), df_add(D, df_neg(Cs)));
   }
 }
 
@@ -845,8 +860,9 @@ cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac
 }
 
 // The forward block of RK_FP32 plans in double-float: blk[f][j] =
-// sum_i c[f][i] E_i(j), E_i as float pairs (re.hi, re.lo, im.hi, im.lo) and
-// c converted to float pairs as it is staged.  A CTA takes FB fields (FB a
+// sum_i c[f][i] E_i(j), E_i as packed pairs (re.hi, im.hi, re.lo, im.lo) and
+// c converted to float pairs as it is staged (hi, hi, lo, lo), so the real
+// and imaginary sums of an entry run as one packed pair sum (dfacc2).  A CTA takes FB fields (FB a
 // power of two covering the batch, at most 16; the fast thread index),
 // kBgE = 16 kBgJ block entries (entry jq + 16 r for thread row jq) and one
 // range of the sites (grid.x); its 256 / (16 FB) = SP thread groups split
@@ -854,9 +870,9 @@ cudaError_t launch_block_gemm(const double* c, int B, int n, const double2* efac
 // thread owns its 2 kBgJ (field, entry) sums for the whole range, so E and c
 // are read from global memory once per CTA: chunks of kBgS sites stream
 // into shared memory by cp.async (E) and register loads (c, converted on the
-// way), double buffered.  Each term costs 12 FP32 instructions (the exact
-// hi * hi product and a two-sum into an unnormalised pair) against two FMAs
-// on the FP64 pipe, which runs at 1/64 of the FP32 rate.  The SP groups'
+// way), double buffered.  A complex term costs 12 packed FP32 instructions
+// (the exact hi * hi products and two-sums into unnormalised pairs) against
+// two FMAs on the FP64 pipe, which runs at 1/64 of the FP32 rate.  The SP groups'
 // sums meet in shared memory, and the ranges' sums are added to the block
 // in double (FP64 atomics, into a block zeroed first).
 constexpr int kBgS = 32;     // sites per staged chunk
@@ -886,7 +902,7 @@ block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
   constexpr int NC = kBgS * FB;                  // coefficients per chunk
   constexpr int CR = (NC + 255) / 256;           // ... per thread
   __shared__ __align__(16) float4 es[2][kBgS][kBgE];
-  __shared__ __align__(16) float2 cs[2][kBgS][FB];
+  __shared__ __align__(16) float4 cs[2][kBgS][FB];     // (hi, hi, lo, lo) of c
   int ks = 0;
   while (ks + 1 < g.n && (int)blockIdx.y >= g.start[ks + 1]) ++ks;
   const BlockGemmDfSlot& sl = g.slot[ks];
@@ -929,11 +945,11 @@ block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
 #pragma unroll
     for (int r = 0; r < CR; ++r) {
       const int q = t + 256 * r, f = q / kBgS, s = q - f * kBgS;
-      const float h = (float)cv[r];
-      if (q < NC) cs[buf][s][f] = make_float2(h, (float)(cv[r] - (double)h));
+      const float h = (float)cv[r], l = (float)(cv[r] - (double)h);
+      if (q < NC) cs[buf][s][f] = make_float4(h, h, l, l);
     }
   };
-  dfacc acc[kBgJ][2];
+  dfacc2 acc[kBgJ];                              // (re, im) of each entry
   stage_e(0, 0);
   load_c(0);
   store_c(0);
@@ -950,13 +966,13 @@ block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
     __syncthreads();                                      // chunk k in shared memory
 #pragma unroll 4
     for (int s = sp; s < kBgS; s += SP) {
-      const float2 cw = cs[buf][s][fq];
-      const dfl cc = {cw.x, cw.y};
+      const float4 cw = cs[buf][s][fq];
+      const float2 chi = make_float2(cw.x, cw.y), clo = make_float2(cw.z, cw.w);
+      const float2 nchi = f2_sub(make_float2(0.f, 0.f), chi);
 #pragma unroll
       for (int r = 0; r < kBgJ; ++r) {
         const float4 e = es[buf][s][jq + 16 * r];
-        dfacc_fma(acc[r][0], cc, {e.x, e.y});
-        dfacc_fma(acc[r][1], cc, {e.z, e.w});
+        dfacc2_fma(acc[r], chi, nchi, clo, make_float2(e.x, e.y), make_float2(e.z, e.w));
       }
     }
     if (more) store_c(buf ^ 1);
@@ -966,8 +982,8 @@ block_gemm_df_kernel(const __grid_constant__ Group<BlockGemmDfSlot> g) {
   dfl v[kBgJ][2];
 #pragma unroll
   for (int r = 0; r < kBgJ; ++r) {
-    v[r][0] = dfacc_value(acc[r][0]);
-    v[r][1] = dfacc_value(acc[r][1]);
+    v[r][0] = dfacc2_x(acc[r]);
+    v[r][1] = dfacc2_y(acc[r]);
   }
   if constexpr (SP > 1) {
     float4* red = &es[0][0][0];                           // [SP - 1][16 FB][kBgJ]
