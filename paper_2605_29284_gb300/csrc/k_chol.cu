@@ -468,18 +468,18 @@ cudaError_t launch_split_pairs(const double* src, size_t count, float2* dst, cud
 
 // ------------------------------------- many right-hand sides, tiled --
 // RK_FP32 plans with B >= kTileRhs right-hand sides (conditional simulation:
-// one per realisation) solve with x held as double-float pairs in place:
+// one per realisation; the adjoint: one per field) solve with x held as
+// double-float pairs in place:
 // each double of x becomes its (hi, lo) float pair in the same 8 bytes first
 // and is formed back at the end, so no FP64 instruction runs in the block
 // steps.  A block step is the diagonal product x_k <- L_kk^{-1} x_k (L_kk^{-T}
 // backward) with the inverted diagonal block (solve_diag_pairs_kernel), then
 // the trailing update tiled like a GEMM (solve_update_tile_kernel): a CTA
-// takes 16 RT rows by kTileRhs right-hand sides, stages the block's columns of
+// takes 16 RT rows by 16 or 64 right-hand sides, stages the block's columns of
 // L for its rows and the block's x for its right-hand sides in shared memory
 // once, and each thread keeps RT x 4 double-float sums; a factor element is
-// read from L2 once per kTileRhs right-hand sides instead of once per SF.
-constexpr int kTileRhs = 64;
-constexpr int kXsLd = kTileRhs + 2;    // padded row of the staged x block (float2)
+// read from L2 once per 16 or 64 right-hand sides instead of once per SF.
+constexpr int kTileRhs = 16;          // right-hand sides from which the tiled solve runs
 
 __device__ __forceinline__ unsigned long long pair_bits(dfl v) {
   return ((unsigned long long)__float_as_uint(v.lo) << 32) | __float_as_uint(v.hi);
@@ -554,22 +554,24 @@ solve_diag_pairs_kernel(const float2* __restrict__ adf, int n, int k, float2* xp
 
 // rows below the block (forward) or above it (backward) lose L(r, k + c)
 // x_{k + c} (forward) or L(k + c, r) x_{k + c} (backward); both read
-// adf[(k + c) n + r] (the mirrored factor)
-template <bool FWD, int RT>
+// adf[(k + c) n + r] (the mirrored factor).  A CTA takes 16 RT rows by FB
+// right-hand sides (FB = 16 or 64): thread (tx, ty) the rows r0 + tx + 16 i
+// and the right-hand sides f0 + FJ ty + j, FJ = FB / 16.
+template <bool FWD, int RT, int FB>
 __global__ void __launch_bounds__(256)
 solve_update_tile_kernel(const float2* __restrict__ adf, int n, int k, float2* __restrict__ xp,
                          int B) {
-  constexpr int RB = 16 * RT;
+  constexpr int RB = 16 * RT, FJ = FB / 16, XLD = FB + 2;   // XLD: padded row of the x block
   extern __shared__ __align__(16) float2 tile_sm[];
-  float2* Xs = tile_sm;                    // [SB][kXsLd]: Xs[c][f]
-  float2* Ls = tile_sm + SB * kXsLd;       // [SB][RB]: Ls[c][rr]
+  float2* Xs = tile_sm;                    // [SB][XLD]: Xs[c][f]
+  float2* Ls = tile_sm + SB * XLD;         // [SB][RB]: Ls[c][rr]
   const int nb = min(SB, n - k);
   const int rbase = FWD ? k + nb : 0, rend = FWD ? n : k;
   const int r0 = rbase + blockIdx.x * RB;
-  const int f0 = blockIdx.y * kTileRhs;
+  const int f0 = blockIdx.y * FB;
   const int t = threadIdx.x;
   // every load of a staging round issued before its stores (one latency)
-  constexpr int NX = SB * kTileRhs / 256, NL = SB * RB / 256;
+  constexpr int NX = SB * FB / 256, NL = SB * RB / 256;
   {
     float2 v[NX];
 #pragma unroll
@@ -580,7 +582,7 @@ solve_update_tile_kernel(const float2* __restrict__ adf, int n, int k, float2* _
 #pragma unroll
     for (int u = 0; u < NX; ++u) {
       const int q = t + 256 * u, f = q / SB, c = q - f * SB;
-      Xs[c * kXsLd + f] = v[u];
+      Xs[c * XLD + f] = v[u];
     }
   }
   {
@@ -598,19 +600,31 @@ solve_update_tile_kernel(const float2* __restrict__ adf, int n, int k, float2* _
     }
   }
   __syncthreads();
-  const int tx = t & 15, ty = t >> 4;       // rows r0 + tx + 16 i, fields f0 + 4 ty + j
-  dfacc acc[RT][4];
+  const int tx = t & 15, ty = t >> 4;
+  dfacc acc[RT][FJ];
 #pragma unroll 4
   for (int c = 0; c < nb; ++c) {
-    const float4 xa = *reinterpret_cast<const float4*>(Xs + c * kXsLd + 4 * ty);
-    const float4 xb = *reinterpret_cast<const float4*>(Xs + c * kXsLd + 4 * ty + 2);
-    const dfl xv[4] = {{xa.x, xa.y}, {xa.z, xa.w}, {xb.x, xb.y}, {xb.z, xb.w}};
+    dfl xv[FJ];
+    if constexpr (FJ == 4) {
+      const float4 xa = *reinterpret_cast<const float4*>(Xs + c * XLD + 4 * ty);
+      const float4 xb = *reinterpret_cast<const float4*>(Xs + c * XLD + 4 * ty + 2);
+      xv[0] = {xa.x, xa.y};
+      xv[1] = {xa.z, xa.w};
+      xv[2] = {xb.x, xb.y};
+      xv[3] = {xb.z, xb.w};
+    } else {
+#pragma unroll
+      for (int j = 0; j < FJ; ++j) {
+        const float2 xw = Xs[c * XLD + FJ * ty + j];
+        xv[j] = {xw.x, xw.y};
+      }
+    }
 #pragma unroll
     for (int i = 0; i < RT; ++i) {
       const float2 l2 = Ls[c * RB + tx + 16 * i];
       const dfl l = {l2.x, l2.y};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) dfacc_fma(acc[i][j], l, xv[j]);
+      for (int j = 0; j < FJ; ++j) dfacc_fma(acc[i][j], l, xv[j]);
     }
   }
 #pragma unroll
@@ -618,8 +632,8 @@ solve_update_tile_kernel(const float2* __restrict__ adf, int n, int k, float2* _
     const int r = r0 + tx + 16 * i;
     if (r >= rend) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int f = f0 + 4 * ty + j;
+    for (int j = 0; j < FJ; ++j) {
+      const int f = f0 + FJ * ty + j;
       if (f >= B) continue;
       float2* p = xp + (size_t)f * n + r;
       const float2 o = *p;
@@ -629,41 +643,44 @@ solve_update_tile_kernel(const float2* __restrict__ adf, int n, int k, float2* _
   }
 }
 
-template <int RT>
+template <int RT, int FB>
 static cudaError_t chol_solve_tiled_rt(const float2* adf, int n, double* x, int B, cudaStream_t s) {
   constexpr int RB = 16 * RT;
-  const size_t sm = sizeof(float2) * ((size_t)SB * kXsLd + (size_t)SB * RB);
+  const size_t sm = sizeof(float2) * ((size_t)SB * (FB + 2) + (size_t)SB * RB);
   static int smem_f = 0, smem_b = 0;
-  cudaError_t e = ensure_smem(solve_update_tile_kernel<true, RT>, sm, smem_f);
-  if (e == cudaSuccess) e = ensure_smem(solve_update_tile_kernel<false, RT>, sm, smem_b);
+  cudaError_t e = ensure_smem(solve_update_tile_kernel<true, RT, FB>, sm, smem_f);
+  if (e == cudaSuccess) e = ensure_smem(solve_update_tile_kernel<false, RT, FB>, sm, smem_b);
   if (e != cudaSuccess) return e;
   const size_t count = (size_t)B * n;
   const unsigned cb = (unsigned)((count + 255) / 256 > 4096 ? 4096 : (count + 255) / 256);
   float2* xp = reinterpret_cast<float2*>(x);
-  const int igrid = (B + kPairRhs - 1) / kPairRhs, fgrid = (B + kTileRhs - 1) / kTileRhs;
+  const int igrid = (B + kPairRhs - 1) / kPairRhs, fgrid = (B + FB - 1) / FB;
   x_to_pairs_kernel<<<cb, 256, 0, s>>>(x, count);
   for (int k = 0; k < n; k += SB) {
     const int nb = n - k < SB ? n - k : SB;
     solve_diag_pairs_kernel<true><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
     const int rest = n - k - nb;
     if (rest > 0)
-      solve_update_tile_kernel<true, RT>
+      solve_update_tile_kernel<true, RT, FB>
           <<<dim3((rest + RB - 1) / RB, fgrid), 256, sm, s>>>(adf, n, k, xp, B);
   }
   for (int k = ((n - 1) / SB) * SB; k >= 0; k -= SB) {
     solve_diag_pairs_kernel<false><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
     if (k > 0)
-      solve_update_tile_kernel<false, RT>
+      solve_update_tile_kernel<false, RT, FB>
           <<<dim3((k + RB - 1) / RB, fgrid), 256, sm, s>>>(adf, n, k, xp, B);
   }
   x_from_pairs_kernel<<<cb, 256, 0, s>>>(x, count);
   return cudaGetLastError();
 }
 
-// RT = 2 (32 rows by 64 right-hand sides per CTA): at n = 5000, 256
-// right-hand sides, 5.5 ms per solve against 6.2 ms with RT = 4
+// RT = 2 (32 rows per CTA): at n = 5000 with 256 right-hand sides 5.5 ms per
+// solve against 6.2 ms with RT = 4; at n = 20000 with 16 (the adjoint) the
+// backward takes 21.4 ms against 22.1 ms with RT = 4 and 24.2 ms on the
+// four-right-hand-side update below
 static cudaError_t chol_solve_tiled(const float2* adf, int n, double* x, int B, cudaStream_t s) {
-  return chol_solve_tiled_rt<2>(adf, n, x, B, s);
+  if (B >= 64) return chol_solve_tiled_rt<2, 64>(adf, n, x, B, s);
+  return chol_solve_tiled_rt<2, 16>(adf, n, x, B, s);
 }
 
 cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
