@@ -477,7 +477,7 @@ cudaError_t launch_split_pairs(const double* src, size_t count, float2* dst, cud
 // the trailing update tiled like a GEMM (solve_update_tile_kernel): a CTA
 // takes 16 RT rows by 16 or 64 right-hand sides, stages the block's columns of
 // L for its rows and the block's x for its right-hand sides in shared memory
-// once, and each thread keeps RT x 4 double-float sums; a factor element is
+// once, and each thread keeps RT x FB / 16 double-float sums; a factor element is
 // read from L2 once per 16 or 64 right-hand sides instead of once per SF.
 constexpr int kTileRhs = 16;          // right-hand sides from which the tiled solve runs
 
@@ -552,36 +552,138 @@ solve_diag_pairs_kernel(const float2* __restrict__ adf, int n, int k, float2* xp
   xf[r] = make_float2(v.hi, v.lo);
 }
 
+// The same step for a block of 2 SB rows [A 0; C D] (A, D the factor's
+// 64 x 64 diagonal blocks, whose inverses adf holds, C the block below A):
+// forward y1 = A^{-1} x1, y2 = D^{-1} (x2 - C y1); backward y2 = D^{-T} x2,
+// y1 = A^{-T} (x1 - C^T y2).  The three blocks are staged in shared memory
+// (C with an odd row stride, read along rows forward and along columns
+// backward); the phases meet at barriers.
+__host__ __device__ constexpr size_t diag2_smem_elems() {
+  return (size_t)2 * SB * SB + (size_t)SB * (SB + 1) + (size_t)2 * kPairRhs * SB;
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(SB * kPairRhs)
+solve_diag2_pairs_kernel(const float2* __restrict__ adf, int n, int k, float2* xp, int B) {
+  extern __shared__ __align__(16) float2 d2_sm[];
+  constexpr int CL = SB + 1;
+  float2* Ta = d2_sm;                      // A^{-1} (both triangles): Ta[c SB + r]
+  float2* Td = Ta + SB * SB;               // D^{-1}
+  float2* Cs = Td + SB * SB;               // Cs[c CL + r] = L(k + SB + r, k + c)
+  float2* x1 = Cs + SB * CL;               // [kPairRhs][SB]
+  float2* x2 = x1 + kPairRhs * SB;
+  const int nb = min(2 * SB, n - k), nb1 = min(SB, nb), nb2 = nb - nb1;
+  constexpr int NT = SB * SB / (SB * kPairRhs);
+  const float2 zero = make_float2(0.f, 0.f);
+  {
+    float2 va[NT], vd[NT], vc[NT];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      const int q = threadIdx.x + u * SB * kPairRhs, c = q / SB, r = q % SB;
+      va[u] = (r < nb1 && c < nb1) ? adf[(size_t)(k + c) * n + k + r] : zero;
+      vd[u] = (r < nb2 && c < nb2) ? adf[(size_t)(k + SB + c) * n + k + SB + r] : zero;
+      vc[u] = (r < nb2 && c < nb1) ? adf[(size_t)(k + c) * n + k + SB + r] : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      const int q = threadIdx.x + u * SB * kPairRhs, c = q / SB, r = q % SB;
+      Ta[q] = va[u];
+      Td[q] = vd[u];
+      Cs[c * CL + r] = vc[u];
+    }
+  }
+  const int r = threadIdx.x % SB, fl = threadIdx.x / SB;
+  const int f = blockIdx.x * kPairRhs + fl;
+  const bool live = f < B;
+  float2* xf = xp + (size_t)(live ? f : 0) * n + k;
+  float2* y1 = x1 + fl * SB;
+  float2* y2 = x2 + fl * SB;
+  y1[r] = live && r < nb1 ? xf[r] : zero;
+  y2[r] = live && r < nb2 ? xf[SB + r] : zero;
+  __syncthreads();
+  // v = T x (T = Ta or Td, both triangles stored): forward c <= r, backward c >= r
+  auto tri = [&](const float2* T, const float2* x, int m) {
+    dfacc a0, a1;
+    const int c0 = FWD ? 0 : r, c1 = FWD ? r + 1 : m;
+    int c = c0;
+#pragma unroll 4
+    for (; c + 1 < c1; c += 2) {
+      const float2 l0 = T[c * SB + r], l1 = T[(c + 1) * SB + r];
+      const float2 u0 = x[c], u1 = x[c + 1];
+      dfacc_fma(a0, {l0.x, l0.y}, {u0.x, u0.y});
+      dfacc_fma(a1, {l1.x, l1.y}, {u1.x, u1.y});
+    }
+    if (c < c1) {
+      const float2 l0 = T[c * SB + r], u0 = x[c];
+      dfacc_fma(a0, {l0.x, l0.y}, {u0.x, u0.y});
+    }
+    return df_add(dfacc_value(a0), dfacc_value(a1));
+  };
+  // w = x - C u (forward, rows r < nb2) or x - C^T u (backward, rows r < nb1)
+  auto offd = [&](const float2* x, const float2* u, int m) {
+    dfacc a0;
+#pragma unroll 4
+    for (int c = 0; c < m; ++c) {
+      const float2 l = FWD ? Cs[c * CL + r] : Cs[r * CL + c];
+      const float2 uc = u[c];
+      dfacc_fma(a0, {l.x, l.y}, {uc.x, uc.y});
+    }
+    const float2 xr = x[r];
+    return df_add({xr.x, xr.y}, df_neg(dfacc_value(a0)));
+  };
+  float2* first = FWD ? y1 : y2;             // the block solved first, then the other
+  float2* second = FWD ? y2 : y1;
+  const float2* Tf = FWD ? Ta : Td;
+  const float2* Ts2 = FWD ? Td : Ta;
+  const int mf = FWD ? nb1 : nb2, ms = FWD ? nb2 : nb1;
+  dfl v = {0.f, 0.f};
+  if (r < mf) v = tri(Tf, first, mf);
+  __syncthreads();
+  if (r < mf) first[r] = make_float2(v.hi, v.lo);
+  __syncthreads();
+  if (r < ms) v = offd(second, first, mf);
+  __syncthreads();
+  if (r < ms) second[r] = make_float2(v.hi, v.lo);
+  __syncthreads();
+  dfl w = {0.f, 0.f};
+  if (r < ms) w = tri(Ts2, second, ms);
+  if (!live) return;
+  const dfl y1v = FWD ? dfl{y1[r].x, y1[r].y} : w;
+  const dfl y2v = FWD ? w : dfl{y2[r].x, y2[r].y};
+  if (r < nb1) xf[r] = make_float2(y1v.hi, y1v.lo);
+  if (r < nb2) xf[SB + r] = make_float2(y2v.hi, y2v.lo);
+}
+
 // rows below the block (forward) or above it (backward) lose L(r, k + c)
 // x_{k + c} (forward) or L(k + c, r) x_{k + c} (backward); both read
 // adf[(k + c) n + r] (the mirrored factor).  A CTA takes 16 RT rows by FB
 // right-hand sides (FB = 16 or 64): thread (tx, ty) the rows r0 + tx + 16 i
 // and the right-hand sides f0 + FJ ty + j, FJ = FB / 16.
-template <bool FWD, int RT, int FB>
+template <bool FWD, int RT, int FB, int NC>
 __global__ void __launch_bounds__(256)
 solve_update_tile_kernel(const float2* __restrict__ adf, int n, int k, float2* __restrict__ xp,
                          int B) {
   constexpr int RB = 16 * RT, FJ = FB / 16, XLD = FB + 2;   // XLD: padded row of the x block
   extern __shared__ __align__(16) float2 tile_sm[];
-  float2* Xs = tile_sm;                    // [SB][XLD]: Xs[c][f]
-  float2* Ls = tile_sm + SB * XLD;         // [SB][RB]: Ls[c][rr]
-  const int nb = min(SB, n - k);
+  float2* Xs = tile_sm;                    // [NC][XLD]: Xs[c][f]
+  float2* Ls = tile_sm + NC * XLD;         // [NC][RB]: Ls[c][rr]
+  const int nb = min(NC, n - k);
   const int rbase = FWD ? k + nb : 0, rend = FWD ? n : k;
   const int r0 = rbase + blockIdx.x * RB;
   const int f0 = blockIdx.y * FB;
   const int t = threadIdx.x;
   // every load of a staging round issued before its stores (one latency)
-  constexpr int NX = SB * FB / 256, NL = SB * RB / 256;
+  constexpr int NX = NC * FB / 256, NL = NC * RB / 256;
   {
     float2 v[NX];
 #pragma unroll
     for (int u = 0; u < NX; ++u) {                     // along each field's row of x
-      const int q = t + 256 * u, f = q / SB, c = q - f * SB;
+      const int q = t + 256 * u, f = q / NC, c = q - f * NC;
       v[u] = (c < nb && f0 + f < B) ? xp[(size_t)(f0 + f) * n + k + c] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < NX; ++u) {
-      const int q = t + 256 * u, f = q / SB, c = q - f * SB;
+      const int q = t + 256 * u, f = q / NC, c = q - f * NC;
       Xs[c * XLD + f] = v[u];
     }
   }
@@ -643,31 +745,43 @@ solve_update_tile_kernel(const float2* __restrict__ adf, int n, int k, float2* _
   }
 }
 
-template <int RT, int FB>
+template <int RT, int FB, int NC>
 static cudaError_t chol_solve_tiled_rt(const float2* adf, int n, double* x, int B, cudaStream_t s) {
+  static_assert(NC == SB || NC == 2 * SB, "block steps of one or two diagonal blocks");
   constexpr int RB = 16 * RT;
-  const size_t sm = sizeof(float2) * ((size_t)SB * (FB + 2) + (size_t)SB * RB);
-  static int smem_f = 0, smem_b = 0;
-  cudaError_t e = ensure_smem(solve_update_tile_kernel<true, RT, FB>, sm, smem_f);
-  if (e == cudaSuccess) e = ensure_smem(solve_update_tile_kernel<false, RT, FB>, sm, smem_b);
+  const size_t sm = sizeof(float2) * ((size_t)NC * (FB + 2) + (size_t)NC * RB);
+  const size_t sd = sizeof(float2) * diag2_smem_elems();
+  static int smem_f = 0, smem_b = 0, smem_d1 = 0, smem_d2 = 0;
+  cudaError_t e = ensure_smem(solve_update_tile_kernel<true, RT, FB, NC>, sm, smem_f);
+  if (e == cudaSuccess) e = ensure_smem(solve_update_tile_kernel<false, RT, FB, NC>, sm, smem_b);
+  if (NC == 2 * SB) {
+    if (e == cudaSuccess) e = ensure_smem(solve_diag2_pairs_kernel<true>, sd, smem_d1);
+    if (e == cudaSuccess) e = ensure_smem(solve_diag2_pairs_kernel<false>, sd, smem_d2);
+  }
   if (e != cudaSuccess) return e;
   const size_t count = (size_t)B * n;
   const unsigned cb = (unsigned)((count + 255) / 256 > 4096 ? 4096 : (count + 255) / 256);
   float2* xp = reinterpret_cast<float2*>(x);
   const int igrid = (B + kPairRhs - 1) / kPairRhs, fgrid = (B + FB - 1) / FB;
   x_to_pairs_kernel<<<cb, 256, 0, s>>>(x, count);
-  for (int k = 0; k < n; k += SB) {
-    const int nb = n - k < SB ? n - k : SB;
-    solve_diag_pairs_kernel<true><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
+  for (int k = 0; k < n; k += NC) {
+    const int nb = n - k < NC ? n - k : NC;
+    if (NC == SB)
+      solve_diag_pairs_kernel<true><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
+    else
+      solve_diag2_pairs_kernel<true><<<igrid, SB * kPairRhs, sd, s>>>(adf, n, k, xp, B);
     const int rest = n - k - nb;
     if (rest > 0)
-      solve_update_tile_kernel<true, RT, FB>
+      solve_update_tile_kernel<true, RT, FB, NC>
           <<<dim3((rest + RB - 1) / RB, fgrid), 256, sm, s>>>(adf, n, k, xp, B);
   }
-  for (int k = ((n - 1) / SB) * SB; k >= 0; k -= SB) {
-    solve_diag_pairs_kernel<false><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
+  for (int k = ((n - 1) / NC) * NC; k >= 0; k -= NC) {
+    if (NC == SB)
+      solve_diag_pairs_kernel<false><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
+    else
+      solve_diag2_pairs_kernel<false><<<igrid, SB * kPairRhs, sd, s>>>(adf, n, k, xp, B);
     if (k > 0)
-      solve_update_tile_kernel<false, RT, FB>
+      solve_update_tile_kernel<false, RT, FB, NC>
           <<<dim3((k + RB - 1) / RB, fgrid), 256, sm, s>>>(adf, n, k, xp, B);
   }
   x_from_pairs_kernel<<<cb, 256, 0, s>>>(x, count);
@@ -678,9 +792,12 @@ static cudaError_t chol_solve_tiled_rt(const float2* adf, int n, double* x, int 
 // solve against 6.2 ms with RT = 4; at n = 20000 with 16 (the adjoint) the
 // backward takes 21.4 ms against 22.1 ms with RT = 4 and 24.2 ms on the
 // four-right-hand-side update below
+// Block steps of two diagonal blocks (128 columns): half the dependent
+// launches; CS solve 5.51 -> 5.05 ms, adjoint backward 21.4 -> 20.2 ms
+// against steps of one block.
 static cudaError_t chol_solve_tiled(const float2* adf, int n, double* x, int B, cudaStream_t s) {
-  if (B >= 64) return chol_solve_tiled_rt<2, 64>(adf, n, x, B, s);
-  return chol_solve_tiled_rt<2, 16>(adf, n, x, B, s);
+  if (B >= 64) return chol_solve_tiled_rt<2, 64, 2 * SB>(adf, n, x, B, s);
+  return chol_solve_tiled_rt<2, 16, 2 * SB>(adf, n, x, B, s);
 }
 
 cudaError_t chol_solve(const double* a, int n, double* x, int B, cudaStream_t s,
