@@ -558,96 +558,108 @@ solve_diag_pairs_kernel(const float2* __restrict__ adf, int n, int k, float2* xp
 // y1 = A^{-T} (x1 - C^T y2).  The three blocks are staged in shared memory
 // (C with an odd row stride, read along rows forward and along columns
 // backward); the phases meet at barriers.
+// kD2Rhs right-hand sides per CTA and kD2Parts threads per (row, right-hand
+// side), each summing one part of a row's terms: short dependent chains and
+// B / kD2Rhs CTAs, so that even 16 right-hand sides spread over 8 SMs.
+constexpr int kD2Rhs = 2, kD2Parts = 4, kD2Threads = SB * kD2Rhs * kD2Parts;
 __host__ __device__ constexpr size_t diag2_smem_elems() {
-  return (size_t)2 * SB * SB + (size_t)SB * (SB + 1) + (size_t)2 * kPairRhs * SB;
+  return (size_t)2 * SB * SB + (size_t)SB * (SB + 1) + (size_t)2 * kD2Rhs * SB +
+         (size_t)(kD2Parts - 1) * kD2Rhs * SB;
 }
 
 template <bool FWD>
-__global__ void __launch_bounds__(SB * kPairRhs)
+__global__ void __launch_bounds__(kD2Threads)
 solve_diag2_pairs_kernel(const float2* __restrict__ adf, int n, int k, float2* xp, int B) {
   extern __shared__ __align__(16) float2 d2_sm[];
   constexpr int CL = SB + 1;
   float2* Ta = d2_sm;                      // A^{-1} (both triangles): Ta[c SB + r]
   float2* Td = Ta + SB * SB;               // D^{-1}
   float2* Cs = Td + SB * SB;               // Cs[c CL + r] = L(k + SB + r, k + c)
-  float2* x1 = Cs + SB * CL;               // [kPairRhs][SB]
-  float2* x2 = x1 + kPairRhs * SB;
+  float2* x1 = Cs + SB * CL;               // [kD2Rhs][SB]
+  float2* x2 = x1 + kD2Rhs * SB;
+  float2* red = x2 + kD2Rhs * SB;          // [kD2Parts - 1][kD2Rhs][SB] partial sums
   const int nb = min(2 * SB, n - k), nb1 = min(SB, nb), nb2 = nb - nb1;
-  constexpr int NT = SB * SB / (SB * kPairRhs);
   const float2 zero = make_float2(0.f, 0.f);
-  {
-    float2 va[NT], vd[NT], vc[NT];
+  // the three blocks, one at a time, each thread's loads of a block first
+  constexpr int NT = SB * SB / kD2Threads;
+  auto stage = [&](float2* dst, int ld, int col0, int row0, int nc, int nr) {
+    float2 v[NT];
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
-      const int q = threadIdx.x + u * SB * kPairRhs, c = q / SB, r = q % SB;
-      va[u] = (r < nb1 && c < nb1) ? adf[(size_t)(k + c) * n + k + r] : zero;
-      vd[u] = (r < nb2 && c < nb2) ? adf[(size_t)(k + SB + c) * n + k + SB + r] : zero;
-      vc[u] = (r < nb2 && c < nb1) ? adf[(size_t)(k + c) * n + k + SB + r] : zero;
+      const int q = threadIdx.x + u * kD2Threads, c = q / SB, r = q % SB;
+      v[u] = (r < nr && c < nc) ? adf[(size_t)(col0 + c) * n + row0 + r] : zero;
     }
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
-      const int q = threadIdx.x + u * SB * kPairRhs, c = q / SB, r = q % SB;
-      Ta[q] = va[u];
-      Td[q] = vd[u];
-      Cs[c * CL + r] = vc[u];
+      const int q = threadIdx.x + u * kD2Threads, c = q / SB, r = q % SB;
+      dst[c * ld + r] = v[u];
     }
-  }
-  const int r = threadIdx.x % SB, fl = threadIdx.x / SB;
-  const int f = blockIdx.x * kPairRhs + fl;
+  };
+  stage(Ta, SB, k, k, nb1, nb1);
+  stage(Td, SB, k + SB, k + SB, nb2, nb2);
+  stage(Cs, CL, k, k + SB, nb1, nb2);
+  const int r = threadIdx.x % SB, fl = (threadIdx.x / SB) % kD2Rhs, part = threadIdx.x / (SB * kD2Rhs);
+  const int f = blockIdx.x * kD2Rhs + fl;
   const bool live = f < B;
   float2* xf = xp + (size_t)(live ? f : 0) * n + k;
   float2* y1 = x1 + fl * SB;
   float2* y2 = x2 + fl * SB;
-  y1[r] = live && r < nb1 ? xf[r] : zero;
-  y2[r] = live && r < nb2 ? xf[SB + r] : zero;
+  if (part == 0) {
+    y1[r] = live && r < nb1 ? xf[r] : zero;
+    y2[r] = live && r < nb2 ? xf[SB + r] : zero;
+  }
   __syncthreads();
-  // v = T x (T = Ta or Td, both triangles stored): forward c <= r, backward c >= r
-  auto tri = [&](const float2* T, const float2* x, int m) {
-    dfacc a0, a1;
-    const int c0 = FWD ? 0 : r, c1 = FWD ? r + 1 : m;
-    int c = c0;
-#pragma unroll 4
-    for (; c + 1 < c1; c += 2) {
-      const float2 l0 = T[c * SB + r], l1 = T[(c + 1) * SB + r];
-      const float2 u0 = x[c], u1 = x[c + 1];
-      dfacc_fma(a0, {l0.x, l0.y}, {u0.x, u0.y});
-      dfacc_fma(a1, {l1.x, l1.y}, {u1.x, u1.y});
-    }
-    if (c < c1) {
-      const float2 l0 = T[c * SB + r], u0 = x[c];
-      dfacc_fma(a0, {l0.x, l0.y}, {u0.x, u0.y});
-    }
-    return df_add(dfacc_value(a0), dfacc_value(a1));
-  };
-  // w = x - C u (forward, rows r < nb2) or x - C^T u (backward, rows r < nb1)
-  auto offd = [&](const float2* x, const float2* u, int m) {
+  // part `part` of sum_{c in [c0, c1)} T(c, r) x[c] (T read as Tm[c ld + r]
+  // or, transposed, Tm[r ld + c])
+  auto psum = [&](const float2* Tm, int ld, bool trans, const float2* x, int c0, int c1) {
     dfacc a0;
+    const int ca = c0 + (c1 - c0) * part / kD2Parts, cb = c0 + (c1 - c0) * (part + 1) / kD2Parts;
 #pragma unroll 4
-    for (int c = 0; c < m; ++c) {
-      const float2 l = FWD ? Cs[c * CL + r] : Cs[r * CL + c];
-      const float2 uc = u[c];
-      dfacc_fma(a0, {l.x, l.y}, {uc.x, uc.y});
+    for (int c = ca; c < cb; ++c) {
+      const float2 l = trans ? Tm[r * ld + c] : Tm[c * ld + r];
+      const float2 u = x[c];
+      dfacc_fma(a0, {l.x, l.y}, {u.x, u.y});
     }
-    const float2 xr = x[r];
-    return df_add({xr.x, xr.y}, df_neg(dfacc_value(a0)));
+    return dfacc_value(a0);
+  };
+  // the parts' sums meet in shared memory; part 0 holds the total (its own
+  // red slots stay unused)
+  auto combine = [&](dfl v, bool active) {
+    if (part > 0 && active) red[((part - 1) * kD2Rhs + fl) * SB + r] = make_float2(v.hi, v.lo);
+    __syncthreads();
+    if (part == 0 && active) {
+#pragma unroll
+      for (int q = 0; q < kD2Parts - 1; ++q) {
+        const float2 w = red[(q * kD2Rhs + fl) * SB + r];
+        v = df_add(v, {w.x, w.y});
+      }
+    }
+    return v;
   };
   float2* first = FWD ? y1 : y2;             // the block solved first, then the other
   float2* second = FWD ? y2 : y1;
   const float2* Tf = FWD ? Ta : Td;
   const float2* Ts2 = FWD ? Td : Ta;
   const int mf = FWD ? nb1 : nb2, ms = FWD ? nb2 : nb1;
-  dfl v = {0.f, 0.f};
-  if (r < mf) v = tri(Tf, first, mf);
+  // first block: forward c <= r, backward c >= r (both triangles stored)
+  dfl v = psum(Tf, SB, false, first, FWD ? 0 : r, FWD ? r + 1 : mf);
+  v = combine(v, r < mf);
   __syncthreads();
-  if (r < mf) first[r] = make_float2(v.hi, v.lo);
+  if (part == 0 && r < mf) first[r] = make_float2(v.hi, v.lo);
   __syncthreads();
-  if (r < ms) v = offd(second, first, mf);
+  // the other block's right-hand side less C y1 (forward) or C^T y2 (backward)
+  v = psum(Cs, CL, !FWD, first, 0, mf);
+  v = combine(v, r < ms);
   __syncthreads();
-  if (r < ms) second[r] = make_float2(v.hi, v.lo);
+  if (part == 0 && r < ms) {
+    const float2 xr = second[r];
+    v = df_add({xr.x, xr.y}, df_neg(v));
+    second[r] = make_float2(v.hi, v.lo);
+  }
   __syncthreads();
-  dfl w = {0.f, 0.f};
-  if (r < ms) w = tri(Ts2, second, ms);
-  if (!live) return;
+  dfl w = psum(Ts2, SB, false, second, FWD ? 0 : r, FWD ? r + 1 : ms);
+  w = combine(w, r < ms);
+  if (!live || part != 0) return;
   const dfl y1v = FWD ? dfl{y1[r].x, y1[r].y} : w;
   const dfl y2v = FWD ? w : dfl{y2[r].x, y2[r].y};
   if (r < nb1) xf[r] = make_float2(y1v.hi, y1v.lo);
@@ -763,13 +775,14 @@ static cudaError_t chol_solve_tiled_rt(const float2* adf, int n, double* x, int 
   const unsigned cb = (unsigned)((count + 255) / 256 > 4096 ? 4096 : (count + 255) / 256);
   float2* xp = reinterpret_cast<float2*>(x);
   const int igrid = (B + kPairRhs - 1) / kPairRhs, fgrid = (B + FB - 1) / FB;
+  const int igrid2 = (B + kD2Rhs - 1) / kD2Rhs;
   x_to_pairs_kernel<<<cb, 256, 0, s>>>(x, count);
   for (int k = 0; k < n; k += NC) {
     const int nb = n - k < NC ? n - k : NC;
     if (NC == SB)
       solve_diag_pairs_kernel<true><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
     else
-      solve_diag2_pairs_kernel<true><<<igrid, SB * kPairRhs, sd, s>>>(adf, n, k, xp, B);
+      solve_diag2_pairs_kernel<true><<<igrid2, kD2Threads, sd, s>>>(adf, n, k, xp, B);
     const int rest = n - k - nb;
     if (rest > 0)
       solve_update_tile_kernel<true, RT, FB, NC>
@@ -779,7 +792,7 @@ static cudaError_t chol_solve_tiled_rt(const float2* adf, int n, double* x, int 
     if (NC == SB)
       solve_diag_pairs_kernel<false><<<igrid, SB * kPairRhs, 0, s>>>(adf, n, k, xp, B);
     else
-      solve_diag2_pairs_kernel<false><<<igrid, SB * kPairRhs, sd, s>>>(adf, n, k, xp, B);
+      solve_diag2_pairs_kernel<false><<<igrid2, kD2Threads, sd, s>>>(adf, n, k, xp, B);
     if (k > 0)
       solve_update_tile_kernel<false, RT, FB, NC>
           <<<dim3((k + RB - 1) / RB, fgrid), 256, sm, s>>>(adf, n, k, xp, B);
