@@ -697,6 +697,13 @@ def measure_backward(dev, steps, peaks, n=None):
         c.synchronize()
         fwd += a.elapsed_time(b)
         bwd += b.elapsed_time(c)
+    # one more adjoint with per-pass events (apart from the timed calls)
+    rk.profile_read()
+    rk.profile_enable(True)
+    p.backward(gbar)
+    torch.cuda.synchronize()
+    rk.profile_enable(False)
+    roof, kernels = roofline(rk.profile_read(), 1, peaks, "grad1024_backward")
     _, g_rho, g_s2 = (t.cpu().numpy() if t is not None else None for t in p.backward(gbar))
     p.close()
     # central differences of sum(gbar * g_hat) in FP64 plans
@@ -731,6 +738,7 @@ def measure_backward(dev, steps, peaks, n=None):
     return {"forward_ms": fwd / steps, "backward_ms": bwd / steps,
             "value": w["B"] * w["nx"] * w["ny"] / ((fwd + bwd) / steps / 1e3),
             "unit": "grid-point predictions/s (forward + adjoint)", "setup_cholesky_s": setup_s,
+            "kernels": kernels, "roofline": roof,
             "gradient_error_vs_fd": {"value": err, "fields": fields, "step": h,
                                      "stencil": "4-point", "detail": detail,
                                      "what": "max over log range and log sigma^2 of |FP32 "

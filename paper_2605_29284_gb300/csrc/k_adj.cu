@@ -185,30 +185,56 @@ cudaError_t launch_block_adjoint(const double2* gblk, int B, int nblk, int bw,
   return cudaGetLastError();
 }
 
-// out[f] (+)= scale * sum_k a[f][k] b[f][k], double accumulation; one CTA per field.
+// out[f] (+)= scale * sum_k a[f][k] b[f][k]: grid.y = f, grid.x splits the
+// row into ranges whose sums are added to out[f] by FP64 atomics (out[f]
+// cleared first unless accumulating).  FP32 rows are summed on the FP32 pipe
+// as exact products in unnormalised double-float pairs (the FP64 pipe runs
+// at 1/64 of its rate), FP64 rows in double.
 template <typename Ta, typename Tb>
-__global__ void dot_rows_kernel(const Ta* __restrict__ a, const Tb* __restrict__ b, long long len,
-                                double scale, int accumulate, double* __restrict__ out) {
-  const int f = blockIdx.x;
+__global__ void __launch_bounds__(256)
+dot_rows_kernel(const Ta* __restrict__ a, const Tb* __restrict__ b, long long len, double scale,
+                double* __restrict__ out) {
+  const int f = blockIdx.y;
   const Ta* x = a + (size_t)f * len;
   const Tb* y = b + (size_t)f * len;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   double s = 0.0;
-  for (long long k = threadIdx.x; k < len; k += blockDim.x) s += (double)x[k] * (double)y[k];
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if constexpr (sizeof(Ta) == sizeof(float) && sizeof(Tb) == sizeof(float)) {
+    dfacc acc;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < len; k += stride)
+      dfacc_fma(acc, {(float)x[k], 0.f}, {(float)y[k], 0.f});
+    dfl v = dfacc_value(acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      v = df_add(v, {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)});
+    s = df_double(v);
+  } else {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < len; k += stride)
+      s += (double)x[k] * (double)y[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __shared__ double red[8];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) out[f] = accumulate ? out[f] + scale * v : scale * v;
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    atomicAdd(out + f, scale * v);
   }
 }
 
 template <typename Ta, typename Tb>
 cudaError_t launch_dot_rows(const Ta* a, const Tb* b, int B, long long len, double scale,
                             int accumulate, double* out, cudaStream_t s) {
-  dot_rows_kernel<Ta, Tb><<<B, 512, 0, s>>>(a, b, len, scale, accumulate, out);
+  if (B <= 0) return cudaSuccess;
+  if (!accumulate) {
+    const cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * B, s);
+    if (e != cudaSuccess) return e;
+  }
+  long long ranges = (len + 256LL * 16 - 1) / (256LL * 16);   // about 16 terms per thread
+  ranges = ranges < 1 ? 1 : (ranges > 128 ? 128 : ranges);
+  dot_rows_kernel<Ta, Tb><<<dim3((unsigned)ranges, B), 256, 0, s>>>(a, b, len, scale, out);
   return cudaGetLastError();
 }
 
