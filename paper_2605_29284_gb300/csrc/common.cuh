@@ -216,6 +216,8 @@ struct rk_plan {
   int gblk_kx = -1, gblk_ky = 0, ngblk = 0;
   double2* efac_g = nullptr;                        // block factors of W, n x ngblk
   double2* efac_d = nullptr;                        // block factors of W', n x ngblk
+  float4* efac_g_df = nullptr;                      // RK_FP32: the same as packed double-float
+  float4* efac_d_df = nullptr;                      // pairs, site-major (block GEMM layout)
   double2* gblk = nullptr; size_t gblk_cap = 0;     // B x ngblk block GEMM result
   double* bw_dk = nullptr; size_t bw_dk_cap = 0;     // per-tile partials of K'_xx c
   double* bw_cbar = nullptr; size_t bw_cbar_cap = 0; // 3 x B x n: zbar, M^-1 c, M^-1 K' c
@@ -401,6 +403,10 @@ cudaError_t launch_weights(const double* xy, int n, const rk_plan* p, int* box, 
 cudaError_t launch_set_weights(const int* box_in, const double* w_in, int n, const rk_plan* p,
                                int* box, double* w64, float* w32, double* ssd, int* flag,
                                cudaStream_t s);
+// FP64 factors (entry-major, e[j n + i]) as packed double-float pairs,
+// site-major (out[i nblk + j]): the layout of the double-float block GEMM
+cudaError_t launch_factors_to_pairs(const double2* e, int n, int nblk, float4* out,
+                                    cudaStream_t s);
 cudaError_t launch_block_factors(const int* box, const double* w64, int n, const rk_plan* p,
                                  int kx, int ky,
                                  double2* efac, cudaStream_t s);

@@ -655,6 +655,35 @@ cudaError_t launch_block_factors(const int* box, const double* w64, int n, const
   return launch_block_factors_group(g, s);
 }
 
+// FP64 factors (entry-major) to packed double-float pairs (site-major): 32 x
+// 32 tiles through shared memory, read along the sites, written along the
+// entries
+__global__ void factors_to_pairs_kernel(const double2* __restrict__ e, int n, int nblk,
+                                        float4* __restrict__ out) {
+  __shared__ float4 tt[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, i = i0 + threadIdx.x;
+    if (j < nblk && i < n) {
+      const double2 v = e[(size_t)j * n + i];
+      tt[r][threadIdx.x] = cdf_pack_pairs(df_make(v.x), df_make(v.y));
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    if (i < n && j < nblk) out[(size_t)i * nblk + j] = tt[threadIdx.x][r];
+  }
+}
+
+cudaError_t launch_factors_to_pairs(const double2* e, int n, int nblk, float4* out,
+                                    cudaStream_t s) {
+  if (n <= 0 || nblk <= 0) return cudaSuccess;
+  factors_to_pairs_kernel<<<dim3((n + 31) / 32, (nblk + 31) / 32), dim3(32, 8), 0, s>>>(e, n, nblk,
+                                                                                        out);
+  return cudaGetLastError();
+}
+
 // The forward block of RK_FP32 plans in double-float on the FP32 pipe: the
 // same two stages as block_factor_kernel, from the weights' float pairs and
 // double-float twiddles (re.hi, re.lo, im.hi, im.lo); E_i is stored site-major

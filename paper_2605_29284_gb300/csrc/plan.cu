@@ -331,7 +331,7 @@ void free_plan(rk_plan* p) {
                   p->d_flag, p->tw64qx, p->tw64qy, p->tw32qx, p->tw32qy, p->ce_sqrt64,
                   p->ce_sqrt32, p->cs_buf, p->h_xy, p->h_out, p->xy, p->wd64,
                   p->wd32, p->efac_d, p->bw_cbar, p->bw_y, p->bw_gblk, p->d_sites_flag,
-                  p->efac_g, p->gblk, p->bw_dk, p->tile_start,
+                  p->efac_g, p->efac_g_df, p->efac_d_df, p->gblk, p->bw_dk, p->tile_start,
                   p->tile_count, p->tile_cursor, p->site_order,
                   p->mchol_df, p->kn_df, p->gls_buf, p->kerr_buf, p->grp_rhs};
   for (void* b : bufs)
@@ -399,9 +399,9 @@ rk_status ensure_w64(rk_plan* p) {
 // the weights in use, and the B x nblk buffer for sum_i c_i E_i(k).
 struct BlockUse {
   int kx, ky, nblk;
-  const double2* efac;     // the gradient blocks: FP64 factors
+  const double2* efac;     // FP64 factors (RK_FP64 plans' gradient blocks)
   double2* blk;
-  const float4* efac_df;   // the forward block: double-float factors (efac unused)
+  const float4* efac_df;   // double-float factors, used when set (RK_FP32 plans)
 };
 
 // Steps 5-7 for nf fields with coefficients c64 (double; the FP32 scatter
@@ -835,6 +835,11 @@ rk_status ensure_adjoint(rk_plan* p) {
                                  p->stream));
       RK_CU(launch_block_factors(p->box, p->wd64, p->n, p, p->gblk_kx, p->gblk_ky, p->efac_d,
                                  p->stream));
+      // the GEMMs of the gradient predictions run in double-float on these
+      RK_TRY(dalloc(&p->efac_g_df, (size_t)p->n * p->ngblk));
+      RK_TRY(dalloc(&p->efac_d_df, (size_t)p->n * p->ngblk));
+      RK_CU(launch_factors_to_pairs(p->efac_g, p->n, p->ngblk, p->efac_g_df, p->stream));
+      RK_CU(launch_factors_to_pairs(p->efac_d, p->n, p->ngblk, p->efac_d_df, p->stream));
     }
   }
   p->have_adj = true;
@@ -863,8 +868,8 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     RK_TRY(dalloc(&p->gblk, (size_t)B * p->ngblk));
     p->bw_gblk_cap = (size_t)B * p->ngblk;
   }
-  const BlockUse gw = {p->gblk_kx, p->gblk_ky, p->ngblk, p->efac_g, p->gblk};
-  const BlockUse gwd = {p->gblk_kx, p->gblk_ky, p->ngblk, p->efac_d, p->gblk};
+  const BlockUse gw = {p->gblk_kx, p->gblk_ky, p->ngblk, p->efac_g, p->gblk, p->efac_g_df};
+  const BlockUse gwd = {p->gblk_kx, p->gblk_ky, p->ngblk, p->efac_d, p->gblk, p->efac_d_df};
   const T* lam = f32 ? (const T*)p->lam32 : (const T*)p->lam64;
   const T* dlam = f32 ? (const T*)p->dlam32 : (const T*)p->dlam64;
   const C<T>* twx = f32 ? (const C<T>*)p->tw32x : (const C<T>*)p->tw64x;
