@@ -471,6 +471,8 @@ cudaError_t launch_gather(const T* abar, int p1x, int p1y, const int* box, const
                           int n, int L, int B, double* cbar, cudaStream_t s);
 cudaError_t launch_block_phase(double2* gblk, int B, int nblk, int bw, int KY, int o, int px,
                                int py, const double2* twx, const double2* twy, cudaStream_t s);
+cudaError_t launch_block_adjoint_df(const double2* gblk, int B, int nblk, int bw,
+                                    const float4* efac, int n, double* cbar, cudaStream_t s);
 cudaError_t launch_block_adjoint(const double2* gblk, int B, int nblk, int bw,
                                  const double2* efac, int n, double* cbar, cudaStream_t s);
 template <typename Ta, typename Tb>

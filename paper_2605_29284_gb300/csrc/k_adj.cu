@@ -150,6 +150,71 @@ __global__ void block_adjoint_kernel(const double2* __restrict__ gblk, int B, in
   }
 }
 
+// The same in double-float (RK_FP32 plans) from the factors as packed pairs,
+// site-major: a CTA takes kBaSites sites and 16 fields (fields f0 + fq + 4 r,
+// four per thread); chunks of kBaJ block entries of E and of w G (converted
+// to packed pairs once per CTA) are staged in shared memory, and each
+// Re(G conj E) term is one packed pair sum (real and imaginary products
+// side by side, added at the end).
+constexpr int kBaSites = 64, kBaJ = 32;
+__global__ void __launch_bounds__(256)
+block_adjoint_df_kernel(const double2* __restrict__ gblk, int B, int nblk, int bw,
+                        const float4* __restrict__ efac, int n, double* __restrict__ cbar,
+                        int f0) {
+  __shared__ float4 Es[kBaSites][kBaJ + 1];
+  __shared__ float4 Gs[16][kBaJ];
+  const int t = threadIdx.x, sl = t % kBaSites, fq = t / kBaSites;
+  const int i0 = blockIdx.x * kBaSites, i = i0 + sl;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  dfacc2 acc[4];
+  for (int j0 = 0; j0 < nblk; j0 += kBaJ) {
+    __syncthreads();                                   // the previous chunk is read
+    for (int q = t; q < kBaSites * kBaJ; q += 256) {
+      const int ss = q / kBaJ, jj = q - ss * kBaJ;
+      const int ii = i0 + ss, j = j0 + jj;
+      Es[ss][jj] = (ii < n && j < nblk) ? efac[(size_t)ii * nblk + j] : zero;
+    }
+    for (int q = t; q < 16 * kBaJ; q += 256) {
+      const int ff = q / kBaJ, jj = q - ff * kBaJ;
+      const int f = f0 + ff, j = j0 + jj;
+      float4 v = zero;
+      if (f < B && j < nblk) {
+        const double2 g = gblk[(size_t)f * nblk + j];
+        const double wk = j < bw ? 1.0 : 2.0;
+        v = cdf_pack_pairs(df_make(wk * g.x), df_make(wk * g.y));
+      }
+      Gs[ff][jj] = v;
+    }
+    __syncthreads();
+    const int m = nblk - j0 < kBaJ ? nblk - j0 : kBaJ;
+    for (int jj = 0; jj < m; ++jj) {
+      const float4 e = Es[sl][jj];
+      const float2 ehi = make_float2(e.x, e.y), elo = make_float2(e.z, e.w);
+      const float2 nehi = f2_sub(make_float2(0.f, 0.f), ehi);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 g = Gs[fq + 4 * r][jj];
+        dfacc2_fma(acc[r], ehi, nehi, elo, make_float2(g.x, g.y), make_float2(g.z, g.w));
+      }
+    }
+  }
+  if (i >= n) return;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int f = f0 + fq + 4 * r;
+    if (f < B) cbar[(size_t)f * n + i] += df_double(df_add(dfacc2_x(acc[r]), dfacc2_y(acc[r])));
+  }
+}
+
+cudaError_t launch_block_adjoint_df(const double2* gblk, int B, int nblk, int bw,
+                                    const float4* efac, int n, double* cbar, cudaStream_t s) {
+  if (n <= 0 || nblk <= 0) return cudaSuccess;
+  for (int f0 = 0; f0 < B; f0 += 16)
+    block_adjoint_df_kernel<<<(n + kBaSites - 1) / kBaSites, 256, 0, s>>>(gblk, B, nblk, bw, efac,
+                                                                          n, cbar, f0);
+  return cudaGetLastError();
+}
+
 // The forward pass reads the prediction window at offset o = L - 1 of the
 // padded grid; seen from the sites, the block spectrum of gbar therefore
 // carries the phase exp(-2 pi i (kx o / px + ky o / py)), applied here in

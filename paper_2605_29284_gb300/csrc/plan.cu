@@ -909,7 +909,10 @@ rk_status backward_impl(rk_plan* p, const T* gbar, double* gz, double* grho, dou
     const int bw = 2 * p->gblk_ky + 1;
     RK_CU(launch_block_phase(p->bw_gblk, B, p->ngblk, bw, p->gblk_ky, p->L - 1, p->px, p->py,
                              p->tw64x, p->tw64y, s));
-    RK_CU(launch_block_adjoint(p->bw_gblk, B, p->ngblk, bw, p->efac_g, n, cbar, s));
+    if (p->efac_g_df)
+      RK_CU(launch_block_adjoint_df(p->bw_gblk, B, p->ngblk, bw, p->efac_g_df, n, cbar, s));
+    else
+      RK_CU(launch_block_adjoint(p->bw_gblk, B, p->ngblk, bw, p->efac_g, n, cbar, s));
   }
   double* c3 = cbar + (size_t)2 * B * n;
   if (nsets == 3) {
