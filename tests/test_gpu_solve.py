@@ -36,12 +36,14 @@ EXT = (0.0, 1.0, 0.0, 1.0)
 TH = (1.5, 0.1, 1.0, 1e-2)     # nu, range, sigma^2, tau^2
 
 
-@pytest.mark.parametrize("n", [1124, 700])
-@pytest.mark.parametrize("B", [5, 16, 23, 64, 70])
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_coefficients_match_oracle_solve(rk, n, B, prec):
-    if prec == "fp64" and B not in (5, 70):
-        pytest.skip("the FP64 substitutions do not depend on the batch")
+# FP32 plans reach every branch; the FP64 substitutions do not depend on the
+# batch width, so two batches cover them
+CASES = ([("fp32", n, B) for n in (1124, 700) for B in (5, 16, 23, 64, 70)] +
+         [("fp64", n, B) for n in (1124, 700) for B in (5, 70)])
+
+
+@pytest.mark.parametrize("prec,n,B", CASES)
+def test_coefficients_match_oracle_solve(rk, prec, n, B):
     xy = synth.sites("uniform", n, EXT, 21000 + n)
     z = synth.normals((B, n), 21001 + B)
     nu, rho, s2, tau2 = TH
